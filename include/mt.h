@@ -1,0 +1,207 @@
+/*
+ * mt.h -- C ABI of libmt.so: muon-tomography log-posterior of layered
+ * block-cave geometries, evaluated for many MCMC chains at once on one GB300
+ * (sm_103a), with the batched Metropolis update.
+ *
+ * The calls follow the paper's statement of the problem ("GPU-accelerated
+ * Bayesian inference for block-cave geometry recovery via muon tomography"):
+ * sensors at known positions in a box-shaped domain (Sec. 2.1.1), pixels as
+ * the directions of a solid-angle partition (Sec. 2.1.1), one observed count
+ * per pixel (Eq. def_likelihood), a layer model H on an n_rows x n_cols grid
+ * with known unit densities (Sec. 2.1.3), and a posterior over H sampled by
+ * MCMC that needs only density ratios (Sec. 2.2).
+ *
+ * Conventions shared by every call
+ *  - Every call returns mt_status; the library never aborts, never calls
+ *    __trap and never prints.  mt_last_error() gives a message for the last
+ *    failing call on that context (library-owned, valid until the next call).
+ *  - Coordinates are metres in a box [0,Lx]x[0,Ly]x[0,Lz]; a height is z above
+ *    the box floor.  Heights are row-major [chain][layer][row][col], column
+ *    (x) fastest; node (r, c) sits at x = c*Lx/(n_cols-1), y = r*Ly/(n_rows-1)
+ *    and heights between nodes are bilinear.  Surfaces are ordered bottom to
+ *    top; unit u (0..n_layers) lies between surface u-1 and surface u.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Pointers
+ *    documented "host or device" may be either (the library asks the CUDA
+ *    driver which); device pointers must be on the context's device and are
+ *    only borrowed for the duration of the call, on the context's stream.
+ *  - Calls are asynchronous on the context's stream unless they write to a
+ *    host pointer, in which case they return after the result is on the host.
+ *  - Device-side failures (a Poisson draw that ran out of attempts) are
+ *    latched in a device status word; mt_sync() reports them as MT_EDEVFLAG.
+ *  - A geometry that breaks the ordering is not an error: its log-prior is
+ *    -inf and a proposal with it is always rejected.
+ *  - One context is used by one host thread at a time.
+ */
+#ifndef MT_H
+#define MT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MT_API __attribute__((visibility("default")))
+#else
+#define MT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mt_ctx mt_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    MT_OK = 0,
+    MT_EINVAL = -1,     /* bad argument (size, pointer, range)              */
+    MT_ENOMEM = -2,     /* device or host allocation failed                 */
+    MT_ESTATE = -3,     /* call order: grid / sensors / pixels / counts /
+                           chains not set yet                               */
+    MT_ECUDA = -4,      /* a CUDA runtime call failed                       */
+    MT_ETIMEDOUT = -5,  /* mt_sync deadline passed, work still in flight    */
+    MT_EDEVFLAG = -6    /* a kernel latched a failure in the status word    */
+} mt_status;
+
+/* Arithmetic of the ray march and the per-chain reduction.
+ *  MT_PREC_F64  : heights, march, flux and reductions in FP64.
+ *  MT_PREC_F32  : FP32 heights and march (compensated sum along each ray),
+ *                 FP64 per-ray flux term and per-chain reduction.
+ *  MT_PREC_F32C : FP32 heights and march; flux term, per-ray and per-chain
+ *                 reductions in compensated FP32 (float-float), no FP64 in
+ *                 the ray kernel.
+ *  MT_PREC_BF16 : FP32 chain state; the ray kernel holds each surface as
+ *                 BF16 offsets h - ref_l from a reference height ref_l (the
+ *                 surface's mean prior height rounded to FP32, or
+ *                 Lz (l+1)/(L+1) when that mean is 0) and widens them to FP32
+ *                 when read; otherwise as MT_PREC_F32.  The FP32 modes use
+ *                 the same offsets in FP32.
+ * Heights passed to and returned by the library are double for MT_PREC_F64
+ * and float for every other mode. */
+enum { MT_PREC_F64 = 0, MT_PREC_F32 = 1, MT_PREC_F32C = 2, MT_PREC_BF16 = 3 };
+
+/* Proposal kernels for mt_run. */
+enum { MT_KERNEL_RW = 0, MT_KERNEL_MALA = 1 };
+
+/* Observed-count generation for mt_generate_data. */
+enum { MT_COUNTS_POISSON = 0, MT_COUNTS_ROUND = 1 };
+
+typedef struct {
+    int precision;     /* MT_PREC_*                                           */
+    int n_grid;        /* samples per ray G >= 1: t_k = (k+1/2) t_exit / G    */
+    double gamma;      /* sigmoid scale in metres (Eq. def_sigmoid); 0 selects
+                          the Heaviside eta with eta(0) = 1/2                 */
+    double I0;         /* expected count at zero opacity (1e4)                */
+    double atten;      /* attenuation length Lambda in mwe (150):
+                          lambda = I0 exp(-O / Lambda)                        */
+    double tau;        /* prior precision scale (1/m^2)                        */
+    double car_r;      /* CAR spatial dependence r in [0,1) (Eq. def_CAR_precision) */
+    double min_thick;  /* minimum thickness delta > 0 between surfaces (m)    */
+} mt_config;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to run on (borrowed; NULL = the library creates and owns one).  *out is set
+ * on success.  Errors: MT_EINVAL (bad config), MT_ECUDA, MT_ENOMEM. */
+MT_API mt_status mt_create(mt_ctx **out, int device, const mt_config *cfg, void *cuda_stream);
+
+/* Release every device buffer, graph and event of the context. NULL is a no-op. */
+MT_API mt_status mt_destroy(mt_ctx *ctx);
+
+/* Message for the last failing call on ctx (or on mt_create when ctx is NULL). */
+MT_API const char *mt_last_error(const mt_ctx *ctx);
+
+/* Layer model (Sec. 2.1.3): n_layers surfaces (1..8) on an n_rows x n_cols
+ * grid (each >= 2), box = {Lx, Ly, Lz} > 0, unit_density[n_layers+1] in g/cc
+ * bottom to top (Eq. def_LM_density_grid), prior_mean[n_layers][n_rows][n_cols]
+ * (host, may be NULL = zero).  Resets sensors/pixels/counts/chains state that
+ * depends on the grid. */
+MT_API mt_status mt_set_grid(mt_ctx *ctx, int n_layers, int n_rows, int n_cols, const double box[3],
+                      const double *unit_density, const double *prior_mean);
+
+/* Sensor positions (Sec. 2.1.1), host [n_sensors][3], each strictly inside the box. */
+MT_API mt_status mt_set_sensors(mt_ctx *ctx, int n_sensors, const double *pos);
+
+/* Pixel directions (Sec. 2.1.1), host [n_pixels][3] unit vectors (|d| within
+ * 1e-6 of 1), shared by every sensor; ray (s, p) has index s*n_pixels + p. */
+MT_API mt_status mt_set_pixels(mt_ctx *ctx, int n_pixels, const double *dirs);
+
+/* Observed counts C_p >= 0 (Eq. def_likelihood), host or device
+ * int32 [n_sensors][n_pixels].  Needs grid, sensors and pixels. */
+MT_API mt_status mt_set_counts(mt_ctx *ctx, const int32_t *counts);
+
+/* Synthetic observations from a true geometry: lambda_p from the FP64 march
+ * of h_true (host [L][R][Q] double), then C_p ~ Poisson(lambda_p) drawn from
+ * Philox4x32-10 stream 1 with key `seed` (count_mode MT_COUNTS_POISSON), or
+ * C_p = round-half-even(lambda_p) (MT_COUNTS_ROUND, the paper's Sec. 4).
+ * The counts become the context's observed counts.  counts_out / lambda_out
+ * (host or device, [S][P], nullable) receive copies. */
+MT_API mt_status mt_generate_data(mt_ctx *ctx, const double *h_true, uint64_t seed, int count_mode,
+                           int32_t *counts_out, double *lambda_out);
+
+/* Log-likelihood (Eq. def_likelihood, summed over every sensor and pixel) and
+ * log-prior of n_chains geometries.  heights: host or device
+ * [n_chains][L][R][Q] (double for MT_PREC_F64, float otherwise).
+ * loglik_out / logprior_out: host or device double [n_chains], nullable. */
+MT_API mt_status mt_logpost(mt_ctx *ctx, int n_chains, const void *heights, double *loglik_out,
+                     double *logprior_out);
+
+/* Per-ray opacity O (mwe) and Poisson log-pmf term of n_chains geometries,
+ * host or device double [n_chains][S][P] each (nullable): the per-ray values
+ * that mt_logpost sums, for element-wise checks. */
+MT_API mt_status mt_ray_terms(mt_ctx *ctx, int n_chains, const void *heights, double *opacity_out,
+                       double *term_out);
+
+/* Gradient of the log-posterior with respect to every node height
+ * (differentiable forward model, Sec. 2.1.4): grad_out host or device double
+ * [n_chains][L][R][Q]; logpost_out (nullable) double [n_chains].  gamma > 0. */
+MT_API mt_status mt_grad(mt_ctx *ctx, int n_chains, const void *heights, double *grad_out,
+                  double *logpost_out);
+
+/* Start n_chains chains at heights0 (host or device, storage type of the
+ * precision) with Philox key `seed`; evaluates their log-posterior.  The step
+ * counter restarts at 0. */
+MT_API mt_status mt_init_chains(mt_ctx *ctx, int n_chains, const void *heights0, uint64_t seed);
+
+/* Run n_super x n_within Metropolis steps on every chain (Sec. 2.2).
+ * kernel MT_KERNEL_RW: H' = H + step * xi; MT_KERNEL_MALA: Langevin proposal
+ * with step size eps = step and the Hastings correction.  Step k of chain c
+ * draws xi from Philox stream 3 (RW) or 5 (MALA), counter {j, k, c}, and its
+ * acceptance uniform from stream 4, counter {0, k, c}.  The n_within steps of
+ * a super-step are one CUDA graph replay; the host only sees super-step
+ * boundaries.  Asynchronous. */
+MT_API mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within);
+
+/* Copy the chains' current state out (each pointer host or device, nullable):
+ * heights [C][L][R][Q] storage type, loglik/logprior double [C], accepts
+ * int64 [C] (accepted proposals so far), *step_out = steps taken. */
+MT_API mt_status mt_get_state(mt_ctx *ctx, void *heights_out, double *loglik_out, double *logprior_out,
+                       int64_t *accepts_out, int64_t *step_out);
+
+/* Diagnostics of the most recent step (nullable, host or device):
+ * proposal [C][L][R][Q] storage type, its loglik/logprior double [C],
+ * accepted int32 [C] (1 = accepted), logu double [C] (ln of the uniform). */
+MT_API mt_status mt_get_last_step(mt_ctx *ctx, void *proposal_out, double *loglik_out,
+                           double *logprior_out, int32_t *accepted_out, double *logu_out);
+
+/* Resume: overwrite the current heights (host or device) and set the step
+ * counter; log-posteriors are re-evaluated.  Acceptance counters are kept. */
+MT_API mt_status mt_set_state(mt_ctx *ctx, const void *heights, int64_t step);
+
+/* Wait for the context's stream, at most timeout_s seconds (<= 0: no limit).
+ * MT_ETIMEDOUT if work is still in flight at the deadline (the context stays
+ * usable); MT_EDEVFLAG if a kernel latched a failure (the flag is cleared). */
+MT_API mt_status mt_sync(mt_ctx *ctx, double timeout_s);
+
+/* Kernel timing: when on, the library brackets each launch of the ray kernel
+ * (id 0) and each whole Metropolis step (id 1) with CUDA events on its stream
+ * and does not use graphs.  mt_get_timing returns the summed milliseconds and
+ * the launch count since the last reset (reset = 1 clears them). */
+MT_API mt_status mt_set_timing(mt_ctx *ctx, int on);
+MT_API mt_status mt_get_timing(mt_ctx *ctx, int id, double *total_ms, int64_t *launches, int reset);
+
+/* Sizes of the loaded problem (any pointer nullable). */
+MT_API mt_status mt_get_sizes(const mt_ctx *ctx, int *n_layers, int *n_rows, int *n_cols,
+                       int *n_sensors, int *n_pixels, int *n_chains);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MT_H */

@@ -1,0 +1,969 @@
+// ctx.cu -- host side of libmt.so: the context, argument checks, device
+// buffers, the Metropolis super-step as a CUDA graph, and the C ABI of
+// include/mt.h.  No kernel runs on the host; every step of the path is one
+// of the kernels in data.cu, march_*.cu and mcmc.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace mt {
+template <int MODE>
+cudaError_t launch_march_mode(const Prob &, HRef, int, int, size_t, void *, double *, double *,
+                              cudaStream_t);
+cudaError_t launch_accept_fused(const Prob &pb, int mode, int n_chains, const void *partial,
+                                const double *lp_prop, const double *extra, double *ll,
+                                double *lp, double *ll_prop_out, uint8_t *cur, uint8_t *prop_sel,
+                                int64_t *accepts, int32_t *acc_last, double *logu_out,
+                                uint64_t seed, const int64_t *step_base, int step_off,
+                                cudaStream_t st);
+size_t nodes_bytes_f64(int L, int N);
+
+int march_rays_per_block(const Prob &pb)
+{
+    // 256 threads x up to 16 rays each; small problems use fewer.
+    const int per = 256 * 16;
+    const int need = ((pb.n_rays + 255) / 256) * 256;
+    return need < per ? need : per;
+}
+
+size_t march_smem_bytes(const Prob &pb, int mode)
+{
+    const int es = mode == MODE_F64 ? 8 : mode == MODE_BF16 ? 2 : 4;
+    const int raw = pb.L * es;
+    const int bytes = raw <= 4 ? 4 : raw <= 8 ? 8 : ((raw + 15) / 16) * 16;
+    return (size_t)bytes * pb.N;
+}
+
+cudaError_t launch_march(const Prob &pb, int mode, HRef h, int n_chains, void *partial,
+                         double *ray_O, double *ray_term, cudaStream_t st)
+{
+    const int rpb = march_rays_per_block(pb);
+    const size_t smem = march_smem_bytes(pb, mode);
+    switch (mode) {
+        case MODE_F64:
+            return launch_march_mode<MODE_F64>(pb, h, n_chains, rpb, smem, partial, ray_O, ray_term, st);
+        case MODE_F32:
+            return launch_march_mode<MODE_F32>(pb, h, n_chains, rpb, smem, partial, ray_O, ray_term, st);
+        case MODE_F32C:
+            return launch_march_mode<MODE_F32C>(pb, h, n_chains, rpb, smem, partial, ray_O, ray_term, st);
+        case MODE_BF16:
+            return launch_march_mode<MODE_BF16>(pb, h, n_chains, rpb, smem, partial, ray_O, ray_term, st);
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace mt
+
+using namespace mt;
+
+struct EvPair {
+    cudaEvent_t a, b;
+};
+
+struct mt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    mt_config cfg{};
+    int mode = MODE_F32;
+    std::string err;
+
+    int L = 0, R = 0, Q = 0, S = 0, P = 0;
+    double box[3] = {0, 0, 0};
+    std::vector<double> rho, mu;
+    bool have_grid = false, have_sensors = false, have_pixels = false, have_counts = false;
+    Prob pb{};
+
+    double *d_mu = nullptr, *d_sensors = nullptr, *d_dirs = nullptr;
+    float4 *d_o4 = nullptr, *d_s4 = nullptr;
+    float *d_kz0 = nullptr;
+    double *d_od = nullptr, *d_sd = nullptr, *d_dt = nullptr, *d_a = nullptr, *d_sumK = nullptr;
+    float2 *d_dtff = nullptr, *d_aff = nullptr;
+    int32_t *d_cnt = nullptr;
+    int *d_flag = nullptr;
+
+    int C = 0;
+    uint64_t seed = 0;
+    void *d_H = nullptr;  // [2][C][n]
+    uint8_t *d_cur = nullptr, *d_psel = nullptr;
+    double *d_ll = nullptr, *d_lp = nullptr, *d_llp = nullptr, *d_lpp = nullptr, *d_logu = nullptr;
+    int64_t *d_acc = nullptr, *d_step = nullptr;
+    int32_t *d_accl = nullptr;
+
+    void *d_part = nullptr;
+    size_t part_cap = 0;
+    void *d_in = nullptr;
+    size_t in_cap = 0;
+    void *d_out = nullptr;
+    size_t out_cap = 0;
+    void *d_out2 = nullptr;
+    size_t out2_cap = 0;
+
+    cudaGraphExec_t gexec = nullptr;
+    int g_kernel = -1, g_nw = 0, g_C = 0;
+    double g_step = 0.0;
+
+    bool timing = false;
+    std::vector<EvPair> ev_open[2];
+    std::vector<cudaEvent_t> ev_pool;
+    double t_ms[2] = {0, 0};
+    int64_t t_n[2] = {0, 0};
+};
+
+static thread_local std::string g_create_err;
+
+static mt_status fail(mt_ctx *ctx, mt_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else g_create_err = buf;
+    return st;
+}
+
+#define CK(ctx, x)                                                                           \
+    do {                                                                                     \
+        cudaError_t e_ = (x);                                                                \
+        if (e_ != cudaSuccess) {                                                             \
+            cudaGetLastError();                                                              \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MT_ENOMEM : MT_ECUDA, "%s: %s", \
+                        #x, cudaGetErrorString(e_));                                         \
+        }                                                                                    \
+    } while (0)
+
+#define TRY(x)                          \
+    do {                                \
+        mt_status s_ = (x);             \
+        if (s_ != MT_OK) return s_;     \
+    } while (0)
+
+static bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T> static void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+static mt_status grow(mt_ctx *ctx, void **p, size_t *cap, size_t bytes)
+{
+    if (bytes <= *cap && *p) return MT_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    size_t want = bytes < 256 ? 256 : bytes;
+    CK(ctx, cudaMalloc(p, want));
+    *cap = want;
+    return MT_OK;
+}
+
+template <typename T> static mt_status dalloc(mt_ctx *ctx, T **p, size_t n)
+{
+    dfree(*p);
+    CK(ctx, cudaMalloc((void **)p, n * sizeof(T) + 16));
+    return MT_OK;
+}
+
+static size_t elem_size(const mt_ctx *ctx) { return ctx->mode == MODE_F64 ? 8 : 4; }
+static size_t n_per_chain(const mt_ctx *ctx) { return (size_t)ctx->L * ctx->R * ctx->Q; }
+
+static void drop_graph(mt_ctx *ctx)
+{
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+    ctx->g_kernel = -1;
+}
+
+static void drop_chains(mt_ctx *ctx)
+{
+    drop_graph(ctx);
+    dfree(ctx->d_H);
+    dfree(ctx->d_cur);
+    dfree(ctx->d_psel);
+    dfree(ctx->d_ll);
+    dfree(ctx->d_lp);
+    dfree(ctx->d_llp);
+    dfree(ctx->d_lpp);
+    dfree(ctx->d_logu);
+    dfree(ctx->d_acc);
+    dfree(ctx->d_accl);
+    ctx->C = 0;
+}
+
+static void refresh_prob(mt_ctx *ctx)
+{
+    Prob &pb = ctx->pb;
+    pb.L = ctx->L;
+    pb.R = ctx->R;
+    pb.Q = ctx->Q;
+    pb.S = ctx->S;
+    pb.P = ctx->P;
+    pb.G = ctx->cfg.n_grid;
+    pb.n_rays = ctx->S * ctx->P;
+    pb.N = ctx->R * ctx->Q;
+    for (int a = 0; a < 3; ++a) pb.box[a] = ctx->box[a];
+    pb.gamma = ctx->cfg.gamma;
+    pb.I0 = ctx->cfg.I0;
+    pb.Lambda = ctx->cfg.atten;
+    pb.inv_Lambda = 1.0 / ctx->cfg.atten;
+    pb.tau = ctx->cfg.tau;
+    pb.car_r = ctx->cfg.car_r;
+    pb.delta = ctx->cfg.min_thick;
+    pb.kg = ctx->cfg.gamma > 0.0 ? (float)(1.4426950408889634074 / ctx->cfg.gamma) : 1.0f;
+    // largest float below n - 3/2 by 8 ulps: keeps the cell index <= n - 2
+    auto hi = [](int n) {
+        float v = (float)n - 1.5f;
+        for (int i = 0; i < 8; ++i) v = nextafterf(v, -INFINITY);
+        return v;
+    };
+    pb.gm_hi_x = hi(ctx->Q);
+    pb.gm_hi_y = hi(ctx->R);
+    if (!ctx->rho.empty()) {
+        pb.rho_top = ctx->rho[ctx->L];
+        for (int l = 0; l < MT_MAX_L; ++l) {
+            pb.drho[l] = l < ctx->L ? ctx->rho[l] - ctx->rho[l + 1] : 0.0;
+            pb.drho_f[l] = (float)pb.drho[l];
+            pb.drho_ff[l] = make_float2(pb.drho_f[l], (float)(pb.drho[l] - (double)pb.drho_f[l]));
+        }
+    }
+    // Reference height per surface for the FP32 paths: the mean prior height
+    // (or evenly spaced levels when the prior mean is all zero), as a float.
+    const size_t N = (size_t)ctx->R * ctx->Q;
+    for (int l = 0; l < MT_MAX_L; ++l) {
+        double m = 0.0;
+        if (l < ctx->L && ctx->mu.size() >= (l + 1) * N) {
+            for (size_t i = 0; i < N; ++i) m += ctx->mu[l * N + i];
+            m /= (double)N;
+            if (m == 0.0) m = ctx->box[2] * (l + 1) / (ctx->L + 1);
+        }
+        pb.ref[l] = (float)m;
+    }
+    pb.kz0 = ctx->d_kz0;
+    pb.o4 = ctx->d_o4;
+    pb.s4 = ctx->d_s4;
+    pb.o_d = ctx->d_od;
+    pb.s_d = ctx->d_sd;
+    pb.dt = ctx->d_dt;
+    pb.a = ctx->d_a;
+    pb.a_ff = ctx->d_aff;
+    pb.dt_ff = ctx->d_dtff;
+    pb.cnt = ctx->d_cnt;
+    const double grho = (double)pb.G * pb.rho_top;
+    pb.grho_ff = make_float2((float)grho, (float)(grho - (double)(float)grho));
+    const double il = pb.inv_Lambda;
+    pb.invL_ff = make_float2((float)il, (float)(il - (double)(float)il));
+}
+
+static mt_status need(mt_ctx *ctx, bool counts)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (!ctx->have_grid) return fail(ctx, MT_ESTATE, "mt_set_grid has not been called");
+    if (!ctx->have_sensors) return fail(ctx, MT_ESTATE, "mt_set_sensors has not been called");
+    if (!ctx->have_pixels) return fail(ctx, MT_ESTATE, "mt_set_pixels has not been called");
+    if (counts && !ctx->have_counts)
+        return fail(ctx, MT_ESTATE, "no observed counts: call mt_set_counts or mt_generate_data");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail(ctx, MT_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return MT_OK;
+}
+
+static mt_status build_raytab(mt_ctx *ctx)
+{
+    if (!(ctx->have_grid && ctx->have_sensors && ctx->have_pixels)) return MT_OK;
+    const size_t n = (size_t)ctx->S * ctx->P;
+    TRY(dalloc(ctx, &ctx->d_o4, n));
+    TRY(dalloc(ctx, &ctx->d_s4, n));
+    TRY(dalloc(ctx, &ctx->d_kz0, 2 * (size_t)ctx->L * n));
+    TRY(dalloc(ctx, &ctx->d_od, 3 * n));
+    TRY(dalloc(ctx, &ctx->d_sd, 3 * n));
+    TRY(dalloc(ctx, &ctx->d_dt, n));
+    TRY(dalloc(ctx, &ctx->d_dtff, n));
+    refresh_prob(ctx);
+    CK(ctx, launch_raytab(ctx->pb, ctx->d_sensors, ctx->d_dirs, ctx->d_o4, ctx->d_s4, ctx->d_kz0,
+                          ctx->d_od, ctx->d_sd, ctx->d_dt, ctx->d_dtff, ctx->d_flag, ctx->stream));
+    return MT_OK;
+}
+
+static mt_status eval_logpost(mt_ctx *ctx, HRef h, int n, double *d_ll, double *d_lp);
+
+static mt_status counts_ready(mt_ctx *ctx)
+{
+    const size_t n = (size_t)ctx->S * ctx->P;
+    TRY(dalloc(ctx, &ctx->d_a, n));
+    TRY(dalloc(ctx, &ctx->d_aff, n));
+    if (!ctx->d_sumK) TRY(dalloc(ctx, &ctx->d_sumK, 1));
+    refresh_prob(ctx);
+    CK(ctx, launch_counts_prep(ctx->pb, ctx->d_a, ctx->d_aff, ctx->d_sumK, ctx->stream));
+    double sk = 0.0;
+    CK(ctx, cudaMemcpyAsync(&sk, ctx->d_sumK, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->have_counts = true;
+    refresh_prob(ctx);
+    ctx->pb.sumK = sk;
+    drop_graph(ctx);
+    if (ctx->C > 0) {  // live chains: their log-likelihoods refer to the old counts
+        const size_t np = n_per_chain(ctx);
+        HRef h{ctx->d_H, (long long)np, ctx->d_cur, (long long)(ctx->C * np), 0};
+        TRY(eval_logpost(ctx, h, ctx->C, ctx->d_ll, ctx->d_lp));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return MT_OK;
+}
+
+// Device view of a caller array of `bytes`: the pointer itself when it is
+// device memory, else a copy in the staging buffer `slot`.
+static mt_status dev_in(mt_ctx *ctx, const void *p, size_t bytes, const void **out)
+{
+    if (is_device_ptr(p)) {
+        *out = p;
+        return MT_OK;
+    }
+    TRY(grow(ctx, &ctx->d_in, &ctx->in_cap, bytes));
+    CK(ctx, cudaMemcpyAsync(ctx->d_in, p, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    *out = ctx->d_in;
+    return MT_OK;
+}
+
+// Output target: device pointer as is, host pointer via a staging buffer.
+struct OutBuf {
+    void *user = nullptr;
+    void *dev = nullptr;
+    size_t bytes = 0;
+    bool host = false;
+};
+
+static mt_status dev_out(mt_ctx *ctx, void *p, size_t bytes, void **slot, size_t *cap, OutBuf *o)
+{
+    o->user = p;
+    o->bytes = bytes;
+    if (!p) {
+        o->dev = nullptr;
+        return MT_OK;
+    }
+    if (is_device_ptr(p)) {
+        o->dev = p;
+        o->host = false;
+        return MT_OK;
+    }
+    TRY(grow(ctx, slot, cap, bytes));
+    o->dev = *slot;
+    o->host = true;
+    return MT_OK;
+}
+
+static mt_status finish_out(mt_ctx *ctx, OutBuf *o)
+{
+    if (o->user && o->host)
+        CK(ctx, cudaMemcpyAsync(o->user, o->dev, o->bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    return MT_OK;
+}
+
+static mt_status ensure_partials(mt_ctx *ctx, int n_chains)
+{
+    const int rpb = march_rays_per_block(ctx->pb);
+    const size_t n_blk = (ctx->pb.n_rays + rpb - 1) / rpb;
+    void *old = ctx->d_part;
+    TRY(grow(ctx, &ctx->d_part, &ctx->part_cap, n_blk * (size_t)n_chains * 8));
+    if (ctx->d_part != old) drop_graph(ctx);  // a captured graph holds the old pointer
+    return MT_OK;
+}
+
+static mt_status check_smem(mt_ctx *ctx)
+{
+    const size_t smem = march_smem_bytes(ctx->pb, ctx->mode);
+    if (smem > MT_MAX_SMEM)
+        return fail(ctx, MT_EINVAL,
+                    "surfaces need %zu bytes of shared memory per block (limit %d): use "
+                    "MT_PREC_BF16 or a smaller grid",
+                    smem, MT_MAX_SMEM);
+    return MT_OK;
+}
+
+static cudaEvent_t ev_get(mt_ctx *ctx)
+{
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static void ev_begin(mt_ctx *ctx, int id, EvPair *p)
+{
+    p->a = ev_get(ctx);
+    p->b = ev_get(ctx);
+    cudaEventRecord(p->a, ctx->stream);
+}
+static void ev_end(mt_ctx *ctx, int id, EvPair *p)
+{
+    cudaEventRecord(p->b, ctx->stream);
+    ctx->ev_open[id].push_back(*p);
+}
+
+// log-likelihood + log-prior of n chains given by h, into device arrays.
+static mt_status eval_logpost(mt_ctx *ctx, HRef h, int n, double *d_ll, double *d_lp)
+{
+    TRY(ensure_partials(ctx, n));
+    if (d_lp) CK(ctx, launch_prior(ctx->pb, ctx->mode, h, ctx->d_mu, n, d_lp, ctx->stream));
+    if (d_ll) {
+        EvPair ep;
+        if (ctx->timing) ev_begin(ctx, 0, &ep);
+        CK(ctx, launch_march(ctx->pb, ctx->mode, h, n, ctx->d_part, nullptr, nullptr, ctx->stream));
+        if (ctx->timing) ev_end(ctx, 0, &ep);
+        CK(ctx, launch_reduce_ll(ctx->pb, ctx->mode, n, ctx->d_part, d_ll, ctx->stream));
+    }
+    return MT_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+mt_status mt_create(mt_ctx **out, int device, const mt_config *cfg, void *cuda_stream)
+{
+    if (!out || !cfg) return fail(nullptr, MT_EINVAL, "mt_create: null argument");
+    *out = nullptr;
+    if (cfg->precision < MT_PREC_F64 || cfg->precision > MT_PREC_BF16)
+        return fail(nullptr, MT_EINVAL, "mt_create: precision %d out of range", cfg->precision);
+    if (cfg->n_grid < 1 || cfg->n_grid > (1 << 20))
+        return fail(nullptr, MT_EINVAL, "mt_create: n_grid %d out of range", cfg->n_grid);
+    if (!(cfg->gamma >= 0.0) || !(cfg->I0 > 0.0) || !(cfg->atten > 0.0) || !(cfg->tau >= 0.0) ||
+        !(cfg->car_r >= 0.0 && cfg->car_r < 1.0) || !(cfg->min_thick > 0.0))
+        return fail(nullptr, MT_EINVAL,
+                    "mt_create: need gamma >= 0, I0 > 0, atten > 0, tau >= 0, 0 <= car_r < 1, "
+                    "min_thick > 0");
+    int n_dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n_dev);
+    if (e != cudaSuccess || device < 0 || device >= n_dev) {
+        cudaGetLastError();
+        return fail(nullptr, MT_ECUDA, "mt_create: no CUDA device %d (%s)", device,
+                    cudaGetErrorString(e));
+    }
+    mt_ctx *ctx = new (std::nothrow) mt_ctx();
+    if (!ctx) return fail(nullptr, MT_ENOMEM, "mt_create: out of host memory");
+    ctx->device = device;
+    ctx->cfg = *cfg;
+    ctx->mode = cfg->precision;
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            ctx->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreate(&ctx->stream);
+            ctx->own_stream = e == cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_step, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_step, 0, sizeof(int64_t), ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        mt_destroy(ctx);
+        return fail(nullptr, MT_ECUDA, "mt_create: %s", cudaGetErrorString(e));
+    }
+    refresh_prob(ctx);
+    *out = ctx;
+    return MT_OK;
+}
+
+mt_status mt_destroy(mt_ctx *ctx)
+{
+    if (!ctx) return MT_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    drop_chains(ctx);
+    dfree(ctx->d_mu);
+    dfree(ctx->d_sensors);
+    dfree(ctx->d_dirs);
+    dfree(ctx->d_o4);
+    dfree(ctx->d_s4);
+    dfree(ctx->d_kz0);
+    dfree(ctx->d_od);
+    dfree(ctx->d_sd);
+    dfree(ctx->d_dt);
+    dfree(ctx->d_dtff);
+    dfree(ctx->d_a);
+    dfree(ctx->d_aff);
+    dfree(ctx->d_sumK);
+    dfree(ctx->d_cnt);
+    dfree(ctx->d_flag);
+    dfree(ctx->d_step);
+    if (ctx->d_part) cudaFree(ctx->d_part);
+    if (ctx->d_in) cudaFree(ctx->d_in);
+    if (ctx->d_out) cudaFree(ctx->d_out);
+    if (ctx->d_out2) cudaFree(ctx->d_out2);
+    for (int i = 0; i < 2; ++i)
+        for (auto &p : ctx->ev_open[i]) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return MT_OK;
+}
+
+const char *mt_last_error(const mt_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+mt_status mt_set_grid(mt_ctx *ctx, int n_layers, int n_rows, int n_cols, const double box[3],
+                      const double *unit_density, const double *prior_mean)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (n_layers < 1 || n_layers > MT_MAX_L)
+        return fail(ctx, MT_EINVAL, "n_layers %d not in [1, %d]", n_layers, MT_MAX_L);
+    if (n_rows < 2 || n_cols < 2 || (long long)n_rows * n_cols > (1 << 22))
+        return fail(ctx, MT_EINVAL, "grid %d x %d: each side must be >= 2", n_rows, n_cols);
+    if (!box || !unit_density) return fail(ctx, MT_EINVAL, "null box or unit_density");
+    for (int a = 0; a < 3; ++a)
+        if (!(box[a] > 0.0)) return fail(ctx, MT_EINVAL, "box side %d must be > 0", a);
+    for (int u = 0; u <= n_layers; ++u)
+        if (!(unit_density[u] >= 0.0)) return fail(ctx, MT_EINVAL, "unit_density[%d] < 0", u);
+    CK(ctx, cudaSetDevice(ctx->device));
+    drop_chains(ctx);
+    ctx->L = n_layers;
+    ctx->R = n_rows;
+    ctx->Q = n_cols;
+    for (int a = 0; a < 3; ++a) ctx->box[a] = box[a];
+    ctx->rho.assign(unit_density, unit_density + n_layers + 1);
+    const size_t n = (size_t)n_layers * n_rows * n_cols;
+    ctx->mu.assign(n, 0.0);
+    if (prior_mean) ctx->mu.assign(prior_mean, prior_mean + n);
+    TRY(dalloc(ctx, &ctx->d_mu, n));
+    CK(ctx, cudaMemcpyAsync(ctx->d_mu, ctx->mu.data(), n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->have_grid = true;
+    ctx->have_counts = false;
+    refresh_prob(ctx);
+    TRY(check_smem(ctx));
+    TRY(build_raytab(ctx));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MT_OK;
+}
+
+mt_status mt_set_sensors(mt_ctx *ctx, int n_sensors, const double *pos)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (!ctx->have_grid) return fail(ctx, MT_ESTATE, "mt_set_grid first");
+    if (n_sensors < 1 || !pos) return fail(ctx, MT_EINVAL, "need n_sensors >= 1 and positions");
+    for (int s = 0; s < n_sensors; ++s)
+        for (int a = 0; a < 3; ++a)
+            if (!(pos[3 * s + a] > 0.0 && pos[3 * s + a] < ctx->box[a]))
+                return fail(ctx, MT_EINVAL, "sensor %d is not strictly inside the box", s);
+    CK(ctx, cudaSetDevice(ctx->device));
+    drop_chains(ctx);
+    ctx->S = n_sensors;
+    TRY(dalloc(ctx, &ctx->d_sensors, 3 * (size_t)n_sensors));
+    CK(ctx, cudaMemcpyAsync(ctx->d_sensors, pos, 24 * (size_t)n_sensors, cudaMemcpyHostToDevice,
+                            ctx->stream));
+    ctx->have_sensors = true;
+    ctx->have_counts = false;
+    TRY(build_raytab(ctx));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MT_OK;
+}
+
+mt_status mt_set_pixels(mt_ctx *ctx, int n_pixels, const double *dirs)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (!ctx->have_grid) return fail(ctx, MT_ESTATE, "mt_set_grid first");
+    if (n_pixels < 1 || !dirs) return fail(ctx, MT_EINVAL, "need n_pixels >= 1 and directions");
+    for (int p = 0; p < n_pixels; ++p) {
+        const double *d = dirs + 3 * p;
+        const double nn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (!(fabs(nn - 1.0) <= 1e-6))
+            return fail(ctx, MT_EINVAL, "pixel %d direction is not a unit vector", p);
+    }
+    if ((long long)ctx->S * n_pixels > (1LL << 30))
+        return fail(ctx, MT_EINVAL, "too many rays");
+    CK(ctx, cudaSetDevice(ctx->device));
+    drop_chains(ctx);
+    ctx->P = n_pixels;
+    TRY(dalloc(ctx, &ctx->d_dirs, 3 * (size_t)n_pixels));
+    CK(ctx, cudaMemcpyAsync(ctx->d_dirs, dirs, 24 * (size_t)n_pixels, cudaMemcpyHostToDevice,
+                            ctx->stream));
+    ctx->have_pixels = true;
+    ctx->have_counts = false;
+    TRY(build_raytab(ctx));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MT_OK;
+}
+
+mt_status mt_set_counts(mt_ctx *ctx, const int32_t *counts)
+{
+    TRY(need(ctx, false));
+    if (!counts) return fail(ctx, MT_EINVAL, "null counts");
+    const size_t n = (size_t)ctx->S * ctx->P;
+    if (!is_device_ptr(counts)) {
+        for (size_t i = 0; i < n; ++i)
+            if (counts[i] < 0) return fail(ctx, MT_EINVAL, "count %zu is negative", i);
+    }
+    TRY(dalloc(ctx, &ctx->d_cnt, n));
+    CK(ctx, cudaMemcpyAsync(ctx->d_cnt, counts, n * 4, cudaMemcpyDefault, ctx->stream));
+    return counts_ready(ctx);
+}
+
+mt_status mt_generate_data(mt_ctx *ctx, const double *h_true, uint64_t seed, int count_mode,
+                           int32_t *counts_out, double *lambda_out)
+{
+    TRY(need(ctx, false));
+    if (!h_true) return fail(ctx, MT_EINVAL, "null h_true");
+    if (count_mode != MT_COUNTS_POISSON && count_mode != MT_COUNTS_ROUND)
+        return fail(ctx, MT_EINVAL, "count_mode %d", count_mode);
+    const size_t n = (size_t)ctx->S * ctx->P;
+    const size_t nh = n_per_chain(ctx);
+    TRY(dalloc(ctx, &ctx->d_cnt, n));
+    refresh_prob(ctx);
+    const size_t scratch = (nh + 1) * 8 + nodes_bytes_f64(ctx->L, ctx->pb.N) + 64;
+    TRY(grow(ctx, &ctx->d_in, &ctx->in_cap, scratch));
+    CK(ctx, cudaMemcpyAsync(ctx->d_in, h_true, nh * 8, cudaMemcpyDefault, ctx->stream));
+    OutBuf lam;
+    TRY(dev_out(ctx, lambda_out, n * 8, &ctx->d_out, &ctx->out_cap, &lam));
+    double *d_lam = (double *)lam.dev;
+    if (!d_lam) {
+        TRY(grow(ctx, &ctx->d_out, &ctx->out_cap, n * 8));
+        d_lam = (double *)ctx->d_out;
+    }
+    CK(ctx, launch_gen_counts(ctx->pb, (const double *)ctx->d_in, seed, count_mode, ctx->d_cnt,
+                              d_lam, ctx->d_flag, ctx->stream));
+    TRY(finish_out(ctx, &lam));
+    if (counts_out)
+        CK(ctx, cudaMemcpyAsync(counts_out, ctx->d_cnt, n * 4, cudaMemcpyDefault, ctx->stream));
+    return counts_ready(ctx);
+}
+
+mt_status mt_logpost(mt_ctx *ctx, int n_chains, const void *heights, double *loglik_out,
+                     double *logprior_out)
+{
+    TRY(need(ctx, true));
+    if (n_chains < 1 || n_chains > 65535 || !heights)
+        return fail(ctx, MT_EINVAL, "need 1 <= n_chains <= 65535 and heights");
+    const size_t np = n_per_chain(ctx);
+    const void *dh;
+    TRY(dev_in(ctx, heights, (size_t)n_chains * np * elem_size(ctx), &dh));
+    OutBuf ll, lp;
+    TRY(dev_out(ctx, loglik_out, (size_t)n_chains * 8, &ctx->d_out, &ctx->out_cap, &ll));
+    TRY(dev_out(ctx, logprior_out, (size_t)n_chains * 8, &ctx->d_out2, &ctx->out2_cap, &lp));
+    HRef h{dh, (long long)np, nullptr, 0, 0};
+    TRY(eval_logpost(ctx, h, n_chains, (double *)ll.dev, (double *)lp.dev));
+    TRY(finish_out(ctx, &ll));
+    TRY(finish_out(ctx, &lp));
+    if (ll.host || lp.host || dh == ctx->d_in) CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MT_OK;
+}
+
+mt_status mt_ray_terms(mt_ctx *ctx, int n_chains, const void *heights, double *opacity_out,
+                       double *term_out)
+{
+    TRY(need(ctx, true));
+    if (n_chains < 1 || n_chains > 65535 || !heights)
+        return fail(ctx, MT_EINVAL, "need 1 <= n_chains <= 65535 and heights");
+    const size_t np = n_per_chain(ctx);
+    const size_t nr = (size_t)n_chains * ctx->pb.n_rays;
+    const void *dh;
+    TRY(dev_in(ctx, heights, (size_t)n_chains * np * elem_size(ctx), &dh));
+    OutBuf o, t;
+    TRY(dev_out(ctx, opacity_out, nr * 8, &ctx->d_out, &ctx->out_cap, &o));
+    TRY(dev_out(ctx, term_out, nr * 8, &ctx->d_out2, &ctx->out2_cap, &t));
+    TRY(ensure_partials(ctx, n_chains));
+    HRef h{dh, (long long)np, nullptr, 0, 0};
+    CK(ctx, launch_march(ctx->pb, ctx->mode, h, n_chains, ctx->d_part, (double *)o.dev,
+                         (double *)t.dev, ctx->stream));
+    TRY(finish_out(ctx, &o));
+    TRY(finish_out(ctx, &t));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MT_OK;
+}
+
+mt_status mt_grad(mt_ctx *ctx, int n_chains, const void *heights, double *grad_out,
+                  double *logpost_out)
+{
+    TRY(need(ctx, true));
+    (void)n_chains;
+    (void)heights;
+    (void)grad_out;
+    (void)logpost_out;
+    return fail(ctx, MT_ESTATE, "mt_grad: the adjoint kernel is not part of this build");
+}
+
+mt_status mt_init_chains(mt_ctx *ctx, int n_chains, const void *heights0, uint64_t seed)
+{
+    TRY(need(ctx, true));
+    if (n_chains < 1 || n_chains > 65535 || !heights0)
+        return fail(ctx, MT_EINVAL, "need 1 <= n_chains <= 65535 and heights0");
+    const size_t np = n_per_chain(ctx), es = elem_size(ctx);
+    if (n_chains != ctx->C) {
+        drop_chains(ctx);
+        void *h = nullptr;
+        CK(ctx, cudaMalloc(&h, 2 * (size_t)n_chains * np * es));
+        ctx->d_H = h;
+        TRY(dalloc(ctx, &ctx->d_cur, n_chains));
+        TRY(dalloc(ctx, &ctx->d_psel, n_chains));
+        TRY(dalloc(ctx, &ctx->d_ll, n_chains));
+        TRY(dalloc(ctx, &ctx->d_lp, n_chains));
+        TRY(dalloc(ctx, &ctx->d_llp, n_chains));
+        TRY(dalloc(ctx, &ctx->d_lpp, n_chains));
+        TRY(dalloc(ctx, &ctx->d_logu, n_chains));
+        TRY(dalloc(ctx, &ctx->d_acc, n_chains));
+        TRY(dalloc(ctx, &ctx->d_accl, n_chains));
+        ctx->C = n_chains;
+    }
+    drop_graph(ctx);
+    ctx->seed = seed;
+    CK(ctx, cudaMemcpyAsync(ctx->d_H, heights0, (size_t)n_chains * np * es, cudaMemcpyDefault,
+                            ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->d_cur, 0, n_chains, ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->d_psel, 1, n_chains, ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->d_acc, 0, 8 * (size_t)n_chains, ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->d_accl, 0, 4 * (size_t)n_chains, ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->d_step, 0, 8, ctx->stream));
+    HRef h{ctx->d_H, (long long)np, nullptr, 0, 0};
+    TRY(eval_logpost(ctx, h, n_chains, ctx->d_ll, ctx->d_lp));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MT_OK;
+}
+
+static mt_status enqueue_step(mt_ctx *ctx, int kernel, double step, int off)
+{
+    const size_t np = n_per_chain(ctx);
+    const long long bs = (long long)ctx->C * np;
+    if (kernel != MT_KERNEL_RW) return fail(ctx, MT_EINVAL, "kernel %d not available", kernel);
+    EvPair es;
+    if (ctx->timing) ev_begin(ctx, 1, &es);
+    CK(ctx, launch_propose_rw(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_cur, ctx->C, step, ctx->seed,
+                              ctx->d_step, off, ctx->stream));
+    HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
+    CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
+    EvPair ep;
+    if (ctx->timing) ev_begin(ctx, 0, &ep);
+    CK(ctx, launch_march(ctx->pb, ctx->mode, hp, ctx->C, ctx->d_part, nullptr, nullptr, ctx->stream));
+    if (ctx->timing) ev_end(ctx, 0, &ep);
+    CK(ctx, launch_accept_fused(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, nullptr,
+                                ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
+                                ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
+                                ctx->stream));
+    if (ctx->timing) ev_end(ctx, 1, &es);
+    return MT_OK;
+}
+
+mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within)
+{
+    TRY(need(ctx, true));
+    if (ctx->C < 1) return fail(ctx, MT_ESTATE, "mt_init_chains first");
+    if (kernel != MT_KERNEL_RW && kernel != MT_KERNEL_MALA)
+        return fail(ctx, MT_EINVAL, "kernel %d", kernel);
+    if (kernel == MT_KERNEL_MALA)
+        return fail(ctx, MT_ESTATE, "MALA needs the adjoint kernel, not part of this build");
+    if (!(step >= 0.0) || n_super < 0 || n_within < 1 || n_within > 4096)
+        return fail(ctx, MT_EINVAL, "need step >= 0, n_super >= 0, 1 <= n_within <= 4096");
+    TRY(ensure_partials(ctx, ctx->C));
+    if (ctx->timing) {
+        for (int s = 0; s < n_super; ++s) {
+            for (int i = 0; i < n_within; ++i) TRY(enqueue_step(ctx, kernel, step, i));
+            CK(ctx, launch_advance(ctx->d_step, n_within, ctx->stream));
+        }
+        return MT_OK;
+    }
+    if (!(ctx->gexec && ctx->g_kernel == kernel && ctx->g_step == step && ctx->g_nw == n_within &&
+          ctx->g_C == ctx->C)) {
+        drop_graph(ctx);
+        cudaGraph_t g = nullptr;
+        CK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        mt_status st = MT_OK;
+        for (int i = 0; i < n_within && st == MT_OK; ++i) st = enqueue_step(ctx, kernel, step, i);
+        if (st == MT_OK) {
+            cudaError_t e = launch_advance(ctx->d_step, n_within, ctx->stream);
+            if (e != cudaSuccess) st = fail(ctx, MT_ECUDA, "advance: %s", cudaGetErrorString(e));
+        }
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        if (st != MT_OK) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return st;
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, MT_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ctx->gexec = nullptr;
+            cudaGetLastError();
+            return fail(ctx, MT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+        ctx->g_kernel = kernel;
+        ctx->g_step = step;
+        ctx->g_nw = n_within;
+        ctx->g_C = ctx->C;
+    }
+    for (int s = 0; s < n_super; ++s) CK(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
+    return MT_OK;
+}
+
+mt_status mt_get_state(mt_ctx *ctx, void *heights_out, double *loglik_out, double *logprior_out,
+                       int64_t *accepts_out, int64_t *step_out)
+{
+    TRY(need(ctx, false));
+    if (ctx->C < 1) return fail(ctx, MT_ESTATE, "mt_init_chains first");
+    const size_t np = n_per_chain(ctx), C = ctx->C;
+    if (heights_out) {
+        OutBuf o;
+        TRY(dev_out(ctx, heights_out, C * np * elem_size(ctx), &ctx->d_out, &ctx->out_cap, &o));
+        HRef h{ctx->d_H, (long long)np, ctx->d_cur, (long long)(C * np), 0};
+        CK(ctx, launch_gather(ctx->mode, h, (int)C, (long long)np, o.dev, ctx->stream));
+        TRY(finish_out(ctx, &o));
+    }
+    if (loglik_out)
+        CK(ctx, cudaMemcpyAsync(loglik_out, ctx->d_ll, C * 8, cudaMemcpyDefault, ctx->stream));
+    if (logprior_out)
+        CK(ctx, cudaMemcpyAsync(logprior_out, ctx->d_lp, C * 8, cudaMemcpyDefault, ctx->stream));
+    if (accepts_out)
+        CK(ctx, cudaMemcpyAsync(accepts_out, ctx->d_acc, C * 8, cudaMemcpyDefault, ctx->stream));
+    int64_t stp = 0;
+    CK(ctx, cudaMemcpyAsync(&stp, ctx->d_step, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (step_out) *step_out = stp;
+    return MT_OK;
+}
+
+mt_status mt_get_last_step(mt_ctx *ctx, void *proposal_out, double *loglik_out,
+                           double *logprior_out, int32_t *accepted_out, double *logu_out)
+{
+    TRY(need(ctx, false));
+    if (ctx->C < 1) return fail(ctx, MT_ESTATE, "mt_init_chains first");
+    const size_t np = n_per_chain(ctx), C = ctx->C;
+    if (proposal_out) {
+        OutBuf o;
+        TRY(dev_out(ctx, proposal_out, C * np * elem_size(ctx), &ctx->d_out, &ctx->out_cap, &o));
+        HRef h{ctx->d_H, (long long)np, ctx->d_psel, (long long)(C * np), 0};
+        CK(ctx, launch_gather(ctx->mode, h, (int)C, (long long)np, o.dev, ctx->stream));
+        TRY(finish_out(ctx, &o));
+    }
+    if (loglik_out)
+        CK(ctx, cudaMemcpyAsync(loglik_out, ctx->d_llp, C * 8, cudaMemcpyDefault, ctx->stream));
+    if (logprior_out)
+        CK(ctx, cudaMemcpyAsync(logprior_out, ctx->d_lpp, C * 8, cudaMemcpyDefault, ctx->stream));
+    if (accepted_out)
+        CK(ctx, cudaMemcpyAsync(accepted_out, ctx->d_accl, C * 4, cudaMemcpyDefault, ctx->stream));
+    if (logu_out)
+        CK(ctx, cudaMemcpyAsync(logu_out, ctx->d_logu, C * 8, cudaMemcpyDefault, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MT_OK;
+}
+
+mt_status mt_set_state(mt_ctx *ctx, const void *heights, int64_t step)
+{
+    TRY(need(ctx, true));
+    if (ctx->C < 1) return fail(ctx, MT_ESTATE, "mt_init_chains first");
+    if (!heights || step < 0) return fail(ctx, MT_EINVAL, "need heights and step >= 0");
+    const size_t np = n_per_chain(ctx), es = elem_size(ctx);
+    CK(ctx, cudaMemcpyAsync(ctx->d_H, heights, (size_t)ctx->C * np * es, cudaMemcpyDefault,
+                            ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->d_cur, 0, ctx->C, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->d_step, &step, 8, cudaMemcpyHostToDevice, ctx->stream));
+    HRef h{ctx->d_H, (long long)np, nullptr, 0, 0};
+    TRY(eval_logpost(ctx, h, ctx->C, ctx->d_ll, ctx->d_lp));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MT_OK;
+}
+
+mt_status mt_sync(mt_ctx *ctx, double timeout_s)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    CK(ctx, cudaSetDevice(ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(ctx->stream);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) {
+            cudaGetLastError();
+            return fail(ctx, MT_ECUDA, "stream: %s", cudaGetErrorString(e));
+        }
+        const double el =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (timeout_s > 0.0 && el > timeout_s)
+            return fail(ctx, MT_ETIMEDOUT, "work still in flight after %.3f s", el);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    int flag = 0;
+    CK(ctx, cudaMemcpy(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(ctx, cudaMemset(ctx->d_flag, 0, sizeof(int)));
+        return fail(ctx, MT_EDEVFLAG, "a kernel latched device status %d (Poisson draw ran out of "
+                                      "attempts)", flag);
+    }
+    return MT_OK;
+}
+
+mt_status mt_set_timing(mt_ctx *ctx, int on)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    ctx->timing = on != 0;
+    drop_graph(ctx);
+    return MT_OK;
+}
+
+mt_status mt_get_timing(mt_ctx *ctx, int id, double *total_ms, int64_t *launches, int reset)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (id < 0 || id > 1) return fail(ctx, MT_EINVAL, "timing id %d", id);
+    CK(ctx, cudaSetDevice(ctx->device));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 2; ++k) {
+        for (auto &p : ctx->ev_open[k]) {
+            float ms = 0.f;
+            CK(ctx, cudaEventElapsedTime(&ms, p.a, p.b));
+            ctx->t_ms[k] += ms;
+            ctx->t_n[k] += 1;
+            ctx->ev_pool.push_back(p.a);
+            ctx->ev_pool.push_back(p.b);
+        }
+        ctx->ev_open[k].clear();
+    }
+    if (total_ms) *total_ms = ctx->t_ms[id];
+    if (launches) *launches = ctx->t_n[id];
+    if (reset) {
+        ctx->t_ms[id] = 0.0;
+        ctx->t_n[id] = 0;
+    }
+    return MT_OK;
+}
+
+mt_status mt_get_sizes(const mt_ctx *ctx, int *n_layers, int *n_rows, int *n_cols, int *n_sensors,
+                       int *n_pixels, int *n_chains)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (n_layers) *n_layers = ctx->L;
+    if (n_rows) *n_rows = ctx->R;
+    if (n_cols) *n_cols = ctx->Q;
+    if (n_sensors) *n_sensors = ctx->S;
+    if (n_pixels) *n_pixels = ctx->P;
+    if (n_chains) *n_chains = ctx->C;
+    return MT_OK;
+}
+
+}  // extern "C"

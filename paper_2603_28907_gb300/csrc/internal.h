@@ -1,0 +1,86 @@
+// internal.h -- types shared by the translation units of libmt.so.
+//
+// The problem descriptor Prob is passed by value to every kernel.  Layouts:
+//   heights (HBM)  [chain][layer][row][col], column fastest (C ABI layout);
+//   heights (smem) node-major [row][col][layer], each node padded to a
+//                  16/8/4-byte vector so one or two vector loads fetch every
+//                  surface of a node;
+//   ray table      structure of arrays over ray = sensor * P + pixel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mt.h"
+
+#define MT_MAX_L 8
+#define MT_MAX_SMEM 232448  // opt-in shared memory per block on sm_100/sm_103
+
+namespace mt {
+
+enum { MODE_F64 = 0, MODE_F32 = 1, MODE_F32C = 2, MODE_BF16 = 3 };
+enum { STREAM_GEOM = 0, STREAM_DATA = 1, STREAM_INIT = 2, STREAM_PROP = 3, STREAM_ACC = 4,
+       STREAM_MALA = 5 };
+
+struct Prob {
+    int L, R, Q, S, P, G, n_rays, N;  // N = R*Q nodes per surface
+    double box[3];
+    double gamma, I0, Lambda, inv_Lambda;
+    double tau, car_r, delta;
+    float kg;                  // log2(e) / gamma (1 for the hard indicator)
+    float gm_hi_x, gm_hi_y;    // upper clamp of the shifted cell coordinates (< n - 3/2)
+    double rho_top;            // density of the top unit
+    double drho[MT_MAX_L];     // rho_l - rho_{l+1}: density step across surface l
+    float drho_f[MT_MAX_L];
+    // ray table (n_rays entries each)
+    const float4 *o4;          // FP32 sample-0 cell coordinates {gx - 1/2, gy - 1/2, 0, 0}
+    const float4 *s4;          // FP32 per-sample step {dgx, dgy, kg*dz hi, kg*dz lo}
+    const float *kz0;          // [2][L][n_rays] kg * (z_0 - ref_l) as FP32 hi, lo
+    float ref[MT_MAX_L];       // per-surface reference height of the FP32 paths
+    float2 drho_ff[MT_MAX_L];  // float-float of drho
+    const double *o_d;         // [3] FP64 sample-0 position {gx, gy, z}
+    const double *s_d;         // [3] FP64 per-sample step
+    const double *dt;          // sample spacing along the ray (m)
+    const double *a;           // ln(I0 / C) (0 where C = 0)
+    const float2 *a_ff;        // float-float of a
+    const float2 *dt_ff;       // float-float of dt
+    const int32_t *cnt;        // observed counts
+    double sumK;               // sum over rays of C ln C - C - lgamma(C + 1)
+    float2 grho_ff;            // float-float of G * rho_top
+    float2 invL_ff;            // float-float of 1 / Lambda
+};
+
+// Where chain c's heights live: base + sel[c] * sel_stride + c * chain_stride
+// (elements), with sel[c] replaced by 1 - sel[c] when sel_flip is set.
+struct HRef {
+    const void *base;
+    long long chain_stride;
+    const uint8_t *sel;
+    long long sel_stride;
+    int sel_flip;
+};
+
+// Launchers (stream-ordered, return cudaGetLastError()).
+cudaError_t launch_raytab(const Prob &pb, const double *d_sensors, const double *d_dirs,
+                          float4 *o4, float4 *s4, float *kz0, double *o_d, double *s_d, double *dt,
+                          float2 *dt_ff, int *flag, cudaStream_t st);
+cudaError_t launch_counts_prep(const Prob &pb, double *a, float2 *a_ff, double *sumK,
+                               cudaStream_t st);
+cudaError_t launch_gen_counts(const Prob &pb, const double *h_nodes, uint64_t seed, int mode,
+                              int32_t *counts, double *lambda, int *flag, cudaStream_t st);
+int march_rays_per_block(const Prob &pb);
+size_t march_smem_bytes(const Prob &pb, int mode);
+cudaError_t launch_march(const Prob &pb, int mode, HRef h, int n_chains, void *partial,
+                         double *ray_O, double *ray_term, cudaStream_t st);
+cudaError_t launch_reduce_ll(const Prob &pb, int mode, int n_chains, const void *partial,
+                             double *ll_out, cudaStream_t st);
+cudaError_t launch_prior(const Prob &pb, int mode, HRef h, const double *mu, int n_chains,
+                         double *lp_out, cudaStream_t st);
+cudaError_t launch_propose_rw(const Prob &pb, int mode, void *hbuf, long long buf_stride,
+                              const uint8_t *cur, int n_chains, double sigma, uint64_t seed,
+                              const int64_t *step_base, int step_off, cudaStream_t st);
+cudaError_t launch_advance(int64_t *step, int n, cudaStream_t st);
+cudaError_t launch_gather(int mode, HRef h, int n_chains, long long n_per_chain, void *out,
+                          cudaStream_t st);
+
+}  // namespace mt

@@ -1,0 +1,505 @@
+// march.cuh -- fused ray march + Poisson log-likelihood (the hot path).
+//
+// One CTA = one chain x one block of rays.  The chain's surfaces are staged
+// node-major in shared memory; each thread marches whole rays (consecutive
+// lanes = consecutive pixels of one sensor, so a warp's rays stay close).
+//
+// Per sample k of a ray (Sec. 2.1.1 opacity integral as a midpoint sum; Eqs.
+// smooth_layer_indicators / def_LM_density_grid_smooth):
+//   position      g = g0 + k*gs  (x, y in cell units, z scaled by log2(e)/gamma)
+//   cell          the bilinear cell holding (x, y); its four corners of every
+//                 surface are cached in registers and reloaded only when the
+//                 ray enters a new cell
+//   indicator     varsigma(s_l - z) for each surface l
+//   density       rho(x) = rho_top + sum_l (rho_l - rho_{l+1}) varsigma(s_l - z),
+//                 which equals sum_u W_u rho_u because the normaliser sum_u D_u
+//                 telescopes to exactly 1
+// Per ray: O = dt * sum_k rho_k, y = ln(I0/C) - O/Lambda and the Poisson term
+// C y - C expm1(y) (Eq. def_likelihood without the constant C ln C - C - ln C!,
+// which is summed once per data set).  Terms are reduced per CTA in a fixed
+// order (warp shuffles, then warps in order) into one partial per (chain, CTA).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace mt {
+
+// ---------------------------------------------------------------- types
+template <int MODE> struct Types;
+template <> struct Types<MODE_F64> { using S = double; using T = double; using H = double; };
+template <> struct Types<MODE_F32> { using S = float; using T = float; using H = float; };
+template <> struct Types<MODE_F32C> { using S = float; using T = float; using H = float; };
+template <> struct Types<MODE_BF16> { using S = __nv_bfloat16; using T = float; using H = float; };
+
+// Node-major shared-memory layout: the L heights of one node, padded to a
+// 4-, 8- or multiple-of-16-byte record so they load as vectors.
+template <typename S, int L> struct NodeLayout {
+    static constexpr int raw = L * (int)sizeof(S);
+    static constexpr int bytes = raw <= 4 ? 4 : raw <= 8 ? 8 : ((raw + 15) / 16) * 16;
+    static constexpr int LP = bytes / (int)sizeof(S);
+};
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_d(double v) { return v; }
+
+template <typename S> __device__ __forceinline__ S from_h(float v);
+template <> __device__ __forceinline__ float from_h<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_h<__nv_bfloat16>(float v)
+{
+    return __float2bfloat16_rn(v);
+}
+template <typename S> __device__ __forceinline__ S from_hd(double v) { return v; }
+
+template <typename H> __device__ __forceinline__ const H *chain_ptr(const HRef &h, int c)
+{
+    long long off = (long long)c * h.chain_stride;
+    if (h.sel) {
+        int s = h.sel[c];
+        if (h.sel_flip) s = 1 - s;
+        off += (long long)s * h.sel_stride;
+    }
+    return reinterpret_cast<const H *>(h.base) + off;
+}
+
+// Copy one chain [L][N] from HBM into node-major shared memory.
+// FP32 / BF16 storage keeps h - ref[l] (ref = nullptr: absolute heights).
+template <typename S, typename H, int L>
+__device__ __forceinline__ void stage_nodes(S *sh, const H *Hc, int N, const float *ref = nullptr)
+{
+    using NL = NodeLayout<S, L>;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        alignas(16) S tmp[NL::LP];
+#pragma unroll
+        for (int l = 0; l < NL::LP; ++l) tmp[l] = (S)0.0f;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            if constexpr (sizeof(S) == 8) tmp[l] = Hc[(size_t)l * N + i];
+            else tmp[l] = from_h<S>(ref ? (float)Hc[(size_t)l * N + i] - ref[l] : (float)Hc[(size_t)l * N + i]);
+        }
+        char *dst = reinterpret_cast<char *>(sh) + (size_t)i * NL::bytes;
+        if constexpr (NL::bytes == 4) {
+            *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(tmp);
+        } else if constexpr (NL::bytes == 8) {
+            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(tmp);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NL::bytes / 16; ++q)
+                reinterpret_cast<uint4 *>(dst)[q] = reinterpret_cast<const uint4 *>(tmp)[q];
+        }
+    }
+}
+
+template <typename S, typename T, int L>
+__device__ __forceinline__ void load_node(const S *sh, int node, T (&v)[L])
+{
+    using NL = NodeLayout<S, L>;
+    const char *src = reinterpret_cast<const char *>(sh) + (size_t)node * NL::bytes;
+    alignas(16) S tmp[NL::LP];
+    if constexpr (NL::bytes == 4) {
+        *reinterpret_cast<uint32_t *>(tmp) = *reinterpret_cast<const uint32_t *>(src);
+    } else if constexpr (NL::bytes == 8) {
+        *reinterpret_cast<uint2 *>(tmp) = *reinterpret_cast<const uint2 *>(src);
+    } else {
+#pragma unroll
+        for (int q = 0; q < NL::bytes / 16; ++q)
+            reinterpret_cast<uint4 *>(tmp)[q] = reinterpret_cast<const uint4 *>(src)[q];
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        if constexpr (sizeof(T) == 8) v[l] = tmp[l];
+        else v[l] = to_f(tmp[l]);
+    }
+}
+
+// ---------------------------------------------------------------- FP32 helpers
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Split a cell coordinate shifted by -1/2 (gm = g - 1/2, g in [0, n_nodes-1])
+// into the cell index n and the centred offset f = g - n - 1/2 in [-1/2, 1/2]:
+// rounding gm to the nearest integer by adding 1.5*2^23 picks a cell whose
+// closed interval holds g, with FP32-pipe operations only.  gm is clamped to
+// [-1/2, hi] where hi, a few ulps below n_nodes - 3/2, keeps n <= n_nodes - 2.
+__device__ __forceinline__ int cell_split(float gm, float hi, float &f)
+{
+    const float M = 12582912.0f;  // 1.5 * 2^23
+    gm = fminf(fmaxf(gm, -0.5f), hi);
+    const float t = gm + M;
+    const float n = t - M;
+    f = gm - n;
+    return __float_as_int(t) - 0x4B400000;
+}
+
+// e^y - 1 - y in FP32 without cancellation (Taylor series for |y| < 1/2).
+__device__ __forceinline__ float g_f32(float y)
+{
+    if (fabsf(y) < 0.5f) {
+        float p = 1.0f / 3628800.0f;
+        p = fmaf(p, y, 1.0f / 362880.0f);
+        p = fmaf(p, y, 1.0f / 40320.0f);
+        p = fmaf(p, y, 1.0f / 5040.0f);
+        p = fmaf(p, y, 1.0f / 720.0f);
+        p = fmaf(p, y, 1.0f / 120.0f);
+        p = fmaf(p, y, 1.0f / 24.0f);
+        p = fmaf(p, y, 1.0f / 6.0f);
+        p = fmaf(p, y, 0.5f);
+        return p * y * y;
+    }
+    return expm1f(y) - y;
+}
+
+// float-float (unevaluated sum hi + lo) arithmetic from error-free transforms.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b)
+{
+    float s = a + b;
+    float v = s - a;
+    float e = (a - (s - v)) + (b - v);
+    return {s, e};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    FF s = ff_two_sum(a.hi, b.hi);
+    float e = s.lo + a.lo + b.lo;
+    return ff_two_sum(s.hi, e);
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b)
+{
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return ff_two_sum(p, e);
+}
+
+// ---------------------------------------------------------------- FP32 march
+// Blackwell's paired FP32 instructions (FFMA2 / FADD2 / FMUL2) do two lanes'
+// worth of FP32 work per issue slot.  Surfaces are processed in pairs; the
+// cell coordinates are computed as duplicated pairs {g, g} so no broadcast
+// moves are needed.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// Per surface l the ray accumulates N_l = sum_k varsigma(s_l - z_k) exactly:
+// each sigma in [0, 1] is added as the integer round(sigma * 2^23), read off
+// the bits of the FP32 sum sigma + 1 (mantissa of a number in [1, 2]), into a
+// wrapping uint32 that is flushed to a uint64 every 256 samples.  Heights in
+// shared memory and the ray's z are both taken relative to a per-surface
+// reference height ref_l, and z is carried as float-float (start and step
+// each split hi + lo), so the sigmoid argument -kg (s_l - z) is formed from
+// numbers the size of the surface relief and rounded only at its own scale.
+// The ray table guarantees every sample's cell coordinate lies in
+// [-1/2, n - 3/2), so the cell split needs no clamp.  Returns
+// tot[l] = N_l * 2^23.
+template <int L, bool HARD, typename S>
+__device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int ray,
+                                              unsigned long long (&tot)[L])
+{
+    constexpr int NP = L / 2;
+    constexpr int NPP = NP > 0 ? NP : 1;
+    constexpr bool ODD = (L & 1) != 0;
+    const float4 o = pb.o4[ray], st = pb.s4[ray];
+    float z0h[L], z0l[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        z0h[l] = pb.kz0[(size_t)l * pb.n_rays + ray];
+        z0l[l] = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
+        tot[l] = 0ull;
+    }
+    float2 zh2[NPP], zl2[NPP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        zh2[q] = make_float2(z0h[2 * q], z0h[2 * q + 1]);
+        zl2[q] = make_float2(z0l[2 * q], z0l[2 * q + 1]);
+    }
+    const float M = 12582912.0f;  // 1.5 * 2^23: adding it rounds to an integer
+    const float2 one2 = f2(1.0f);
+    const float2 nkg2 = f2(-pb.kg);
+    const float2 szh2 = f2(st.z), szl2 = f2(st.w);
+    const int Q = pb.Q;
+    float2 h00[NPP], h01[NPP], h10[NPP], h11[NPP];
+    float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;  // last surface when L is odd
+#pragma unroll
+    for (int q = 0; q < NPP; ++q) h00[q] = h01[q] = h10[q] = h11[q] = f2(0.f);
+    int cur = -1;
+    float kf = 0.f;
+    for (int k0 = 0; k0 < pb.G; k0 += 256) {
+        const int kn = min(256, pb.G - k0);
+        uint32_t acc[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) acc[l] = 0u;
+        for (int k = 0; k < kn; ++k, kf += 1.0f) {
+            // cell split in scalar FP32 (the pairs below are broadcasts of it)
+            const float gxs = fmaf(kf, st.x, o.x), gys = fmaf(kf, st.y, o.y);
+            const float txs = gxs + M, tys = gys + M;
+            const float fxs = (gxs - (txs - M)) + 0.5f, fys = (gys - (tys - M)) + 0.5f;  // in [0, 1]
+            const int node = (__float_as_int(tys) - 0x4B400000) * Q + (__float_as_int(txs) - 0x4B400000);
+            const float2 kf2 = f2(kf), fx = f2(fxs), fy = f2(fys);
+            if (node != cur) {
+                cur = node;
+                float a00[L], a01[L], a10[L], a11[L];
+                load_node<S, float, L>(sh, node, a00);
+                load_node<S, float, L>(sh, node + 1, a01);
+                load_node<S, float, L>(sh, node + Q, a10);
+                load_node<S, float, L>(sh, node + Q + 1, a11);
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    h00[q] = make_float2(a00[2 * q], a00[2 * q + 1]);
+                    h01[q] = make_float2(a01[2 * q], a01[2 * q + 1]);
+                    h10[q] = make_float2(a10[2 * q], a10[2 * q + 1]);
+                    h11[q] = make_float2(a11[2 * q], a11[2 * q + 1]);
+                }
+                if constexpr (ODD) {
+                    s00 = a00[L - 1];
+                    s01 = a01[L - 1];
+                    s10 = a10[L - 1];
+                    s11 = a11[L - 1];
+                }
+            }
+            const float2 omfx = f2(1.0f - fxs), omfy = f2(1.0f - fys);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const float2 a = fma2(fx, h01[q], mul2(omfx, h00[q]));     // row r0
+                const float2 b = fma2(fx, h11[q], mul2(omfx, h10[q]));     // row r0 + 1
+                const float2 sl = fma2(fy, b, mul2(omfy, a));              // s_l - ref_l
+                const float2 zl = fma2(kf2, szl2, add2(fma2(kf2, szh2, zh2[q]), zl2[q]));
+                const float2 arg = fma2(nkg2, sl, zl);                     // -kg (s_l - z)
+                float2 sg;
+                if constexpr (HARD) {
+                    sg.x = arg.x < 0.f ? 1.f : (arg.x > 0.f ? 0.f : 0.5f);
+                    sg.y = arg.y < 0.f ? 1.f : (arg.y > 0.f ? 0.f : 0.5f);
+                } else {
+                    const float2 d = add2(make_float2(ex2_approx(arg.x), ex2_approx(arg.y)), one2);
+                    sg = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+                }
+                const float2 t = add2(sg, one2);
+                acc[2 * q] += __float_as_uint(t.x);
+                acc[2 * q + 1] += __float_as_uint(t.y);
+            }
+            if constexpr (ODD) {
+                const float a = fmaf(fx.x, s01, omfx.x * s00);
+                const float b = fmaf(fx.x, s11, omfx.x * s10);
+                const float sl = fmaf(fy.x, b, omfy.x * a);
+                const float zl = fmaf(kf, st.w, fmaf(kf, st.z, z0h[L - 1]) + z0l[L - 1]);
+                const float arg = fmaf(nkg2.x, sl, zl);
+                float sig;
+                if constexpr (HARD) sig = arg < 0.f ? 1.f : (arg > 0.f ? 0.f : 0.5f);
+                else sig = rcp_approx(1.0f + ex2_approx(arg));
+                acc[L - 1] += __float_as_uint(sig + 1.0f);
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < L; ++l) tot[l] += (unsigned long long)(acc[l] - (uint32_t)kn * 0x3F800000u);
+    }
+}
+
+// ---------------------------------------------------------------- FP64 march
+// Plain FP64 sum of rho(x) - rho_top along one ray (nodes: node-major, any
+// address space).
+template <int L, bool HARD>
+__device__ __forceinline__ double march_ray_f64(const Prob &pb, const double *nodes, int ray)
+{
+    const double gx0 = pb.o_d[3 * ray], gy0 = pb.o_d[3 * ray + 1], z0 = pb.o_d[3 * ray + 2];
+    const double sgx = pb.s_d[3 * ray], sgy = pb.s_d[3 * ray + 1], sz = pb.s_d[3 * ray + 2];
+    const double gxmax = (double)(pb.Q - 1), gymax = (double)(pb.R - 1);
+    const int Q = pb.Q;
+    const double inv_gamma = HARD ? 1.0 : 1.0 / pb.gamma;
+    double cA[L], cB[L], cC[L], cD[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) cA[l] = cB[l] = cC[l] = cD[l] = 0.0;
+    int cur = -1;
+    double sum = 0.0;
+    for (int k = 0; k < pb.G; ++k) {
+        const double kd = (double)k;
+        double gx = fmin(fmax(fma(kd, sgx, gx0), 0.0), gxmax);
+        double gy = fmin(fmax(fma(kd, sgy, gy0), 0.0), gymax);
+        const double z = fma(kd, sz, z0);
+        int c0 = min((int)gx, pb.Q - 2), r0 = min((int)gy, pb.R - 2);
+        const double fx = gx - (double)c0, fy = gy - (double)r0;
+        const int node = r0 * Q + c0;
+        if (node != cur) {
+            cur = node;
+            double h00[L], h01[L], h10[L], h11[L];
+            load_node<double, double, L>(nodes, node, h00);
+            load_node<double, double, L>(nodes, node + 1, h01);
+            load_node<double, double, L>(nodes, node + Q, h10);
+            load_node<double, double, L>(nodes, node + Q + 1, h11);
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                cA[l] = h00[l];
+                cB[l] = h01[l] - h00[l];
+                cC[l] = h10[l] - h00[l];
+                cD[l] = (h11[l] - h10[l]) - cB[l];
+            }
+        }
+        double rho = 0.0;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const double s = fma(fy, fma(fx, cD[l], cC[l]), fma(fx, cB[l], cA[l]));
+            const double u = s - z;
+            double sig;
+            if constexpr (HARD) sig = u > 0.0 ? 1.0 : (u < 0.0 ? 0.0 : 0.5);
+            else sig = 1.0 / (1.0 + exp(-u * inv_gamma));
+            rho = fma(pb.drho[l], sig, rho);
+        }
+        sum += rho;
+    }
+    return sum;
+}
+
+// Poisson constant of one pixel: C ln C - C - ln C! (0 for C = 0).
+__device__ __forceinline__ double poisson_K(int C)
+{
+    if (C <= 0) return 0.0;
+    const double c = (double)C;
+    return c * log(c) - c - lgamma(c + 1.0);
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ FF warp_sum(FF v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        FF w = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+        v = ff_add(v, w);
+    }
+    return v;
+}
+
+// Fixed-order block sums; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double red_d[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red_d[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? red_d[lane] : 0.0;
+        v = warp_sum(v);
+    }
+    return v;
+}
+__device__ __forceinline__ FF block_sum(FF v)
+{
+    __shared__ float2 red_f[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red_f[warp] = make_float2(v.hi, v.lo);
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        const float2 w = lane < nw ? red_f[lane] : make_float2(0.f, 0.f);
+        v = warp_sum(FF{w.x, w.y});
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- kernel
+template <int MODE, int L, bool HARD>
+__global__ void __launch_bounds__(256)
+k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, double *ray_term)
+{
+    using Ty = Types<MODE>;
+    using S = typename Ty::S;
+    using Hh = typename Ty::H;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S *sh = reinterpret_cast<S *>(smem_raw);
+    const int c = blockIdx.y;
+    stage_nodes<S, Hh, L>(sh, chain_ptr<Hh>(h, c), pb.N, pb.ref);
+    __syncthreads();
+
+    const int r_begin = blockIdx.x * rays_per_block;
+    const int r_end = min(r_begin + rays_per_block, pb.n_rays);
+    double acc = 0.0;
+    FF accf = {0.f, 0.f};
+    for (int ray = r_begin + threadIdx.x; ray < r_end; ray += blockDim.x) {
+        const int Cp = pb.cnt[ray];
+        double O, term;
+        if constexpr (MODE == MODE_F64) {
+            const double S_ = march_ray_f64<L, HARD>(pb, sh, ray);
+            O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
+            if (Cp > 0) {
+                const double y = pb.a[ray] - O * pb.inv_Lambda;
+                term = (double)Cp * y - (double)Cp * expm1(y);
+            } else {
+                term = -pb.I0 * exp(-O * pb.inv_Lambda);
+            }
+            acc += term;
+        } else {
+            unsigned long long tot[L];
+            march_ray_f32<L, HARD, S>(pb, sh, ray, tot);
+            if constexpr (MODE == MODE_F32C) {
+                // O = dt (G rho_top + sum_l drho_l N_l), y = a - O / Lambda, in float-float
+                FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    const FF n = ff_two_sum((float)(uint32_t)(tot[l] >> 20) * 1048576.0f * 0x1p-23f,
+                                            (float)(uint32_t)(tot[l] & 0xFFFFFu) * 0x1p-23f);
+                    Sff = ff_add(Sff, ff_mul(FF{pb.drho_ff[l].x, pb.drho_ff[l].y}, n));
+                }
+                const FF Off = ff_mul(FF{pb.dt_ff[ray].x, pb.dt_ff[ray].y}, Sff);
+                const FF OL = ff_mul(Off, FF{pb.invL_ff.x, pb.invL_ff.y});
+                float t32;
+                if (Cp > 0) {
+                    const FF yff = ff_add(FF{pb.a_ff[ray].x, pb.a_ff[ray].y}, FF{-OL.hi, -OL.lo});
+                    t32 = -(float)Cp * g_f32(yff.hi + yff.lo);
+                } else {
+                    t32 = -(float)pb.I0 * expf(-(OL.hi + OL.lo));
+                }
+                accf = ff_add(accf, FF{t32, 0.f});
+                O = (double)Off.hi + (double)Off.lo;
+                term = (double)t32;
+            } else {
+                double S_ = 0.0;
+#pragma unroll
+                for (int l = 0; l < L; ++l) S_ = fma(pb.drho[l], (double)tot[l] * 0x1p-23, S_);
+                O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
+                if (Cp > 0) {
+                    const double y = pb.a[ray] - O * pb.inv_Lambda;
+                    term = -(double)Cp * (double)g_f32((float)y);
+                } else {
+                    term = -pb.I0 * exp(-O * pb.inv_Lambda);
+                }
+                acc += term;
+            }
+        }
+        if (ray_O) ray_O[(size_t)c * pb.n_rays + ray] = O;
+        if (ray_term) ray_term[(size_t)c * pb.n_rays + ray] = term + poisson_K(Cp);
+    }
+    if constexpr (MODE == MODE_F32C) {
+        accf = block_sum(accf);
+        if (threadIdx.x == 0)
+            reinterpret_cast<float2 *>(partial)[(size_t)c * gridDim.x + blockIdx.x] =
+                make_float2(accf.hi, accf.lo);
+    } else {
+        acc = block_sum(acc);
+        if (threadIdx.x == 0) reinterpret_cast<double *>(partial)[(size_t)c * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
+}  // namespace mt

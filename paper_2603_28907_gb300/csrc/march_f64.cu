@@ -1,0 +1,8 @@
+// march_f64.cu -- k_march instantiations for MODE_F64 (one translation unit
+// per precision so they compile in parallel).
+#include "march_launch.cuh"
+
+namespace mt {
+template cudaError_t launch_march_mode<MODE_F64>(const Prob &, HRef, int, int, size_t, void *,
+                                                 double *, double *, cudaStream_t);
+}  // namespace mt

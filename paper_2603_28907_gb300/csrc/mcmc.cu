@@ -1,0 +1,218 @@
+// mcmc.cu -- per-chain kernels around the ray march: random-walk proposal,
+// log-prior, fixed-order reduction + Metropolis accept, state gather.
+//
+// The Metropolis step needs only the ratio of posterior densities (Sec. 2.2):
+// accept iff the proposal's prior is finite and ln u < (ll' + lp') - (ll + lp).
+// Chain state is double-buffered: cur[c] says which of the two height buffers
+// holds chain c; a proposal is written to the other one and an accept just
+// flips cur[c], so no heights are copied.
+#include <math.h>
+
+#include "march.cuh"
+#include "philox.cuh"
+
+namespace mt {
+
+// ---------------------------------------------------------------- prior
+// lp = -tau/2 sum_l (h_l - mu_l)^T Q (h_l - mu_l), Q = diag(A 1) - r A on the
+// periodic 4-neighbour grid (Eq. def_CAR_precision, Fig. neighbors), and -inf
+// unless every height is in [0, Lz] and every thickness is >= delta (Sec.
+// 2.1.3, strictly positive thicknesses).  FP64, one block per chain.
+template <typename H>
+__global__ void __launch_bounds__(256) k_prior(Prob pb, HRef h, const double *mu, double *lp_out)
+{
+    const int c = blockIdx.x;
+    const H *Hc = chain_ptr<H>(h, c);
+    const int N = pb.N, Q = pb.Q, R = pb.R;
+    const int n = pb.L * N;
+    double quad = 0.0;
+    int bad = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int l = i / N, rc = i - l * N, r = rc / Q, cc = rc - r * Q;
+        const double hv = (double)Hc[i];
+        if (!(hv >= 0.0 && hv <= pb.box[2])) bad = 1;
+        if (l > 0 && !(hv - (double)Hc[i - N] >= pb.delta)) bad = 1;
+        const int up = r + 1 == R ? 0 : r + 1, dn = r == 0 ? R - 1 : r - 1;
+        const int rt = cc + 1 == Q ? 0 : cc + 1, lf = cc == 0 ? Q - 1 : cc - 1;
+        const H *hl = Hc + (size_t)l * N;
+        const double *ml = mu + (size_t)l * N;
+        const double e = hv - ml[rc];
+        const double nb = ((double)hl[up * Q + cc] - ml[up * Q + cc]) +
+                          ((double)hl[dn * Q + cc] - ml[dn * Q + cc]) +
+                          ((double)hl[r * Q + rt] - ml[r * Q + rt]) +
+                          ((double)hl[r * Q + lf] - ml[r * Q + lf]);
+        quad += e * (4.0 * e - pb.car_r * nb);
+    }
+    quad = block_sum(quad);
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) lp_out[c] = bad ? -INFINITY : -0.5 * pb.tau * quad;
+}
+
+cudaError_t launch_prior(const Prob &pb, int mode, HRef h, const double *mu, int n_chains,
+                         double *lp_out, cudaStream_t st)
+{
+    if (mode == MODE_F64) k_prior<double><<<n_chains, 256, 0, st>>>(pb, h, mu, lp_out);
+    else k_prior<float><<<n_chains, 256, 0, st>>>(pb, h, mu, lp_out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- proposal
+// Random walk H' = H + sigma xi; the normal pair (xi_2j, xi_2j+1) comes from
+// Philox stream PROP, counter {j, step, chain} by Box-Muller.
+template <typename H>
+__global__ void __launch_bounds__(256)
+k_propose_rw(int n, H *hbuf, long long buf_stride, const uint8_t *cur, double sigma, uint64_t seed,
+             const int64_t *step_base, int step_off)
+{
+    const int c = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * j >= n) return;
+    const uint32_t step = (uint32_t)(*step_base + step_off);
+    const uint4 w = draw4(seed, STREAM_PROP, (uint32_t)c, step, (uint32_t)j);
+    const int cs = cur[c];
+    const H *src = hbuf + (long long)cs * buf_stride + (long long)c * n;
+    H *dst = hbuf + (long long)(1 - cs) * buf_stride + (long long)c * n;
+    if constexpr (sizeof(H) == 8) {
+        const double u1 = u01_f64(w.x, w.y), u2 = u01_f64(w.z, w.w);
+        const double rad = sqrt(-2.0 * log(u1));
+        double sn, cn;
+        sincospi(2.0 * u2, &sn, &cn);
+        dst[2 * j] = src[2 * j] + sigma * (rad * cn);
+        if (2 * j + 1 < n) dst[2 * j + 1] = src[2 * j + 1] + sigma * (rad * sn);
+    } else {
+        const float u1 = u01_to_f32(w.x, w.y), u2 = u01_to_f32(w.z, w.w);
+        const float rad = sqrtf(-2.0f * logf(u1));
+        float sn, cn;
+        sincospif(2.0f * u2, &sn, &cn);
+        const float sg = (float)sigma;
+        dst[2 * j] = fmaf(sg, rad * cn, src[2 * j]);
+        if (2 * j + 1 < n) dst[2 * j + 1] = fmaf(sg, rad * sn, src[2 * j + 1]);
+    }
+}
+
+cudaError_t launch_propose_rw(const Prob &pb, int mode, void *hbuf, long long buf_stride,
+                              const uint8_t *cur, int n_chains, double sigma, uint64_t seed,
+                              const int64_t *step_base, int step_off, cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    dim3 grid((n / 2 + 1 + 255) / 256, n_chains);
+    if (mode == MODE_F64)
+        k_propose_rw<double><<<grid, 256, 0, st>>>(n, (double *)hbuf, buf_stride, cur, sigma, seed,
+                                                   step_base, step_off);
+    else
+        k_propose_rw<float><<<grid, 256, 0, st>>>(n, (float *)hbuf, buf_stride, cur, sigma, seed,
+                                                  step_base, step_off);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- reduce
+// ll[c] = sum over data of the Poisson constants + the CTA partials of chain c
+// added in CTA order (deterministic).
+__device__ __forceinline__ double chain_loglik(int mode, const void *partial, int n_blk, int c,
+                                               double sumK)
+{
+    if (mode == MODE_F32C) {
+        const float2 *p = reinterpret_cast<const float2 *>(partial) + (size_t)c * n_blk;
+        FF s = {0.f, 0.f};
+        for (int b = 0; b < n_blk; ++b) s = ff_add(s, FF{p[b].x, p[b].y});
+        return sumK + ((double)s.hi + (double)s.lo);
+    }
+    const double *p = reinterpret_cast<const double *>(partial) + (size_t)c * n_blk;
+    double s = 0.0;
+    for (int b = 0; b < n_blk; ++b) s += p[b];
+    return sumK + s;
+}
+
+__global__ void k_reduce_ll(int mode, int n_chains, int n_blk, const void *partial, double sumK,
+                            double *ll_out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n_chains) ll_out[c] = chain_loglik(mode, partial, n_blk, c, sumK);
+}
+
+cudaError_t launch_reduce_ll(const Prob &pb, int mode, int n_chains, const void *partial,
+                             double *ll_out, cudaStream_t st)
+{
+    const int n_blk = (pb.n_rays + march_rays_per_block(pb) - 1) / march_rays_per_block(pb);
+    k_reduce_ll<<<(n_chains + 127) / 128, 128, 0, st>>>(mode, n_chains, n_blk, partial, pb.sumK,
+                                                        ll_out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- accept
+__global__ void k_accept(int n_chains, int mode, const void *partial, int n_blk, double sumK,
+                         const double *lp_prop, const double *extra, double *ll, double *lp,
+                         double *ll_prop_out, uint8_t *cur, uint8_t *prop_sel, int64_t *accepts,
+                         int32_t *acc_last, double *logu_out, uint64_t seed,
+                         const int64_t *step_base, int step_off)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chains) return;
+    const double lln = chain_loglik(mode, partial, n_blk, c, sumK);
+    const double lpn = lp_prop[c];
+    const uint32_t step = (uint32_t)(*step_base + step_off);
+    const uint4 w = draw4(seed, STREAM_ACC, (uint32_t)c, step, 0u);
+    const double logu = log(u01_f64(w.x, w.y));
+    double delta = (lln + lpn) - (ll[c] + lp[c]);
+    if (extra) delta += extra[c];
+    const int acc = (lpn > -INFINITY) && (logu < delta);
+    const uint8_t cs = cur[c];
+    prop_sel[c] = (uint8_t)(1 - cs);
+    if (acc) {
+        cur[c] = (uint8_t)(1 - cs);
+        ll[c] = lln;
+        lp[c] = lpn;
+        accepts[c] += 1;
+    }
+    acc_last[c] = acc;
+    ll_prop_out[c] = lln;
+    logu_out[c] = logu;
+}
+
+cudaError_t launch_accept_fused(const Prob &pb, int mode, int n_chains, const void *partial,
+                                const double *lp_prop, const double *extra, double *ll,
+                                double *lp, double *ll_prop_out, uint8_t *cur, uint8_t *prop_sel,
+                                int64_t *accepts, int32_t *acc_last, double *logu_out,
+                                uint64_t seed, const int64_t *step_base, int step_off,
+                                cudaStream_t st)
+{
+    const int n_blk = (pb.n_rays + march_rays_per_block(pb) - 1) / march_rays_per_block(pb);
+    k_accept<<<(n_chains + 127) / 128, 128, 0, st>>>(n_chains, mode, partial, n_blk, pb.sumK,
+                                                     lp_prop, extra, ll, lp, ll_prop_out, cur,
+                                                     prop_sel, accepts, acc_last, logu_out, seed,
+                                                     step_base, step_off);
+    return cudaGetLastError();
+}
+
+__global__ void k_advance(int64_t *step, int n)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *step += n;
+}
+
+cudaError_t launch_advance(int64_t *step, int n, cudaStream_t st)
+{
+    k_advance<<<1, 32, 0, st>>>(step, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- gather
+template <typename H>
+__global__ void k_gather(HRef h, long long n_per_chain, H *out)
+{
+    const int c = blockIdx.y;
+    const H *src = chain_ptr<H>(h, c);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_per_chain;
+         i += (long long)gridDim.x * blockDim.x)
+        out[(long long)c * n_per_chain + i] = src[i];
+}
+
+cudaError_t launch_gather(int mode, HRef h, int n_chains, long long n_per_chain, void *out,
+                          cudaStream_t st)
+{
+    dim3 grid((unsigned)((n_per_chain + 255) / 256 < 64 ? (n_per_chain + 255) / 256 : 64), n_chains);
+    if (mode == MODE_F64) k_gather<double><<<grid, 256, 0, st>>>(h, n_per_chain, (double *)out);
+    else k_gather<float><<<grid, 256, 0, st>>>(h, n_per_chain, (float *)out);
+    return cudaGetLastError();
+}
+
+}  // namespace mt

@@ -1,0 +1,230 @@
+"""ctypes binding of libmt.so (include/mt.h): argument marshalling only.
+
+Every function here forwards to the C ABI of the same name; all arithmetic of
+the path runs in the library's CUDA kernels.  Arrays may be torch tensors
+(device or host) or numpy arrays (host).  There is no fallback: if the
+library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmt.so")
+
+PREC_F64, PREC_F32, PREC_F32C, PREC_BF16 = 0, 1, 2, 3
+KERNEL_RW, KERNEL_MALA = 0, 1
+COUNTS_POISSON, COUNTS_ROUND = 0, 1
+
+STATUS = {0: "MT_OK", -1: "MT_EINVAL", -2: "MT_ENOMEM", -3: "MT_ESTATE", -4: "MT_ECUDA",
+          -5: "MT_ETIMEDOUT", -6: "MT_EDEVFLAG"}
+
+
+class MtError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__(f"{fn}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("n_grid", C.c_int), ("gamma", C.c_double),
+                ("I0", C.c_double), ("atten", C.c_double), ("tau", C.c_double),
+                ("car_r", C.c_double), ("min_thick", C.c_double)]
+
+
+_lib = None
+_vp, _dp, _ip, _lp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int64)
+
+SIGNATURES = {
+    "mt_create": [C.POINTER(C.c_void_p), C.c_int, C.POINTER(Config), _vp],
+    "mt_destroy": [_vp],
+    "mt_set_grid": [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp],
+    "mt_set_sensors": [_vp, C.c_int, _vp],
+    "mt_set_pixels": [_vp, C.c_int, _vp],
+    "mt_set_counts": [_vp, _vp],
+    "mt_generate_data": [_vp, _vp, C.c_uint64, C.c_int, _vp, _vp],
+    "mt_logpost": [_vp, C.c_int, _vp, _vp, _vp],
+    "mt_ray_terms": [_vp, C.c_int, _vp, _vp, _vp],
+    "mt_grad": [_vp, C.c_int, _vp, _vp, _vp],
+    "mt_init_chains": [_vp, C.c_int, _vp, C.c_uint64],
+    "mt_run": [_vp, C.c_int, C.c_double, C.c_int, C.c_int],
+    "mt_get_state": [_vp, _vp, _vp, _vp, _vp, _lp],
+    "mt_get_last_step": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "mt_set_state": [_vp, _vp, C.c_int64],
+    "mt_sync": [_vp, C.c_double],
+    "mt_set_timing": [_vp, C.c_int],
+    "mt_get_timing": [_vp, C.c_int, _dp, _lp, C.c_int],
+    "mt_get_sizes": [_vp, _ip, _ip, _ip, _ip, _ip, _ip],
+}
+
+
+def load():
+    """Load libmt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2603_28907_gb300.build` (needs nvcc)")
+        lib = C.CDLL(LIB_PATH)
+        for name, args in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        lib.mt_last_error.argtypes = [_vp]
+        lib.mt_last_error.restype = C.c_char_p
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Context:
+    """One mt_ctx: a problem (grid, sensors, pixels, counts) and its chains."""
+
+    def __init__(self, device: int = 0, precision: int = PREC_F32, n_grid: int = 64,
+                 gamma: float = 1.0, I0: float = 1e4, atten: float = 150.0, tau: float = 0.01,
+                 car_r: float = 0.99, min_thick: float = 0.1, stream=None):
+        self.lib = load()
+        self.cfg = Config(precision, n_grid, gamma, I0, atten, tau, car_r, min_thick)
+        h = C.c_void_p()
+        st = self.lib.mt_create(C.byref(h), device, C.byref(self.cfg),
+                                None if stream is None else C.c_void_p(int(stream)))
+        if st != 0:
+            raise MtError("mt_create", st, self.lib.mt_last_error(None).decode())
+        self.h = h
+        self.precision = precision
+        self._keep = []
+
+    # -- plumbing
+    def _ck(self, name, st):
+        if st != 0:
+            raise MtError(name, st, self.lib.mt_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def height_dtype(self):
+        return np.float64 if self.precision == PREC_F64 else np.float32
+
+    # -- problem set-up
+    def set_grid(self, n_layers, n_rows, n_cols, box, unit_density, prior_mean=None):
+        box = np.ascontiguousarray(box, np.float64)
+        rho = np.ascontiguousarray(unit_density, np.float64)
+        mu = None if prior_mean is None else np.ascontiguousarray(prior_mean, np.float64)
+        self._ck("mt_set_grid", self.lib.mt_set_grid(self.h, n_layers, n_rows, n_cols, _ptr(box),
+                                                     _ptr(rho), _ptr(mu)))
+
+    def set_sensors(self, pos):
+        pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
+        self._ck("mt_set_sensors", self.lib.mt_set_sensors(self.h, pos.shape[0], _ptr(pos)))
+
+    def set_pixels(self, dirs):
+        dirs = np.ascontiguousarray(dirs, np.float64).reshape(-1, 3)
+        self._ck("mt_set_pixels", self.lib.mt_set_pixels(self.h, dirs.shape[0], _ptr(dirs)))
+
+    def set_counts(self, counts):
+        if not hasattr(counts, "data_ptr"):
+            counts = np.ascontiguousarray(counts, np.int32)
+        self._ck("mt_set_counts", self.lib.mt_set_counts(self.h, _ptr(counts)))
+
+    def generate_data(self, h_true, seed, count_mode=COUNTS_POISSON, counts_out=None,
+                      lambda_out=None):
+        h = np.ascontiguousarray(h_true, np.float64)
+        self._ck("mt_generate_data", self.lib.mt_generate_data(
+            self.h, _ptr(h), seed, count_mode, _ptr(counts_out), _ptr(lambda_out)))
+
+    def sizes(self):
+        v = [C.c_int() for _ in range(6)]
+        self._ck("mt_get_sizes", self.lib.mt_get_sizes(self.h, *[C.byref(x) for x in v]))
+        return dict(zip(["L", "R", "Q", "S", "P", "C"], [x.value for x in v]))
+
+    # -- evaluation
+    def logpost(self, heights, loglik_out=None, logprior_out=None):
+        n = heights.shape[0]
+        self._ck("mt_logpost", self.lib.mt_logpost(self.h, n, _ptr(heights), _ptr(loglik_out),
+                                                   _ptr(logprior_out)))
+
+    def ray_terms(self, heights, opacity_out=None, term_out=None):
+        n = heights.shape[0]
+        self._ck("mt_ray_terms", self.lib.mt_ray_terms(self.h, n, _ptr(heights),
+                                                       _ptr(opacity_out), _ptr(term_out)))
+
+    def grad(self, heights, grad_out, logpost_out=None):
+        n = heights.shape[0]
+        self._ck("mt_grad", self.lib.mt_grad(self.h, n, _ptr(heights), _ptr(grad_out),
+                                             _ptr(logpost_out)))
+
+    # -- chains
+    def init_chains(self, heights0, seed):
+        self._ck("mt_init_chains", self.lib.mt_init_chains(self.h, heights0.shape[0],
+                                                           _ptr(heights0), seed))
+
+    def run(self, kernel, step, n_super, n_within):
+        self._ck("mt_run", self.lib.mt_run(self.h, kernel, float(step), n_super, n_within))
+
+    def get_state(self, heights_out=None, loglik_out=None, logprior_out=None, accepts_out=None):
+        stp = C.c_int64()
+        self._ck("mt_get_state", self.lib.mt_get_state(self.h, _ptr(heights_out), _ptr(loglik_out),
+                                                       _ptr(logprior_out), _ptr(accepts_out),
+                                                       C.byref(stp)))
+        return stp.value
+
+    def get_last_step(self, proposal_out=None, loglik_out=None, logprior_out=None,
+                      accepted_out=None, logu_out=None):
+        self._ck("mt_get_last_step", self.lib.mt_get_last_step(
+            self.h, _ptr(proposal_out), _ptr(loglik_out), _ptr(logprior_out), _ptr(accepted_out),
+            _ptr(logu_out)))
+
+    def set_state(self, heights, step):
+        self._ck("mt_set_state", self.lib.mt_set_state(self.h, _ptr(heights), step))
+
+    def sync(self, timeout_s=0.0):
+        self._ck("mt_sync", self.lib.mt_sync(self.h, float(timeout_s)))
+
+    def set_timing(self, on):
+        self._ck("mt_set_timing", self.lib.mt_set_timing(self.h, int(on)))
+
+    def get_timing(self, kernel_id, reset=False):
+        ms, n = C.c_double(), C.c_int64()
+        self._ck("mt_get_timing", self.lib.mt_get_timing(self.h, kernel_id, C.byref(ms),
+                                                         C.byref(n), int(reset)))
+        return ms.value, n.value
+
+
+def from_workload(prob: dict, precision=PREC_F32, device=0, stream=None, **over) -> Context:
+    """Context for a problem dict from workloads.problem() (grid, sensors, pixels; no counts)."""
+    kw = dict(n_grid=int(prob["G"]), gamma=float(prob["gamma"]), I0=float(prob["I0"]),
+              atten=float(prob["Lambda"]), tau=float(prob["tau"]), car_r=float(prob["car_r"]),
+              min_thick=float(prob["delta"]))
+    kw.update(over)
+    ctx = Context(device=device, precision=precision, stream=stream, **kw)
+    ctx.set_grid(int(prob["L"]), int(prob["R"]), int(prob["Q"]), prob["box"], prob["rho"],
+                 prob["mu"])
+    ctx.set_sensors(prob["sensors"])
+    ctx.set_pixels(prob["dirs"])
+    return ctx

@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads without a GPU, and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2603_28907_gb300 import build as B
+from paper_2603_28907_gb300 import mt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "mt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mt_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return ctypes.CDLL(B.OUT)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    names = set(declared_symbols())
+    bound = set(mt.SIGNATURES) | {"mt_last_error"}
+    assert names == bound, names ^ bound
+
+
+def test_build_targets_sm103a_only():
+    flags = B._flags(False)
+    assert flags[:2] == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert sum(1 for f in flags if f == "-gencode") == 1
+
+
+def test_create_fails_cleanly_without_gpu(lib):
+    """With no usable device mt_create returns an error code and a message (no abort)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cfg = mt.Config(1, 64, 1.0, 1e4, 150.0, 0.01, 0.99, 0.1)
+    lib.mt_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(mt.Config),
+                              ctypes.c_void_p]
+    lib.mt_last_error.restype = ctypes.c_char_p
+    lib.mt_last_error.argtypes = [ctypes.c_void_p]
+    h = ctypes.c_void_p()
+    st = lib.mt_create(ctypes.byref(h), 0, ctypes.byref(cfg), None)
+    assert st == -4  # MT_ECUDA
+    assert h.value is None
+    assert b"device" in lib.mt_last_error(None)
+
+
+def test_create_rejects_bad_config(lib):
+    lib.mt_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(mt.Config),
+                              ctypes.c_void_p]
+    h = ctypes.c_void_p()
+    for bad in (mt.Config(7, 64, 1.0, 1e4, 150.0, 0.01, 0.99, 0.1),
+                mt.Config(1, 0, 1.0, 1e4, 150.0, 0.01, 0.99, 0.1),
+                mt.Config(1, 64, -1.0, 1e4, 150.0, 0.01, 0.99, 0.1),
+                mt.Config(1, 64, 1.0, 1e4, 150.0, 0.01, 1.0, 0.1)):
+        assert lib.mt_create(ctypes.byref(h), 0, ctypes.byref(bad), None) == -1  # MT_EINVAL
+
+
+def test_null_context_calls_return_einval(lib):
+    lib.mt_logpost.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p]
+    assert lib.mt_logpost(None, 1, None, None, None) == -1
+    assert lib.mt_destroy(None) == 0
