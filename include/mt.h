@@ -142,6 +142,27 @@ MT_API mt_status mt_generate_data(mt_ctx *ctx, const double *h_true, uint64_t se
 MT_API mt_status mt_logpost(mt_ctx *ctx, int n_chains, const void *heights, double *loglik_out,
                      double *logprior_out);
 
+/* mt_logpost without any device allocation, for callers that cannot
+ * allocate: a host that hands out all device memory through its own
+ * fixed-budget allocator, or a latency-critical serving loop in which a
+ * cudaMalloc / cudaFree (cudaFree synchronises the whole device) must never
+ * happen after start-up.  The paper has no counterpart of this call.
+ *  - heights, loglik_out and logprior_out (nullable) must be device memory on
+ *    the context's device; host pointers are rejected with MT_EINVAL because
+ *    staging them would need an allocation.
+ *  - The per-(chain, CTA) partial sums live in one 1 MiB array inside the
+ *    library (held by every GPU that loads it until the process exits), so
+ *    n_chains * ceil(S*P / 4096) * 8 bytes must fit in 1 MiB (8192 chains of
+ *    a 16 x 4096-ray problem); larger calls fail with MT_EINVAL.
+ *  - The first call on each device looks up the array's device address;
+ *    make that first call before any stream capture.
+ *  - All calls share the array: two calls whose kernels overlap on the GPU
+ *    (on different streams or contexts) race and both may return garbage.
+ *    Calls on one stream are ordered and safe.
+ * Results equal mt_logpost's.  Asynchronous on the context's stream. */
+MT_API mt_status mt_logpost_noalloc(mt_ctx *ctx, int n_chains, const void *heights,
+                                    double *loglik_out, double *logprior_out);
+
 /* Per-ray opacity O (mwe) and Poisson log-pmf term of n_chains geometries,
  * host or device double [n_chains][S][P] each (nullable): the per-ray values
  * that mt_logpost sums, for element-wise checks. */

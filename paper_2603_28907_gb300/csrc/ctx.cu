@@ -437,6 +437,21 @@ static mt_status eval_logpost(mt_ctx *ctx, HRef h, int n, double *d_ll, double *
     return MT_OK;
 }
 
+namespace mt {
+mt_status ctx_view(mt_ctx *ctx, CtxView *v)
+{
+    TRY(need(ctx, true));
+    v->pb = ctx->pb;
+    v->mode = ctx->mode;
+    v->device = ctx->device;
+    v->mu = ctx->d_mu;
+    v->stream = ctx->stream;
+    return MT_OK;
+}
+
+mt_status ctx_fail(mt_ctx *ctx, mt_status st, const char *msg) { return fail(ctx, st, "%s", msg); }
+}  // namespace mt
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 

@@ -60,6 +60,18 @@ struct HRef {
     int sel_flip;
 };
 
+// What a context holds for a call that must not allocate (filled by ctx_view,
+// which also checks that grid, sensors, pixels and counts are set).
+struct CtxView {
+    Prob pb;
+    int mode;
+    int device;
+    const double *mu;
+    cudaStream_t stream;
+};
+mt_status ctx_view(mt_ctx *ctx, CtxView *v);
+mt_status ctx_fail(mt_ctx *ctx, mt_status st, const char *msg);
+
 // Launchers (stream-ordered, return cudaGetLastError()).
 cudaError_t launch_raytab(const Prob &pb, const double *d_sensors, const double *d_dirs,
                           float4 *o4, float4 *s4, float *kz0, double *o_d, double *s_d, double *dt,

@@ -48,6 +48,7 @@ SIGNATURES = {
     "mt_generate_data": [_vp, _vp, C.c_uint64, C.c_int, _vp, _vp],
     "mt_logpost": [_vp, C.c_int, _vp, _vp, _vp],
     "mt_ray_terms": [_vp, C.c_int, _vp, _vp, _vp],
+    "mt_logpost_noalloc": [_vp, C.c_int, _vp, _vp, _vp],
     "mt_grad": [_vp, C.c_int, _vp, _vp, _vp],
     "mt_init_chains": [_vp, C.c_int, _vp, C.c_uint64],
     "mt_run": [_vp, C.c_int, C.c_double, C.c_int, C.c_int],
@@ -168,6 +169,12 @@ class Context:
         n = heights.shape[0]
         self._ck("mt_logpost", self.lib.mt_logpost(self.h, n, _ptr(heights), _ptr(loglik_out),
                                                    _ptr(logprior_out)))
+
+    def logpost_noalloc(self, heights, loglik_out, logprior_out=None):
+        """mt_logpost_noalloc: device arrays only; allocates nothing."""
+        n = heights.shape[0]
+        self._ck("mt_logpost_noalloc", self.lib.mt_logpost_noalloc(
+            self.h, n, _ptr(heights), _ptr(loglik_out), _ptr(logprior_out)))
 
     def ray_terms(self, heights, opacity_out=None, term_out=None):
         n = heights.shape[0]
