@@ -35,8 +35,31 @@ from paper_2603_28907_gb300 import workloads as W  # noqa: E402
 
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-MUFU_PER_CLK_SM = 16     # SFU results per clock per SM (ex2, rcp)
-FP32_PER_CLK_SM = 128    # FP32 lanes per SM
+EX2_PER_CLK_SM = 32      # SFU ex2.approx results per clock per SM (GB300; probe: 30.2)
+RCP_PER_CLK_SM = 16      # SFU rcp.approx results per clock per SM (probe: 15.1)
+FP32_PER_CLK_SM = 128    # FP32 lanes per SM (probe: 114.6 FMA/clk at the nominal clock)
+
+
+# DRAM traffic of one k_march launch (read + write bytes) from the ncu capture
+# summarised in profiles/k_march_scenario_c128_ncu.md, scaled from 128 to 1024
+# chains; valid only for the kernel source it was measured on.
+MARCH_TRAFFIC = {"source_sha1": "215987152a0e", "bytes": 72.0e6}
+
+
+def march_traffic():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2603_28907_gb300", "csrc", "march.cuh")
+    h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    return MARCH_TRAFFIC["bytes"] if h == MARCH_TRAFFIC["source_sha1"] else None
+
+
+def march_peak(L):
+    """Surface-samples per second the ray kernel's pipes allow (one logistic =
+    ex2 + rcp per surface-sample; 12 + 9L FP32 ops per sample)."""
+    clk = SM_COUNT * SM_MAX_MHZ * 1e6
+    sfu = clk / (1.0 / EX2_PER_CLK_SM + 1.0 / RCP_PER_CLK_SM)
+    fp32 = clk * FP32_PER_CLK_SM / ((12.0 + 9.0 * L) / L)
+    return min(sfu, fp32), sfu, fp32
 
 
 def parse():
@@ -250,13 +273,11 @@ def main():
     acc = torch.zeros(C, dtype=torch.int64, device=dev)
     ctx.get_state(accepts_out=acc)
 
-    # roofline of the ray kernel: one logistic (ex2 + rcp on the SFU) per surface per sample
+    # roofline of the ray kernel in surface-samples (logistic evaluations) per second
     avg_launch_s = (march_ms / max(march_n, 1)) / 1e3
-    sig_per_launch = float(C) * rays * w.G * w.L
-    achieved = sig_per_launch / avg_launch_s / 1e12            # T sigmoid / s
-    peak = SM_COUNT * SM_MAX_MHZ * 1e6 * MUFU_PER_CLK_SM / 2 / 1e12
-    fp32_ops = float(C) * rays * w.G * (12 + 9 * w.L)
-    fp32_frac = fp32_ops / avg_launch_s / (SM_COUNT * SM_MAX_MHZ * 1e6 * FP32_PER_CLK_SM)
+    units_per_launch = float(C) * rays * w.G * w.L
+    achieved = units_per_launch / avg_launch_s / 1e12
+    peak, sfu_peak, fp32_peak = (x / 1e12 for x in march_peak(w.L))
 
     out = None
     if rank == 0:
@@ -280,10 +301,13 @@ def main():
             "acceptance": float(acc.double().mean().item()) / (args.warmup + args.steps),
             "gpu_launches": 5 * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "Tsigmoid/s", "frac": achieved / peak, "traffic": None,
-                         "pipe": "SFU (ex2 + rcp per surface-sample)",
-                         "fp32_frac_of_peak": fp32_frac,
-                         "kernel_ms_avg": avg_launch_s * 1e3, "launches": march_n},
+                         "unit": "T surface-samples/s", "frac": achieved / peak,
+                         "traffic": march_traffic() if C == 1024 else None,
+                         "peak_sfu": sfu_peak, "peak_fp32": fp32_peak,
+                         "peak_basis": "152 SM x 2070 MHz; ex2 32/clk, rcp 16/clk per SM; "
+                                       "128 FP32 lanes with 12+9L ops per sample",
+                         "kernel": "k_march", "kernel_ms_avg": avg_launch_s * 1e3,
+                         "launches": march_n},
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -36,8 +36,10 @@ int march_rays_per_block(const Prob &pb)
 
 size_t march_smem_bytes(const Prob &pb, int mode)
 {
+    // FP32 modes store (h, dx) per surface and node; see NodeLayoutDX
+    const bool dx = mode == MODE_F32 || mode == MODE_F32C;
     const int es = mode == MODE_F64 ? 8 : mode == MODE_BF16 ? 2 : 4;
-    const int raw = pb.L * es;
+    const int raw = pb.L * es * (dx ? 2 : 1);
     const int bytes = raw <= 4 ? 4 : raw <= 8 ? 8 : ((raw + 15) / 16) * 16;
     return (size_t)bytes * pb.N;
 }

@@ -92,6 +92,61 @@ __device__ __forceinline__ void stage_nodes(S *sh, const H *Hc, int N, const flo
     }
 }
 
+// FP32 node records holding, per surface, the height offset h - ref_l and
+// its difference to the next node in x, dx = h(r, c+1) - h(r, c) (0 in the
+// last column): a cell then needs the records of its two left corners only.
+template <int L> struct NodeLayoutDX {
+    static constexpr int raw = 2 * L * 4;
+    static constexpr int bytes = raw <= 8 ? 8 : ((raw + 15) / 16) * 16;
+    static constexpr int LP = bytes / 4;
+};
+
+template <typename H, int L>
+__device__ __forceinline__ void stage_nodes_dx(float *sh, const H *Hc, int N, int Q, const float *ref)
+{
+    using NL = NodeLayoutDX<L>;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        alignas(16) float tmp[NL::LP];
+#pragma unroll
+        for (int l = 0; l < NL::LP; ++l) tmp[l] = 0.f;
+        const bool last = (i % Q) == Q - 1;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const float h = (float)Hc[(size_t)l * N + i] - ref[l];
+            tmp[l] = h;
+            tmp[L + l] = last ? 0.f : ((float)Hc[(size_t)l * N + i + 1] - ref[l]) - h;
+        }
+        char *dst = reinterpret_cast<char *>(sh) + (size_t)i * NL::bytes;
+        if constexpr (NL::bytes == 8) {
+            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(tmp);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NL::bytes / 16; ++q)
+                reinterpret_cast<uint4 *>(dst)[q] = reinterpret_cast<const uint4 *>(tmp)[q];
+        }
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void load_node_dx(const float *sh, int node, float (&h)[L], float (&dx)[L])
+{
+    using NL = NodeLayoutDX<L>;
+    const char *src = reinterpret_cast<const char *>(sh) + (size_t)node * NL::bytes;
+    alignas(16) float tmp[NL::LP];
+    if constexpr (NL::bytes == 8) {
+        *reinterpret_cast<uint2 *>(tmp) = *reinterpret_cast<const uint2 *>(src);
+    } else {
+#pragma unroll
+        for (int q = 0; q < NL::bytes / 16; ++q)
+            reinterpret_cast<uint4 *>(tmp)[q] = reinterpret_cast<const uint4 *>(src)[q];
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        h[l] = tmp[l];
+        dx[l] = tmp[L + l];
+    }
+}
+
 template <typename S, typename T, int L>
 __device__ __forceinline__ void load_node(const S *sh, int node, T (&v)[L])
 {
@@ -208,7 +263,7 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 // The ray table guarantees every sample's cell coordinate lies in
 // [-1/2, n - 3/2), so the cell split needs no clamp.  Returns
 // tot[l] = N_l * 2^23.
-template <int L, bool HARD, typename S>
+template <int L, bool HARD, bool DX, typename S>
 __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int ray,
                                               unsigned long long (&tot)[L])
 {
@@ -255,10 +310,16 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
             if (node != cur) {
                 cur = node;
                 float a00[L], a01[L], a10[L], a11[L];
-                load_node<S, float, L>(sh, node, a00);
-                load_node<S, float, L>(sh, node + 1, a01);
-                load_node<S, float, L>(sh, node + Q, a10);
-                load_node<S, float, L>(sh, node + Q + 1, a11);
+                if constexpr (DX) {
+                    // a01 / a11 hold the x-differences of the two left corners
+                    load_node_dx<L>(reinterpret_cast<const float *>(sh), node, a00, a01);
+                    load_node_dx<L>(reinterpret_cast<const float *>(sh), node + Q, a10, a11);
+                } else {
+                    load_node<S, float, L>(sh, node, a00);
+                    load_node<S, float, L>(sh, node + 1, a01);
+                    load_node<S, float, L>(sh, node + Q, a10);
+                    load_node<S, float, L>(sh, node + Q + 1, a11);
+                }
 #pragma unroll
                 for (int q = 0; q < NP; ++q) {
                     h00[q] = make_float2(a00[2 * q], a00[2 * q + 1]);
@@ -273,12 +334,23 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
                     s11 = a11[L - 1];
                 }
             }
-            const float2 omfx = f2(1.0f - fxs), omfy = f2(1.0f - fys);
+            float2 omfx = f2(0.f), omfy = f2(0.f);
+            if constexpr (!DX) {
+                omfx = f2(1.0f - fxs);
+                omfy = f2(1.0f - fys);
+            }
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                const float2 a = fma2(fx, h01[q], mul2(omfx, h00[q]));     // row r0
-                const float2 b = fma2(fx, h11[q], mul2(omfx, h10[q]));     // row r0 + 1
-                const float2 sl = fma2(fy, b, mul2(omfy, a));              // s_l - ref_l
+                float2 a, b, sl;
+                if constexpr (DX) {
+                    a = fma2(fx, h01[q], h00[q]);                          // row r0
+                    b = fma2(fx, h11[q], h10[q]);                          // row r0 + 1
+                    sl = fma2(fy, fma2(a, f2(-1.0f), b), a);               // s_l - ref_l
+                } else {
+                    a = fma2(fx, h01[q], mul2(omfx, h00[q]));
+                    b = fma2(fx, h11[q], mul2(omfx, h10[q]));
+                    sl = fma2(fy, b, mul2(omfy, a));
+                }
                 const float2 zl = fma2(kf2, szl2, add2(fma2(kf2, szh2, zh2[q]), zl2[q]));
                 const float2 arg = fma2(nkg2, sl, zl);                     // -kg (s_l - z)
                 float2 sg;
@@ -294,9 +366,16 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
                 acc[2 * q + 1] += __float_as_uint(t.y);
             }
             if constexpr (ODD) {
-                const float a = fmaf(fx.x, s01, omfx.x * s00);
-                const float b = fmaf(fx.x, s11, omfx.x * s10);
-                const float sl = fmaf(fy.x, b, omfy.x * a);
+                float sl;
+                if constexpr (DX) {
+                    const float a = fmaf(fxs, s01, s00);
+                    const float b = fmaf(fxs, s11, s10);
+                    sl = fmaf(fys, b - a, a);
+                } else {
+                    const float a = fmaf(fxs, s01, omfx.x * s00);
+                    const float b = fmaf(fxs, s11, omfx.x * s10);
+                    sl = fmaf(fys, b, omfy.x * a);
+                }
                 const float zl = fmaf(kf, st.w, fmaf(kf, st.z, z0h[L - 1]) + z0l[L - 1]);
                 const float arg = fmaf(nkg2.x, sl, zl);
                 float sig;
@@ -420,17 +499,27 @@ __device__ __forceinline__ FF block_sum(FF v)
 }
 
 // ---------------------------------------------------------------- kernel
+// FP32 and float-float modes use (h, dx) node records and 1024-thread CTAs
+// (one per SM with the scenario's 128 KB of records); BF16 keeps 4-corner
+// records to halve shared memory; FP64 has its own march.
+template <int MODE, int L> struct MarchCfg {
+    static constexpr bool DX = MODE == MODE_F32 || MODE == MODE_F32C;
+    static constexpr int THREADS = DX ? (L <= 4 ? 1024 : 512) : 256;  // >= 5 surfaces need > 64 registers
+};
+
 template <int MODE, int L, bool HARD>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(MarchCfg<MODE, L>::THREADS)
 k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, double *ray_term)
 {
     using Ty = Types<MODE>;
     using S = typename Ty::S;
     using Hh = typename Ty::H;
+    constexpr bool DX = MarchCfg<MODE, L>::DX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S *sh = reinterpret_cast<S *>(smem_raw);
     const int c = blockIdx.y;
-    stage_nodes<S, Hh, L>(sh, chain_ptr<Hh>(h, c), pb.N, pb.ref);
+    if constexpr (DX) stage_nodes_dx<Hh, L>(reinterpret_cast<float *>(sh), chain_ptr<Hh>(h, c), pb.N, pb.Q, pb.ref);
+    else stage_nodes<S, Hh, L>(sh, chain_ptr<Hh>(h, c), pb.N, pb.ref);
     __syncthreads();
 
     const int r_begin = blockIdx.x * rays_per_block;
@@ -452,7 +541,7 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
             acc += term;
         } else {
             unsigned long long tot[L];
-            march_ray_f32<L, HARD, S>(pb, sh, ray, tot);
+            march_ray_f32<L, HARD, DX, S>(pb, sh, ray, tot);
             if constexpr (MODE == MODE_F32C) {
                 // O = dt (G rho_top + sum_l drho_l N_l), y = a - O / Lambda, in float-float
                 FF Sff = {pb.grho_ff.x, pb.grho_ff.y};

@@ -21,7 +21,7 @@ static cudaError_t launch_l(const Prob &pb, HRef h, int n_chains, int rpb, size_
         smem_set[hard] = smem;
     }
     dim3 grid((pb.n_rays + rpb - 1) / rpb, n_chains);
-    fn<<<grid, 256, smem, st>>>(pb, h, rpb, partial, ray_O, ray_term);
+    fn<<<grid, MarchCfg<MODE, L>::THREADS, smem, st>>>(pb, h, rpb, partial, ray_O, ray_term);
     return cudaGetLastError();
 }
 
