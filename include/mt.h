@@ -170,8 +170,12 @@ MT_API mt_status mt_ray_terms(mt_ctx *ctx, int n_chains, const void *heights, do
                        double *term_out);
 
 /* Gradient of the log-posterior with respect to every node height
- * (differentiable forward model, Sec. 2.1.4): grad_out host or device double
- * [n_chains][L][R][Q]; logpost_out (nullable) double [n_chains].  gamma > 0. */
+ * (differentiable forward model, Sec. 2.1.4; the hand-written adjoint of the
+ * ray march plus -tau Q (h - mu) from the prior): grad_out host or device
+ * double [n_chains][L][R][Q]; logpost_out (nullable) double [n_chains].
+ * FP32 march arithmetic with 64-bit fixed-point (2^-32) accumulation, so the
+ * result is reproducible bit for bit.  Needs gamma > 0 and an FP32 precision
+ * mode (MT_EINVAL otherwise); heights as for mt_logpost. */
 MT_API mt_status mt_grad(mt_ctx *ctx, int n_chains, const void *heights, double *grad_out,
                   double *logpost_out);
 
@@ -182,7 +186,9 @@ MT_API mt_status mt_init_chains(mt_ctx *ctx, int n_chains, const void *heights0,
 
 /* Run n_super x n_within Metropolis steps on every chain (Sec. 2.2).
  * kernel MT_KERNEL_RW: H' = H + step * xi; MT_KERNEL_MALA: Langevin proposal
- * with step size eps = step and the Hastings correction.  Step k of chain c
+ * H' = H + (eps^2/2) grad(H) + eps xi with eps = step, the gradient from the
+ * adjoint (FP32 precision modes, gamma > 0), and the Hastings correction
+ * ln q(H|H') - ln q(H'|H) in the accept test.  Step k of chain c
  * draws xi from Philox stream 3 (RW) or 5 (MALA), counter {j, k, c}, and its
  * acceptance uniform from stream 4, counter {0, k, c}.  The n_within steps of
  * a super-step are one CUDA graph replay; the host only sees super-step

@@ -1,0 +1,288 @@
+// adjoint.cu -- gradient of the log-posterior with respect to every node
+// height (the differentiable forward model of Sec. 2.1.4), hand-written.
+//
+// For ray p with opacity O_p: d ll / d O_p = (lambda_p - C_p) / Lambda
+// (Eq. def_likelihood with lambda = I0 exp(-O/Lambda)).  The opacity is
+// dt * sum_k rho(x_k) with rho = rho_top + sum_l (rho_l - rho_{l+1})
+// varsigma((s_l - z)/gamma), so a node height h_{l,n} receives
+//   (lambda_p - C_p)/Lambda * dt * (rho_l - rho_{l+1}) * varsigma' * w_n(x_k)
+// from every sample k, with varsigma' = varsigma (1 - varsigma) / gamma and
+// w_n the bilinear weight of the node.  The log-prior adds -tau Q (h_l - mu_l).
+//
+// Each ray is marched twice by its thread: pass 1 gives O_p (the same
+// arithmetic as the forward kernel), pass 2 recomputes the samples and
+// scatters.  Contributions are accumulated as 64-bit fixed-point integers
+// (units of 2^-32) with integer atomics, so the gradient does not depend on
+// the order in which threads add and is reproducible bit for bit; a term
+// that rounds to zero at that resolution is skipped.
+#include <math.h>
+
+#include "march.cuh"
+
+namespace mt {
+
+constexpr float kFix = 4294967296.0f;  // 2^32
+constexpr double kInvFix = 1.0 / 4294967296.0;
+
+__device__ __forceinline__ void add_fixed(unsigned long long *p, float v)
+{
+    const long long q = llrintf(v);
+    if (q != 0) atomicAdd(p, (unsigned long long)q);
+}
+
+// Pass 2 for one ray: scatter coef_l * varsigma' * w_n into acc[l][node].
+template <int L>
+__device__ __forceinline__ void scatter_ray(const Prob &pb, const float *sh, int ray,
+                                            const float (&coef)[L], unsigned long long *acc)
+{
+    const float4 o = pb.o4[ray], st = pb.s4[ray];
+    float z0h[L], z0l[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        z0h[l] = pb.kz0[(size_t)l * pb.n_rays + ray];
+        z0l[l] = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
+    }
+    const float M = 12582912.0f;
+    const float nkg = -pb.kg;
+    const int Q = pb.Q, N = pb.N;
+    float h00[L], h01[L], h10[L], h11[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) h00[l] = h01[l] = h10[l] = h11[l] = 0.f;
+    int cur = -1;
+    float kf = 0.f;
+    for (int k = 0; k < pb.G; ++k, kf += 1.0f) {
+        const float gx = fmaf(kf, st.x, o.x), gy = fmaf(kf, st.y, o.y);
+        const float tx = gx + M, ty = gy + M;
+        const float fx = (gx - (tx - M)) + 0.5f, fy = (gy - (ty - M)) + 0.5f;
+        const int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
+        if (node != cur) {
+            cur = node;
+            load_node<float, float, L>(sh, node, h00);
+            load_node<float, float, L>(sh, node + 1, h01);
+            load_node<float, float, L>(sh, node + Q, h10);
+            load_node<float, float, L>(sh, node + Q + 1, h11);
+        }
+        const float w01 = fx * (1.0f - fy), w00 = (1.0f - fx) * (1.0f - fy);
+        const float w11 = fx * fy, w10 = (1.0f - fx) * fy;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const float a = fmaf(fx, h01[l] - h00[l], h00[l]);
+            const float b = fmaf(fx, h11[l] - h10[l], h10[l]);
+            const float sl = fmaf(fy, b - a, a);
+            const float zl = fmaf(kf, st.w, fmaf(kf, st.z, z0h[l]) + z0l[l]);
+            const float e = ex2_approx(fmaf(nkg, sl, zl));
+            const float sg = rcp_approx(1.0f + e);
+            const float v = coef[l] * (e * sg * sg);  // coef * varsigma (1 - varsigma)
+            if (fabsf(v) >= 0.5f) {
+                unsigned long long *al = acc + (size_t)l * N + node;
+                add_fixed(al, v * w00);
+                add_fixed(al + 1, v * w01);
+                add_fixed(al + Q, v * w10);
+                add_fixed(al + Q + 1, v * w11);
+            }
+        }
+    }
+}
+
+// One CTA = one chain x one block of rays.  SMEM: accumulate in shared memory
+// and flush once per CTA; otherwise add straight into global memory.
+template <int L, bool SMEM>
+__global__ void __launch_bounds__(256)
+k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long long *gacc)
+{
+    using NL = NodeLayout<float, L>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *sh = reinterpret_cast<float *>(smem_raw);
+    const int c = blockIdx.y;
+    const int N = pb.N;
+    const size_t rec = ((size_t)N * NL::bytes + 255) & ~(size_t)255;
+    unsigned long long *acc_s = reinterpret_cast<unsigned long long *>(smem_raw + rec);
+    unsigned long long *gc = gacc + (size_t)c * L * N;
+    stage_nodes<float, float, L>(sh, chain_ptr<float>(h, c), N, pb.ref);
+    if constexpr (SMEM)
+        for (int i = threadIdx.x; i < L * N; i += blockDim.x) acc_s[i] = 0ull;
+    __syncthreads();
+    unsigned long long *acc = SMEM ? acc_s : gc;
+
+    const int r_begin = blockIdx.x * rays_per_block;
+    const int r_end = min(r_begin + rays_per_block, pb.n_rays);
+    double ll = 0.0;
+    for (int ray = r_begin + threadIdx.x; ray < r_end; ray += blockDim.x) {
+        unsigned long long tot[L];
+        march_ray_f32<L, false, false, float>(pb, sh, ray, tot);
+        double S_ = 0.0;
+#pragma unroll
+        for (int l = 0; l < L; ++l) S_ = fma(pb.drho[l], (double)tot[l] * 0x1p-23, S_);
+        const double O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
+        const int Cp = pb.cnt[ray];
+        const double lam = pb.I0 * exp(-O * pb.inv_Lambda);
+        if (Cp > 0) {
+            const double y = pb.a[ray] - O * pb.inv_Lambda;
+            ll += -(double)Cp * (double)g_f32((float)y);
+        } else {
+            ll += -lam;
+        }
+        const double dO = (lam - (double)Cp) * pb.inv_Lambda;  // d ll / d O_p
+        const double base = dO * pb.dt[ray] / pb.gamma * (double)kFix;
+        float coef[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) coef[l] = (float)(base * pb.drho[l]);
+        scatter_ray<L>(pb, sh, ray, coef, acc);
+    }
+    ll = block_sum(ll);
+    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = ll;
+    if constexpr (SMEM) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < L * N; i += blockDim.x) {
+            const unsigned long long v = acc_s[i];
+            if (v) atomicAdd(gc + i, v);
+        }
+    }
+}
+
+size_t adjoint_smem_bytes(const Prob &pb, bool with_acc)
+{
+    const int raw = pb.L * 4;
+    const int bytes = raw <= 4 ? 4 : raw <= 8 ? 8 : ((raw + 15) / 16) * 16;
+    const size_t rec = ((size_t)pb.N * bytes + 255) & ~(size_t)255;
+    return rec + (with_acc ? (size_t)pb.L * pb.N * 8 : 0);
+}
+
+template <int L>
+static cudaError_t adj_l(const Prob &pb, HRef h, int n_chains, int rpb, double *partial,
+                         unsigned long long *gacc, cudaStream_t st)
+{
+    const size_t with = adjoint_smem_bytes(pb, true);
+    const bool smem_acc = with <= MT_MAX_SMEM;
+    const size_t bytes = smem_acc ? with : adjoint_smem_bytes(pb, false);
+    void (*fn)(Prob, HRef, int, double *, unsigned long long *) =
+        smem_acc ? k_adjoint<L, true> : k_adjoint<L, false>;
+    static size_t set[2] = {0, 0};
+    if (bytes > 48 * 1024 && bytes > set[smem_acc]) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        set[smem_acc] = bytes;
+    }
+    dim3 grid((pb.n_rays + rpb - 1) / rpb, n_chains);
+    fn<<<grid, 256, bytes, st>>>(pb, h, rpb, partial, gacc);
+    return cudaGetLastError();
+}
+
+// gacc: [n_chains][L][N] zeroed by the caller; partial: [n_chains][blocks].
+cudaError_t launch_adjoint(const Prob &pb, HRef h, int n_chains, double *partial,
+                           unsigned long long *gacc, cudaStream_t st)
+{
+    const int rpb = march_rays_per_block(pb);
+    switch (pb.L) {
+        case 1: return adj_l<1>(pb, h, n_chains, rpb, partial, gacc, st);
+        case 2: return adj_l<2>(pb, h, n_chains, rpb, partial, gacc, st);
+        case 3: return adj_l<3>(pb, h, n_chains, rpb, partial, gacc, st);
+        case 4: return adj_l<4>(pb, h, n_chains, rpb, partial, gacc, st);
+        case 5: return adj_l<5>(pb, h, n_chains, rpb, partial, gacc, st);
+        case 6: return adj_l<6>(pb, h, n_chains, rpb, partial, gacc, st);
+        case 7: return adj_l<7>(pb, h, n_chains, rpb, partial, gacc, st);
+        case 8: return adj_l<8>(pb, h, n_chains, rpb, partial, gacc, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// grad[c][i] = gacc * 2^-32 - tau (Q (h - mu))_i, and logpost = ll + lp.
+template <typename H>
+__global__ void k_grad_finish(Prob pb, HRef h, const double *mu, const unsigned long long *gacc,
+                              double *grad)
+{
+    const int c = blockIdx.y;
+    const int n = pb.L * pb.N;
+    const H *Hc = chain_ptr<H>(h, c);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int l = i / pb.N, rc = i - l * pb.N, r = rc / pb.Q, cc = rc - r * pb.Q;
+        const int up = r + 1 == pb.R ? 0 : r + 1, dn = r == 0 ? pb.R - 1 : r - 1;
+        const int rt = cc + 1 == pb.Q ? 0 : cc + 1, lf = cc == 0 ? pb.Q - 1 : cc - 1;
+        const H *hl = Hc + (size_t)l * pb.N;
+        const double *ml = mu + (size_t)l * pb.N;
+        const double e = (double)hl[rc] - ml[rc];
+        const double nb = ((double)hl[up * pb.Q + cc] - ml[up * pb.Q + cc]) +
+                          ((double)hl[dn * pb.Q + cc] - ml[dn * pb.Q + cc]) +
+                          ((double)hl[r * pb.Q + rt] - ml[r * pb.Q + rt]) +
+                          ((double)hl[r * pb.Q + lf] - ml[r * pb.Q + lf]);
+        const double gl = (double)(long long)gacc[(size_t)c * n + i] * kInvFix;
+        grad[(size_t)c * n + i] = gl - pb.tau * (4.0 * e - pb.car_r * nb);
+    }
+}
+
+cudaError_t launch_grad_finish(const Prob &pb, int mode, HRef h, const double *mu, int n_chains,
+                               const unsigned long long *gacc, double *grad, cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    dim3 grid((n + 255) / 256 < 256 ? (n + 255) / 256 : 256, n_chains);
+    if (mode == MODE_F64) k_grad_finish<double><<<grid, 256, 0, st>>>(pb, h, mu, gacc, grad);
+    else k_grad_finish<float><<<grid, 256, 0, st>>>(pb, h, mu, gacc, grad);
+    return cudaGetLastError();
+}
+
+// Gradient of proposals (heights selected by h) into G[1 - cur[c]] of [2][C][n].
+template <typename H>
+__global__ void k_grad_finish_sel(Prob pb, HRef h, const double *mu, const unsigned long long *gacc,
+                                  double *G, const uint8_t *cur, int n_chains)
+{
+    const int c = blockIdx.y;
+    const int n = pb.L * pb.N;
+    double *dst = G + ((size_t)(1 - cur[c]) * n_chains + c) * n;
+    const H *Hc = chain_ptr<H>(h, c);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int l = i / pb.N, rc = i - l * pb.N, r = rc / pb.Q, cc = rc - r * pb.Q;
+        const int up = r + 1 == pb.R ? 0 : r + 1, dn = r == 0 ? pb.R - 1 : r - 1;
+        const int rt = cc + 1 == pb.Q ? 0 : cc + 1, lf = cc == 0 ? pb.Q - 1 : cc - 1;
+        const H *hl = Hc + (size_t)l * pb.N;
+        const double *ml = mu + (size_t)l * pb.N;
+        const double e = (double)hl[rc] - ml[rc];
+        const double nb = ((double)hl[up * pb.Q + cc] - ml[up * pb.Q + cc]) +
+                          ((double)hl[dn * pb.Q + cc] - ml[dn * pb.Q + cc]) +
+                          ((double)hl[r * pb.Q + rt] - ml[r * pb.Q + rt]) +
+                          ((double)hl[r * pb.Q + lf] - ml[r * pb.Q + lf]);
+        const double gl = (double)(long long)gacc[(size_t)c * n + i] * kInvFix;
+        dst[i] = gl - pb.tau * (4.0 * e - pb.car_r * nb);
+    }
+}
+
+cudaError_t launch_grad_finish_sel(const Prob &pb, int mode, HRef h, const double *mu, int n_chains,
+                                   const unsigned long long *gacc, double *G, const uint8_t *cur,
+                                   cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    dim3 grid((n + 255) / 256 < 256 ? (n + 255) / 256 : 256, n_chains);
+    if (mode == MODE_F64) k_grad_finish_sel<double><<<grid, 256, 0, st>>>(pb, h, mu, gacc, G, cur, n_chains);
+    else k_grad_finish_sel<float><<<grid, 256, 0, st>>>(pb, h, mu, gacc, G, cur, n_chains);
+    return cudaGetLastError();
+}
+
+// src [C][n] -> G[cur[c]][c] of [2][C][n].
+__global__ void k_scatter_sel(int n_chains, long long n, const double *src, const uint8_t *cur, double *G)
+{
+    const int c = blockIdx.y;
+    double *dst = G + ((size_t)cur[c] * n_chains + c) * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[(size_t)c * n + i];
+}
+
+cudaError_t launch_scatter_sel(int n_chains, long long n, const double *src, const uint8_t *cur,
+                               double *G, cudaStream_t st)
+{
+    dim3 grid((unsigned)((n + 255) / 256 < 256 ? (n + 255) / 256 : 256), n_chains);
+    k_scatter_sel<<<grid, 256, 0, st>>>(n_chains, n, src, cur, G);
+    return cudaGetLastError();
+}
+
+__global__ void k_add(int n, const double *a, const double *b, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] + b[i];
+}
+
+cudaError_t launch_add(int n, const double *a, const double *b, double *out, cudaStream_t st)
+{
+    k_add<<<(n + 255) / 256, 256, 0, st>>>(n, a, b, out);
+    return cudaGetLastError();
+}
+
+}  // namespace mt

@@ -98,6 +98,13 @@ struct mt_ctx {
     double *d_ll = nullptr, *d_lp = nullptr, *d_llp = nullptr, *d_lpp = nullptr, *d_logu = nullptr;
     int64_t *d_acc = nullptr, *d_step = nullptr;
     int32_t *d_accl = nullptr;
+    double *d_G = nullptr;           // [2][C][n] log-posterior gradients (MALA)
+    bool g_valid = false;            // d_G[cur] holds the current states' gradients
+    double *d_extra = nullptr;       // [C] Hastings terms
+    void *d_gacc = nullptr;          // adjoint fixed-point accumulators
+    size_t gacc_cap = 0;
+    void *d_tmp = nullptr;           // small per-chain scratch
+    size_t tmp_cap = 0;
 
     void *d_part = nullptr;
     size_t part_cap = 0;
@@ -208,6 +215,9 @@ static void drop_chains(mt_ctx *ctx)
     dfree(ctx->d_logu);
     dfree(ctx->d_acc);
     dfree(ctx->d_accl);
+    dfree(ctx->d_G);
+    dfree(ctx->d_extra);
+    ctx->g_valid = false;
     ctx->C = 0;
 }
 
@@ -322,6 +332,7 @@ static mt_status counts_ready(mt_ctx *ctx)
     refresh_prob(ctx);
     ctx->pb.sumK = sk;
     drop_graph(ctx);
+    ctx->g_valid = false;
     if (ctx->C > 0) {  // live chains: their log-likelihoods refer to the old counts
         const size_t np = n_per_chain(ctx);
         HRef h{ctx->d_H, (long long)np, ctx->d_cur, (long long)(ctx->C * np), 0};
@@ -454,6 +465,38 @@ mt_status ctx_view(mt_ctx *ctx, CtxView *v)
 mt_status ctx_fail(mt_ctx *ctx, mt_status st, const char *msg) { return fail(ctx, st, "%s", msg); }
 }  // namespace mt
 
+// Gradient of the log-posterior (and its value) of n chains given by h, into
+// device arrays grad [n][L][R][Q] and (nullable) ll / lp.  FP32 arithmetic.
+static mt_status eval_grad(mt_ctx *ctx, HRef h, int n, double *d_grad, double *d_ll, double *d_lp)
+{
+    const size_t np = n_per_chain(ctx);
+    void *old_g = ctx->d_gacc;
+    TRY(grow(ctx, &ctx->d_gacc, &ctx->gacc_cap, (size_t)n * np * 8));
+    if (ctx->d_gacc != old_g) drop_graph(ctx);
+    TRY(ensure_partials(ctx, n));
+    CK(ctx, cudaMemsetAsync(ctx->d_gacc, 0, (size_t)n * np * 8, ctx->stream));
+    CK(ctx, launch_adjoint(ctx->pb, h, n, (double *)ctx->d_part, (unsigned long long *)ctx->d_gacc,
+                           ctx->stream));
+    if (d_ll) CK(ctx, launch_reduce_ll(ctx->pb, MODE_F32, n, ctx->d_part, d_ll, ctx->stream));
+    if (d_lp) CK(ctx, launch_prior(ctx->pb, ctx->mode, h, ctx->d_mu, n, d_lp, ctx->stream));
+    CK(ctx, launch_grad_finish(ctx->pb, ctx->mode, h, ctx->d_mu, n,
+                               (const unsigned long long *)ctx->d_gacc, d_grad, ctx->stream));
+    return MT_OK;
+}
+
+static mt_status grad_ok(mt_ctx *ctx)
+{
+    if (ctx->mode == MODE_F64)
+        return fail(ctx, MT_EINVAL, "the adjoint computes in FP32: use an FP32 precision mode");
+    if (!(ctx->cfg.gamma > 0.0))
+        return fail(ctx, MT_EINVAL, "the gradient needs gamma > 0 (the hard indicator is flat)");
+    return MT_OK;
+}
+
+namespace mt {
+mt_status ctx_view(mt_ctx *ctx, CtxView *v);
+}
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
@@ -531,6 +574,8 @@ mt_status mt_destroy(mt_ctx *ctx)
     if (ctx->d_in) cudaFree(ctx->d_in);
     if (ctx->d_out) cudaFree(ctx->d_out);
     if (ctx->d_out2) cudaFree(ctx->d_out2);
+    if (ctx->d_gacc) cudaFree(ctx->d_gacc);
+    if (ctx->d_tmp) cudaFree(ctx->d_tmp);
     for (int i = 0; i < 2; ++i)
         for (auto &p : ctx->ev_open[i]) {
             cudaEventDestroy(p.a);
@@ -719,11 +764,24 @@ mt_status mt_grad(mt_ctx *ctx, int n_chains, const void *heights, double *grad_o
                   double *logpost_out)
 {
     TRY(need(ctx, true));
-    (void)n_chains;
-    (void)heights;
-    (void)grad_out;
-    (void)logpost_out;
-    return fail(ctx, MT_ESTATE, "mt_grad: the adjoint kernel is not part of this build");
+    TRY(grad_ok(ctx));
+    if (n_chains < 1 || n_chains > 65535 || !heights || !grad_out)
+        return fail(ctx, MT_EINVAL, "need 1 <= n_chains <= 65535, heights and grad_out");
+    const size_t np = n_per_chain(ctx);
+    const void *dh;
+    TRY(dev_in(ctx, heights, (size_t)n_chains * np * elem_size(ctx), &dh));
+    OutBuf g, lp;
+    TRY(dev_out(ctx, grad_out, (size_t)n_chains * np * 8, &ctx->d_out, &ctx->out_cap, &g));
+    TRY(dev_out(ctx, logpost_out, (size_t)n_chains * 8, &ctx->d_out2, &ctx->out2_cap, &lp));
+    TRY(grow(ctx, &ctx->d_tmp, &ctx->tmp_cap, (size_t)n_chains * 16));
+    double *t_ll = (double *)ctx->d_tmp, *t_lp = t_ll + n_chains;
+    HRef h{dh, (long long)np, nullptr, 0, 0};
+    TRY(eval_grad(ctx, h, n_chains, (double *)g.dev, lp.dev ? t_ll : nullptr, lp.dev ? t_lp : nullptr));
+    if (lp.dev) CK(ctx, launch_add(n_chains, t_ll, t_lp, (double *)lp.dev, ctx->stream));
+    TRY(finish_out(ctx, &g));
+    TRY(finish_out(ctx, &lp));
+    if (g.host || lp.host || dh == ctx->d_in) CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MT_OK;
 }
 
 mt_status mt_init_chains(mt_ctx *ctx, int n_chains, const void *heights0, uint64_t seed)
@@ -749,6 +807,7 @@ mt_status mt_init_chains(mt_ctx *ctx, int n_chains, const void *heights0, uint64
         ctx->C = n_chains;
     }
     drop_graph(ctx);
+    ctx->g_valid = false;
     ctx->seed = seed;
     CK(ctx, cudaMemcpyAsync(ctx->d_H, heights0, (size_t)n_chains * np * es, cudaMemcpyDefault,
                             ctx->stream));
@@ -763,10 +822,60 @@ mt_status mt_init_chains(mt_ctx *ctx, int n_chains, const void *heights0, uint64
     return MT_OK;
 }
 
+// Gradients of the current states, for MALA (computed once, then carried).
+static mt_status ensure_chain_grads(mt_ctx *ctx)
+{
+    if (ctx->g_valid) return MT_OK;
+    const size_t np = n_per_chain(ctx);
+    if (!ctx->d_G) TRY(dalloc(ctx, &ctx->d_G, 2 * (size_t)ctx->C * np));
+    if (!ctx->d_extra) TRY(dalloc(ctx, &ctx->d_extra, (size_t)ctx->C));
+    // gradients of the current heights into G[cur]; the current log-likelihoods
+    // are refreshed with the adjoint's forward pass so that the proposals'
+    // (computed by the same pass) are compared against the same arithmetic
+    HRef hc{ctx->d_H, (long long)np, ctx->d_cur, (long long)(ctx->C * np), 0};
+    TRY(grow(ctx, &ctx->d_out, &ctx->out_cap, (size_t)ctx->C * np * 8));
+    TRY(eval_grad(ctx, hc, ctx->C, (double *)ctx->d_out, ctx->d_ll, nullptr));
+    CK(ctx, launch_scatter_sel(ctx->C, (long long)np, (const double *)ctx->d_out, ctx->d_cur,
+                               ctx->d_G, ctx->stream));
+    ctx->g_valid = true;
+    return MT_OK;
+}
+
+static mt_status enqueue_mala(mt_ctx *ctx, double eps, int off)
+{
+    const size_t np = n_per_chain(ctx);
+    const long long bs = (long long)ctx->C * np;
+    EvPair es;
+    if (ctx->timing) ev_begin(ctx, 1, &es);
+    CK(ctx, launch_propose_mala(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps,
+                                ctx->seed, ctx->d_step, off, ctx->stream));
+    HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
+    CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
+    EvPair ep;
+    if (ctx->timing) ev_begin(ctx, 0, &ep);
+    CK(ctx, cudaMemsetAsync(ctx->d_gacc, 0, (size_t)ctx->C * np * 8, ctx->stream));
+    CK(ctx, launch_adjoint(ctx->pb, hp, ctx->C, (double *)ctx->d_part,
+                           (unsigned long long *)ctx->d_gacc, ctx->stream));
+    if (ctx->timing) ev_end(ctx, 0, &ep);
+    // gradient of the proposals into G[1 - cur]
+    CK(ctx, launch_grad_finish_sel(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C,
+                                   (const unsigned long long *)ctx->d_gacc, ctx->d_G, ctx->d_cur,
+                                   ctx->stream));
+    CK(ctx, launch_mala_hastings(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps,
+                                 ctx->d_extra, ctx->stream));
+    CK(ctx, launch_accept_fused(ctx->pb, MODE_F32, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
+                                ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
+                                ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
+                                ctx->stream));
+    if (ctx->timing) ev_end(ctx, 1, &es);
+    return MT_OK;
+}
+
 static mt_status enqueue_step(mt_ctx *ctx, int kernel, double step, int off)
 {
     const size_t np = n_per_chain(ctx);
     const long long bs = (long long)ctx->C * np;
+    if (kernel == MT_KERNEL_MALA) return enqueue_mala(ctx, step, off);
     if (kernel != MT_KERNEL_RW) return fail(ctx, MT_EINVAL, "kernel %d not available", kernel);
     EvPair es;
     if (ctx->timing) ev_begin(ctx, 1, &es);
@@ -792,10 +901,13 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
     if (ctx->C < 1) return fail(ctx, MT_ESTATE, "mt_init_chains first");
     if (kernel != MT_KERNEL_RW && kernel != MT_KERNEL_MALA)
         return fail(ctx, MT_EINVAL, "kernel %d", kernel);
-    if (kernel == MT_KERNEL_MALA)
-        return fail(ctx, MT_ESTATE, "MALA needs the adjoint kernel, not part of this build");
     if (!(step >= 0.0) || n_super < 0 || n_within < 1 || n_within > 4096)
         return fail(ctx, MT_EINVAL, "need step >= 0, n_super >= 0, 1 <= n_within <= 4096");
+    if (kernel == MT_KERNEL_MALA) {
+        TRY(grad_ok(ctx));
+        if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA needs a step size eps > 0");
+        TRY(ensure_chain_grads(ctx));
+    }
     TRY(ensure_partials(ctx, ctx->C));
     if (ctx->timing) {
         for (int s = 0; s < n_super; ++s) {
@@ -902,6 +1014,7 @@ mt_status mt_set_state(mt_ctx *ctx, const void *heights, int64_t step)
                             ctx->stream));
     CK(ctx, cudaMemsetAsync(ctx->d_cur, 0, ctx->C, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->d_step, &step, 8, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->g_valid = false;
     HRef h{ctx->d_H, (long long)np, nullptr, 0, 0};
     TRY(eval_logpost(ctx, h, ctx->C, ctx->d_ll, ctx->d_lp));
     CK(ctx, cudaStreamSynchronize(ctx->stream));

@@ -92,6 +92,23 @@ cudaError_t launch_propose_rw(const Prob &pb, int mode, void *hbuf, long long bu
                               const uint8_t *cur, int n_chains, double sigma, uint64_t seed,
                               const int64_t *step_base, int step_off, cudaStream_t st);
 cudaError_t launch_advance(int64_t *step, int n, cudaStream_t st);
+cudaError_t launch_adjoint(const Prob &pb, HRef h, int n_chains, double *partial,
+                           unsigned long long *gacc, cudaStream_t st);
+cudaError_t launch_grad_finish(const Prob &pb, int mode, HRef h, const double *mu, int n_chains,
+                               const unsigned long long *gacc, double *grad, cudaStream_t st);
+cudaError_t launch_add(int n, const double *a, const double *b, double *out, cudaStream_t st);
+cudaError_t launch_grad_finish_sel(const Prob &pb, int mode, HRef h, const double *mu, int n_chains,
+                                   const unsigned long long *gacc, double *G, const uint8_t *cur,
+                                   cudaStream_t st);
+cudaError_t launch_scatter_sel(int n_chains, long long n, const double *src, const uint8_t *cur,
+                               double *G, cudaStream_t st);
+cudaError_t launch_propose_mala(const Prob &pb, int mode, void *hbuf, long long buf_stride,
+                                const double *gbuf, const uint8_t *cur, int n_chains, double eps,
+                                uint64_t seed, const int64_t *step_base, int step_off,
+                                cudaStream_t st);
+cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, long long buf_stride,
+                                 const double *gbuf, const uint8_t *cur, int n_chains, double eps,
+                                 double *extra, cudaStream_t st);
 cudaError_t launch_gather(int mode, HRef h, int n_chains, long long n_per_chain, void *out,
                           cudaStream_t st);
 

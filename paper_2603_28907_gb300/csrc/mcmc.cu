@@ -105,6 +105,90 @@ cudaError_t launch_propose_rw(const Prob &pb, int mode, void *hbuf, long long bu
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- MALA
+// Langevin proposal H' = H + (eps^2/2) grad(H) + eps xi, xi from Philox stream
+// MALA, counter {j, step, chain}; grad holds the log-posterior gradient of the
+// current state (double, [2][C][n], buffer chosen by cur like the heights).
+template <typename H>
+__global__ void __launch_bounds__(256)
+k_propose_mala(int n, H *hbuf, long long buf_stride, const double *gbuf, const uint8_t *cur,
+               double eps, uint64_t seed, const int64_t *step_base, int step_off)
+{
+    const int c = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * j >= n) return;
+    const uint32_t step = (uint32_t)(*step_base + step_off);
+    const uint4 w = draw4(seed, STREAM_MALA, (uint32_t)c, step, (uint32_t)j);
+    const int cs = cur[c];
+    const long long off = (long long)cs * buf_stride + (long long)c * n;
+    const long long dst = (long long)(1 - cs) * buf_stride + (long long)c * n;
+    const double u1 = u01_f64(w.x, w.y), u2 = u01_f64(w.z, w.w);
+    const double rad = sqrt(-2.0 * log(u1));
+    double sn, cn;
+    sincospi(2.0 * u2, &sn, &cn);
+    const double half = 0.5 * eps * eps;
+    hbuf[dst + 2 * j] = (H)((double)hbuf[off + 2 * j] + half * gbuf[off + 2 * j] + eps * (rad * cn));
+    if (2 * j + 1 < n)
+        hbuf[dst + 2 * j + 1] =
+            (H)((double)hbuf[off + 2 * j + 1] + half * gbuf[off + 2 * j + 1] + eps * (rad * sn));
+}
+
+cudaError_t launch_propose_mala(const Prob &pb, int mode, void *hbuf, long long buf_stride,
+                                const double *gbuf, const uint8_t *cur, int n_chains, double eps,
+                                uint64_t seed, const int64_t *step_base, int step_off,
+                                cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    dim3 grid((n / 2 + 1 + 255) / 256, n_chains);
+    if (mode == MODE_F64)
+        k_propose_mala<double><<<grid, 256, 0, st>>>(n, (double *)hbuf, buf_stride, gbuf, cur, eps,
+                                                     seed, step_base, step_off);
+    else
+        k_propose_mala<float><<<grid, 256, 0, st>>>(n, (float *)hbuf, buf_stride, gbuf, cur, eps,
+                                                    seed, step_base, step_off);
+    return cudaGetLastError();
+}
+
+// Hastings term ln q(H | H') - ln q(H' | H) with q(b | a) = N(a + (eps^2/2) g(a), eps^2 I),
+// from the stored heights and gradients in FP64; one block per chain.
+template <typename H>
+__global__ void __launch_bounds__(256)
+k_mala_hastings(int n, const H *hbuf, long long buf_stride, const double *gbuf, const uint8_t *cur,
+                double eps, double *extra)
+{
+    const int c = blockIdx.x;
+    const int cs = cur[c];
+    const long long a = (long long)cs * buf_stride + (long long)c * n;       // current
+    const long long b = (long long)(1 - cs) * buf_stride + (long long)c * n; // proposal
+    const double half = 0.5 * eps * eps;
+    double fwd = 0.0, rev = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double ha = (double)hbuf[a + i], hb = (double)hbuf[b + i];
+        const double rf = hb - ha - half * gbuf[a + i];
+        const double rr = ha - hb - half * gbuf[b + i];
+        fwd += rf * rf;
+        rev += rr * rr;
+    }
+    fwd = block_sum(fwd);
+    __syncthreads();
+    rev = block_sum(rev);
+    if (threadIdx.x == 0) extra[c] = (fwd - rev) / (2.0 * eps * eps);
+}
+
+cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, long long buf_stride,
+                                 const double *gbuf, const uint8_t *cur, int n_chains, double eps,
+                                 double *extra, cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    if (mode == MODE_F64)
+        k_mala_hastings<double><<<n_chains, 256, 0, st>>>(n, (const double *)hbuf, buf_stride, gbuf,
+                                                          cur, eps, extra);
+    else
+        k_mala_hastings<float><<<n_chains, 256, 0, st>>>(n, (const float *)hbuf, buf_stride, gbuf,
+                                                         cur, eps, extra);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- reduce
 // ll[c] = sum over data of the Poisson constants + the CTA partials of chain c
 // added in CTA order (deterministic).
