@@ -227,6 +227,83 @@ MT_API mt_status mt_get_timing(mt_ctx *ctx, int id, double *total_ms, int64_t *l
 MT_API mt_status mt_get_sizes(const mt_ctx *ctx, int *n_layers, int *n_rows, int *n_cols,
                        int *n_sensors, int *n_pixels, int *n_chains);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of inversion requests on one GPU.
+ *
+ * A request is a whole inversion (Sec. 2: problem, data, prior and an MCMC
+ * run): grid, sensors, pixels, counts (or a true geometry to draw them from),
+ * chain starts and a step budget.  The server admits queued requests in
+ * arrival order while their estimated device memory fits the budget and a
+ * slot is free; each admitted request keeps its chains resident in its own
+ * context and stream, and gets its next super-step (one graph replay of
+ * n_within steps) as soon as the previous one finishes, so the work of
+ * different requests overlaps on the device.  Finished requests free their
+ * memory and slot for the next ones.  A request's result depends only on its
+ * own inputs and seeds: it is the same alone and in any mix.
+ * ---------------------------------------------------------------------- */
+typedef struct mt_server mt_server; /* opaque, owned by the library */
+
+typedef struct {
+    mt_config cfg;
+    int n_layers, n_rows, n_cols;
+    const double *box;            /* [3] */
+    const double *unit_density;   /* [n_layers + 1] */
+    const double *prior_mean;     /* [L][R][Q] or NULL */
+    int n_sensors;
+    const double *sensors;        /* [S][3] */
+    int n_pixels;
+    const double *dirs;           /* [P][3] unit vectors */
+    const int32_t *counts;        /* [S][P], or NULL: Poisson counts drawn from h_true */
+    const double *h_true;         /* [L][R][Q], used when counts is NULL */
+    uint64_t data_seed;
+    int n_chains;
+    const void *heights0;         /* [C][L][R][Q], storage type of cfg.precision */
+    uint64_t seed;                /* Philox key of the chains */
+    int kernel;                   /* MT_KERNEL_RW or MT_KERNEL_MALA */
+    double step;                  /* random-walk sigma or MALA eps */
+    int n_super, n_within;        /* super-steps and steps per super-step */
+} mt_request;
+
+typedef struct {
+    int status;                   /* MT_OK or the request's error */
+    int n_supersteps;
+    double submit_s, admit_s, done_s;          /* server clock, seconds */
+    double superstep_ms_p50, superstep_ms_p99; /* CUDA-event time per super-step */
+} mt_request_info;
+
+typedef struct {
+    int64_t n_done, n_pending, n_active;
+    double superstep_ms_p50, superstep_ms_p99; /* over all finished requests */
+    double ttp_s_p50, ttp_s_p99;               /* time to posterior: submit -> done */
+    double chain_ray_evals_per_s;              /* finished work / (last done - first admit) */
+    size_t bytes_in_use;                       /* estimated device memory of active requests */
+} mt_server_stats_t;
+
+/* Start a server on `device` with a device-memory budget (bytes) and at most
+ * max_active requests in flight.  A host thread runs the scheduler. */
+MT_API mt_status mt_server_create(mt_server **out, int device, size_t hbm_budget_bytes,
+                                  int max_active);
+
+/* Queue a request (host arrays, copied).  MT_ENOMEM if it alone needs more than
+ * the budget; MT_EINVAL for an incomplete request.  *id_out names it. */
+MT_API mt_status mt_server_submit(mt_server *s, const mt_request *req, int64_t *id_out);
+
+/* Wait for request `id` (timeout_s <= 0: no limit; MT_ETIMEDOUT otherwise) and
+ * copy its final chains out (host pointers, nullable): heights [C][L][R][Q],
+ * loglik / logprior double [C], accepts int64 [C]; info (nullable) gets its
+ * timing.  Returns the request's own error if it failed. */
+MT_API mt_status mt_server_wait(mt_server *s, int64_t id, double timeout_s, void *heights_out,
+                                double *loglik_out, double *logprior_out, int64_t *accepts_out,
+                                mt_request_info *info);
+
+/* Aggregate latency and throughput of the requests finished so far. */
+MT_API mt_status mt_server_stats(mt_server *s, mt_server_stats_t *out);
+
+/* Stop the scheduler (requests still running end with MT_ESTATE) and free all. */
+MT_API mt_status mt_server_destroy(mt_server *s);
+
+MT_API const char *mt_server_last_error(const mt_server *s);
+
 #ifdef __cplusplus
 }
 #endif

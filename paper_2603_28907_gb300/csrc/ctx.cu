@@ -108,6 +108,8 @@ struct mt_ctx {
 
     void *d_part = nullptr;
     size_t part_cap = 0;
+    void *d_nodes = nullptr;         // HBM node records for large grids
+    size_t nodes_cap = 0;
     void *d_in = nullptr;
     size_t in_cap = 0;
     void *d_out = nullptr;
@@ -270,6 +272,7 @@ static void refresh_prob(mt_ctx *ctx)
         pb.ref[l] = (float)m;
     }
     pb.kz0 = ctx->d_kz0;
+    pb.gnodes = nullptr;  // set per launch by ensure_nodes when the grid needs it
     pb.o4 = ctx->d_o4;
     pb.s4 = ctx->d_s4;
     pb.o_d = ctx->d_od;
@@ -390,6 +393,8 @@ static mt_status finish_out(mt_ctx *ctx, OutBuf *o)
     return MT_OK;
 }
 
+static mt_status ensure_nodes(mt_ctx *ctx, int n);
+
 static mt_status ensure_partials(mt_ctx *ctx, int n_chains)
 {
     const int rpb = march_rays_per_block(ctx->pb);
@@ -397,17 +402,39 @@ static mt_status ensure_partials(mt_ctx *ctx, int n_chains)
     void *old = ctx->d_part;
     TRY(grow(ctx, &ctx->d_part, &ctx->part_cap, n_blk * (size_t)n_chains * 8));
     if (ctx->d_part != old) drop_graph(ctx);  // a captured graph holds the old pointer
-    return MT_OK;
+    return ensure_nodes(ctx, n_chains);
+}
+
+// Grids whose node records exceed shared memory run the FP32 modes from
+// records in HBM (see k_stage_dx_global); the other modes need them to fit.
+static bool use_global_nodes(const mt_ctx *ctx)
+{
+    return march_smem_bytes(ctx->pb, ctx->mode) > MT_MAX_SMEM &&
+           (ctx->mode == MODE_F32 || ctx->mode == MODE_F32C);
 }
 
 static mt_status check_smem(mt_ctx *ctx)
 {
     const size_t smem = march_smem_bytes(ctx->pb, ctx->mode);
-    if (smem > MT_MAX_SMEM)
+    if (smem > MT_MAX_SMEM && !use_global_nodes(ctx))
         return fail(ctx, MT_EINVAL,
                     "surfaces need %zu bytes of shared memory per block (limit %d): use "
-                    "MT_PREC_BF16 or a smaller grid",
+                    "MT_PREC_F32 (records in HBM) or a smaller grid",
                     smem, MT_MAX_SMEM);
+    return MT_OK;
+}
+
+// HBM node records for n chains when the grid is too large for shared memory.
+static mt_status ensure_nodes(mt_ctx *ctx, int n)
+{
+    if (!use_global_nodes(ctx)) {
+        ctx->pb.gnodes = nullptr;
+        return MT_OK;
+    }
+    void *old = ctx->d_nodes;
+    TRY(grow(ctx, &ctx->d_nodes, &ctx->nodes_cap, march_smem_bytes(ctx->pb, ctx->mode) * (size_t)n));
+    if (ctx->d_nodes != old) drop_graph(ctx);
+    ctx->pb.gnodes = (float *)ctx->d_nodes;
     return MT_OK;
 }
 
@@ -488,6 +515,8 @@ static mt_status grad_ok(mt_ctx *ctx)
 {
     if (ctx->mode == MODE_F64)
         return fail(ctx, MT_EINVAL, "the adjoint computes in FP32: use an FP32 precision mode");
+    if (adjoint_smem_bytes(ctx->pb, false) > MT_MAX_SMEM)
+        return fail(ctx, MT_EINVAL, "grid too large for the adjoint's shared-memory surfaces");
     if (!(ctx->cfg.gamma > 0.0))
         return fail(ctx, MT_EINVAL, "the gradient needs gamma > 0 (the hard indicator is flat)");
     return MT_OK;
@@ -575,6 +604,7 @@ mt_status mt_destroy(mt_ctx *ctx)
     if (ctx->d_out) cudaFree(ctx->d_out);
     if (ctx->d_out2) cudaFree(ctx->d_out2);
     if (ctx->d_gacc) cudaFree(ctx->d_gacc);
+    if (ctx->d_nodes) cudaFree(ctx->d_nodes);
     if (ctx->d_tmp) cudaFree(ctx->d_tmp);
     for (int i = 0; i < 2; ++i)
         for (auto &p : ctx->ev_open[i]) {

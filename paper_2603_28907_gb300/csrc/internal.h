@@ -46,6 +46,8 @@ struct Prob {
     const float2 *dt_ff;       // float-float of dt
     const int32_t *cnt;        // observed counts
     double sumK;               // sum over rays of C ln C - C - lgamma(C + 1)
+    float *gnodes;             // grids too large for shared memory: per-chain (h, dx)
+                               // node records in HBM, [chain][N][record]; else nullptr
     float2 grho_ff;            // float-float of G * rho_top
     float2 invL_ff;            // float-float of 1 / Lambda
 };
@@ -92,6 +94,7 @@ cudaError_t launch_propose_rw(const Prob &pb, int mode, void *hbuf, long long bu
                               const uint8_t *cur, int n_chains, double sigma, uint64_t seed,
                               const int64_t *step_base, int step_off, cudaStream_t st);
 cudaError_t launch_advance(int64_t *step, int n, cudaStream_t st);
+size_t adjoint_smem_bytes(const Prob &pb, bool with_acc);
 cudaError_t launch_adjoint(const Prob &pb, HRef h, int n_chains, double *partial,
                            unsigned long long *gacc, cudaStream_t st);
 cudaError_t launch_grad_finish(const Prob &pb, int mode, HRef h, const double *mu, int n_chains,

@@ -127,18 +127,21 @@ __device__ __forceinline__ void stage_nodes_dx(float *sh, const H *Hc, int N, in
     }
 }
 
-template <int L>
+template <int L, bool GLOBAL = false>
 __device__ __forceinline__ void load_node_dx(const float *sh, int node, float (&h)[L], float (&dx)[L])
 {
     using NL = NodeLayoutDX<L>;
     const char *src = reinterpret_cast<const char *>(sh) + (size_t)node * NL::bytes;
     alignas(16) float tmp[NL::LP];
     if constexpr (NL::bytes == 8) {
-        *reinterpret_cast<uint2 *>(tmp) = *reinterpret_cast<const uint2 *>(src);
+        if constexpr (GLOBAL) *reinterpret_cast<uint2 *>(tmp) = __ldg(reinterpret_cast<const uint2 *>(src));
+        else *reinterpret_cast<uint2 *>(tmp) = *reinterpret_cast<const uint2 *>(src);
     } else {
 #pragma unroll
-        for (int q = 0; q < NL::bytes / 16; ++q)
-            reinterpret_cast<uint4 *>(tmp)[q] = reinterpret_cast<const uint4 *>(src)[q];
+        for (int q = 0; q < NL::bytes / 16; ++q) {
+            if constexpr (GLOBAL) reinterpret_cast<uint4 *>(tmp)[q] = __ldg(reinterpret_cast<const uint4 *>(src) + q);
+            else reinterpret_cast<uint4 *>(tmp)[q] = reinterpret_cast<const uint4 *>(src)[q];
+        }
     }
 #pragma unroll
     for (int l = 0; l < L; ++l) {
@@ -263,7 +266,7 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 // The ray table guarantees every sample's cell coordinate lies in
 // [-1/2, n - 3/2), so the cell split needs no clamp.  Returns
 // tot[l] = N_l * 2^23.
-template <int L, bool HARD, bool DX, typename S>
+template <int L, bool HARD, bool DX, typename S, bool GLOBAL = false>
 __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int ray,
                                               unsigned long long (&tot)[L])
 {
@@ -312,8 +315,8 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
                 float a00[L], a01[L], a10[L], a11[L];
                 if constexpr (DX) {
                     // a01 / a11 hold the x-differences of the two left corners
-                    load_node_dx<L>(reinterpret_cast<const float *>(sh), node, a00, a01);
-                    load_node_dx<L>(reinterpret_cast<const float *>(sh), node + Q, a10, a11);
+                    load_node_dx<L, GLOBAL>(reinterpret_cast<const float *>(sh), node, a00, a01);
+                    load_node_dx<L, GLOBAL>(reinterpret_cast<const float *>(sh), node + Q, a10, a11);
                 } else {
                     load_node<S, float, L>(sh, node, a00);
                     load_node<S, float, L>(sh, node + 1, a01);
@@ -507,7 +510,41 @@ template <int MODE, int L> struct MarchCfg {
     static constexpr int THREADS = DX ? (L <= 4 ? 1024 : 512) : 256;  // >= 5 surfaces need > 64 registers
 };
 
-template <int MODE, int L, bool HARD>
+// Records of every chain into HBM for grids too large for shared memory
+// (one block of threads per chain and node slice).
+template <typename H, int L>
+__global__ void __launch_bounds__(256) k_stage_dx_global(Prob pb, HRef h)
+{
+    using NL = NodeLayoutDX<L>;
+    const int c = blockIdx.y;
+    float *dst = pb.gnodes + (size_t)c * pb.N * NL::LP;
+    const H *Hc = chain_ptr<H>(h, c);
+    // stage_nodes_dx strides by blockDim over all nodes; split nodes over blocks
+    const int per = (pb.N + gridDim.x - 1) / gridDim.x;
+    const int n0 = blockIdx.x * per, n1 = min(pb.N, n0 + per);
+    for (int i = n0 + threadIdx.x; i < n1; i += blockDim.x) {
+        alignas(16) float tmp[NL::LP];
+#pragma unroll
+        for (int l = 0; l < NL::LP; ++l) tmp[l] = 0.f;
+        const bool last = (i % pb.Q) == pb.Q - 1;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const float v = (float)Hc[(size_t)l * pb.N + i] - pb.ref[l];
+            tmp[l] = v;
+            tmp[L + l] = last ? 0.f : ((float)Hc[(size_t)l * pb.N + i + 1] - pb.ref[l]) - v;
+        }
+        char *d = reinterpret_cast<char *>(dst) + (size_t)i * NL::bytes;
+        if constexpr (NL::bytes == 8) {
+            *reinterpret_cast<uint2 *>(d) = *reinterpret_cast<const uint2 *>(tmp);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NL::bytes / 16; ++q)
+                reinterpret_cast<uint4 *>(d)[q] = reinterpret_cast<const uint4 *>(tmp)[q];
+        }
+    }
+}
+
+template <int MODE, int L, bool HARD, bool GLOBAL = false>
 __global__ void __launch_bounds__(MarchCfg<MODE, L>::THREADS)
 k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, double *ray_term)
 {
@@ -516,11 +553,17 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
     using Hh = typename Ty::H;
     constexpr bool DX = MarchCfg<MODE, L>::DX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S *sh = reinterpret_cast<S *>(smem_raw);
     const int c = blockIdx.y;
-    if constexpr (DX) stage_nodes_dx<Hh, L>(reinterpret_cast<float *>(sh), chain_ptr<Hh>(h, c), pb.N, pb.Q, pb.ref);
-    else stage_nodes<S, Hh, L>(sh, chain_ptr<Hh>(h, c), pb.N, pb.ref);
-    __syncthreads();
+    S *sh;
+    if constexpr (GLOBAL) {
+        // node records were written to HBM by k_stage_dx_global
+        sh = reinterpret_cast<S *>(pb.gnodes + (size_t)c * pb.N * NodeLayoutDX<L>::LP);
+    } else {
+        sh = reinterpret_cast<S *>(smem_raw);
+        if constexpr (DX) stage_nodes_dx<Hh, L>(reinterpret_cast<float *>(sh), chain_ptr<Hh>(h, c), pb.N, pb.Q, pb.ref);
+        else stage_nodes<S, Hh, L>(sh, chain_ptr<Hh>(h, c), pb.N, pb.ref);
+        __syncthreads();
+    }
 
     const int r_begin = blockIdx.x * rays_per_block;
     const int r_end = min(r_begin + rays_per_block, pb.n_rays);
@@ -541,7 +584,7 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
             acc += term;
         } else {
             unsigned long long tot[L];
-            march_ray_f32<L, HARD, DX, S>(pb, sh, ray, tot);
+            march_ray_f32<L, HARD, DX, S, GLOBAL>(pb, sh, ray, tot);
             if constexpr (MODE == MODE_F32C) {
                 // O = dt (G rho_top + sum_l drho_l N_l), y = a - O / Lambda, in float-float
                 FF Sff = {pb.grho_ff.x, pb.grho_ff.y};

@@ -6,9 +6,28 @@
 namespace mt {
 
 template <int MODE, int L>
+static cudaError_t launch_global(const Prob &pb, HRef h, int n_chains, int rpb, void *partial,
+                                 double *ray_O, double *ray_term, cudaStream_t st)
+{
+    if constexpr (MODE == MODE_F32 || MODE == MODE_F32C) {
+        using Hh = typename Types<MODE>::H;
+        dim3 sg((pb.N + 4095) / 4096, n_chains);
+        k_stage_dx_global<Hh, L><<<sg, 256, 0, st>>>(pb, h);
+        void (*fn)(Prob, HRef, int, void *, double *, double *) =
+            pb.gamma == 0.0 ? k_march<MODE, L, true, true> : k_march<MODE, L, false, true>;
+        dim3 grid((pb.n_rays + rpb - 1) / rpb, n_chains);
+        fn<<<grid, MarchCfg<MODE, L>::THREADS, 0, st>>>(pb, h, rpb, partial, ray_O, ray_term);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <int MODE, int L>
 static cudaError_t launch_l(const Prob &pb, HRef h, int n_chains, int rpb, size_t smem,
                             void *partial, double *ray_O, double *ray_term, cudaStream_t st)
 {
+    if (pb.gnodes) return launch_global<MODE, L>(pb, h, n_chains, rpb, partial, ray_O, ray_term, st);
     const bool hard = pb.gamma == 0.0;
     void (*fn)(Prob, HRef, int, void *, double *, double *) =
         hard ? k_march<MODE, L, true> : k_march<MODE, L, false>;

@@ -66,6 +66,11 @@ extern "C" MT_API mt_status mt_logpost_noalloc(mt_ctx *ctx, int n_chains, const 
         return ctx_fail(ctx, MT_EINVAL,
                         "mt_logpost_noalloc: every array must be device memory (staging host "
                         "memory would need an allocation)");
+    if (march_smem_bytes(v.pb, v.mode) > MT_MAX_SMEM)
+        return ctx_fail(ctx, MT_EINVAL,
+                        "mt_logpost_noalloc: the grid's surfaces do not fit in shared memory "
+                        "(that path needs an HBM buffer); use mt_logpost");
+    v.pb.gnodes = nullptr;
     const int rpb = march_rays_per_block(v.pb);
     const size_t n_blk = (size_t)(v.pb.n_rays + rpb - 1) / rpb;
     const size_t need = (size_t)n_chains * n_blk * 8;

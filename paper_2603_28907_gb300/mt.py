@@ -35,6 +35,29 @@ class Config(C.Structure):
                 ("car_r", C.c_double), ("min_thick", C.c_double)]
 
 
+class Request(C.Structure):
+    _fields_ = [("cfg", Config), ("n_layers", C.c_int), ("n_rows", C.c_int), ("n_cols", C.c_int),
+                ("box", C.c_void_p), ("unit_density", C.c_void_p), ("prior_mean", C.c_void_p),
+                ("n_sensors", C.c_int), ("sensors", C.c_void_p), ("n_pixels", C.c_int),
+                ("dirs", C.c_void_p), ("counts", C.c_void_p), ("h_true", C.c_void_p),
+                ("data_seed", C.c_uint64), ("n_chains", C.c_int), ("heights0", C.c_void_p),
+                ("seed", C.c_uint64), ("kernel", C.c_int), ("step", C.c_double),
+                ("n_super", C.c_int), ("n_within", C.c_int)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("n_supersteps", C.c_int), ("submit_s", C.c_double),
+                ("admit_s", C.c_double), ("done_s", C.c_double),
+                ("superstep_ms_p50", C.c_double), ("superstep_ms_p99", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("n_done", C.c_int64), ("n_pending", C.c_int64), ("n_active", C.c_int64),
+                ("superstep_ms_p50", C.c_double), ("superstep_ms_p99", C.c_double),
+                ("ttp_s_p50", C.c_double), ("ttp_s_p99", C.c_double),
+                ("chain_ray_evals_per_s", C.c_double), ("bytes_in_use", C.c_size_t)]
+
+
 _lib = None
 _vp, _dp, _ip, _lp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int64)
 
@@ -59,6 +82,11 @@ SIGNATURES = {
     "mt_set_timing": [_vp, C.c_int],
     "mt_get_timing": [_vp, C.c_int, _dp, _lp, C.c_int],
     "mt_get_sizes": [_vp, _ip, _ip, _ip, _ip, _ip, _ip],
+    "mt_server_create": [C.POINTER(C.c_void_p), C.c_int, C.c_size_t, C.c_int],
+    "mt_server_submit": [_vp, C.POINTER(Request), C.POINTER(C.c_int64)],
+    "mt_server_wait": [_vp, C.c_int64, C.c_double, _vp, _vp, _vp, _vp, C.POINTER(RequestInfo)],
+    "mt_server_stats": [_vp, C.POINTER(ServerStats)],
+    "mt_server_destroy": [_vp],
 }
 
 
@@ -76,6 +104,8 @@ def load():
             fn.restype = C.c_int
         lib.mt_last_error.argtypes = [_vp]
         lib.mt_last_error.restype = C.c_char_p
+        lib.mt_server_last_error.argtypes = [_vp]
+        lib.mt_server_last_error.restype = C.c_char_p
         _lib = lib
     return _lib
 
@@ -235,3 +265,84 @@ def from_workload(prob: dict, precision=PREC_F32, device=0, stream=None, **over)
     ctx.set_sensors(prob["sensors"])
     ctx.set_pixels(prob["dirs"])
     return ctx
+
+
+class Server:
+    """mt_server: continuous batching of whole inversions on one GPU."""
+
+    def __init__(self, device=0, hbm_budget_bytes=64 << 30, max_active=8):
+        self.lib = load()
+        h = C.c_void_p()
+        st = self.lib.mt_server_create(C.byref(h), device, int(hbm_budget_bytes), int(max_active))
+        if st != 0:
+            raise MtError("mt_server_create", st, self.lib.mt_server_last_error(None).decode())
+        self.h = h
+        self._keep = {}
+
+    def _ck(self, name, st):
+        if st != 0:
+            raise MtError(name, st, self.lib.mt_server_last_error(self.h).decode())
+
+    def submit(self, prob, heights0, precision=PREC_F32, counts=None, data_seed=2, seed=4,
+               kernel=KERNEL_RW, step=0.01, n_super=1, n_within=1, **cfg_over):
+        """Queue one inversion of a workloads.problem() dict; returns its id."""
+        cfg = dict(n_grid=int(prob["G"]), gamma=float(prob["gamma"]), I0=float(prob["I0"]),
+                   atten=float(prob["Lambda"]), tau=float(prob["tau"]),
+                   car_r=float(prob["car_r"]), min_thick=float(prob["delta"]))
+        cfg.update(cfg_over)
+        arrs = dict(box=np.ascontiguousarray(prob["box"], np.float64),
+                    rho=np.ascontiguousarray(prob["rho"], np.float64),
+                    mu=np.ascontiguousarray(prob["mu"], np.float64),
+                    sensors=np.ascontiguousarray(prob["sensors"], np.float64),
+                    dirs=np.ascontiguousarray(prob["dirs"], np.float64),
+                    h0=np.ascontiguousarray(heights0, np.float64 if precision == PREC_F64 else np.float32))
+        if counts is not None:
+            arrs["counts"] = np.ascontiguousarray(counts, np.int32)
+        else:
+            arrs["h_true"] = np.ascontiguousarray(prob["H_true"], np.float64)
+        r = Request()
+        r.cfg = Config(precision, cfg["n_grid"], cfg["gamma"], cfg["I0"], cfg["atten"], cfg["tau"],
+                       cfg["car_r"], cfg["min_thick"])
+        r.n_layers, r.n_rows, r.n_cols = int(prob["L"]), int(prob["R"]), int(prob["Q"])
+        r.box, r.unit_density, r.prior_mean = _ptr(arrs["box"]), _ptr(arrs["rho"]), _ptr(arrs["mu"])
+        r.n_sensors, r.sensors = arrs["sensors"].shape[0], _ptr(arrs["sensors"])
+        r.n_pixels, r.dirs = arrs["dirs"].shape[0], _ptr(arrs["dirs"])
+        r.counts = _ptr(arrs.get("counts"))
+        r.h_true = _ptr(arrs.get("h_true"))
+        r.data_seed = data_seed
+        r.n_chains, r.heights0 = arrs["h0"].shape[0], _ptr(arrs["h0"])
+        r.seed, r.kernel, r.step = seed, kernel, float(step)
+        r.n_super, r.n_within = int(n_super), int(n_within)
+        rid = C.c_int64()
+        self._ck("mt_server_submit", self.lib.mt_server_submit(self.h, C.byref(r), C.byref(rid)))
+        self._keep[rid.value] = (prob, arrs["h0"].shape, arrs["h0"].dtype)
+        return rid.value
+
+    def wait(self, rid, timeout_s=0.0):
+        prob, shape, dtype = self._keep[rid]
+        H = np.zeros(shape, dtype)
+        ll = np.zeros(shape[0])
+        lp = np.zeros(shape[0])
+        acc = np.zeros(shape[0], np.int64)
+        info = RequestInfo()
+        self._ck("mt_server_wait", self.lib.mt_server_wait(self.h, rid, float(timeout_s), _ptr(H),
+                                                           _ptr(ll), _ptr(lp), _ptr(acc),
+                                                           C.byref(info)))
+        return dict(heights=H, loglik=ll, logprior=lp, accepts=acc,
+                    info={k: getattr(info, k) for k, _ in RequestInfo._fields_})
+
+    def stats(self):
+        st = ServerStats()
+        self._ck("mt_server_stats", self.lib.mt_server_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mt_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -303,3 +303,27 @@ def test_bad_arguments():
         ctx.run(mt.KERNEL_RW, 0.1, 1, 1)  # no chains yet
     with pytest.raises(mt.MtError):
         ctx.set_grid(9, 4, 4, [1, 1, 1], np.ones(10))
+
+
+def test_large_grid_uses_hbm_records():
+    """A 100x100 grid with 4 surfaces exceeds shared memory in the FP32 layout; the
+    kernel then reads node records from HBM and must agree with the oracle."""
+    w = W.small(R=100, Q=100, bases=(40.0, 70.0, 110.0, 140.0),
+                rho=(2.65, 1.9, 0.0012, 2.65, 0.0012), G=64, n_zenith=6, n_azimuth=9,
+                n_sensors=2)
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    Hs = np.concatenate([pr["H_true"][None], W.init_chains(w, 2)])
+    H = heights(Hs, mt.PREC_F32)
+    ll, lp = logpost(ctx, H)
+    Hn = H.double().cpu().numpy()
+    for c in range(3):
+        assert abs(ll[c] - op.loglik(Hn[c])) <= fp32_loglik_tol(pr)
+    # and the Metropolis loop runs on that path too
+    ctx.init_chains(H, 5)
+    ctx.run(mt.KERNEL_RW, 0.01, 2, 2)
+    Hs2 = torch.zeros_like(H)
+    ll2 = torch.zeros(3, dtype=torch.float64, device=DEV)
+    assert ctx.get_state(Hs2, ll2) == 4
+    H2 = Hs2.double().cpu().numpy()
+    for c in range(3):
+        assert abs(ll2[c].item() - op.loglik(H2[c])) <= fp32_loglik_tol(pr)

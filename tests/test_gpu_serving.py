@@ -1,0 +1,85 @@
+"""Continuous-batching server: every request's result is the same alone and in a mix.
+
+Requests of uneven grids, surfaces, sensors, pixels, samples and chains
+(a scaled-down serving mix) are submitted at their Poisson arrival times to a
+server whose memory budget and slot count force queueing, and again one at a
+time to a server with a single slot.  Final chain states, log-likelihoods and
+acceptance counts must be bit-identical (the kernels are deterministic and each
+request draws only from its own Philox key); one request is also checked
+against the FP64 oracle.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_28907_gb300 import mt, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _submit_all(srv, reqs, pace=True):
+    ids, t0 = [], time.perf_counter()
+    for w in reqs:
+        if pace:
+            wait = w.extra["arrival_s"] * 0.05 - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        pr = W.problem(w)
+        ids.append(srv.submit(pr, W.init_chains(w).astype(np.float32), precision=mt.PREC_F32,
+                              data_seed=w.seed_data, seed=w.seed_mcmc, step=0.02,
+                              n_super=w.n_super, n_within=w.n_within))
+    return ids
+
+
+def test_mix_equals_alone_and_batches_continuously():
+    reqs = W.serving_mix(7, seed=5, small_scale=True)
+    mix = mt.Server(hbm_budget_bytes=80 << 20, max_active=3)
+    ids = _submit_all(mix, reqs)
+    res_mix = [mix.wait(i, 120.0) for i in ids]
+    st = mix.stats()
+    mix.close()
+    alone = mt.Server(hbm_budget_bytes=8 << 30, max_active=1)
+    res_alone = []
+    for w in reqs:
+        [i] = _submit_all(alone, [w], pace=False)
+        res_alone.append(alone.wait(i, 120.0))
+    alone.close()
+    for a, b in zip(res_mix, res_alone):
+        np.testing.assert_array_equal(a["heights"], b["heights"])
+        np.testing.assert_array_equal(a["loglik"], b["loglik"])
+        np.testing.assert_array_equal(a["accepts"], b["accepts"])
+    infos = [r["info"] for r in res_mix]
+    # continuous batching: some request was admitted while an earlier one was still running
+    overlap = any(infos[j]["admit_s"] < infos[i]["done_s"] for i in range(len(infos))
+                  for j in range(i + 1, len(infos)))
+    assert overlap
+    assert st["n_done"] == len(reqs) and st["n_pending"] == 0
+    assert np.isfinite(st["superstep_ms_p50"]) and st["superstep_ms_p99"] >= st["superstep_ms_p50"]
+    assert st["ttp_s_p99"] >= st["ttp_s_p50"] > 0
+
+
+def test_served_result_matches_oracle():
+    w = W.serving_mix(3, seed=11, small_scale=True)[1]
+    pr = W.problem(w)
+    srv = mt.Server(hbm_budget_bytes=1 << 30, max_active=2)
+    [i] = _submit_all(srv, [w], pace=False)
+    r = srv.wait(i, 120.0)
+    srv.close()
+    op = oracle.OracleProblem(pr)
+    counts, _, _ = op.generate_counts(pr["H_true"], w.seed_data)
+    op.with_counts(counts)
+    for c in range(r["heights"].shape[0]):
+        H = r["heights"][c].astype(np.float64)
+        assert abs(r["loglik"][c] - op.loglik(H)) <= 1e-3
+        assert abs(r["logprior"][c] - op.logprior(H)) <= 1e-9 * max(1.0, abs(r["logprior"][c]))
+
+
+def test_budget_and_bad_requests():
+    w = W.serving_mix(1, seed=3, small_scale=True)[0]
+    srv = mt.Server(hbm_budget_bytes=1 << 20, max_active=1)   # 1 MiB: smaller than any request
+    with pytest.raises(mt.MtError) as e:
+        _submit_all(srv, [w], pace=False)
+    assert e.value.status == -2
+    srv.close()
