@@ -71,6 +71,11 @@ def parse():
     ap.add_argument("--chains", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving mix instead of the Metropolis step benchmark")
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--step-scale", type=float, default=1e-2,
+                    help="fraction of each served request's step budget that is run")
     return ap.parse_args()
 
 
@@ -199,9 +204,66 @@ def run_reference(args, w, rank):
     }), flush=True)
 
 
+def run_serve(args, rank, local):
+    """Poisson-arriving inversion requests (mean 20/s) of uneven sizes through the
+    continuous-batching server; latency and aggregate throughput."""
+    if rank != 0:
+        return
+    import torch
+    from paper_2603_28907_gb300 import mt
+    torch.cuda.set_device(local)
+    reqs = W.serving_mix(args.requests, seed=5)
+    for w in reqs:
+        steps = max(1, int(round(w.n_super * w.n_within * args.step_scale)))
+        w.n_within = min(10, steps)
+        w.n_super = max(1, steps // w.n_within)
+    free, total = torch.cuda.mem_get_info()
+    srv = mt.Server(device=local, hbm_budget_bytes=int(free * 0.8), max_active=8)
+    probs = [W.problem(w) for w in reqs]
+    starts = [W.init_chains(w).astype(np.float32) for w in reqs]
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    ids = []
+    for w, pr, h0 in zip(reqs, probs, starts):
+        wait = w.extra["arrival_s"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        ids.append(srv.submit(pr, h0, precision=mt.PREC_F32, data_seed=w.seed_data,
+                              seed=w.seed_mcmc, step=0.002, n_super=w.n_super,
+                              n_within=w.n_within))
+    res = [srv.wait(i) for i in ids]
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    evals = sum(w.n_chains * w.S * w.P * w.n_super * w.n_within for w in reqs)
+    sizes = [dict(grid=w.R, L=w.L, sensors=w.S, pixels=w.P, G=w.G, chains=w.n_chains,
+                  steps=w.n_super * w.n_within) for w in reqs]
+    print(json.dumps({
+        "metric": "served super-step latency p50 (p99, time-to-posterior alongside)",
+        "value": st["superstep_ms_p50"], "unit": "ms", "higher_is_better": False,
+        "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serving mix: {len(reqs)} requests, Poisson arrivals 20/s, "
+                               f"grids 32-128, 3-5 surfaces, 4-32 sensors, 32-96 px per side, "
+                               f"G 128-384, 64-1024 chains; step budgets x{args.step_scale:g}",
+                   "max_active": 8, "hbm_budget_gb": round(free * 0.8 / 1e9, 1)},
+        "serving": {"superstep_ms_p50": st["superstep_ms_p50"], "superstep_ms_p99": st["superstep_ms_p99"],
+                    "ttp_s_p50": st["ttp_s_p50"], "ttp_s_p99": st["ttp_s_p99"],
+                    "chain_ray_evals_per_s": st["chain_ray_evals_per_s"],
+                    "wall_s": wall, "chain_ray_evals": evals, "n_done": st["n_done"],
+                    "queue_wait_s_max": max(r["info"]["admit_s"] - r["info"]["submit_s"] for r in res)},
+        "requests": sizes,
+        "clocks": clk,
+    }), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.serve:
+        run_serve(args, rank, local)
+        return
     w = W.scenario()
     if args.chains:
         w.n_chains = args.chains
