@@ -43,7 +43,7 @@ FP32_PER_CLK_SM = 128    # FP32 lanes per SM (probe: 114.6 FMA/clk at the nomina
 # DRAM traffic of one k_march launch (read + write bytes) from the ncu capture
 # summarised in profiles/k_march_scenario_c128_ncu.md, scaled from 128 to 1024
 # chains; valid only for the kernel source it was measured on.
-MARCH_TRAFFIC = {"source_sha1": "215987152a0e", "bytes": 72.0e6}
+MARCH_TRAFFIC = {"source_sha1": "ed2b8ee00cfe", "bytes": 72.0e6}
 
 
 def march_traffic():
@@ -74,9 +74,32 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving mix instead of the Metropolis step benchmark")
     ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--study", choices=["precision", "gradient"], default=None,
+                    help="precision-mode or gradient/MALA study on the scenario data")
+    ap.add_argument("--proposals", type=int, default=100000)
     ap.add_argument("--step-scale", type=float, default=1e-2,
                     help="fraction of each served request's step budget that is run")
     return ap.parse_args()
+
+
+def rank_chains(rank, n_per_rank):
+    """Weak scaling: rank r owns global chains r*C .. r*C + C - 1 (no exchange)."""
+    return list(range(rank * n_per_rank, (rank + 1) * n_per_rank))
+
+
+def rank_seed(base, rank):
+    """Philox key of a rank's chains: distinct per rank, fixed per run."""
+    return base + 7919 * rank
+
+
+def max_over_ranks(value, dist=None, device=None):
+    """The slowest rank's time (the job's time); identity without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_env():
@@ -258,11 +281,198 @@ def run_serve(args, rank, local):
     }), flush=True)
 
 
+def _scenario_contexts(precisions, local):
+    import torch
+    from paper_2603_28907_gb300 import mt
+    w = W.scenario()
+    pr = W.problem(w)
+    ctxs = {p: mt.from_workload(pr, precision=p, device=local) for p in precisions}
+    first = ctxs[precisions[0]]
+    counts = torch.zeros((w.S, w.P), dtype=torch.int32, device=f"cuda:{local}")
+    first.generate_data(pr["H_true"], w.seed_data, counts_out=counts)
+    for p, c in ctxs.items():
+        if c is not first:
+            c.set_counts(counts)
+    return w, pr, ctxs, counts
+
+
+def run_precision_study(args, local):
+    """Accept-decision agreement, log-likelihood and MH-ratio error of the
+    reduced-precision modes on the same (current, proposal) pairs, against the
+    FP64 mode (which matches the oracle to ~1e-12 relative; two chains are
+    re-checked against the oracle).  The trajectory itself is an FP32 random
+    walk, so every state is exactly representable in all modes."""
+    import torch
+    from paper_2603_28907_gb300 import mt
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    modes = {"f32_fp64_reduce": mt.PREC_F32, "f32_compensated": mt.PREC_F32C, "bf16_heights": mt.PREC_BF16}
+    w, pr, ctxs, counts = _scenario_contexts([mt.PREC_F64] + list(modes.values()), local)
+    traj = ctxs[mt.PREC_F32]
+    ref = ctxs[mt.PREC_F64]
+    out = {}
+    for C in (1024, 4096):
+        steps = max(1, int(round(args.proposals / C)))
+        H0 = torch.tensor(np.stack([W.geometry(w, [w.seed_init, c]) for c in range(C)]).astype(np.float32),
+                          device=dev)
+        traj.init_chains(H0, w.seed_mcmc)
+        cur, prop = torch.zeros_like(H0), torch.zeros_like(H0)
+        f64 = lambda n: torch.zeros(n, dtype=torch.float64, device=dev)
+        llp, lpp, logu, lp_cur = f64(C), f64(C), f64(C), f64(C)
+        acc = torch.zeros(C, dtype=torch.int32, device=dev)
+        traj.get_state(cur, None, lp_cur)
+        ll64_cur = f64(C)
+        ref.logpost(cur.double(), ll64_cur, None)
+        stats = {k: dict(agree=0, total=0, dll_max=0.0, dll_sum=0.0, n_fin=0, dd_max=0.0, dd_sum=0.0)
+                 for k in modes}
+        t0 = time.perf_counter()
+        for k in range(steps):
+            traj.get_state(cur, None, lp_cur)
+            traj.run(mt.KERNEL_RW, w.rw_sigma, 1, 1)
+            traj.get_last_step(prop, llp, lpp, acc, logu)
+            ll64_prop = f64(C)
+            ref.logpost(prop.double(), ll64_prop, None)
+            fin = torch.isfinite(lpp)
+            delta_ref = (ll64_prop + lpp) - (ll64_cur + lp_cur)
+            a_ref = fin & (logu < delta_ref)
+            pair = torch.cat([cur, prop])
+            for name, p in modes.items():
+                ll = f64(2 * C)
+                ctxs[p].logpost(pair, ll, None)
+                delta = (ll[C:] + lpp) - (ll[:C] + lp_cur)
+                a_m = fin & (logu < delta)
+                st = stats[name]
+                st["agree"] += int((a_m == a_ref).sum().item())
+                st["total"] += C
+                if fin.any():
+                    dll = (ll[C:] - ll64_prop).abs()[fin]
+                    dd = (delta - delta_ref).abs()[fin]
+                    st["dll_max"] = max(st["dll_max"], float(dll.max().item()))
+                    st["dll_sum"] += float(dll.sum().item())
+                    st["dd_max"] = max(st["dd_max"], float(dd.max().item()))
+                    st["dd_sum"] += float(dd.sum().item())
+                    st["n_fin"] += int(fin.sum().item())
+            took = acc.bool()
+            ll64_cur = torch.where(took, ll64_prop, ll64_cur)
+        wall = time.perf_counter() - t0
+        res = {}
+        for name, st in stats.items():
+            nf = max(st["n_fin"], 1)
+            res[name] = dict(proposals=st["total"], agreement=st["agree"] / st["total"],
+                             dll_abs_max=st["dll_max"], dll_abs_mean=st["dll_sum"] / nf,
+                             mh_ratio_err_max=st["dd_max"], mh_ratio_err_mean=st["dd_sum"] / nf)
+        out[f"chains_{C}"] = dict(steps=steps, wall_s=wall, modes=res)
+    import oracle
+    op = oracle.OracleProblem(pr, counts=counts.cpu().numpy())
+    Hf = cur[:2].double()
+    llg = f64(2)
+    ref.logpost(Hf.contiguous(), llg, None)
+    Hn = Hf.cpu().numpy()
+    out["fp64_mode_vs_oracle_rel"] = max(abs(llg[i].item() - op.loglik(Hn[i])) / abs(op.loglik(Hn[i]))
+                                         for i in range(2))
+    print(json.dumps({"study": "precision", "workload": w.name, "reference": "FP64 mode", **out}), flush=True)
+
+
+def _ess(x):
+    """Effective sample size of one chain's trace (Geyer's initial positive sequence)."""
+    x = np.asarray(x, np.float64)
+    n = x.size
+    x = x - x.mean()
+    v = np.dot(x, x) / n
+    if v == 0:
+        return 0.0  # the chain never moved
+    f = np.fft.rfft(x, 2 * n)
+    ac = np.fft.irfft(f * np.conj(f))[:n] / (n * v)
+    s, t = 0.0, 1
+    while t + 1 < n:
+        pair = ac[t] + ac[t + 1]
+        if pair <= 0:
+            break
+        s += pair
+        t += 2
+    return n / (1.0 + 2.0 * s)
+
+
+def run_gradient_study(args, local):
+    import torch
+    import oracle
+    from paper_2603_28907_gb300 import mt
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w, pr, ctxs, counts = _scenario_contexts([mt.PREC_F32, mt.PREC_F64], local)
+    c32, c64 = ctxs[mt.PREC_F32], ctxs[mt.PREC_F64]
+    out = {}
+    # 1. gradient against the oracle on a 16x16 sub-grid of every surface
+    H = W.geometry(w, [w.seed_init, 0]).astype(np.float32)   # an ordered geometry
+    g = torch.zeros((1,) + H.shape, dtype=torch.float64, device=dev)
+    t = time.perf_counter()
+    c32.grad(torch.tensor(H[None], device=dev), g)
+    torch.cuda.synchronize()
+    out["grad_ms_one_chain"] = (time.perf_counter() - t) * 1e3
+    g = g[0].cpu().numpy()
+    op = oracle.OracleProblem(pr, counts=counts.cpu().numpy())
+    ref = op.grad_loglik(H.astype(np.float64)) + op.grad_logprior(H.astype(np.float64))
+    sub = (slice(None), slice(24, 40), slice(24, 40))
+    out["grad_vs_oracle_subgrid_max_abs_err_rel_to_max"] = float(np.abs(g[sub] - ref[sub]).max() / np.abs(ref[sub]).max())
+    # 2. central differences (h = 1e-3 m) of the FP64-mode log-posterior at 16 sub-grid nodes
+    rng = np.random.default_rng(0)
+    idx = [(int(rng.integers(0, w.L)), int(rng.integers(24, 40)), int(rng.integers(24, 40))) for _ in range(16)]
+    Hp = np.stack([H.astype(np.float64)] * 32)
+    for j, ix in enumerate(idx):
+        Hp[2 * j][ix] += 1e-3
+        Hp[2 * j + 1][ix] -= 1e-3
+    ll = torch.zeros(32, dtype=torch.float64, device=dev)
+    lp = torch.zeros_like(ll)
+    c64.logpost(torch.tensor(Hp, device=dev), ll, lp)
+    f = (ll + lp).cpu().numpy()
+    fd = np.array([(f[2 * j] - f[2 * j + 1]) / 2e-3 for j in range(16)])
+    ga = np.array([g[ix] for ix in idx])
+    out["grad_vs_fd_max_rel_err"] = float(np.max(np.abs(ga - fd) / np.maximum(np.abs(fd), 1e-3 * np.abs(g).max())))
+    # 3. MALA vs random walk on 1024 chains: ESS per second of the mean height of each surface
+    C, n_steps = 1024, 200
+    H0 = torch.tensor(np.stack([W.geometry(w, [w.seed_init, c]) for c in range(C)]).astype(np.float32), device=dev)
+    runs = {"rw_sigma_0.002": (mt.KERNEL_RW, 0.002), "mala_eps_0.5": (mt.KERNEL_MALA, 0.5),
+            "mala_eps_0.005": (mt.KERNEL_MALA, 0.005)}
+    cur = torch.zeros_like(H0)
+    for name, (kern, step) in runs.items():
+        c32.init_chains(H0, w.seed_mcmc)
+        c32.run(kern, step, 1, 1)   # build the graph / initial gradients outside the timing
+        c32.sync(600.0)
+        trace = np.zeros((n_steps, C, w.L))
+        t_gpu = 0.0
+        for k in range(n_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            c32.run(kern, step, 1, 1)
+            c32.sync(600.0)
+            b.record()
+            b.synchronize()
+            t_gpu += a.elapsed_time(b) / 1e3
+            c32.get_state(cur)
+            trace[k] = cur.mean(dim=(2, 3)).double().cpu().numpy()
+        acc = torch.zeros(C, dtype=torch.int64, device=dev)
+        c32.get_state(accepts_out=acc)
+        burn = n_steps // 2
+        ess = np.array([[_ess(trace[burn:, c, l]) for l in range(w.L)] for c in range(C)])
+        out[name] = dict(acceptance=float(acc.double().mean().item()) / (n_steps + 1),
+                         step_ms=t_gpu / n_steps * 1e3, ess_per_chain_mean=float(ess.mean()),
+                         ess_per_s_total=float(ess.sum(0).mean() / (t_gpu * (n_steps - burn) / n_steps)))
+    print(json.dumps({"study": "gradient", "workload": w.name, **out}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.serve:
         run_serve(args, rank, local)
+        return
+    if args.study == "precision":
+        if rank == 0:
+            run_precision_study(args, local)
+        return
+    if args.study == "gradient":
+        if rank == 0:
+            run_gradient_study(args, local)
         return
     w = W.scenario()
     if args.chains:
@@ -290,9 +500,9 @@ def main():
     ctx.generate_data(pr["H_true"], w.seed_data, counts_out=counts)
     ctx.sync(120.0)
     # each rank runs its own chains (weak scaling): rank r takes chains r*C .. r*C+C-1
-    H0np = np.stack([W.geometry(w, [w.seed_init, rank * C + c]) for c in range(C)]).astype(np.float32)
+    H0np = np.stack([W.geometry(w, [w.seed_init, g]) for g in rank_chains(rank, C)]).astype(np.float32)
     H0 = torch.tensor(H0np, device=dev)
-    ctx.init_chains(H0, w.seed_mcmc + 7919 * rank)
+    ctx.init_chains(H0, rank_seed(w.seed_mcmc, rank))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     ctx.set_timing(True)
@@ -324,9 +534,7 @@ def main():
     march_ms, march_n = ctx.get_timing(0, reset=True)
     step_ms, step_n = ctx.get_timing(1, reset=True)
     if pg:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, pg, dev)
         pg.barrier()
 
     rays = pr["S"] * pr["P"]

@@ -11,10 +11,11 @@
 //
 // Each ray is marched twice by its thread: pass 1 gives O_p (the same
 // arithmetic as the forward kernel), pass 2 recomputes the samples and
-// scatters.  Contributions are accumulated as 64-bit fixed-point integers
+// scatters.  A lane sums its contributions per cell in FP32 registers (in
+// sample order) and adds each cell's sums to 64-bit fixed-point accumulators
 // (units of 2^-32) with integer atomics, so the gradient does not depend on
-// the order in which threads add and is reproducible bit for bit; a term
-// that rounds to zero at that resolution is skipped.
+// the order in which threads add and is reproducible bit for bit; a sum that
+// rounds to zero at that resolution is not added.
 #include <math.h>
 
 #include "march.cuh"
@@ -30,7 +31,26 @@ __device__ __forceinline__ void add_fixed(unsigned long long *p, float v)
     if (q != 0) atomicAdd(p, (unsigned long long)q);
 }
 
-// Pass 2 for one ray: scatter coef_l * varsigma' * w_n into acc[l][node].
+// Flush one lane's per-cell sums (4 corners x L surfaces) to the accumulators.
+template <int L>
+__device__ __forceinline__ void flush_cell(unsigned long long *acc, int N, int Q, int node,
+                                           float (&c00)[L], float (&c01)[L], float (&c10)[L],
+                                           float (&c11)[L])
+{
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        unsigned long long *al = acc + (size_t)l * N + node;
+        add_fixed(al, c00[l]);
+        add_fixed(al + 1, c01[l]);
+        add_fixed(al + Q, c10[l]);
+        add_fixed(al + Q + 1, c11[l]);
+        c00[l] = c01[l] = c10[l] = c11[l] = 0.f;
+    }
+}
+
+// Pass 2 for one ray: scatter coef_l * varsigma' * w_n into acc[l][node].  The
+// lane sums its contributions in registers while it stays in one cell (in
+// sample order) and adds them to the fixed-point accumulators when it leaves.
 template <int L>
 __device__ __forceinline__ void scatter_ray(const Prob &pb, const float *sh, int ray,
                                             const float (&coef)[L], unsigned long long *acc)
@@ -46,8 +66,9 @@ __device__ __forceinline__ void scatter_ray(const Prob &pb, const float *sh, int
     const float nkg = -pb.kg;
     const int Q = pb.Q, N = pb.N;
     float h00[L], h01[L], h10[L], h11[L];
+    float c00[L], c01[L], c10[L], c11[L];
 #pragma unroll
-    for (int l = 0; l < L; ++l) h00[l] = h01[l] = h10[l] = h11[l] = 0.f;
+    for (int l = 0; l < L; ++l) h00[l] = h01[l] = h10[l] = h11[l] = c00[l] = c01[l] = c10[l] = c11[l] = 0.f;
     int cur = -1;
     float kf = 0.f;
     for (int k = 0; k < pb.G; ++k, kf += 1.0f) {
@@ -56,6 +77,7 @@ __device__ __forceinline__ void scatter_ray(const Prob &pb, const float *sh, int
         const float fx = (gx - (tx - M)) + 0.5f, fy = (gy - (ty - M)) + 0.5f;
         const int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
         if (node != cur) {
+            if (cur >= 0) flush_cell<L>(acc, N, Q, cur, c00, c01, c10, c11);
             cur = node;
             load_node<float, float, L>(sh, node, h00);
             load_node<float, float, L>(sh, node + 1, h01);
@@ -70,24 +92,26 @@ __device__ __forceinline__ void scatter_ray(const Prob &pb, const float *sh, int
             const float b = fmaf(fx, h11[l] - h10[l], h10[l]);
             const float sl = fmaf(fy, b - a, a);
             const float zl = fmaf(kf, st.w, fmaf(kf, st.z, z0h[l]) + z0l[l]);
-            const float e = ex2_approx(fmaf(nkg, sl, zl));
+            // varsigma (1 - varsigma) = e / (1 + e)^2 is symmetric in the sign of
+            // the argument; with e = 2^-|arg| <= 1 nothing overflows
+            const float e = ex2_approx(-fabsf(fmaf(nkg, sl, zl)));
             const float sg = rcp_approx(1.0f + e);
-            const float v = coef[l] * (e * sg * sg);  // coef * varsigma (1 - varsigma)
-            if (fabsf(v) >= 0.5f) {
-                unsigned long long *al = acc + (size_t)l * N + node;
-                add_fixed(al, v * w00);
-                add_fixed(al + 1, v * w01);
-                add_fixed(al + Q, v * w10);
-                add_fixed(al + Q + 1, v * w11);
-            }
+            const float v = coef[l] * (e * sg * sg);
+            c00[l] = fmaf(v, w00, c00[l]);
+            c01[l] = fmaf(v, w01, c01[l]);
+            c10[l] = fmaf(v, w10, c10[l]);
+            c11[l] = fmaf(v, w11, c11[l]);
         }
     }
+    if (cur >= 0) flush_cell<L>(acc, N, Q, cur, c00, c01, c10, c11);
 }
 
 // One CTA = one chain x one block of rays.  SMEM: accumulate in shared memory
 // and flush once per CTA; otherwise add straight into global memory.
+constexpr int kAdjThreads = 512;  // one CTA per SM with the scenario's 192 KB of shared memory
+
 template <int L, bool SMEM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kAdjThreads)
 k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long long *gacc)
 {
     using NL = NodeLayout<float, L>;
@@ -164,7 +188,7 @@ static cudaError_t adj_l(const Prob &pb, HRef h, int n_chains, int rpb, double *
         set[smem_acc] = bytes;
     }
     dim3 grid((pb.n_rays + rpb - 1) / rpb, n_chains);
-    fn<<<grid, 256, bytes, st>>>(pb, h, rpb, partial, gacc);
+    fn<<<grid, kAdjThreads, bytes, st>>>(pb, h, rpb, partial, gacc);
     return cudaGetLastError();
 }
 
