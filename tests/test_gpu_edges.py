@@ -1,0 +1,126 @@
+"""Edge cases of the GPU path against the FP64 oracle: sample counts across the
+256-sample accumulation chunks, the maximum of 8 surfaces, the hard indicator
+in FP32, many chains in one call, long runs, and the full-size scenario in the
+launch configuration the bench times (sampled chains)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_28907_gb300 import mt, workloads as W
+from tests.gpu_common import DEV, heights, logpost, setup
+from tests.test_gpu_parity import fp32_loglik_tol
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("G", [255, 256, 257, 300, 600])
+@pytest.mark.parametrize("precision", [mt.PREC_F32, mt.PREC_F64])
+def test_sample_counts_across_chunks(G, precision):
+    w = W.small(R=5, Q=6, bases=(40.0, 75.0, 110.0), rho=(2.65, 1.9, 0.0012, 2.65), G=G,
+                n_zenith=5, n_azimuth=7, n_sensors=2)
+    pr, ctx, op, counts, _ = setup(w, precision=precision)
+    Hs = np.concatenate([pr["H_true"][None], W.init_chains(w, 2)])
+    H = heights(Hs, precision)
+    ll, lp = logpost(ctx, H)
+    Hn = H.double().cpu().numpy()
+    for c in range(3):
+        ref = op.loglik(Hn[c])
+        tol = 1e-6 * abs(ref) if precision == mt.PREC_F64 else fp32_loglik_tol(pr, op, Hn[c])
+        assert abs(ll[c] - ref) <= tol, (G, c, ll[c], ref)
+
+
+@pytest.mark.parametrize("precision", [mt.PREC_F32, mt.PREC_F64, mt.PREC_BF16])
+def test_eight_surfaces(precision):
+    bases = tuple(20.0 + 15.0 * l for l in range(8))
+    rho = tuple([2.65, 1.9, 0.0012, 1.9, 2.65, 1.9, 0.0012, 2.65, 0.0012])
+    w = W.small(R=7, Q=5, bases=bases, rho=rho, G=64, n_zenith=4, n_azimuth=9, n_sensors=2)
+    w.sensors = tuple((x, y, 5.0) for x, y, _ in w.sensors)
+    pr, ctx, op, counts, _ = setup(w, precision=precision)
+    Hs = np.concatenate([pr["H_true"][None], W.init_chains(w, 1)])
+    H = heights(Hs, precision)
+    ll, lp = logpost(ctx, H)
+    Hn = H.double().cpu().numpy()
+    if precision == mt.PREC_BF16:
+        ref_h = torch.tensor([np.float32(pr["mu"][l].mean()) for l in range(w.L)],
+                             dtype=torch.float32, device=DEV).view(1, -1, 1, 1)
+        Hn = ((H - ref_h).to(torch.bfloat16).float() + ref_h).double().cpu().numpy()
+    for c in range(2):
+        ref = op.loglik(Hn[c])
+        tol = 1e-6 * abs(ref) if precision == mt.PREC_F64 else fp32_loglik_tol(pr, op, Hn[c])
+        assert abs(ll[c] - ref) <= tol, (c, ll[c], ref)
+
+
+def test_hard_indicator_fp32_per_ray():
+    """gamma = 0 in FP32: a sample exactly at an interface may flip between units
+    under FP32 positions; each ray's opacity may then differ from the oracle by
+    whole samples (dt * |drho|), and most rays must agree to 1e-9 relative."""
+    w = W.tiny()
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32, gamma=0.0)
+    H = heights(W.perturbed(pr["H_true"], 1.5, [2])[None], mt.PREC_F32)
+    O = torch.zeros((1, w.S * w.P), dtype=torch.float64, device=DEV)
+    ctx.ray_terms(H, O, None)
+    Og = O[0].cpu().numpy()
+    Or = op.opacities(H.double().cpu().numpy()[0]).ravel()
+    T = np.array([oracle.t_exit(s_, d_, pr["box"]) for s_ in pr["sensors"] for d_ in pr["dirs"]])
+    dt = T / w.G
+    drho = np.abs(np.diff(pr["rho"])).max()
+    diff = np.abs(Og - Or)
+    assert np.all(diff <= 2.0 * dt * drho + 1e-6)
+    assert np.mean(diff <= 1e-9 * Or) > 0.95
+
+
+def test_many_chains_one_call():
+    w = W.tiny()
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    C = 3000
+    rng = np.random.default_rng(0)
+    base = W.init_chains(w, 8)
+    Hs = base[rng.integers(0, 8, C)] + 0.01 * rng.standard_normal((C,) + base.shape[1:])
+    H = heights(Hs, mt.PREC_F32)
+    ll, lp = logpost(ctx, H)
+    Hn = H.double().cpu().numpy()
+    for c in rng.choice(C, 6, replace=False):
+        assert abs(ll[c] - op.loglik(Hn[c])) <= fp32_loglik_tol(pr, op, Hn[c])
+
+
+def test_long_run_counters():
+    w = W.tiny()
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    H0 = heights(W.init_chains(w), mt.PREC_F32)
+    ctx.init_chains(H0, 3)
+    ctx.run(mt.KERNEL_RW, w.rw_sigma, 100, 10)
+    Hs = torch.zeros_like(H0)
+    ll = torch.zeros(w.n_chains, dtype=torch.float64, device=DEV)
+    lp = torch.zeros_like(ll)
+    acc = torch.zeros(w.n_chains, dtype=torch.int64, device=DEV)
+    assert ctx.get_state(Hs, ll, lp, acc) == 1000
+    assert torch.all(acc > 0) and torch.all(acc < 1000)
+    Hn = Hs.double().cpu().numpy()
+    for c in range(w.n_chains):
+        assert abs(ll[c].item() - op.loglik(Hn[c])) <= fp32_loglik_tol(pr, op, Hn[c])
+        assert abs(lp[c].item() - op.logprior(Hn[c])) <= 1e-9 * abs(lp[c].item())
+
+
+@pytest.mark.slow
+def test_scenario_full_size_sampled_chains():
+    """1024 scenario chains through mt_logpost (the bench's kernel and launch
+    configuration); two sampled chains checked against the oracle: per-ray
+    opacity within 3e-5 mwe, per-chain log-likelihood within the FP32 bound
+    of fp32_loglik_tol (1e-3 plus the first-order propagation of the per-ray
+    opacity error)."""
+    w = W.scenario()
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    Hs = np.stack([W.geometry(w, [w.seed_init, c]) for c in range(1024)]).astype(np.float32)
+    H = heights(Hs, mt.PREC_F32)
+    ll, lp = logpost(ctx, H)
+    for c in (0, 777):
+        Hc = Hs[c].astype(np.float64)
+        Or = op.opacities(Hc).ravel()
+        O = torch.zeros((1, w.S * w.P), dtype=torch.float64, device=DEV)
+        ctx.ray_terms(H[c:c + 1].contiguous(), O, None)
+        assert np.max(np.abs(O[0].cpu().numpy() - Or)) <= 3e-5
+        ref = op.loglik(Hc)
+        tol = fp32_loglik_tol(pr, op, Hc)
+        assert abs(ll[c] - ref) <= tol, (c, ll[c] - ref, tol)
+        assert abs(lp[c] - op.logprior(Hc)) <= 1e-9 * abs(lp[c])

@@ -81,13 +81,21 @@ def test_ray_opacity_f32(precision):
     assert err.max() < 2e-6, err.max()
 
 
-def fp32_loglik_tol(pr):
-    """Per-chain |ll_FP32 - ll_oracle| bound: 1e-3 while the sample spacing is at
-    most the sigmoid width gamma; coarser sampling makes each sample's indicator
-    more sensitive to the FP32 position error in proportion to dt / gamma."""
+def fp32_loglik_tol(pr, op=None, H=None):
+    """Per-chain |ll_FP32 - ll_oracle| bound.  1e-3, times dt/gamma when the
+    sample spacing exceeds the sigmoid width (each sample's indicator is then
+    more sensitive to FP32 position error), plus the first-order propagation
+    of the FP32 per-ray opacity error, |d ll / d O_p| = |lambda_p - C_p| / Lambda
+    times 5e-7 mwe (measured bias <= 3e-7 mwe per ray): negligible near the
+    data-generating geometry, dominant for chains far from it."""
     T = [oracle.t_exit(s_, d_, pr["box"]) for s_ in pr["sensors"] for d_ in pr["dirs"]]
     dt_max = max(T) / pr["G"]
-    return 1e-3 * max(1.0, dt_max / pr["gamma"]) if pr["gamma"] > 0 else 1e-3
+    tol = 1e-3 * max(1.0, dt_max / pr["gamma"]) if pr["gamma"] > 0 else 1e-3
+    if op is not None:
+        O = op.opacities(H).ravel()
+        sens = np.abs(pr["I0"] * np.exp(-O / pr["Lambda"]) - op.counts.ravel()) / pr["Lambda"]
+        tol += 5e-7 * sens.sum()
+    return tol
 
 
 # ---------------------------------------------------------------- per chain
@@ -117,9 +125,9 @@ def test_logpost_reduced_precision(w, precision):
         Hq = ((H - ref).to(torch.bfloat16).float() + ref).double().cpu().numpy()
     else:
         Hq = Hn
-    tol = fp32_loglik_tol(pr)
     for c in range(Hs.shape[0]):
         ref_ll = op.loglik(Hq[c])
+        tol = fp32_loglik_tol(pr, op, Hq[c])
         assert abs(ll[c] - ref_ll) <= tol, (c, ll[c], ref_ll, ll[c] - ref_ll, tol)
         ref_lp = op.logprior(Hn[c])
         assert abs(lp[c] - ref_lp) <= 1e-9 * max(1.0, abs(ref_lp))
@@ -317,7 +325,7 @@ def test_large_grid_uses_hbm_records():
     ll, lp = logpost(ctx, H)
     Hn = H.double().cpu().numpy()
     for c in range(3):
-        assert abs(ll[c] - op.loglik(Hn[c])) <= fp32_loglik_tol(pr)
+        assert abs(ll[c] - op.loglik(Hn[c])) <= fp32_loglik_tol(pr, op, Hn[c])
     # and the Metropolis loop runs on that path too
     ctx.init_chains(H, 5)
     ctx.run(mt.KERNEL_RW, 0.01, 2, 2)
@@ -326,4 +334,4 @@ def test_large_grid_uses_hbm_records():
     assert ctx.get_state(Hs2, ll2) == 4
     H2 = Hs2.double().cpu().numpy()
     for c in range(3):
-        assert abs(ll2[c].item() - op.loglik(H2[c])) <= fp32_loglik_tol(pr)
+        assert abs(ll2[c].item() - op.loglik(H2[c])) <= fp32_loglik_tol(pr, op, H2[c])
