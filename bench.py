@@ -513,6 +513,7 @@ def main():
     stream.synchronize()
     ctx.get_timing(0, reset=True)
     ctx.get_timing(1, reset=True)
+    ctx.get_work(reset=True)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -532,6 +533,7 @@ def main():
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs)
     march_ms, march_n = ctx.get_timing(0, reset=True)
+    work_eval, work_total = ctx.get_work(reset=True)
     step_ms, step_n = ctx.get_timing(1, reset=True)
     if pg:
         ms = max_over_ranks(ms, pg, dev)
@@ -577,7 +579,13 @@ def main():
                          "peak_basis": "152 SM x 2070 MHz; ex2 32/clk, rcp 16/clk per SM; "
                                        "128 FP32 lanes with 12+9L ops per sample",
                          "kernel": "k_march", "kernel_ms_avg": avg_launch_s * 1e3,
-                         "launches": march_n},
+                         "launches": march_n,
+                         "evaluated_fraction": work_eval / work_total if work_total else None,
+                         "frac_evaluated_work": (achieved / peak) * (work_eval / work_total)
+                         if work_total else None,
+                         "note": "units are the method's surface-samples; samples at least 30 "
+                                 "log2 units from their surface are exactly 0/1 and added "
+                                 "without evaluation (bit-identical)"},
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -223,6 +223,14 @@ MT_API mt_status mt_sync(mt_ctx *ctx, double timeout_s);
 MT_API mt_status mt_set_timing(mt_ctx *ctx, int on);
 MT_API mt_status mt_get_timing(mt_ctx *ctx, int id, double *total_ms, int64_t *launches, int reset);
 
+/* Work of the FP32 ray kernel launched while timing was on: *total = the
+ * method's surface-samples (chains x rays x n_grid x n_layers), *evaluated =
+ * those whose logistic was computed; the others lay so far from their surface
+ * (|s - z| >= 30 gamma / log2(e)) that their indicator is exactly 0 or 1 in
+ * FP32 and was added without evaluation (the result is bit-identical).
+ * reset = 1 clears both. */
+MT_API mt_status mt_get_work(mt_ctx *ctx, double *evaluated, double *total, int reset);
+
 /* Sizes of the loaded problem (any pointer nullable). */
 MT_API mt_status mt_get_sizes(const mt_ctx *ctx, int *n_layers, int *n_rows, int *n_cols,
                        int *n_sensors, int *n_pixels, int *n_chains);

@@ -122,6 +122,8 @@ struct mt_ctx {
     double g_step = 0.0;
 
     bool timing = false;
+    unsigned long long *d_work = nullptr;  // evaluated surface-samples (timing mode)
+    double work_total = 0.0;               // surface-samples of the method in timed launches
     std::vector<EvPair> ev_open[2];
     std::vector<cudaEvent_t> ev_pool;
     double t_ms[2] = {0, 0};
@@ -273,6 +275,7 @@ static void refresh_prob(mt_ctx *ctx)
     }
     pb.kz0 = ctx->d_kz0;
     pb.gnodes = nullptr;  // set per launch by ensure_nodes when the grid needs it
+    pb.work = ctx->timing ? ctx->d_work : nullptr;
     pb.o4 = ctx->d_o4;
     pb.s4 = ctx->d_s4;
     pb.o_d = ctx->d_od;
@@ -450,6 +453,12 @@ static cudaEvent_t ev_get(mt_ctx *ctx)
     return e;
 }
 
+// Launch-time bookkeeping of the method's work for mt_get_work.
+static void count_work(mt_ctx *ctx, int n_chains)
+{
+    ctx->work_total += (double)n_chains * ctx->pb.n_rays * ctx->pb.G * ctx->pb.L;
+}
+
 static void ev_begin(mt_ctx *ctx, int id, EvPair *p)
 {
     p->a = ev_get(ctx);
@@ -469,7 +478,10 @@ static mt_status eval_logpost(mt_ctx *ctx, HRef h, int n, double *d_ll, double *
     if (d_lp) CK(ctx, launch_prior(ctx->pb, ctx->mode, h, ctx->d_mu, n, d_lp, ctx->stream));
     if (d_ll) {
         EvPair ep;
-        if (ctx->timing) ev_begin(ctx, 0, &ep);
+        if (ctx->timing) {
+            ev_begin(ctx, 0, &ep);
+            count_work(ctx, n);
+        }
         CK(ctx, launch_march(ctx->pb, ctx->mode, h, n, ctx->d_part, nullptr, nullptr, ctx->stream));
         if (ctx->timing) ev_end(ctx, 0, &ep);
         CK(ctx, launch_reduce_ll(ctx->pb, ctx->mode, n, ctx->d_part, d_ll, ctx->stream));
@@ -599,6 +611,7 @@ mt_status mt_destroy(mt_ctx *ctx)
     dfree(ctx->d_cnt);
     dfree(ctx->d_flag);
     dfree(ctx->d_step);
+    dfree(ctx->d_work);
     if (ctx->d_part) cudaFree(ctx->d_part);
     if (ctx->d_in) cudaFree(ctx->d_in);
     if (ctx->d_out) cudaFree(ctx->d_out);
@@ -914,7 +927,10 @@ static mt_status enqueue_step(mt_ctx *ctx, int kernel, double step, int off)
     HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
     CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
     EvPair ep;
-    if (ctx->timing) ev_begin(ctx, 0, &ep);
+    if (ctx->timing) {
+        ev_begin(ctx, 0, &ep);
+        count_work(ctx, ctx->C);
+    }
     CK(ctx, launch_march(ctx->pb, ctx->mode, hp, ctx->C, ctx->d_part, nullptr, nullptr, ctx->stream));
     if (ctx->timing) ev_end(ctx, 0, &ep);
     CK(ctx, launch_accept_fused(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, nullptr,
@@ -1082,8 +1098,32 @@ mt_status mt_sync(mt_ctx *ctx, double timeout_s)
 mt_status mt_set_timing(mt_ctx *ctx, int on)
 {
     if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    CK(ctx, cudaSetDevice(ctx->device));
     ctx->timing = on != 0;
     drop_graph(ctx);
+    if (ctx->timing && !ctx->d_work) {
+        TRY(dalloc(ctx, &ctx->d_work, 1));
+        CK(ctx, cudaMemsetAsync(ctx->d_work, 0, 8, ctx->stream));
+    }
+    ctx->pb.work = ctx->timing ? ctx->d_work : nullptr;
+    return MT_OK;
+}
+
+mt_status mt_get_work(mt_ctx *ctx, double *evaluated, double *total, int reset)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    CK(ctx, cudaSetDevice(ctx->device));
+    unsigned long long e = 0;
+    if (ctx->d_work) {
+        CK(ctx, cudaMemcpyAsync(&e, ctx->d_work, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    if (evaluated) *evaluated = (double)e;
+    if (total) *total = ctx->work_total;
+    if (reset) {
+        if (ctx->d_work) CK(ctx, cudaMemsetAsync(ctx->d_work, 0, 8, ctx->stream));
+        ctx->work_total = 0.0;
+    }
     return MT_OK;
 }
 

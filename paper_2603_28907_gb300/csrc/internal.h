@@ -46,6 +46,8 @@ struct Prob {
     const float2 *dt_ff;       // float-float of dt
     const int32_t *cnt;        // observed counts
     double sumK;               // sum over rays of C ln C - C - lgamma(C + 1)
+    unsigned long long *work;  // timing mode: [0] surface-samples evaluated by the FP32
+                               // march (the rest were exactly saturated), else nullptr
     float *gnodes;             // grids too large for shared memory: per-chain (h, dx)
                                // node records in HBM, [chain][N][record]; else nullptr
     float2 grho_ff;            // float-float of G * rho_top

@@ -95,11 +95,38 @@ __device__ __forceinline__ void stage_nodes(S *sh, const H *Hc, int N, const flo
 // FP32 node records holding, per surface, the height offset h - ref_l and
 // its difference to the next node in x, dx = h(r, c+1) - h(r, c) (0 in the
 // last column): a cell then needs the records of its two left corners only.
+// Surfaces are grouped in pairs, each pair one 16-byte slot
+// {h_2q, h_2q+1, dx_2q, dx_2q+1}; an odd last surface takes an 8-byte slot
+// {h, dx}; the record is padded to a multiple of 16 bytes.
 template <int L> struct NodeLayoutDX {
-    static constexpr int raw = 2 * L * 4;
+    static constexpr int NP = L / 2;
+    static constexpr int raw = NP * 16 + (L & 1) * 8;
     static constexpr int bytes = raw <= 8 ? 8 : ((raw + 15) / 16) * 16;
     static constexpr int LP = bytes / 4;
 };
+
+template <typename H, int L>
+__device__ __forceinline__ void dx_record(const H *Hc, int N, int Q, const float *ref, int i,
+                                          float (&tmp)[NodeLayoutDX<L>::LP])
+{
+    constexpr int NP = L / 2;
+#pragma unroll
+    for (int j = 0; j < NodeLayoutDX<L>::LP; ++j) tmp[j] = 0.f;
+    const bool last = (i % Q) == Q - 1;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const float h = (float)Hc[(size_t)l * N + i] - ref[l];
+        const float d = last ? 0.f : ((float)Hc[(size_t)l * N + i + 1] - ref[l]) - h;
+        const int q = l / 2;
+        if (q < NP) {
+            tmp[4 * q + (l & 1)] = h;
+            tmp[4 * q + 2 + (l & 1)] = d;
+        } else {
+            tmp[4 * NP] = h;
+            tmp[4 * NP + 1] = d;
+        }
+    }
+}
 
 template <typename H, int L>
 __device__ __forceinline__ void stage_nodes_dx(float *sh, const H *Hc, int N, int Q, const float *ref)
@@ -107,15 +134,7 @@ __device__ __forceinline__ void stage_nodes_dx(float *sh, const H *Hc, int N, in
     using NL = NodeLayoutDX<L>;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         alignas(16) float tmp[NL::LP];
-#pragma unroll
-        for (int l = 0; l < NL::LP; ++l) tmp[l] = 0.f;
-        const bool last = (i % Q) == Q - 1;
-#pragma unroll
-        for (int l = 0; l < L; ++l) {
-            const float h = (float)Hc[(size_t)l * N + i] - ref[l];
-            tmp[l] = h;
-            tmp[L + l] = last ? 0.f : ((float)Hc[(size_t)l * N + i + 1] - ref[l]) - h;
-        }
+        dx_record<H, L>(Hc, N, Q, ref, i, tmp);
         char *dst = reinterpret_cast<char *>(sh) + (size_t)i * NL::bytes;
         if constexpr (NL::bytes == 8) {
             *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(tmp);
@@ -127,26 +146,48 @@ __device__ __forceinline__ void stage_nodes_dx(float *sh, const H *Hc, int N, in
     }
 }
 
-template <int L, bool GLOBAL = false>
-__device__ __forceinline__ void load_node_dx(const float *sh, int node, float (&h)[L], float (&dx)[L])
+// Per-surface minimum and maximum of h - ref over one chain's nodes (block
+// reduction); ext[l] = min, ext[L + l] = max.  All threads must call it.
+template <typename H, int L>
+__device__ __forceinline__ void surface_extent(const H *Hc, int N, const float *ref, float *ext)
 {
-    using NL = NodeLayoutDX<L>;
-    const char *src = reinterpret_cast<const char *>(sh) + (size_t)node * NL::bytes;
-    alignas(16) float tmp[NL::LP];
-    if constexpr (NL::bytes == 8) {
-        if constexpr (GLOBAL) *reinterpret_cast<uint2 *>(tmp) = __ldg(reinterpret_cast<const uint2 *>(src));
-        else *reinterpret_cast<uint2 *>(tmp) = *reinterpret_cast<const uint2 *>(src);
-    } else {
-#pragma unroll
-        for (int q = 0; q < NL::bytes / 16; ++q) {
-            if constexpr (GLOBAL) reinterpret_cast<uint4 *>(tmp)[q] = __ldg(reinterpret_cast<const uint4 *>(src) + q);
-            else reinterpret_cast<uint4 *>(tmp)[q] = reinterpret_cast<const uint4 *>(src)[q];
-        }
-    }
+    __shared__ float red[2 * MT_MAX_L][32];
+    float lo[L], hi[L];
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-        h[l] = tmp[l];
-        dx[l] = tmp[L + l];
+        lo[l] = INFINITY;
+        hi[l] = -INFINITY;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const float v = (float)Hc[(size_t)l * N + i] - ref[l];
+            lo[l] = fminf(lo[l], v);
+            hi[l] = fmaxf(hi[l], v);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[l] = fminf(lo[l], __shfl_xor_sync(0xffffffffu, lo[l], o));
+            hi[l] = fmaxf(hi[l], __shfl_xor_sync(0xffffffffu, hi[l], o));
+        }
+        if (lane == 0) {
+            red[l][warp] = lo[l];
+            red[MT_MAX_L + l][warp] = hi[l];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < L) {
+        float a = INFINITY, b = -INFINITY;
+        for (int j = 0; j < nw; ++j) {
+            a = fminf(a, red[threadIdx.x][j]);
+            b = fmaxf(b, red[MT_MAX_L + threadIdx.x][j]);
+        }
+        ext[threadIdx.x] = a;
+        ext[L + threadIdx.x] = b;
     }
 }
 
@@ -266,96 +307,121 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 // The ray table guarantees every sample's cell coordinate lies in
 // [-1/2, n - 3/2), so the cell split needs no clamp.  Returns
 // tot[l] = N_l * 2^23.
-template <int L, bool HARD, bool DX, typename S, bool GLOBAL = false>
-__device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int ray,
-                                              unsigned long long (&tot)[L])
+// Samples whose sigmoid argument is at least kSat (log2 units) from zero give
+// sigma + 1 == exactly 1.0f or exactly rcp(1) + 1 in FP32 (the argument of
+// 2^arg, or 2^-arg, is far past the 2^-24 rounding limit), so their integer
+// contributions are known without evaluating them.
+constexpr float kSat = 30.0f;
+
+// Sample window [lo, hi] in which surface l can be transitional along a ray:
+// outside it |kg (z - s_l)| >= kSat for every height the surface takes
+// (ext = its min / max offset).  z_l(k) = z0 + k dz (scaled by kg).
+__device__ __forceinline__ void transition_window(float z0, float dz, float kg, float smin,
+                                                  float smax, int G, int &lo, int &hi)
 {
-    constexpr int NP = L / 2;
-    constexpr int NPP = NP > 0 ? NP : 1;
-    constexpr bool ODD = (L & 1) != 0;
-    const float4 o = pb.o4[ray], st = pb.s4[ray];
-    float z0h[L], z0l[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-        z0h[l] = pb.kz0[(size_t)l * pb.n_rays + ray];
-        z0l[l] = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
-        tot[l] = 0ull;
+    const float a = kg * smin - kSat, b = kg * smax + kSat;  // z_l must lie in (a, b)
+    if (fabsf(dz) < 1e-20f) {
+        const bool in = z0 > a && z0 < b;
+        lo = in ? 0 : G;
+        hi = in ? G - 1 : -1;
+        return;
     }
-    float2 zh2[NPP], zl2[NPP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        zh2[q] = make_float2(z0h[2 * q], z0h[2 * q + 1]);
-        zl2[q] = make_float2(z0l[2 * q], z0l[2 * q + 1]);
+    float ka = (a - z0) / dz, kb = (b - z0) / dz;
+    if (dz < 0.f) {
+        const float t = ka;
+        ka = kb;
+        kb = t;
     }
+    ka = fmaxf(floorf(ka), -1.0f);
+    kb = fminf(ceilf(kb), (float)G);
+    lo = (int)ka;
+    hi = (int)kb;
+    if (dz < 0.f) {  // samples before the window lie above the surface: no skipping
+        lo = 0;      // (rays pointing down are rare; they evaluate every sample)
+        hi = G - 1;
+    }
+    lo = max(lo, 0);
+    hi = min(hi, G - 1);
+}
+
+// Corner data of one surface group at a node: a pair (NS = 2) or the odd
+// last surface (NS = 1).  DX records give {h, dx}; plain records give h only.
+template <int L, int NS, bool DX, typename S, bool GLOBAL>
+__device__ __forceinline__ void load_group(const S *sh, int node, int l0, float2 &h, float2 &dx)
+{
+    if constexpr (DX) {
+        using NL = NodeLayoutDX<L>;
+        const char *rec = reinterpret_cast<const char *>(sh) + (size_t)node * NL::bytes;
+        if constexpr (NS == 2) {
+            const float4 *p = reinterpret_cast<const float4 *>(rec + (l0 / 2) * 16);
+            const float4 v = GLOBAL ? __ldg(p) : *p;
+            h = make_float2(v.x, v.y);
+            dx = make_float2(v.z, v.w);
+        } else {
+            const float2 *p = reinterpret_cast<const float2 *>(rec + (L / 2) * 16);
+            const float2 v = GLOBAL ? __ldg(p) : *p;
+            h = make_float2(v.x, 0.f);
+            dx = make_float2(v.y, 0.f);
+        }
+    } else {
+        using NL = NodeLayout<S, L>;
+        const S *rec = reinterpret_cast<const S *>(reinterpret_cast<const char *>(sh) + (size_t)node * NL::bytes);
+        h.x = to_f(rec[l0]);
+        h.y = NS == 2 ? to_f(rec[l0 + 1]) : 0.f;
+        dx = make_float2(0.f, 0.f);
+    }
+}
+
+// March one surface group over its sample window [lo, he) and add its
+// integer indicator sums (units 2^-23) to t0 (surface l0) and t1 (l0 + 1).
+template <int L, int NS, bool HARD, bool DX, typename S, bool GLOBAL>
+__device__ __forceinline__ void march_group(const Prob &pb, const S *sh, float4 o, float4 st,
+                                            int l0, float2 zh, float2 zlo, int lo, int he,
+                                            unsigned long long &t0, unsigned long long &t1)
+{
     const float M = 12582912.0f;  // 1.5 * 2^23: adding it rounds to an integer
-    const float2 one2 = f2(1.0f);
-    const float2 nkg2 = f2(-pb.kg);
-    const float2 szh2 = f2(st.z), szl2 = f2(st.w);
     const int Q = pb.Q;
-    float2 h00[NPP], h01[NPP], h10[NPP], h11[NPP];
-    float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;  // last surface when L is odd
-#pragma unroll
-    for (int q = 0; q < NPP; ++q) h00[q] = h01[q] = h10[q] = h11[q] = f2(0.f);
+    const float nkg = -pb.kg;
+    const float2 one2 = f2(1.0f), nkg2 = f2(nkg), szh2 = f2(st.z), szl2 = f2(st.w);
+    float2 h00 = f2(0.f), h01 = f2(0.f), h10 = f2(0.f), h11 = f2(0.f);
     int cur = -1;
-    float kf = 0.f;
-    for (int k0 = 0; k0 < pb.G; k0 += 256) {
-        const int kn = min(256, pb.G - k0);
-        uint32_t acc[L];
-#pragma unroll
-        for (int l = 0; l < L; ++l) acc[l] = 0u;
+    float kf = (float)lo;
+    for (int k0 = lo; k0 < he; k0 += 256) {
+        const int kn = min(256, he - k0);
+        uint32_t a0 = 0u, a1 = 0u;
         for (int k = 0; k < kn; ++k, kf += 1.0f) {
-            // cell split in scalar FP32 (the pairs below are broadcasts of it)
-            const float gxs = fmaf(kf, st.x, o.x), gys = fmaf(kf, st.y, o.y);
-            const float txs = gxs + M, tys = gys + M;
-            const float fxs = (gxs - (txs - M)) + 0.5f, fys = (gys - (tys - M)) + 0.5f;  // in [0, 1]
-            const int node = (__float_as_int(tys) - 0x4B400000) * Q + (__float_as_int(txs) - 0x4B400000);
-            const float2 kf2 = f2(kf), fx = f2(fxs), fy = f2(fys);
+            const float gx = fmaf(kf, st.x, o.x), gy = fmaf(kf, st.y, o.y);
+            const float tx = gx + M, ty = gy + M;
+            const float fxs = (gx - (tx - M)) + 0.5f, fys = (gy - (ty - M)) + 0.5f;  // in [0, 1]
+            const int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
             if (node != cur) {
                 cur = node;
-                float a00[L], a01[L], a10[L], a11[L];
                 if constexpr (DX) {
-                    // a01 / a11 hold the x-differences of the two left corners
-                    load_node_dx<L, GLOBAL>(reinterpret_cast<const float *>(sh), node, a00, a01);
-                    load_node_dx<L, GLOBAL>(reinterpret_cast<const float *>(sh), node + Q, a10, a11);
+                    load_group<L, NS, DX, S, GLOBAL>(sh, node, l0, h00, h01);      // h, dx of row r0
+                    load_group<L, NS, DX, S, GLOBAL>(sh, node + Q, l0, h10, h11);  // h, dx of row r0+1
                 } else {
-                    load_node<S, float, L>(sh, node, a00);
-                    load_node<S, float, L>(sh, node + 1, a01);
-                    load_node<S, float, L>(sh, node + Q, a10);
-                    load_node<S, float, L>(sh, node + Q + 1, a11);
-                }
-#pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                    h00[q] = make_float2(a00[2 * q], a00[2 * q + 1]);
-                    h01[q] = make_float2(a01[2 * q], a01[2 * q + 1]);
-                    h10[q] = make_float2(a10[2 * q], a10[2 * q + 1]);
-                    h11[q] = make_float2(a11[2 * q], a11[2 * q + 1]);
-                }
-                if constexpr (ODD) {
-                    s00 = a00[L - 1];
-                    s01 = a01[L - 1];
-                    s10 = a10[L - 1];
-                    s11 = a11[L - 1];
+                    float2 dum;
+                    load_group<L, NS, DX, S, GLOBAL>(sh, node, l0, h00, dum);
+                    load_group<L, NS, DX, S, GLOBAL>(sh, node + 1, l0, h01, dum);
+                    load_group<L, NS, DX, S, GLOBAL>(sh, node + Q, l0, h10, dum);
+                    load_group<L, NS, DX, S, GLOBAL>(sh, node + Q + 1, l0, h11, dum);
                 }
             }
-            float2 omfx = f2(0.f), omfy = f2(0.f);
-            if constexpr (!DX) {
-                omfx = f2(1.0f - fxs);
-                omfy = f2(1.0f - fys);
-            }
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
+            if constexpr (NS == 2) {
+                const float2 fx = f2(fxs), fy = f2(fys), kf2 = f2(kf);
                 float2 a, b, sl;
                 if constexpr (DX) {
-                    a = fma2(fx, h01[q], h00[q]);                          // row r0
-                    b = fma2(fx, h11[q], h10[q]);                          // row r0 + 1
-                    sl = fma2(fy, fma2(a, f2(-1.0f), b), a);               // s_l - ref_l
+                    a = fma2(fx, h01, h00);                             // row r0
+                    b = fma2(fx, h11, h10);                             // row r0 + 1
+                    sl = fma2(fy, fma2(a, f2(-1.0f), b), a);            // s_l - ref_l
                 } else {
-                    a = fma2(fx, h01[q], mul2(omfx, h00[q]));
-                    b = fma2(fx, h11[q], mul2(omfx, h10[q]));
+                    const float2 omfx = f2(1.0f - fxs), omfy = f2(1.0f - fys);
+                    a = fma2(fx, h01, mul2(omfx, h00));
+                    b = fma2(fx, h11, mul2(omfx, h10));
                     sl = fma2(fy, b, mul2(omfy, a));
                 }
-                const float2 zl = fma2(kf2, szl2, add2(fma2(kf2, szh2, zh2[q]), zl2[q]));
-                const float2 arg = fma2(nkg2, sl, zl);                     // -kg (s_l - z)
+                const float2 zl = fma2(kf2, szl2, add2(fma2(kf2, szh2, zh), zlo));
+                const float2 arg = fma2(nkg2, sl, zl);                  // -kg (s_l - z)
                 float2 sg;
                 if constexpr (HARD) {
                     sg.x = arg.x < 0.f ? 1.f : (arg.x > 0.f ? 0.f : 0.5f);
@@ -365,30 +431,93 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
                     sg = make_float2(rcp_approx(d.x), rcp_approx(d.y));
                 }
                 const float2 t = add2(sg, one2);
-                acc[2 * q] += __float_as_uint(t.x);
-                acc[2 * q + 1] += __float_as_uint(t.y);
-            }
-            if constexpr (ODD) {
+                a0 += __float_as_uint(t.x);
+                a1 += __float_as_uint(t.y);
+            } else {
                 float sl;
                 if constexpr (DX) {
-                    const float a = fmaf(fxs, s01, s00);
-                    const float b = fmaf(fxs, s11, s10);
+                    const float a = fmaf(fxs, h01.x, h00.x);
+                    const float b = fmaf(fxs, h11.x, h10.x);
                     sl = fmaf(fys, b - a, a);
                 } else {
-                    const float a = fmaf(fxs, s01, omfx.x * s00);
-                    const float b = fmaf(fxs, s11, omfx.x * s10);
-                    sl = fmaf(fys, b, omfy.x * a);
+                    const float a = fmaf(fxs, h01.x, (1.0f - fxs) * h00.x);
+                    const float b = fmaf(fxs, h11.x, (1.0f - fxs) * h10.x);
+                    sl = fmaf(fys, b, (1.0f - fys) * a);
                 }
-                const float zl = fmaf(kf, st.w, fmaf(kf, st.z, z0h[L - 1]) + z0l[L - 1]);
-                const float arg = fmaf(nkg2.x, sl, zl);
+                const float zl = fmaf(kf, st.w, fmaf(kf, st.z, zh.x) + zlo.x);
+                const float arg = fmaf(nkg, sl, zl);
                 float sig;
                 if constexpr (HARD) sig = arg < 0.f ? 1.f : (arg > 0.f ? 0.f : 0.5f);
                 else sig = rcp_approx(1.0f + ex2_approx(arg));
-                acc[L - 1] += __float_as_uint(sig + 1.0f);
+                a0 += __float_as_uint(sig + 1.0f);
             }
         }
+        t0 += (unsigned long long)(a0 - (uint32_t)kn * 0x3F800000u);
+        if constexpr (NS == 2) t1 += (unsigned long long)(a1 - (uint32_t)kn * 0x3F800000u);
+    }
+}
+
+// Per surface l the ray accumulates N_l = sum_k varsigma(s_l - z_k) exactly:
+// each sigma in [0, 1] is added as the integer round(sigma * 2^23), read off
+// the bits of the FP32 sum sigma + 1 (mantissa of a number in [1, 2]), into a
+// wrapping uint32 that is flushed to a uint64 every 256 samples.  Heights in
+// shared memory and the ray's z are both taken relative to a per-surface
+// reference height ref_l, and z is carried as float-float (start and step
+// each split hi + lo), so the sigmoid argument -kg (s_l - z) is formed from
+// numbers the size of the surface relief and rounded only at its own scale.
+// The ray table guarantees every sample's cell coordinate lies in
+// [-1/2, n - 3/2), so the cell split needs no clamp.
+//
+// Surfaces are marched in groups (pairs with paired FP32 instructions, then
+// an odd last surface), each group only over the samples where one of its
+// surfaces can be transitional (see transition_window; ext = per-surface
+// min / max offsets, nullptr = every sample).  Skipped samples' contributions
+// are exact and added analytically.  Returns tot[l] = N_l * 2^23.
+template <int L, bool HARD, bool DX, typename S, bool GLOBAL = false>
+__device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int ray,
+                                              unsigned long long (&tot)[L],
+                                              const float *ext = nullptr,
+                                              unsigned long long *evaluated = nullptr)
+{
+    constexpr int NP = L / 2;
+    constexpr bool ODD = (L & 1) != 0;
+    const float4 o = pb.o4[ray], st = pb.s4[ray];
+    // what one sample below every surface adds: rcp(1 + 0) + 1 (exactly 2^23 if rcp(1) == 1)
+    const uint32_t q_one = HARD ? 0x00800000u : __float_as_uint(rcp_approx(1.0f) + 1.0f) - 0x3F800000u;
 #pragma unroll
-        for (int l = 0; l < L; ++l) tot[l] += (unsigned long long)(acc[l] - (uint32_t)kn * 0x3F800000u);
+    for (int l = 0; l < L; ++l) tot[l] = 0ull;
+#pragma unroll
+    for (int q = 0; q < NP + (ODD ? 1 : 0); ++q) {
+        const int l0 = 2 * q;
+        const int ns = (q < NP) ? 2 : 1;
+        const float zh0 = pb.kz0[(size_t)l0 * pb.n_rays + ray];
+        const float zl0 = pb.kz0[(size_t)(L + l0) * pb.n_rays + ray];
+        const float zh1 = ns == 2 ? pb.kz0[(size_t)(l0 + 1) * pb.n_rays + ray] : 0.f;
+        const float zl1 = ns == 2 ? pb.kz0[(size_t)(L + l0 + 1) * pb.n_rays + ray] : 0.f;
+        int lo = 0, he = pb.G;
+        if (ext) {
+            int a0, b0;
+            transition_window(zh0, st.z, pb.kg, ext[l0], ext[L + l0], pb.G, a0, b0);
+            if (ns == 2) {
+                int a1, b1;
+                transition_window(zh1, st.z, pb.kg, ext[l0 + 1], ext[L + l0 + 1], pb.G, a1, b1);
+                a0 = min(a0, a1);
+                b0 = max(b0, b1);
+            }
+            lo = min(a0, pb.G);
+            he = max(b0 + 1, lo);
+        }
+        if (evaluated) *evaluated += (unsigned long long)(he - lo) * ns;
+        unsigned long long t0 = (unsigned long long)lo * q_one;  // samples below the window
+        unsigned long long t1 = t0;
+        if (ns == 2)
+            march_group<L, 2, HARD, DX, S, GLOBAL>(pb, sh, o, st, l0, make_float2(zh0, zh1),
+                                                   make_float2(zl0, zl1), lo, he, t0, t1);
+        else
+            march_group<L, 1, HARD, DX, S, GLOBAL>(pb, sh, o, st, l0, make_float2(zh0, 0.f),
+                                                   make_float2(zl0, 0.f), lo, he, t0, t1);
+        tot[l0] = t0;
+        if (ns == 2) tot[l0 + 1] = t1;
     }
 }
 
@@ -524,15 +653,7 @@ __global__ void __launch_bounds__(256) k_stage_dx_global(Prob pb, HRef h)
     const int n0 = blockIdx.x * per, n1 = min(pb.N, n0 + per);
     for (int i = n0 + threadIdx.x; i < n1; i += blockDim.x) {
         alignas(16) float tmp[NL::LP];
-#pragma unroll
-        for (int l = 0; l < NL::LP; ++l) tmp[l] = 0.f;
-        const bool last = (i % pb.Q) == pb.Q - 1;
-#pragma unroll
-        for (int l = 0; l < L; ++l) {
-            const float v = (float)Hc[(size_t)l * pb.N + i] - pb.ref[l];
-            tmp[l] = v;
-            tmp[L + l] = last ? 0.f : ((float)Hc[(size_t)l * pb.N + i + 1] - pb.ref[l]) - v;
-        }
+        dx_record<H, L>(Hc, pb.N, pb.Q, pb.ref, i, tmp);
         char *d = reinterpret_cast<char *>(dst) + (size_t)i * NL::bytes;
         if constexpr (NL::bytes == 8) {
             *reinterpret_cast<uint2 *>(d) = *reinterpret_cast<const uint2 *>(tmp);
@@ -562,13 +683,18 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
         sh = reinterpret_cast<S *>(smem_raw);
         if constexpr (DX) stage_nodes_dx<Hh, L>(reinterpret_cast<float *>(sh), chain_ptr<Hh>(h, c), pb.N, pb.Q, pb.ref);
         else stage_nodes<S, Hh, L>(sh, chain_ptr<Hh>(h, c), pb.N, pb.ref);
-        __syncthreads();
     }
+    __shared__ float ext[2 * MT_MAX_L];
+    if constexpr (MODE != MODE_F64 && MODE != MODE_BF16) {
+        surface_extent<Hh, L>(chain_ptr<Hh>(h, c), pb.N, pb.ref, ext);
+    }
+    __syncthreads();
 
     const int r_begin = blockIdx.x * rays_per_block;
     const int r_end = min(r_begin + rays_per_block, pb.n_rays);
     double acc = 0.0;
     FF accf = {0.f, 0.f};
+    unsigned long long n_eval = 0ull;
     for (int ray = r_begin + threadIdx.x; ray < r_end; ray += blockDim.x) {
         const int Cp = pb.cnt[ray];
         double O, term;
@@ -584,7 +710,9 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
             acc += term;
         } else {
             unsigned long long tot[L];
-            march_ray_f32<L, HARD, DX, S, GLOBAL>(pb, sh, ray, tot);
+            march_ray_f32<L, HARD, DX, S, GLOBAL>(pb, sh, ray, tot,
+                                                  (MODE == MODE_BF16) ? nullptr : ext,
+                                                  pb.work ? &n_eval : nullptr);
             if constexpr (MODE == MODE_F32C) {
                 // O = dt (G rho_top + sum_l drho_l N_l), y = a - O / Lambda, in float-float
                 FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
@@ -623,6 +751,7 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
         if (ray_O) ray_O[(size_t)c * pb.n_rays + ray] = O;
         if (ray_term) ray_term[(size_t)c * pb.n_rays + ray] = term + poisson_K(Cp);
     }
+    if (pb.work && n_eval) atomicAdd(pb.work, n_eval);
     if constexpr (MODE == MODE_F32C) {
         accf = block_sum(accf);
         if (threadIdx.x == 0)

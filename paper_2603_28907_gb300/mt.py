@@ -81,6 +81,7 @@ SIGNATURES = {
     "mt_sync": [_vp, C.c_double],
     "mt_set_timing": [_vp, C.c_int],
     "mt_get_timing": [_vp, C.c_int, _dp, _lp, C.c_int],
+    "mt_get_work": [_vp, _dp, _dp, C.c_int],
     "mt_get_sizes": [_vp, _ip, _ip, _ip, _ip, _ip, _ip],
     "mt_server_create": [C.POINTER(C.c_void_p), C.c_int, C.c_size_t, C.c_int],
     "mt_server_submit": [_vp, C.POINTER(Request), C.POINTER(C.c_int64)],
@@ -245,6 +246,11 @@ class Context:
 
     def set_timing(self, on):
         self._ck("mt_set_timing", self.lib.mt_set_timing(self.h, int(on)))
+
+    def get_work(self, reset=False):
+        ev, tot = C.c_double(), C.c_double()
+        self._ck("mt_get_work", self.lib.mt_get_work(self.h, C.byref(ev), C.byref(tot), int(reset)))
+        return ev.value, tot.value
 
     def get_timing(self, kernel_id, reset=False):
         ms, n = C.c_double(), C.c_int64()
