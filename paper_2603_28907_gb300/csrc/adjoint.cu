@@ -133,7 +133,7 @@ k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long lo
     double ll = 0.0;
     for (int ray = r_begin + threadIdx.x; ray < r_end; ray += blockDim.x) {
         unsigned long long tot[L];
-        march_ray_f32<L, false, false, float>(pb, sh, ray, tot);
+        march_ray_f32<L, false, float>(pb, sh, ray, tot);
         double S_ = 0.0;
 #pragma unroll
         for (int l = 0; l < L; ++l) S_ = fma(pb.drho[l], (double)tot[l] * 0x1p-23, S_);

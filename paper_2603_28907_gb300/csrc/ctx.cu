@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <string>
 #include <thread>
@@ -36,10 +37,10 @@ int march_rays_per_block(const Prob &pb)
 
 size_t march_smem_bytes(const Prob &pb, int mode)
 {
-    // FP32 modes store (h, dx) per surface and node; see NodeLayoutDX
-    const bool dx = mode == MODE_F32 || mode == MODE_F32C;
-    const int es = mode == MODE_F64 ? 8 : mode == MODE_BF16 ? 2 : 4;
-    const int raw = pb.L * es * (dx ? 2 : 1);
+    // FP32 modes: one plane of (h, dx) float pairs per surface
+    if (mode == MODE_F32 || mode == MODE_F32C) return (size_t)8 * pb.L * pb.N;
+    const int es = mode == MODE_F64 ? 8 : 2;
+    const int raw = pb.L * es;
     const int bytes = raw <= 4 ? 4 : raw <= 8 ? 8 : ((raw + 15) / 16) * 16;
     return (size_t)bytes * pb.N;
 }
@@ -90,6 +91,7 @@ struct mt_ctx {
     float2 *d_dtff = nullptr, *d_aff = nullptr;
     int32_t *d_cnt = nullptr;
     int *d_flag = nullptr;
+    int *d_perm = nullptr;           // march order of the rays
 
     int C = 0;
     uint64_t seed = 0;
@@ -274,6 +276,7 @@ static void refresh_prob(mt_ctx *ctx)
         pb.ref[l] = (float)m;
     }
     pb.kz0 = ctx->d_kz0;
+    pb.perm = ctx->d_perm;
     pb.gnodes = nullptr;  // set per launch by ensure_nodes when the grid needs it
     pb.work = ctx->timing ? ctx->d_work : nullptr;
     pb.o4 = ctx->d_o4;
@@ -315,9 +318,27 @@ static mt_status build_raytab(mt_ctx *ctx)
     TRY(dalloc(ctx, &ctx->d_sd, 3 * n));
     TRY(dalloc(ctx, &ctx->d_dt, n));
     TRY(dalloc(ctx, &ctx->d_dtff, n));
+    TRY(dalloc(ctx, &ctx->d_perm, n));
     refresh_prob(ctx);
     CK(ctx, launch_raytab(ctx->pb, ctx->d_sensors, ctx->d_dirs, ctx->d_o4, ctx->d_s4, ctx->d_kz0,
                           ctx->d_od, ctx->d_sd, ctx->d_dt, ctx->d_dtff, ctx->d_flag, ctx->stream));
+    // March order: rays sorted by their vertical step per sample, then by the
+    // height of their first sample (ties by ray index).  A surface's sample
+    // window depends on those two numbers only, so a warp's 32 rays then run
+    // loops of near-equal length.
+    std::vector<float4> s4(n);
+    std::vector<float> z0(n);
+    CK(ctx, cudaMemcpyAsync(s4.data(), ctx->d_s4, n * sizeof(float4), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(z0.data(), ctx->d_kz0, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<int> perm(n);
+    for (size_t i = 0; i < n; ++i) perm[i] = (int)i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+        if (s4[a].z != s4[b].z) return s4[a].z < s4[b].z;
+        return z0[a] < z0[b];
+    });
+    CK(ctx, cudaMemcpyAsync(ctx->d_perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
     return MT_OK;
 }
 
@@ -610,6 +631,7 @@ mt_status mt_destroy(mt_ctx *ctx)
     dfree(ctx->d_sumK);
     dfree(ctx->d_cnt);
     dfree(ctx->d_flag);
+    dfree(ctx->d_perm);
     dfree(ctx->d_step);
     dfree(ctx->d_work);
     if (ctx->d_part) cudaFree(ctx->d_part);

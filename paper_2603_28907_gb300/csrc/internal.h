@@ -2,9 +2,9 @@
 //
 // The problem descriptor Prob is passed by value to every kernel.  Layouts:
 //   heights (HBM)  [chain][layer][row][col], column fastest (C ABI layout);
-//   heights (smem) node-major [row][col][layer], each node padded to a
-//                  16/8/4-byte vector so one or two vector loads fetch every
-//                  surface of a node;
+//   heights (smem) FP32 modes: per-surface planes of (h - ref_l, dx) pairs,
+//                  [layer][row][col]; FP64 / BF16: node-major [row][col][layer],
+//                  each node padded to a 16/8/4-byte vector;
 //   ray table      structure of arrays over ray = sensor * P + pixel.
 #pragma once
 
@@ -49,7 +49,9 @@ struct Prob {
     unsigned long long *work;  // timing mode: [0] surface-samples evaluated by the FP32
                                // march (the rest were exactly saturated), else nullptr
     float *gnodes;             // grids too large for shared memory: per-chain (h, dx)
-                               // node records in HBM, [chain][N][record]; else nullptr
+                               // planes in HBM, [chain][l][node] float2; else nullptr
+    const int *perm;           // march order of the rays (ray table sorted by vertical
+                               // step, then start height); nullptr = ray order
     float2 grho_ff;            // float-float of G * rho_top
     float2 invL_ff;            // float-float of 1 / Lambda
 };

@@ -92,57 +92,24 @@ __device__ __forceinline__ void stage_nodes(S *sh, const H *Hc, int N, const flo
     }
 }
 
-// FP32 node records holding, per surface, the height offset h - ref_l and
-// its difference to the next node in x, dx = h(r, c+1) - h(r, c) (0 in the
-// last column): a cell then needs the records of its two left corners only.
-// Surfaces are grouped in pairs, each pair one 16-byte slot
-// {h_2q, h_2q+1, dx_2q, dx_2q+1}; an odd last surface takes an 8-byte slot
-// {h, dx}; the record is padded to a multiple of 16 bytes.
-template <int L> struct NodeLayoutDX {
-    static constexpr int NP = L / 2;
-    static constexpr int raw = NP * 16 + (L & 1) * 8;
-    static constexpr int bytes = raw <= 8 ? 8 : ((raw + 15) / 16) * 16;
-    static constexpr int LP = bytes / 4;
-};
-
-template <typename H, int L>
-__device__ __forceinline__ void dx_record(const H *Hc, int N, int Q, const float *ref, int i,
-                                          float (&tmp)[NodeLayoutDX<L>::LP])
+// FP32 node records, one plane per surface: plane l holds for every node
+// {h - ref_l, dx} with dx = h(r, c+1) - h(r, c) (0 in the last column), so a
+// cell needs the 8-byte records of its two left corners only.  A chain's
+// planes take 8 L N bytes, [l][node].
+template <typename H>
+__device__ __forceinline__ float2 dx_record(const H *Hc, int N, int Q, float ref, int l, int i)
 {
-    constexpr int NP = L / 2;
-#pragma unroll
-    for (int j = 0; j < NodeLayoutDX<L>::LP; ++j) tmp[j] = 0.f;
-    const bool last = (i % Q) == Q - 1;
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-        const float h = (float)Hc[(size_t)l * N + i] - ref[l];
-        const float d = last ? 0.f : ((float)Hc[(size_t)l * N + i + 1] - ref[l]) - h;
-        const int q = l / 2;
-        if (q < NP) {
-            tmp[4 * q + (l & 1)] = h;
-            tmp[4 * q + 2 + (l & 1)] = d;
-        } else {
-            tmp[4 * NP] = h;
-            tmp[4 * NP + 1] = d;
-        }
-    }
+    const float h = (float)Hc[(size_t)l * N + i] - ref;
+    const float d = (i % Q) == Q - 1 ? 0.f : ((float)Hc[(size_t)l * N + i + 1] - ref) - h;
+    return make_float2(h, d);
 }
 
 template <typename H, int L>
-__device__ __forceinline__ void stage_nodes_dx(float *sh, const H *Hc, int N, int Q, const float *ref)
+__device__ __forceinline__ void stage_planes_dx(float2 *sh, const H *Hc, int N, int Q, const float *ref)
 {
-    using NL = NodeLayoutDX<L>;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        alignas(16) float tmp[NL::LP];
-        dx_record<H, L>(Hc, N, Q, ref, i, tmp);
-        char *dst = reinterpret_cast<char *>(sh) + (size_t)i * NL::bytes;
-        if constexpr (NL::bytes == 8) {
-            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(tmp);
-        } else {
 #pragma unroll
-            for (int q = 0; q < NL::bytes / 16; ++q)
-                reinterpret_cast<uint4 *>(dst)[q] = reinterpret_cast<const uint4 *>(tmp)[q];
-        }
+        for (int l = 0; l < L; ++l) sh[(size_t)l * N + i] = dx_record<H>(Hc, N, Q, ref[l], l, i);
     }
 }
 
@@ -227,20 +194,6 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// Split a cell coordinate shifted by -1/2 (gm = g - 1/2, g in [0, n_nodes-1])
-// into the cell index n and the centred offset f = g - n - 1/2 in [-1/2, 1/2]:
-// rounding gm to the nearest integer by adding 1.5*2^23 picks a cell whose
-// closed interval holds g, with FP32-pipe operations only.  gm is clamped to
-// [-1/2, hi] where hi, a few ulps below n_nodes - 3/2, keeps n <= n_nodes - 2.
-__device__ __forceinline__ int cell_split(float gm, float hi, float &f)
-{
-    const float M = 12582912.0f;  // 1.5 * 2^23
-    gm = fminf(fmaxf(gm, -0.5f), hi);
-    const float t = gm + M;
-    const float n = t - M;
-    f = gm - n;
-    return __float_as_int(t) - 0x4B400000;
-}
 
 // e^y - 1 - y in FP32 without cancellation (Taylor series for |y| < 1/2).
 __device__ __forceinline__ float g_f32(float y)
@@ -296,6 +249,82 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
+// Corner heights of one surface group at a node: a pair (NS = 2) or the odd
+// last surface (NS = 1), from node-major records.
+template <int L, int NS, typename S, bool GLOBAL>
+__device__ __forceinline__ float2 load_group(const S *sh, int node, int l0)
+{
+    using NL = NodeLayout<S, L>;
+    const S *rec = reinterpret_cast<const S *>(reinterpret_cast<const char *>(sh) + (size_t)node * NL::bytes);
+    return make_float2(to_f(rec[l0]), NS == 2 ? to_f(rec[l0 + 1]) : 0.f);
+}
+
+// March one surface group over every sample of a ray from node-major
+// records (BF16 mode and the adjoint's forward pass) and add its integer
+// indicator sums (units 2^-23) to t0 (surface l0) and t1 (l0 + 1).
+template <int L, int NS, bool HARD, typename S>
+__device__ __forceinline__ void march_group(const Prob &pb, const S *sh, float4 o, float4 st,
+                                            int l0, float2 zh, float2 zlo,
+                                            unsigned long long &t0, unsigned long long &t1)
+{
+    const float M = 12582912.0f;  // 1.5 * 2^23: adding it rounds to an integer
+    const int Q = pb.Q;
+    const float nkg = -pb.kg;
+    const float2 one2 = f2(1.0f), nkg2 = f2(nkg), szh2 = f2(st.z), szl2 = f2(st.w);
+    float2 h00 = f2(0.f), h01 = f2(0.f), h10 = f2(0.f), h11 = f2(0.f);
+    int cur = -1;
+    float kf = 0.0f;
+    for (int k0 = 0; k0 < pb.G; k0 += 256) {
+        const int kn = min(256, pb.G - k0);
+        uint32_t a0 = 0u, a1 = 0u;
+        for (int k = 0; k < kn; ++k, kf += 1.0f) {
+            const float gx = fmaf(kf, st.x, o.x), gy = fmaf(kf, st.y, o.y);
+            const float tx = gx + M, ty = gy + M;
+            const float fxs = (gx - (tx - M)) + 0.5f, fys = (gy - (ty - M)) + 0.5f;  // in [0, 1]
+            const int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
+            if (node != cur) {
+                cur = node;
+                h00 = load_group<L, NS, S, false>(sh, node, l0);
+                h01 = load_group<L, NS, S, false>(sh, node + 1, l0);
+                h10 = load_group<L, NS, S, false>(sh, node + Q, l0);
+                h11 = load_group<L, NS, S, false>(sh, node + Q + 1, l0);
+            }
+            if constexpr (NS == 2) {
+                const float2 fx = f2(fxs), fy = f2(fys), kf2 = f2(kf);
+                const float2 omfx = f2(1.0f - fxs), omfy = f2(1.0f - fys);
+                const float2 a = fma2(fx, h01, mul2(omfx, h00));
+                const float2 b = fma2(fx, h11, mul2(omfx, h10));
+                const float2 sl = fma2(fy, b, mul2(omfy, a));
+                const float2 zl = fma2(kf2, szl2, add2(fma2(kf2, szh2, zh), zlo));
+                const float2 arg = fma2(nkg2, sl, zl);                  // -kg (s_l - z)
+                float2 sg;
+                if constexpr (HARD) {
+                    sg.x = arg.x < 0.f ? 1.f : (arg.x > 0.f ? 0.f : 0.5f);
+                    sg.y = arg.y < 0.f ? 1.f : (arg.y > 0.f ? 0.f : 0.5f);
+                } else {
+                    const float2 d = add2(make_float2(ex2_approx(arg.x), ex2_approx(arg.y)), one2);
+                    sg = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+                }
+                const float2 t = add2(sg, one2);
+                a0 += __float_as_uint(t.x);
+                a1 += __float_as_uint(t.y);
+            } else {
+                const float a = fmaf(fxs, h01.x, (1.0f - fxs) * h00.x);
+                const float b = fmaf(fxs, h11.x, (1.0f - fxs) * h10.x);
+                const float sl = fmaf(fys, b, (1.0f - fys) * a);
+                const float zl = fmaf(kf, st.w, fmaf(kf, st.z, zh.x) + zlo.x);
+                const float arg = fmaf(nkg, sl, zl);
+                float sig;
+                if constexpr (HARD) sig = arg < 0.f ? 1.f : (arg > 0.f ? 0.f : 0.5f);
+                else sig = rcp_approx(1.0f + ex2_approx(arg));
+                a0 += __float_as_uint(sig + 1.0f);
+            }
+        }
+        t0 += (unsigned long long)(a0 - (uint32_t)kn * 0x3F800000u);
+        if constexpr (NS == 2) t1 += (unsigned long long)(a1 - (uint32_t)kn * 0x3F800000u);
+    }
+}
+
 // Per surface l the ray accumulates N_l = sum_k varsigma(s_l - z_k) exactly:
 // each sigma in [0, 1] is added as the integer round(sigma * 2^23), read off
 // the bits of the FP32 sum sigma + 1 (mantissa of a number in [1, 2]), into a
@@ -305,8 +334,115 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 // each split hi + lo), so the sigmoid argument -kg (s_l - z) is formed from
 // numbers the size of the surface relief and rounded only at its own scale.
 // The ray table guarantees every sample's cell coordinate lies in
-// [-1/2, n - 3/2), so the cell split needs no clamp.  Returns
+// [-1/2, n - 3/2), so the cell split needs no clamp.  Surfaces are marched in
+// pairs with paired FP32 instructions, every sample.  Returns
 // tot[l] = N_l * 2^23.
+template <int L, bool HARD, typename S>
+__device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int ray,
+                                              unsigned long long (&tot)[L])
+{
+    constexpr int NP = L / 2;
+    constexpr bool ODD = (L & 1) != 0;
+    const float4 o = pb.o4[ray], st = pb.s4[ray];
+#pragma unroll
+    for (int q = 0; q < NP + (ODD ? 1 : 0); ++q) {
+        const int l0 = 2 * q;
+        const int ns = (q < NP) ? 2 : 1;
+        const float zh0 = pb.kz0[(size_t)l0 * pb.n_rays + ray];
+        const float zl0 = pb.kz0[(size_t)(L + l0) * pb.n_rays + ray];
+        const float zh1 = ns == 2 ? pb.kz0[(size_t)(l0 + 1) * pb.n_rays + ray] : 0.f;
+        const float zl1 = ns == 2 ? pb.kz0[(size_t)(L + l0 + 1) * pb.n_rays + ray] : 0.f;
+        unsigned long long t0 = 0ull, t1 = 0ull;
+        if (ns == 2)
+            march_group<L, 2, HARD, S>(pb, sh, o, st, l0, make_float2(zh0, zh1), make_float2(zl0, zl1),
+                                       t0, t1);
+        else
+            march_group<L, 1, HARD, S>(pb, sh, o, st, l0, make_float2(zh0, 0.f), make_float2(zl0, 0.f),
+                                       t0, t1);
+        tot[l0] = t0;
+        if (ns == 2) tot[l0 + 1] = t1;
+    }
+}
+
+// ---------------------------------------------------------------- FP32 march, (h, dx) planes
+// One surface along one ray, two consecutive samples per step: lane .x of
+// every paired FP32 instruction carries sample k, lane .y sample k + 1.  Each
+// lane's arithmetic is that of one sample: position g = o + k gs, cell split,
+// bilinear height from the two left corners' (h, dx) records, float-float
+// z, sigmoid argument, 2^arg, reciprocal, sigma + 1.  The corner records of
+// both samples are cached and reloaded when either sample enters a new cell.
+template <bool HARD, bool GLOBAL>
+__device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, float2 kf2, float2 ox2, float2 oy2,
+                                          float2 sx2, float2 sy2, float2 szh2, float2 szl2,
+                                          float2 zh2, float2 zl2, float2 nkg2, int &curA, int &curB,
+                                          float2 &h00, float2 &d0, float2 &h10, float2 &d1)
+{
+    const float2 M2 = f2(12582912.0f);  // 1.5 * 2^23: adding it rounds to an integer
+    const float2 gx = fma2(kf2, sx2, ox2), gy = fma2(kf2, sy2, oy2);
+    const float2 tx = add2(gx, M2), ty = add2(gy, M2);
+    const float2 fx = add2(fma2(add2(tx, f2(-12582912.0f)), f2(-1.0f), gx), f2(0.5f));  // in [0, 1]
+    const float2 fy = add2(fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy), f2(0.5f));
+    const int nA = (__float_as_int(ty.x) - 0x4B400000) * Q + (__float_as_int(tx.x) - 0x4B400000);
+    const int nB = (__float_as_int(ty.y) - 0x4B400000) * Q + (__float_as_int(tx.y) - 0x4B400000);
+    if (nA != curA || nB != curB) {
+        curA = nA;
+        curB = nB;
+        const float2 a0 = GLOBAL ? __ldg(pl + nA) : pl[nA], a1 = GLOBAL ? __ldg(pl + nA + Q) : pl[nA + Q];
+        const float2 b0 = GLOBAL ? __ldg(pl + nB) : pl[nB], b1 = GLOBAL ? __ldg(pl + nB + Q) : pl[nB + Q];
+        h00 = make_float2(a0.x, b0.x);
+        d0 = make_float2(a0.y, b0.y);
+        h10 = make_float2(a1.x, b1.x);
+        d1 = make_float2(a1.y, b1.y);
+    }
+    const float2 a = fma2(fx, d0, h00);                                 // row r0
+    const float2 b = fma2(fx, d1, h10);                                 // row r0 + 1
+    const float2 sl = fma2(fy, fma2(a, f2(-1.0f), b), a);               // s_l - ref_l
+    const float2 zl = fma2(kf2, szl2, add2(fma2(kf2, szh2, zh2), zl2));
+    const float2 arg = fma2(nkg2, sl, zl);                              // -kg (s_l - z)
+    float2 sg;
+    if constexpr (HARD) {
+        sg.x = arg.x < 0.f ? 1.f : (arg.x > 0.f ? 0.f : 0.5f);
+        sg.y = arg.y < 0.f ? 1.f : (arg.y > 0.f ? 0.f : 0.5f);
+    } else {
+        const float2 e = add2(make_float2(ex2_approx(arg.x), ex2_approx(arg.y)), f2(1.0f));
+        sg = make_float2(rcp_approx(e.x), rcp_approx(e.y));
+    }
+    return add2(sg, f2(1.0f));
+}
+
+// Samples [lo, he) of one surface; adds the integer indicator sum (units
+// 2^-23) to t.  An odd count ends with one sample evaluated in both lanes and
+// counted once.
+template <bool HARD, bool GLOBAL>
+__device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, float4 o, float4 st,
+                                                 float nkg, float zh, float zl, int lo, int he,
+                                                 unsigned long long &t)
+{
+    const float2 ox2 = f2(o.x), oy2 = f2(o.y), sx2 = f2(st.x), sy2 = f2(st.y);
+    const float2 szh2 = f2(st.z), szl2 = f2(st.w), zh2 = f2(zh), zl2 = f2(zl), nkg2 = f2(nkg);
+    float2 h00 = f2(0.f), d0 = f2(0.f), h10 = f2(0.f), d1 = f2(0.f);
+    int curA = -1, curB = -1;
+    float2 kf2 = make_float2((float)lo, (float)lo + 1.0f);
+    const int np = (he - lo) >> 1;
+    for (int j0 = 0; j0 < np; j0 += 128) {
+        const int jn = min(128, np - j0);
+        uint32_t acc = 0u;
+        for (int j = 0; j < jn; ++j) {
+            const float2 v = dx_pair<HARD, GLOBAL>(pl, Q, kf2, ox2, oy2, sx2, sy2, szh2, szl2, zh2, zl2,
+                                                   nkg2, curA, curB, h00, d0, h10, d1);
+            acc += __float_as_uint(v.x) + __float_as_uint(v.y);
+            kf2 = add2(kf2, f2(2.0f));
+        }
+        t += (unsigned long long)(acc - (uint32_t)(2 * jn) * 0x3F800000u);
+    }
+    if ((he - lo) & 1) {
+        kf2 = f2((float)(he - 1));
+        const float2 v = dx_pair<HARD, GLOBAL>(pl, Q, kf2, ox2, oy2, sx2, sy2, szh2, szl2, zh2, zl2,
+                                               nkg2, curA, curB, h00, d0, h10, d1);
+        t += (unsigned long long)(__float_as_uint(v.x) - 0x3F800000u);
+    }
+}
+
 // Samples whose sigmoid argument is at least kSat (log2 units) from zero give
 // sigma + 1 == exactly 1.0f or exactly rcp(1) + 1 in FP32 (the argument of
 // 2^arg, or 2^-arg, is far past the 2^-24 rounding limit), so their integer
@@ -344,180 +480,39 @@ __device__ __forceinline__ void transition_window(float z0, float dz, float kg, 
     hi = min(hi, G - 1);
 }
 
-// Corner data of one surface group at a node: a pair (NS = 2) or the odd
-// last surface (NS = 1).  DX records give {h, dx}; plain records give h only.
-template <int L, int NS, bool DX, typename S, bool GLOBAL>
-__device__ __forceinline__ void load_group(const S *sh, int node, int l0, float2 &h, float2 &dx)
+// The FP32 modes' march of one ray: per surface l, the exact integer sum
+// N_l = sum_k varsigma(s_l - z_k) * 2^23 (see march_ray_f32 for the
+// arithmetic), computed over the samples where surface l can be
+// transitional (transition_window with ext = per-surface min / max offsets);
+// the other samples' contributions are exact and added analytically (one
+// sample below the surface adds rcp(1) + 1 - 1 in units of 2^-23, one above
+// adds 0).  A window of odd length is widened by one saturated sample where
+// the ray has one, so that samples go in pairs.  emit(l, N_l * 2^23) is
+// called for l = 0 .. L-1 in order.
+template <int L, bool HARD, bool GLOBAL, typename Emit>
+__device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *planes, int ray,
+                                             const float *ext, unsigned long long *evaluated,
+                                             Emit &&emit)
 {
-    if constexpr (DX) {
-        using NL = NodeLayoutDX<L>;
-        const char *rec = reinterpret_cast<const char *>(sh) + (size_t)node * NL::bytes;
-        if constexpr (NS == 2) {
-            const float4 *p = reinterpret_cast<const float4 *>(rec + (l0 / 2) * 16);
-            const float4 v = GLOBAL ? __ldg(p) : *p;
-            h = make_float2(v.x, v.y);
-            dx = make_float2(v.z, v.w);
-        } else {
-            const float2 *p = reinterpret_cast<const float2 *>(rec + (L / 2) * 16);
-            const float2 v = GLOBAL ? __ldg(p) : *p;
-            h = make_float2(v.x, 0.f);
-            dx = make_float2(v.y, 0.f);
-        }
-    } else {
-        using NL = NodeLayout<S, L>;
-        const S *rec = reinterpret_cast<const S *>(reinterpret_cast<const char *>(sh) + (size_t)node * NL::bytes);
-        h.x = to_f(rec[l0]);
-        h.y = NS == 2 ? to_f(rec[l0 + 1]) : 0.f;
-        dx = make_float2(0.f, 0.f);
-    }
-}
-
-// March one surface group over its sample window [lo, he) and add its
-// integer indicator sums (units 2^-23) to t0 (surface l0) and t1 (l0 + 1).
-template <int L, int NS, bool HARD, bool DX, typename S, bool GLOBAL>
-__device__ __forceinline__ void march_group(const Prob &pb, const S *sh, float4 o, float4 st,
-                                            int l0, float2 zh, float2 zlo, int lo, int he,
-                                            unsigned long long &t0, unsigned long long &t1)
-{
-    const float M = 12582912.0f;  // 1.5 * 2^23: adding it rounds to an integer
-    const int Q = pb.Q;
-    const float nkg = -pb.kg;
-    const float2 one2 = f2(1.0f), nkg2 = f2(nkg), szh2 = f2(st.z), szl2 = f2(st.w);
-    float2 h00 = f2(0.f), h01 = f2(0.f), h10 = f2(0.f), h11 = f2(0.f);
-    int cur = -1;
-    float kf = (float)lo;
-    for (int k0 = lo; k0 < he; k0 += 256) {
-        const int kn = min(256, he - k0);
-        uint32_t a0 = 0u, a1 = 0u;
-        for (int k = 0; k < kn; ++k, kf += 1.0f) {
-            const float gx = fmaf(kf, st.x, o.x), gy = fmaf(kf, st.y, o.y);
-            const float tx = gx + M, ty = gy + M;
-            const float fxs = (gx - (tx - M)) + 0.5f, fys = (gy - (ty - M)) + 0.5f;  // in [0, 1]
-            const int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
-            if (node != cur) {
-                cur = node;
-                if constexpr (DX) {
-                    load_group<L, NS, DX, S, GLOBAL>(sh, node, l0, h00, h01);      // h, dx of row r0
-                    load_group<L, NS, DX, S, GLOBAL>(sh, node + Q, l0, h10, h11);  // h, dx of row r0+1
-                } else {
-                    float2 dum;
-                    load_group<L, NS, DX, S, GLOBAL>(sh, node, l0, h00, dum);
-                    load_group<L, NS, DX, S, GLOBAL>(sh, node + 1, l0, h01, dum);
-                    load_group<L, NS, DX, S, GLOBAL>(sh, node + Q, l0, h10, dum);
-                    load_group<L, NS, DX, S, GLOBAL>(sh, node + Q + 1, l0, h11, dum);
-                }
-            }
-            if constexpr (NS == 2) {
-                const float2 fx = f2(fxs), fy = f2(fys), kf2 = f2(kf);
-                float2 a, b, sl;
-                if constexpr (DX) {
-                    a = fma2(fx, h01, h00);                             // row r0
-                    b = fma2(fx, h11, h10);                             // row r0 + 1
-                    sl = fma2(fy, fma2(a, f2(-1.0f), b), a);            // s_l - ref_l
-                } else {
-                    const float2 omfx = f2(1.0f - fxs), omfy = f2(1.0f - fys);
-                    a = fma2(fx, h01, mul2(omfx, h00));
-                    b = fma2(fx, h11, mul2(omfx, h10));
-                    sl = fma2(fy, b, mul2(omfy, a));
-                }
-                const float2 zl = fma2(kf2, szl2, add2(fma2(kf2, szh2, zh), zlo));
-                const float2 arg = fma2(nkg2, sl, zl);                  // -kg (s_l - z)
-                float2 sg;
-                if constexpr (HARD) {
-                    sg.x = arg.x < 0.f ? 1.f : (arg.x > 0.f ? 0.f : 0.5f);
-                    sg.y = arg.y < 0.f ? 1.f : (arg.y > 0.f ? 0.f : 0.5f);
-                } else {
-                    const float2 d = add2(make_float2(ex2_approx(arg.x), ex2_approx(arg.y)), one2);
-                    sg = make_float2(rcp_approx(d.x), rcp_approx(d.y));
-                }
-                const float2 t = add2(sg, one2);
-                a0 += __float_as_uint(t.x);
-                a1 += __float_as_uint(t.y);
-            } else {
-                float sl;
-                if constexpr (DX) {
-                    const float a = fmaf(fxs, h01.x, h00.x);
-                    const float b = fmaf(fxs, h11.x, h10.x);
-                    sl = fmaf(fys, b - a, a);
-                } else {
-                    const float a = fmaf(fxs, h01.x, (1.0f - fxs) * h00.x);
-                    const float b = fmaf(fxs, h11.x, (1.0f - fxs) * h10.x);
-                    sl = fmaf(fys, b, (1.0f - fys) * a);
-                }
-                const float zl = fmaf(kf, st.w, fmaf(kf, st.z, zh.x) + zlo.x);
-                const float arg = fmaf(nkg, sl, zl);
-                float sig;
-                if constexpr (HARD) sig = arg < 0.f ? 1.f : (arg > 0.f ? 0.f : 0.5f);
-                else sig = rcp_approx(1.0f + ex2_approx(arg));
-                a0 += __float_as_uint(sig + 1.0f);
-            }
-        }
-        t0 += (unsigned long long)(a0 - (uint32_t)kn * 0x3F800000u);
-        if constexpr (NS == 2) t1 += (unsigned long long)(a1 - (uint32_t)kn * 0x3F800000u);
-    }
-}
-
-// Per surface l the ray accumulates N_l = sum_k varsigma(s_l - z_k) exactly:
-// each sigma in [0, 1] is added as the integer round(sigma * 2^23), read off
-// the bits of the FP32 sum sigma + 1 (mantissa of a number in [1, 2]), into a
-// wrapping uint32 that is flushed to a uint64 every 256 samples.  Heights in
-// shared memory and the ray's z are both taken relative to a per-surface
-// reference height ref_l, and z is carried as float-float (start and step
-// each split hi + lo), so the sigmoid argument -kg (s_l - z) is formed from
-// numbers the size of the surface relief and rounded only at its own scale.
-// The ray table guarantees every sample's cell coordinate lies in
-// [-1/2, n - 3/2), so the cell split needs no clamp.
-//
-// Surfaces are marched in groups (pairs with paired FP32 instructions, then
-// an odd last surface), each group only over the samples where one of its
-// surfaces can be transitional (see transition_window; ext = per-surface
-// min / max offsets, nullptr = every sample).  Skipped samples' contributions
-// are exact and added analytically.  Returns tot[l] = N_l * 2^23.
-template <int L, bool HARD, bool DX, typename S, bool GLOBAL = false>
-__device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int ray,
-                                              unsigned long long (&tot)[L],
-                                              const float *ext = nullptr,
-                                              unsigned long long *evaluated = nullptr)
-{
-    constexpr int NP = L / 2;
-    constexpr bool ODD = (L & 1) != 0;
     const float4 o = pb.o4[ray], st = pb.s4[ray];
-    // what one sample below every surface adds: rcp(1 + 0) + 1 (exactly 2^23 if rcp(1) == 1)
     const uint32_t q_one = HARD ? 0x00800000u : __float_as_uint(rcp_approx(1.0f) + 1.0f) - 0x3F800000u;
-#pragma unroll
-    for (int l = 0; l < L; ++l) tot[l] = 0ull;
-#pragma unroll
-    for (int q = 0; q < NP + (ODD ? 1 : 0); ++q) {
-        const int l0 = 2 * q;
-        const int ns = (q < NP) ? 2 : 1;
-        const float zh0 = pb.kz0[(size_t)l0 * pb.n_rays + ray];
-        const float zl0 = pb.kz0[(size_t)(L + l0) * pb.n_rays + ray];
-        const float zh1 = ns == 2 ? pb.kz0[(size_t)(l0 + 1) * pb.n_rays + ray] : 0.f;
-        const float zl1 = ns == 2 ? pb.kz0[(size_t)(L + l0 + 1) * pb.n_rays + ray] : 0.f;
-        int lo = 0, he = pb.G;
-        if (ext) {
-            int a0, b0;
-            transition_window(zh0, st.z, pb.kg, ext[l0], ext[L + l0], pb.G, a0, b0);
-            if (ns == 2) {
-                int a1, b1;
-                transition_window(zh1, st.z, pb.kg, ext[l0 + 1], ext[L + l0 + 1], pb.G, a1, b1);
-                a0 = min(a0, a1);
-                b0 = max(b0, b1);
-            }
-            lo = min(a0, pb.G);
-            he = max(b0 + 1, lo);
+    const int G = pb.G;
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+        const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
+        const float zl = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
+        int lo, hi;
+        transition_window(zh, st.z, pb.kg, ext[l], ext[L + l], G, lo, hi);
+        lo = min(lo, G);
+        int he = max(hi + 1, lo);
+        if ((he - lo) & 1) {
+            if (he < G) ++he;
+            else if (lo > 0) --lo;
         }
-        if (evaluated) *evaluated += (unsigned long long)(he - lo) * ns;
-        unsigned long long t0 = (unsigned long long)lo * q_one;  // samples below the window
-        unsigned long long t1 = t0;
-        if (ns == 2)
-            march_group<L, 2, HARD, DX, S, GLOBAL>(pb, sh, o, st, l0, make_float2(zh0, zh1),
-                                                   make_float2(zl0, zl1), lo, he, t0, t1);
-        else
-            march_group<L, 1, HARD, DX, S, GLOBAL>(pb, sh, o, st, l0, make_float2(zh0, 0.f),
-                                                   make_float2(zl0, 0.f), lo, he, t0, t1);
-        tot[l0] = t0;
-        if (ns == 2) tot[l0 + 1] = t1;
+        if (evaluated) *evaluated += (unsigned long long)(he - lo);
+        unsigned long long t = (unsigned long long)lo * q_one;  // samples below the window
+        march_surface_dx<HARD, GLOBAL>(planes + (size_t)l * pb.N, pb.Q, o, st, -pb.kg, zh, zl, lo, he, t);
+        emit(l, t);
     }
 }
 
@@ -631,40 +626,33 @@ __device__ __forceinline__ FF block_sum(FF v)
 }
 
 // ---------------------------------------------------------------- kernel
-// FP32 and float-float modes use (h, dx) node records and 1024-thread CTAs
-// (one per SM with the scenario's 128 KB of records); BF16 keeps 4-corner
-// records to halve shared memory; FP64 has its own march.
+// FP32 and float-float modes use per-surface (h, dx) planes and 1024-thread
+// CTAs (one per SM with the scenario's 128 KB of records); BF16 keeps
+// 4-corner node records to halve shared memory; FP64 has its own march.
 template <int MODE, int L> struct MarchCfg {
     static constexpr bool DX = MODE == MODE_F32 || MODE == MODE_F32C;
-    static constexpr int THREADS = DX ? (L <= 4 ? 1024 : 512) : 256;  // >= 5 surfaces need > 64 registers
+    static constexpr int THREADS = DX ? 1024 : 256;
 };
 
-// Records of every chain into HBM for grids too large for shared memory
-// (one block of threads per chain and node slice).
+// (h, dx) planes of every chain into HBM for grids too large for shared
+// memory, [chain][l][node] (one block of threads per chain and node slice).
 template <typename H, int L>
 __global__ void __launch_bounds__(256) k_stage_dx_global(Prob pb, HRef h)
 {
-    using NL = NodeLayoutDX<L>;
     const int c = blockIdx.y;
-    float *dst = pb.gnodes + (size_t)c * pb.N * NL::LP;
+    float2 *dst = reinterpret_cast<float2 *>(pb.gnodes) + (size_t)c * L * pb.N;
     const H *Hc = chain_ptr<H>(h, c);
-    // stage_nodes_dx strides by blockDim over all nodes; split nodes over blocks
     const int per = (pb.N + gridDim.x - 1) / gridDim.x;
     const int n0 = blockIdx.x * per, n1 = min(pb.N, n0 + per);
     for (int i = n0 + threadIdx.x; i < n1; i += blockDim.x) {
-        alignas(16) float tmp[NL::LP];
-        dx_record<H, L>(Hc, pb.N, pb.Q, pb.ref, i, tmp);
-        char *d = reinterpret_cast<char *>(dst) + (size_t)i * NL::bytes;
-        if constexpr (NL::bytes == 8) {
-            *reinterpret_cast<uint2 *>(d) = *reinterpret_cast<const uint2 *>(tmp);
-        } else {
 #pragma unroll
-            for (int q = 0; q < NL::bytes / 16; ++q)
-                reinterpret_cast<uint4 *>(d)[q] = reinterpret_cast<const uint4 *>(tmp)[q];
-        }
+        for (int l = 0; l < L; ++l) dst[(size_t)l * pb.N + i] = dx_record<H>(Hc, pb.N, pb.Q, pb.ref[l], l, i);
     }
 }
 
+// One CTA = one chain x rays_per_block ray slots.  Slot i marches ray
+// perm[i]: the ray table orders rays by their vertical step so that the
+// 32 rays of a warp have near-equal sample windows.
 template <int MODE, int L, bool HARD, bool GLOBAL = false>
 __global__ void __launch_bounds__(MarchCfg<MODE, L>::THREADS)
 k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, double *ray_term)
@@ -675,19 +663,21 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
     constexpr bool DX = MarchCfg<MODE, L>::DX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int c = blockIdx.y;
-    S *sh;
-    if constexpr (GLOBAL) {
-        // node records were written to HBM by k_stage_dx_global
-        sh = reinterpret_cast<S *>(pb.gnodes + (size_t)c * pb.N * NodeLayoutDX<L>::LP);
+    S *sh = reinterpret_cast<S *>(smem_raw);
+    const float2 *planes = nullptr;
+    if constexpr (DX) {
+        if constexpr (GLOBAL) {
+            // planes were written to HBM by k_stage_dx_global
+            planes = reinterpret_cast<const float2 *>(pb.gnodes) + (size_t)c * L * pb.N;
+        } else {
+            stage_planes_dx<Hh, L>(reinterpret_cast<float2 *>(smem_raw), chain_ptr<Hh>(h, c), pb.N, pb.Q, pb.ref);
+            planes = reinterpret_cast<const float2 *>(smem_raw);
+        }
     } else {
-        sh = reinterpret_cast<S *>(smem_raw);
-        if constexpr (DX) stage_nodes_dx<Hh, L>(reinterpret_cast<float *>(sh), chain_ptr<Hh>(h, c), pb.N, pb.Q, pb.ref);
-        else stage_nodes<S, Hh, L>(sh, chain_ptr<Hh>(h, c), pb.N, pb.ref);
+        stage_nodes<S, Hh, L>(sh, chain_ptr<Hh>(h, c), pb.N, (MODE == MODE_F64) ? nullptr : pb.ref);
     }
     __shared__ float ext[2 * MT_MAX_L];
-    if constexpr (MODE != MODE_F64 && MODE != MODE_BF16) {
-        surface_extent<Hh, L>(chain_ptr<Hh>(h, c), pb.N, pb.ref, ext);
-    }
+    if constexpr (DX) surface_extent<Hh, L>(chain_ptr<Hh>(h, c), pb.N, pb.ref, ext);
     __syncthreads();
 
     const int r_begin = blockIdx.x * rays_per_block;
@@ -695,7 +685,8 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
     double acc = 0.0;
     FF accf = {0.f, 0.f};
     unsigned long long n_eval = 0ull;
-    for (int ray = r_begin + threadIdx.x; ray < r_end; ray += blockDim.x) {
+    for (int slot = r_begin + threadIdx.x; slot < r_end; slot += blockDim.x) {
+        const int ray = pb.perm ? pb.perm[slot] : slot;
         const int Cp = pb.cnt[ray];
         double O, term;
         if constexpr (MODE == MODE_F64) {
@@ -708,45 +699,49 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
                 term = -pb.I0 * exp(-O * pb.inv_Lambda);
             }
             acc += term;
-        } else {
-            unsigned long long tot[L];
-            march_ray_f32<L, HARD, DX, S, GLOBAL>(pb, sh, ray, tot,
-                                                  (MODE == MODE_BF16) ? nullptr : ext,
-                                                  pb.work ? &n_eval : nullptr);
-            if constexpr (MODE == MODE_F32C) {
-                // O = dt (G rho_top + sum_l drho_l N_l), y = a - O / Lambda, in float-float
-                FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
-#pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    const FF n = ff_two_sum((float)(uint32_t)(tot[l] >> 20) * 1048576.0f * 0x1p-23f,
-                                            (float)(uint32_t)(tot[l] & 0xFFFFFu) * 0x1p-23f);
-                    Sff = ff_add(Sff, ff_mul(FF{pb.drho_ff[l].x, pb.drho_ff[l].y}, n));
-                }
-                const FF Off = ff_mul(FF{pb.dt_ff[ray].x, pb.dt_ff[ray].y}, Sff);
-                const FF OL = ff_mul(Off, FF{pb.invL_ff.x, pb.invL_ff.y});
-                float t32;
-                if (Cp > 0) {
-                    const FF yff = ff_add(FF{pb.a_ff[ray].x, pb.a_ff[ray].y}, FF{-OL.hi, -OL.lo});
-                    t32 = -(float)Cp * g_f32(yff.hi + yff.lo);
-                } else {
-                    t32 = -(float)pb.I0 * expf(-(OL.hi + OL.lo));
-                }
-                accf = ff_add(accf, FF{t32, 0.f});
-                O = (double)Off.hi + (double)Off.lo;
-                term = (double)t32;
+        } else if constexpr (MODE == MODE_F32C) {
+            // O = dt (G rho_top + sum_l drho_l N_l), y = a - O / Lambda, in float-float
+            FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
+            march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, pb.work ? &n_eval : nullptr,
+                                          [&](int l, unsigned long long tl) {
+                const FF n = ff_two_sum((float)(uint32_t)(tl >> 20) * 1048576.0f * 0x1p-23f,
+                                        (float)(uint32_t)(tl & 0xFFFFFu) * 0x1p-23f);
+                Sff = ff_add(Sff, ff_mul(FF{pb.drho_ff[l].x, pb.drho_ff[l].y}, n));
+            });
+            const FF Off = ff_mul(FF{pb.dt_ff[ray].x, pb.dt_ff[ray].y}, Sff);
+            const FF OL = ff_mul(Off, FF{pb.invL_ff.x, pb.invL_ff.y});
+            float t32;
+            if (Cp > 0) {
+                const FF yff = ff_add(FF{pb.a_ff[ray].x, pb.a_ff[ray].y}, FF{-OL.hi, -OL.lo});
+                t32 = -(float)Cp * g_f32(yff.hi + yff.lo);
             } else {
-                double S_ = 0.0;
+                t32 = -(float)pb.I0 * expf(-(OL.hi + OL.lo));
+            }
+            accf = ff_add(accf, FF{t32, 0.f});
+            O = (double)Off.hi + (double)Off.lo;
+            term = (double)t32;
+        } else {
+            double S_ = 0.0;
+            if constexpr (MODE == MODE_F32) {
+                march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, pb.work ? &n_eval : nullptr,
+                                              [&](int l, unsigned long long tl) {
+                    S_ = fma(pb.drho[l], (double)tl * 0x1p-23, S_);
+                });
+            } else {
+                unsigned long long tot[L];
+                march_ray_f32<L, HARD, S>(pb, sh, ray, tot);
+                if (pb.work) n_eval += (unsigned long long)L * pb.G;
 #pragma unroll
                 for (int l = 0; l < L; ++l) S_ = fma(pb.drho[l], (double)tot[l] * 0x1p-23, S_);
-                O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
-                if (Cp > 0) {
-                    const double y = pb.a[ray] - O * pb.inv_Lambda;
-                    term = -(double)Cp * (double)g_f32((float)y);
-                } else {
-                    term = -pb.I0 * exp(-O * pb.inv_Lambda);
-                }
-                acc += term;
             }
+            O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
+            if (Cp > 0) {
+                const double y = pb.a[ray] - O * pb.inv_Lambda;
+                term = -(double)Cp * (double)g_f32((float)y);
+            } else {
+                term = -pb.I0 * exp(-O * pb.inv_Lambda);
+            }
+            acc += term;
         }
         if (ray_O) ray_O[(size_t)c * pb.n_rays + ray] = O;
         if (ray_term) ray_term[(size_t)c * pb.n_rays + ray] = term + poisson_K(Cp);
