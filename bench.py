@@ -583,7 +583,7 @@ def main():
                          "evaluated_fraction": work_eval / work_total if work_total else None,
                          "frac_evaluated_work": (achieved / peak) * (work_eval / work_total)
                          if work_total else None,
-                         "note": "units are the method's surface-samples; samples at least 30 "
+                         "note": "units are the method's surface-samples; samples at least 25 "
                                  "log2 units from their surface are exactly 0/1 and added "
                                  "without evaluation (bit-identical)"},
             "clocks": clk,

@@ -177,7 +177,7 @@ static cudaError_t adj_l(const Prob &pb, HRef h, int n_chains, int rpb, double *
                          unsigned long long *gacc, cudaStream_t st)
 {
     const size_t with = adjoint_smem_bytes(pb, true);
-    const bool smem_acc = with <= MT_MAX_SMEM;
+    const bool smem_acc = with + MT_SMEM_STATIC <= MT_MAX_SMEM;
     const size_t bytes = smem_acc ? with : adjoint_smem_bytes(pb, false);
     void (*fn)(Prob, HRef, int, double *, unsigned long long *) =
         smem_acc ? k_adjoint<L, true> : k_adjoint<L, false>;

@@ -45,6 +45,12 @@ size_t march_smem_bytes(const Prob &pb, int mode)
     return (size_t)bytes * pb.N;
 }
 
+bool march_fits_smem(const Prob &pb, int mode)
+{
+    const bool dx = mode == MODE_F32 || mode == MODE_F32C;
+    return march_smem_bytes(pb, mode) + (dx ? MT_SMEM_STATIC_DX : MT_SMEM_STATIC) <= MT_MAX_SMEM;
+}
+
 cudaError_t launch_march(const Prob &pb, int mode, HRef h, int n_chains, void *partial,
                          double *ray_O, double *ray_term, cudaStream_t st)
 {
@@ -255,6 +261,14 @@ static void refresh_prob(mt_ctx *ctx)
     };
     pb.gm_hi_x = hi(ctx->Q);
     pb.gm_hi_y = hi(ctx->R);
+    // tiles of the window refinement: 8 x 8 cells, coarser where they would not fit
+    pb.tile_T = 8;
+    for (;;) {
+        pb.tile_nx = (ctx->Q - 1 + pb.tile_T - 1) / pb.tile_T;
+        pb.tile_ny = (ctx->R - 1 + pb.tile_T - 1) / pb.tile_T;
+        if ((long long)ctx->L * pb.tile_nx * pb.tile_ny <= MT_MAX_TILES) break;
+        pb.tile_T *= 2;
+    }
     if (!ctx->rho.empty()) {
         pb.rho_top = ctx->rho[ctx->L];
         for (int l = 0; l < MT_MAX_L; ++l) {
@@ -433,18 +447,17 @@ static mt_status ensure_partials(mt_ctx *ctx, int n_chains)
 // records in HBM (see k_stage_dx_global); the other modes need them to fit.
 static bool use_global_nodes(const mt_ctx *ctx)
 {
-    return march_smem_bytes(ctx->pb, ctx->mode) > MT_MAX_SMEM &&
-           (ctx->mode == MODE_F32 || ctx->mode == MODE_F32C);
+    return !march_fits_smem(ctx->pb, ctx->mode) && (ctx->mode == MODE_F32 || ctx->mode == MODE_F32C);
 }
 
 static mt_status check_smem(mt_ctx *ctx)
 {
     const size_t smem = march_smem_bytes(ctx->pb, ctx->mode);
-    if (smem > MT_MAX_SMEM && !use_global_nodes(ctx))
+    if (!march_fits_smem(ctx->pb, ctx->mode) && !use_global_nodes(ctx))
         return fail(ctx, MT_EINVAL,
                     "surfaces need %zu bytes of shared memory per block (limit %d): use "
                     "MT_PREC_F32 (records in HBM) or a smaller grid",
-                    smem, MT_MAX_SMEM);
+                    smem, MT_MAX_SMEM - MT_SMEM_STATIC);
     return MT_OK;
 }
 
@@ -548,7 +561,7 @@ static mt_status grad_ok(mt_ctx *ctx)
 {
     if (ctx->mode == MODE_F64)
         return fail(ctx, MT_EINVAL, "the adjoint computes in FP32: use an FP32 precision mode");
-    if (adjoint_smem_bytes(ctx->pb, false) > MT_MAX_SMEM)
+    if (adjoint_smem_bytes(ctx->pb, false) + MT_SMEM_STATIC > MT_MAX_SMEM)
         return fail(ctx, MT_EINVAL, "grid too large for the adjoint's shared-memory surfaces");
     if (!(ctx->cfg.gamma > 0.0))
         return fail(ctx, MT_EINVAL, "the gradient needs gamma > 0 (the hard indicator is flat)");

@@ -158,6 +158,42 @@ __device__ __forceinline__ void surface_extent(const H *Hc, int N, const float *
     }
 }
 
+// Per-tile bounds of the staged planes: tb[l * nt + t] = {min, max} of
+// h - ref_l over the nodes of tile t (tile_T x tile_T cells, its nodes rows
+// [ty T, ty T + T] x cols [tx T, tx T + T] clipped to the grid: every corner
+// of the tile's cells), then ext[l] / ext[L + l] = the surface's min / max.
+// All threads must call it; the planes must be staged and synchronised.
+template <int L>
+__device__ __forceinline__ void tile_bounds(const Prob &pb, const float2 *planes, float2 *tb, float *ext)
+{
+    const int T = pb.tile_T, nx = pb.tile_nx, nt = pb.tile_nx * pb.tile_ny;
+    for (int idx = threadIdx.x; idx < L * nt; idx += blockDim.x) {
+        const int l = idx / nt, t = idx - l * nt;
+        const int ty = t / nx, tx = t - ty * nx;
+        const int r0 = ty * T, r1 = min(r0 + T, pb.R - 1), c0 = tx * T, c1 = min(c0 + T, pb.Q - 1);
+        const float2 *pl = planes + (size_t)l * pb.N;
+        float lo = INFINITY, hi = -INFINITY;
+        for (int r = r0; r <= r1; ++r)
+            for (int c = c0; c <= c1; ++c) {
+                const float v = pl[r * pb.Q + c].x;
+                lo = fminf(lo, v);
+                hi = fmaxf(hi, v);
+            }
+        tb[idx] = make_float2(lo, hi);
+    }
+    __syncthreads();
+    if (threadIdx.x < L) {
+        const int l = threadIdx.x;
+        float lo = INFINITY, hi = -INFINITY;
+        for (int t = 0; t < nt; ++t) {
+            lo = fminf(lo, tb[l * nt + t].x);
+            hi = fmaxf(hi, tb[l * nt + t].y);
+        }
+        ext[l] = lo;
+        ext[L + l] = hi;
+    }
+}
+
 template <typename S, typename T, int L>
 __device__ __forceinline__ void load_node(const S *sh, int node, T (&v)[L])
 {
@@ -443,47 +479,85 @@ __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, float4
     }
 }
 
-// Samples whose sigmoid argument is at least kSat (log2 units) from zero give
-// sigma + 1 == exactly 1.0f or exactly rcp(1) + 1 in FP32 (the argument of
-// 2^arg, or 2^-arg, is far past the 2^-24 rounding limit), so their integer
-// contributions are known without evaluating them.
-constexpr float kSat = 30.0f;
+// Samples whose sigmoid argument is at least kSat (log2 units) from zero have
+// integer contributions known without evaluating them.  Above the surface
+// (arg >= kSat) sigma = rcp(1 + 2^arg) <= 2^-24, and sigma + 1 rounds to
+// exactly 1.0f (round to nearest even); below it (arg <= -kSat) 2^arg <=
+// 2^-24, 1 + 2^arg rounds to exactly 1.0f, and the sample adds rcp(1) + 1.
+// |arg| >= 24 suffices; kSat = 25 leaves a whole log2 unit for the relative
+// error of ex2.approx / rcp.approx (~2^-22) and for the FP32 rounding of the
+// argument and of the window bounds (~1e-5 log2 units).
+constexpr float kSat = 25.0f;
 
 // Sample window [lo, hi] in which surface l can be transitional along a ray:
-// outside it |kg (z - s_l)| >= kSat for every height the surface takes
-// (ext = its min / max offset).  z_l(k) = z0 + k dz (scaled by kg).
-__device__ __forceinline__ void transition_window(float z0, float dz, float kg, float smin,
+// outside it |kg (z - s_l)| >= kSat for every height in [smin, smax] (offsets
+// h - ref_l).  z_l(k) = z0 + k dz (scaled by kg); rdz ~ 1 / dz.  The sample
+// bounds are widened by 2^-20 (|k| + 1), many times the relative rounding
+// error of (bound - z0) * rdz, so the window never loses a sample.
+__device__ __forceinline__ void transition_window(float z0, float dz, float rdz, float kg, float smin,
                                                   float smax, int G, int &lo, int &hi)
 {
     const float a = kg * smin - kSat, b = kg * smax + kSat;  // z_l must lie in (a, b)
-    if (fabsf(dz) < 1e-20f) {
+    if (!(fabsf(dz) >= 1e-20f)) {
         const bool in = z0 > a && z0 < b;
         lo = in ? 0 : G;
         hi = in ? G - 1 : -1;
         return;
     }
-    float ka = (a - z0) / dz, kb = (b - z0) / dz;
-    if (dz < 0.f) {
-        const float t = ka;
-        ka = kb;
-        kb = t;
-    }
-    ka = fmaxf(floorf(ka), -1.0f);
-    kb = fminf(ceilf(kb), (float)G);
-    lo = (int)ka;
-    hi = (int)kb;
-    if (dz < 0.f) {  // samples before the window lie above the surface: no skipping
+    if (dz < 0.f) {  // samples before the window would lie above the surface: no skipping
         lo = 0;      // (rays pointing down are rare; they evaluate every sample)
         hi = G - 1;
+        return;
     }
-    lo = max(lo, 0);
-    hi = min(hi, G - 1);
+    float ka = (a - z0) * rdz, kb = (b - z0) * rdz;
+    ka -= fmaf(fabsf(ka), 0x1p-20f, 0x1p-20f);
+    kb += fmaf(fabsf(kb), 0x1p-20f, 0x1p-20f);
+    ka = fminf(fmaxf(floorf(ka), -1.0f), (float)G);
+    kb = fminf(fmaxf(ceilf(kb), -1.0f), (float)G);
+    lo = max((int)ka, 0);
+    hi = min((int)kb, G - 1);
+}
+
+// Narrow a surface's window [lo, hi] of an upward ray (dz > 0) with tile
+// bounds (tbl = the surface's {min, max} per tile): the window's samples lie
+// in cells between those of its end samples (cells from the same FP32
+// arithmetic as the march, which is monotone in k), hence in the tiles of
+// that bounding box; samples outside the bounds' own window are saturated on
+// the same side as before it or after it.  Bounding boxes of more than 16
+// tiles are left alone.
+__device__ __forceinline__ void refine_window(const Prob &pb, const float2 *tbl, float4 o, float4 st,
+                                              float rdz, float zh, int &lo, int &hi)
+{
+    if (lo > hi) return;
+    const float M = 12582912.0f;
+    const int T = pb.tile_T, nx = pb.tile_nx;
+    const float ka = (float)lo, kb = (float)hi;
+    const int cxa = __float_as_int(fmaf(ka, st.x, o.x) + M) - 0x4B400000;
+    const int cxb = __float_as_int(fmaf(kb, st.x, o.x) + M) - 0x4B400000;
+    const int cya = __float_as_int(fmaf(ka, st.y, o.y) + M) - 0x4B400000;
+    const int cyb = __float_as_int(fmaf(kb, st.y, o.y) + M) - 0x4B400000;
+    const int tx0 = min(cxa, cxb) / T, tx1 = max(cxa, cxb) / T;
+    const int ty0 = min(cya, cyb) / T, ty1 = max(cya, cyb) / T;
+    if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) > 16) return;
+    float bmin = INFINITY, bmax = -INFINITY;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            const float2 b = tbl[ty * nx + tx];
+            bmin = fminf(bmin, b.x);
+            bmax = fmaxf(bmax, b.y);
+        }
+    int lo2, hi2;
+    transition_window(zh, st.z, rdz, pb.kg, bmin, bmax, pb.G, lo2, hi2);
+    const int nlo = min(max(lo2, lo), hi + 1);
+    hi = max(min(hi2, hi), nlo - 1);
+    lo = nlo;
 }
 
 // The FP32 modes' march of one ray: per surface l, the exact integer sum
 // N_l = sum_k varsigma(s_l - z_k) * 2^23 (see march_ray_f32 for the
 // arithmetic), computed over the samples where surface l can be
-// transitional (transition_window with ext = per-surface min / max offsets);
+// transitional (transition_window with ext = per-surface min / max offsets,
+// narrowed by refine_window where tile bounds tb are given);
 // the other samples' contributions are exact and added analytically (one
 // sample below the surface adds rcp(1) + 1 - 1 in units of 2^-23, one above
 // adds 0).  A window of odd length is widened by one saturated sample where
@@ -491,18 +565,21 @@ __device__ __forceinline__ void transition_window(float z0, float dz, float kg, 
 // called for l = 0 .. L-1 in order.
 template <int L, bool HARD, bool GLOBAL, typename Emit>
 __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *planes, int ray,
-                                             const float *ext, unsigned long long *evaluated,
-                                             Emit &&emit)
+                                             const float *ext, const float2 *tb,
+                                             unsigned long long *evaluated, Emit &&emit)
 {
     const float4 o = pb.o4[ray], st = pb.s4[ray];
     const uint32_t q_one = HARD ? 0x00800000u : __float_as_uint(rcp_approx(1.0f) + 1.0f) - 0x3F800000u;
     const int G = pb.G;
+    const float rdz = rcp_approx(st.z);
 #pragma unroll 1
     for (int l = 0; l < L; ++l) {
         const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
         const float zl = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
         int lo, hi;
-        transition_window(zh, st.z, pb.kg, ext[l], ext[L + l], G, lo, hi);
+        transition_window(zh, st.z, rdz, pb.kg, ext[l], ext[L + l], G, lo, hi);
+        if (tb && st.z >= 1e-20f)
+            refine_window(pb, tb + (size_t)l * pb.tile_nx * pb.tile_ny, o, st, rdz, zh, lo, hi);
         lo = min(lo, G);
         int he = max(hi + 1, lo);
         if ((he - lo) & 1) {
@@ -677,7 +754,17 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
         stage_nodes<S, Hh, L>(sh, chain_ptr<Hh>(h, c), pb.N, (MODE == MODE_F64) ? nullptr : pb.ref);
     }
     __shared__ float ext[2 * MT_MAX_L];
-    if constexpr (DX) surface_extent<Hh, L>(chain_ptr<Hh>(h, c), pb.N, pb.ref, ext);
+    __shared__ float2 tiles[DX && !GLOBAL ? MT_MAX_TILES : 1];
+    const float2 *tb = nullptr;
+    if constexpr (DX) {
+        if constexpr (GLOBAL) {
+            surface_extent<Hh, L>(chain_ptr<Hh>(h, c), pb.N, pb.ref, ext);
+        } else {
+            __syncthreads();  // planes staged
+            tile_bounds<L>(pb, planes, tiles, ext);
+            tb = tiles;
+        }
+    }
     __syncthreads();
 
     const int r_begin = blockIdx.x * rays_per_block;
@@ -702,7 +789,7 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
         } else if constexpr (MODE == MODE_F32C) {
             // O = dt (G rho_top + sum_l drho_l N_l), y = a - O / Lambda, in float-float
             FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
-            march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, pb.work ? &n_eval : nullptr,
+            march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, tb, pb.work ? &n_eval : nullptr,
                                           [&](int l, unsigned long long tl) {
                 const FF n = ff_two_sum((float)(uint32_t)(tl >> 20) * 1048576.0f * 0x1p-23f,
                                         (float)(uint32_t)(tl & 0xFFFFFu) * 0x1p-23f);
@@ -723,7 +810,7 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
         } else {
             double S_ = 0.0;
             if constexpr (MODE == MODE_F32) {
-                march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, pb.work ? &n_eval : nullptr,
+                march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, tb, pb.work ? &n_eval : nullptr,
                                               [&](int l, unsigned long long tl) {
                     S_ = fma(pb.drho[l], (double)tl * 0x1p-23, S_);
                 });

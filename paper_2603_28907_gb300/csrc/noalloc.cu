@@ -66,7 +66,7 @@ extern "C" MT_API mt_status mt_logpost_noalloc(mt_ctx *ctx, int n_chains, const 
         return ctx_fail(ctx, MT_EINVAL,
                         "mt_logpost_noalloc: every array must be device memory (staging host "
                         "memory would need an allocation)");
-    if (march_smem_bytes(v.pb, v.mode) > MT_MAX_SMEM)
+    if (!march_fits_smem(v.pb, v.mode))
         return ctx_fail(ctx, MT_EINVAL,
                         "mt_logpost_noalloc: the grid's surfaces do not fit in shared memory "
                         "(that path needs an HBM buffer); use mt_logpost");
