@@ -152,8 +152,8 @@ MT_API mt_status mt_logpost(mt_ctx *ctx, int n_chains, const void *heights, doub
  *    staging them would need an allocation.
  *  - The per-(chain, CTA) partial sums live in one 1 MiB array inside the
  *    library (held by every GPU that loads it until the process exits), so
- *    n_chains * ceil(S*P / 4096) * 8 bytes must fit in 1 MiB (8192 chains of
- *    a 16 x 4096-ray problem); larger calls fail with MT_EINVAL.
+ *    n_chains * ceil(S*P / 8192) * 8 bytes must fit in 1 MiB (16384 chains
+ *    of a 16 x 4096-ray problem); larger calls fail with MT_EINVAL.
  *  - The first call on each device looks up the array's device address;
  *    make that first call before any stream capture.
  *  - All calls share the array: two calls whose kernels overlap on the GPU
@@ -226,7 +226,7 @@ MT_API mt_status mt_get_timing(mt_ctx *ctx, int id, double *total_ms, int64_t *l
 /* Work of the FP32 ray kernel launched while timing was on: *total = the
  * method's surface-samples (chains x rays x n_grid x n_layers), *evaluated =
  * those whose logistic was computed; the others lay so far from their surface
- * (|s - z| >= 30 gamma / log2(e)) that their indicator is exactly 0 or 1 in
+ * (|s - z| >= 25 gamma / log2(e)) that their indicator is exactly 0 or 1 in
  * FP32 and was added without evaluation (the result is bit-identical).
  * reset = 1 clears both. */
 MT_API mt_status mt_get_work(mt_ctx *ctx, double *evaluated, double *total, int reset);

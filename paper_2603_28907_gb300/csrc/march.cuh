@@ -775,19 +775,10 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
     for (int slot = r_begin + threadIdx.x; slot < r_end; slot += blockDim.x) {
         const int ray = pb.perm ? pb.perm[slot] : slot;
         const int Cp = pb.cnt[ray];
-        double O, term;
-        if constexpr (MODE == MODE_F64) {
-            const double S_ = march_ray_f64<L, HARD>(pb, sh, ray);
-            O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
-            if (Cp > 0) {
-                const double y = pb.a[ray] - O * pb.inv_Lambda;
-                term = (double)Cp * y - (double)Cp * expm1(y);
-            } else {
-                term = -pb.I0 * exp(-O * pb.inv_Lambda);
-            }
-            acc += term;
-        } else if constexpr (MODE == MODE_F32C) {
-            // O = dt (G rho_top + sum_l drho_l N_l), y = a - O / Lambda, in float-float
+        if constexpr (DX) {
+            // O = dt (G rho_top + sum_l drho_l N_l) and y = a - O / Lambda in
+            // float-float; the term -C (e^y - 1 - y) (or -I0 e^{-O/Lambda} for
+            // C = 0) in FP32, its product by C kept exact as a float-float.
             FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
             march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, tb, pb.work ? &n_eval : nullptr,
                                           [&](int l, unsigned long long tl) {
@@ -797,41 +788,49 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
             });
             const FF Off = ff_mul(FF{pb.dt_ff[ray].x, pb.dt_ff[ray].y}, Sff);
             const FF OL = ff_mul(Off, FF{pb.invL_ff.x, pb.invL_ff.y});
-            float t32;
+            FF tf;
             if (Cp > 0) {
                 const FF yff = ff_add(FF{pb.a_ff[ray].x, pb.a_ff[ray].y}, FF{-OL.hi, -OL.lo});
-                t32 = -(float)Cp * g_f32(yff.hi + yff.lo);
+                const float g = g_f32(yff.hi + yff.lo), cf = (float)Cp;
+                const float cg = cf * g;
+                tf = FF{-cg, -fmaf(cf, g, -cg)};
             } else {
-                t32 = -(float)pb.I0 * expf(-(OL.hi + OL.lo));
+                tf = FF{-(float)pb.I0 * expf(-(OL.hi + OL.lo)), 0.f};
             }
-            accf = ff_add(accf, FF{t32, 0.f});
-            O = (double)Off.hi + (double)Off.lo;
-            term = (double)t32;
+            accf = ff_add(accf, tf);
+            if (ray_O) ray_O[(size_t)c * pb.n_rays + ray] = (double)Off.hi + (double)Off.lo;
+            if (ray_term)
+                ray_term[(size_t)c * pb.n_rays + ray] = ((double)tf.hi + (double)tf.lo) + poisson_K(Cp);
         } else {
-            double S_ = 0.0;
-            if constexpr (MODE == MODE_F32) {
-                march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, tb, pb.work ? &n_eval : nullptr,
-                                              [&](int l, unsigned long long tl) {
-                    S_ = fma(pb.drho[l], (double)tl * 0x1p-23, S_);
-                });
+            double O, term;
+            if constexpr (MODE == MODE_F64) {
+                const double S_ = march_ray_f64<L, HARD>(pb, sh, ray);
+                O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
+                if (Cp > 0) {
+                    const double y = pb.a[ray] - O * pb.inv_Lambda;
+                    term = (double)Cp * y - (double)Cp * expm1(y);
+                } else {
+                    term = -pb.I0 * exp(-O * pb.inv_Lambda);
+                }
             } else {
                 unsigned long long tot[L];
                 march_ray_f32<L, HARD, S>(pb, sh, ray, tot);
                 if (pb.work) n_eval += (unsigned long long)L * pb.G;
+                double S_ = 0.0;
 #pragma unroll
                 for (int l = 0; l < L; ++l) S_ = fma(pb.drho[l], (double)tot[l] * 0x1p-23, S_);
-            }
-            O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
-            if (Cp > 0) {
-                const double y = pb.a[ray] - O * pb.inv_Lambda;
-                term = -(double)Cp * (double)g_f32((float)y);
-            } else {
-                term = -pb.I0 * exp(-O * pb.inv_Lambda);
+                O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
+                if (Cp > 0) {
+                    const double y = pb.a[ray] - O * pb.inv_Lambda;
+                    term = -(double)Cp * (double)g_f32((float)y);
+                } else {
+                    term = -pb.I0 * exp(-O * pb.inv_Lambda);
+                }
             }
             acc += term;
+            if (ray_O) ray_O[(size_t)c * pb.n_rays + ray] = O;
+            if (ray_term) ray_term[(size_t)c * pb.n_rays + ray] = term + poisson_K(Cp);
         }
-        if (ray_O) ray_O[(size_t)c * pb.n_rays + ray] = O;
-        if (ray_term) ray_term[(size_t)c * pb.n_rays + ray] = term + poisson_K(Cp);
     }
     if (pb.work && n_eval) atomicAdd(pb.work, n_eval);
     if constexpr (MODE == MODE_F32C) {
@@ -839,6 +838,11 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
         if (threadIdx.x == 0)
             reinterpret_cast<float2 *>(partial)[(size_t)c * gridDim.x + blockIdx.x] =
                 make_float2(accf.hi, accf.lo);
+    } else if constexpr (MODE == MODE_F32) {
+        // a thread's few ray terms were summed in float-float; across threads,
+        // CTAs and the chain the sum is FP64
+        acc = block_sum((double)accf.hi + (double)accf.lo);
+        if (threadIdx.x == 0) reinterpret_cast<double *>(partial)[(size_t)c * gridDim.x + blockIdx.x] = acc;
     } else {
         acc = block_sum(acc);
         if (threadIdx.x == 0) reinterpret_cast<double *>(partial)[(size_t)c * gridDim.x + blockIdx.x] = acc;

@@ -53,11 +53,12 @@ def test_noalloc_rejects_host_memory_and_oversize():
     pr2 = W.problem(w2)
     ctx2 = mt.from_workload(pr2, precision=mt.PREC_F32)
     ctx2.set_counts(np.ones((w2.S, w2.P), np.int32))
-    # 65536 rays -> 16 partials per chain: 8192 chains fit, 8193 do not.  The
-    # arrays are sized for 8193 chains so the call stays in bounds either way.
-    Hbig = heights(pr2["H_true"][None], mt.PREC_F32).expand(8193, -1, -1, -1).contiguous()
-    obig = torch.zeros(8193, dtype=torch.float64, device=DEV)
-    st = lib.mt_logpost_noalloc(ctx2.h, 8193, ctypes.c_void_p(Hbig.data_ptr()),
+    # 65536 rays -> 8 partials per chain (8192 rays per block): 16384 chains
+    # fit, 16385 do not.  The arrays are sized for 16385 chains so the call
+    # stays in bounds either way.
+    Hbig = heights(pr2["H_true"][None], mt.PREC_F32).expand(16385, -1, -1, -1).contiguous()
+    obig = torch.zeros(16385, dtype=torch.float64, device=DEV)
+    st = lib.mt_logpost_noalloc(ctx2.h, 16385, ctypes.c_void_p(Hbig.data_ptr()),
                                 ctypes.c_void_p(obig.data_ptr()), None)
     assert st == -1
     assert b"1048576" in lib.mt_last_error(ctx2.h)
