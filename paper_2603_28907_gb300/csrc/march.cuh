@@ -405,13 +405,15 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
 // every paired FP32 instruction carries sample k, lane .y sample k + 1.  Each
 // lane's arithmetic is that of one sample: position g = o + k gs, cell split,
 // bilinear height from the two left corners' (h, dx) records, float-float
-// z, sigmoid argument, 2^arg, reciprocal, sigma + 1.  The corner records of
-// both samples are cached and reloaded when either sample enters a new cell.
+// z, sigmoid argument, 2^arg, reciprocal, sigma + 1.  The x-lerps read the
+// records as loaded (scalar FMAs), which leaves no register shuffling when a
+// sample enters a new cell; the corner records of both samples are cached
+// and reloaded when either sample enters a new cell.
 template <bool HARD, bool GLOBAL>
 __device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, float2 kf2, float2 ox2, float2 oy2,
                                           float2 sx2, float2 sy2, float2 szh2, float2 szl2,
                                           float2 zh2, float2 zl2, float2 nkg2, int &curA, int &curB,
-                                          float2 &h00, float2 &d0, float2 &h10, float2 &d1)
+                                          float2 &rA0, float2 &rA1, float2 &rB0, float2 &rB1)  // (h, dx): A/B x row r0/r0+1
 {
     const float2 M2 = f2(12582912.0f);  // 1.5 * 2^23: adding it rounds to an integer
     const float2 gx = fma2(kf2, sx2, ox2), gy = fma2(kf2, sy2, oy2);
@@ -423,15 +425,13 @@ __device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, float2 kf2, f
     if (nA != curA || nB != curB) {
         curA = nA;
         curB = nB;
-        const float2 a0 = GLOBAL ? __ldg(pl + nA) : pl[nA], a1 = GLOBAL ? __ldg(pl + nA + Q) : pl[nA + Q];
-        const float2 b0 = GLOBAL ? __ldg(pl + nB) : pl[nB], b1 = GLOBAL ? __ldg(pl + nB + Q) : pl[nB + Q];
-        h00 = make_float2(a0.x, b0.x);
-        d0 = make_float2(a0.y, b0.y);
-        h10 = make_float2(a1.x, b1.x);
-        d1 = make_float2(a1.y, b1.y);
+        rA0 = GLOBAL ? __ldg(pl + nA) : pl[nA];
+        rA1 = GLOBAL ? __ldg(pl + nA + Q) : pl[nA + Q];
+        rB0 = GLOBAL ? __ldg(pl + nB) : pl[nB];
+        rB1 = GLOBAL ? __ldg(pl + nB + Q) : pl[nB + Q];
     }
-    const float2 a = fma2(fx, d0, h00);                                 // row r0
-    const float2 b = fma2(fx, d1, h10);                                 // row r0 + 1
+    const float2 a = make_float2(fmaf(fx.x, rA0.y, rA0.x), fmaf(fx.y, rB0.y, rB0.x));  // row r0
+    const float2 b = make_float2(fmaf(fx.x, rA1.y, rA1.x), fmaf(fx.y, rB1.y, rB1.x));  // row r0 + 1
     const float2 sl = fma2(fy, fma2(a, f2(-1.0f), b), a);               // s_l - ref_l
     const float2 zl = fma2(kf2, szl2, add2(fma2(kf2, szh2, zh2), zl2));
     const float2 arg = fma2(nkg2, sl, zl);                              // -kg (s_l - z)
@@ -456,7 +456,7 @@ __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, float4
 {
     const float2 ox2 = f2(o.x), oy2 = f2(o.y), sx2 = f2(st.x), sy2 = f2(st.y);
     const float2 szh2 = f2(st.z), szl2 = f2(st.w), zh2 = f2(zh), zl2 = f2(zl), nkg2 = f2(nkg);
-    float2 h00 = f2(0.f), d0 = f2(0.f), h10 = f2(0.f), d1 = f2(0.f);
+    float2 rA0 = f2(0.f), rA1 = f2(0.f), rB0 = f2(0.f), rB1 = f2(0.f);
     int curA = -1, curB = -1;
     float2 kf2 = make_float2((float)lo, (float)lo + 1.0f);
     const int np = (he - lo) >> 1;
@@ -465,7 +465,7 @@ __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, float4
         uint32_t acc = 0u;
         for (int j = 0; j < jn; ++j) {
             const float2 v = dx_pair<HARD, GLOBAL>(pl, Q, kf2, ox2, oy2, sx2, sy2, szh2, szl2, zh2, zl2,
-                                                   nkg2, curA, curB, h00, d0, h10, d1);
+                                                   nkg2, curA, curB, rA0, rA1, rB0, rB1);
             acc += __float_as_uint(v.x) + __float_as_uint(v.y);
             kf2 = add2(kf2, f2(2.0f));
         }
@@ -474,7 +474,7 @@ __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, float4
     if ((he - lo) & 1) {
         kf2 = f2((float)(he - 1));
         const float2 v = dx_pair<HARD, GLOBAL>(pl, Q, kf2, ox2, oy2, sx2, sy2, szh2, szl2, zh2, zl2,
-                                               nkg2, curA, curB, h00, d0, h10, d1);
+                                               nkg2, curA, curB, rA0, rA1, rB0, rB1);
         t += (unsigned long long)(__float_as_uint(v.x) - 0x3F800000u);
     }
 }
@@ -839,10 +839,12 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
             reinterpret_cast<float2 *>(partial)[(size_t)c * gridDim.x + blockIdx.x] =
                 make_float2(accf.hi, accf.lo);
     } else if constexpr (MODE == MODE_F32) {
-        // a thread's few ray terms were summed in float-float; across threads,
-        // CTAs and the chain the sum is FP64
-        acc = block_sum((double)accf.hi + (double)accf.lo);
-        if (threadIdx.x == 0) reinterpret_cast<double *>(partial)[(size_t)c * gridDim.x + blockIdx.x] = acc;
+        // the CTA's ray terms are summed in float-float (relative error ~2^-44,
+        // and it leaves the FP32 pipes to the march); the chain's CTA partials
+        // are summed in FP64
+        accf = block_sum(accf);
+        if (threadIdx.x == 0)
+            reinterpret_cast<double *>(partial)[(size_t)c * gridDim.x + blockIdx.x] = (double)accf.hi + (double)accf.lo;
     } else {
         acc = block_sum(acc);
         if (threadIdx.x == 0) reinterpret_cast<double *>(partial)[(size_t)c * gridDim.x + blockIdx.x] = acc;
