@@ -48,8 +48,7 @@ size_t march_smem_bytes(const Prob &pb, int mode)
 
 bool march_fits_smem(const Prob &pb, int mode)
 {
-    const bool dx = mode == MODE_F32 || mode == MODE_F32C;
-    return march_smem_bytes(pb, mode) + (dx ? MT_SMEM_STATIC_DX : MT_SMEM_STATIC) <= MT_MAX_SMEM;
+    return march_smem_bytes(pb, mode) + MT_SMEM_STATIC <= MT_MAX_SMEM;
 }
 
 cudaError_t launch_march(const Prob &pb, int mode, HRef h, int n_chains, void *partial,
@@ -262,14 +261,6 @@ static void refresh_prob(mt_ctx *ctx)
     };
     pb.gm_hi_x = hi(ctx->Q);
     pb.gm_hi_y = hi(ctx->R);
-    // tiles of the window refinement: 8 x 8 cells, coarser where they would not fit
-    pb.tile_T = 8;
-    for (;;) {
-        pb.tile_nx = (ctx->Q - 1 + pb.tile_T - 1) / pb.tile_T;
-        pb.tile_ny = (ctx->R - 1 + pb.tile_T - 1) / pb.tile_T;
-        if ((long long)ctx->L * pb.tile_nx * pb.tile_ny <= MT_MAX_TILES) break;
-        pb.tile_T *= 2;
-    }
     if (!ctx->rho.empty()) {
         pb.rho_top = ctx->rho[ctx->L];
         for (int l = 0; l < MT_MAX_L; ++l) {

@@ -15,10 +15,8 @@
 
 #define MT_MAX_L 8
 #define MT_MAX_SMEM 232448  // opt-in shared memory per block on sm_100/sm_103
-#define MT_MAX_TILES 2048   // per-tile surface bounds held in shared memory (float2 each)
 // static shared memory a kernel may use on top of its dynamic allocation
 #define MT_SMEM_STATIC 4096
-#define MT_SMEM_STATIC_DX 20480  // FP32 march: tile bounds + reductions
 
 namespace mt {
 
@@ -54,8 +52,6 @@ struct Prob {
                                // march (the rest were exactly saturated), else nullptr
     float *gnodes;             // grids too large for shared memory: per-chain (h, dx)
                                // planes in HBM, [chain][l][node] float2; else nullptr
-    int tile_T, tile_nx, tile_ny;  // FP32 window refinement: blocks of tile_T x tile_T cells,
-                                   // tile_nx x tile_ny of them (L * nx * ny <= MT_MAX_TILES)
     const int *perm;           // march order of the rays (ray table sorted by vertical
                                // step, then start height); nullptr = ray order
     float2 grho_ff;            // float-float of G * rho_top

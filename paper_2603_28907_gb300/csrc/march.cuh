@@ -113,10 +113,11 @@ __device__ __forceinline__ void stage_planes_dx(float2 *sh, const H *Hc, int N, 
     }
 }
 
-// Per-surface minimum and maximum of h - ref over one chain's nodes (block
-// reduction); ext[l] = min, ext[L + l] = max.  All threads must call it.
-template <typename H, int L>
-__device__ __forceinline__ void surface_extent(const H *Hc, int N, const float *ref, float *ext)
+// Per-surface minimum and maximum of the staged offsets h - ref_l (planes in
+// shared memory or HBM): ext[l] = min, ext[L + l] = max.  All threads must
+// call it, after the planes are complete and visible.
+template <int L>
+__device__ __forceinline__ void surface_extent(const float2 *planes, int N, float *ext)
 {
     __shared__ float red[2 * MT_MAX_L][32];
     float lo[L], hi[L];
@@ -128,7 +129,7 @@ __device__ __forceinline__ void surface_extent(const H *Hc, int N, const float *
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
 #pragma unroll
         for (int l = 0; l < L; ++l) {
-            const float v = (float)Hc[(size_t)l * N + i] - ref[l];
+            const float v = planes[(size_t)l * N + i].x;
             lo[l] = fminf(lo[l], v);
             hi[l] = fmaxf(hi[l], v);
         }
@@ -155,42 +156,6 @@ __device__ __forceinline__ void surface_extent(const H *Hc, int N, const float *
         }
         ext[threadIdx.x] = a;
         ext[L + threadIdx.x] = b;
-    }
-}
-
-// Per-tile bounds of the staged planes: tb[l * nt + t] = {min, max} of
-// h - ref_l over the nodes of tile t (tile_T x tile_T cells, its nodes rows
-// [ty T, ty T + T] x cols [tx T, tx T + T] clipped to the grid: every corner
-// of the tile's cells), then ext[l] / ext[L + l] = the surface's min / max.
-// All threads must call it; the planes must be staged and synchronised.
-template <int L>
-__device__ __forceinline__ void tile_bounds(const Prob &pb, const float2 *planes, float2 *tb, float *ext)
-{
-    const int T = pb.tile_T, nx = pb.tile_nx, nt = pb.tile_nx * pb.tile_ny;
-    for (int idx = threadIdx.x; idx < L * nt; idx += blockDim.x) {
-        const int l = idx / nt, t = idx - l * nt;
-        const int ty = t / nx, tx = t - ty * nx;
-        const int r0 = ty * T, r1 = min(r0 + T, pb.R - 1), c0 = tx * T, c1 = min(c0 + T, pb.Q - 1);
-        const float2 *pl = planes + (size_t)l * pb.N;
-        float lo = INFINITY, hi = -INFINITY;
-        for (int r = r0; r <= r1; ++r)
-            for (int c = c0; c <= c1; ++c) {
-                const float v = pl[r * pb.Q + c].x;
-                lo = fminf(lo, v);
-                hi = fmaxf(hi, v);
-            }
-        tb[idx] = make_float2(lo, hi);
-    }
-    __syncthreads();
-    if (threadIdx.x < L) {
-        const int l = threadIdx.x;
-        float lo = INFINITY, hi = -INFINITY;
-        for (int t = 0; t < nt; ++t) {
-            lo = fminf(lo, tb[l * nt + t].x);
-            hi = fmaxf(hi, tb[l * nt + t].y);
-        }
-        ext[l] = lo;
-        ext[L + l] = hi;
     }
 }
 
@@ -463,6 +428,7 @@ __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, float4
     for (int j0 = 0; j0 < np; j0 += 128) {
         const int jn = min(128, np - j0);
         uint32_t acc = 0u;
+#pragma unroll 4
         for (int j = 0; j < jn; ++j) {
             const float2 v = dx_pair<HARD, GLOBAL>(pl, Q, kf2, ox2, oy2, sx2, sy2, szh2, szl2, zh2, zl2,
                                                    nkg2, curA, curB, rA0, rA1, rB0, rB1);
@@ -518,46 +484,10 @@ __device__ __forceinline__ void transition_window(float z0, float dz, float rdz,
     hi = min((int)kb, G - 1);
 }
 
-// Narrow a surface's window [lo, hi] of an upward ray (dz > 0) with tile
-// bounds (tbl = the surface's {min, max} per tile): the window's samples lie
-// in cells between those of its end samples (cells from the same FP32
-// arithmetic as the march, which is monotone in k), hence in the tiles of
-// that bounding box; samples outside the bounds' own window are saturated on
-// the same side as before it or after it.  Bounding boxes of more than 16
-// tiles are left alone.
-__device__ __forceinline__ void refine_window(const Prob &pb, const float2 *tbl, float4 o, float4 st,
-                                              float rdz, float zh, int &lo, int &hi)
-{
-    if (lo > hi) return;
-    const float M = 12582912.0f;
-    const int T = pb.tile_T, nx = pb.tile_nx;
-    const float ka = (float)lo, kb = (float)hi;
-    const int cxa = __float_as_int(fmaf(ka, st.x, o.x) + M) - 0x4B400000;
-    const int cxb = __float_as_int(fmaf(kb, st.x, o.x) + M) - 0x4B400000;
-    const int cya = __float_as_int(fmaf(ka, st.y, o.y) + M) - 0x4B400000;
-    const int cyb = __float_as_int(fmaf(kb, st.y, o.y) + M) - 0x4B400000;
-    const int tx0 = min(cxa, cxb) / T, tx1 = max(cxa, cxb) / T;
-    const int ty0 = min(cya, cyb) / T, ty1 = max(cya, cyb) / T;
-    if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) > 16) return;
-    float bmin = INFINITY, bmax = -INFINITY;
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            const float2 b = tbl[ty * nx + tx];
-            bmin = fminf(bmin, b.x);
-            bmax = fmaxf(bmax, b.y);
-        }
-    int lo2, hi2;
-    transition_window(zh, st.z, rdz, pb.kg, bmin, bmax, pb.G, lo2, hi2);
-    const int nlo = min(max(lo2, lo), hi + 1);
-    hi = max(min(hi2, hi), nlo - 1);
-    lo = nlo;
-}
-
 // The FP32 modes' march of one ray: per surface l, the exact integer sum
 // N_l = sum_k varsigma(s_l - z_k) * 2^23 (see march_ray_f32 for the
 // arithmetic), computed over the samples where surface l can be
-// transitional (transition_window with ext = per-surface min / max offsets,
-// narrowed by refine_window where tile bounds tb are given);
+// transitional (transition_window with ext = per-surface min / max offsets);
 // the other samples' contributions are exact and added analytically (one
 // sample below the surface adds rcp(1) + 1 - 1 in units of 2^-23, one above
 // adds 0).  A window of odd length is widened by one saturated sample where
@@ -565,21 +495,19 @@ __device__ __forceinline__ void refine_window(const Prob &pb, const float2 *tbl,
 // called for l = 0 .. L-1 in order.
 template <int L, bool HARD, bool GLOBAL, typename Emit>
 __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *planes, int ray,
-                                             const float *ext, const float2 *tb,
-                                             unsigned long long *evaluated, Emit &&emit)
+                                             const float *ext, unsigned long long *evaluated,
+                                             Emit &&emit)
 {
     const float4 o = pb.o4[ray], st = pb.s4[ray];
     const uint32_t q_one = HARD ? 0x00800000u : __float_as_uint(rcp_approx(1.0f) + 1.0f) - 0x3F800000u;
     const int G = pb.G;
     const float rdz = rcp_approx(st.z);
-#pragma unroll 1
+#pragma unroll (L <= 5 ? L : 1)  // unrolled where registers allow (no spills)
     for (int l = 0; l < L; ++l) {
         const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
         const float zl = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
         int lo, hi;
         transition_window(zh, st.z, rdz, pb.kg, ext[l], ext[L + l], G, lo, hi);
-        if (tb && st.z >= 1e-20f)
-            refine_window(pb, tb + (size_t)l * pb.tile_nx * pb.tile_ny, o, st, rdz, zh, lo, hi);
         lo = min(lo, G);
         int he = max(hi + 1, lo);
         if ((he - lo) & 1) {
@@ -754,16 +682,9 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
         stage_nodes<S, Hh, L>(sh, chain_ptr<Hh>(h, c), pb.N, (MODE == MODE_F64) ? nullptr : pb.ref);
     }
     __shared__ float ext[2 * MT_MAX_L];
-    __shared__ float2 tiles[DX && !GLOBAL ? MT_MAX_TILES : 1];
-    const float2 *tb = nullptr;
     if constexpr (DX) {
-        if constexpr (GLOBAL) {
-            surface_extent<Hh, L>(chain_ptr<Hh>(h, c), pb.N, pb.ref, ext);
-        } else {
-            __syncthreads();  // planes staged
-            tile_bounds<L>(pb, planes, tiles, ext);
-            tb = tiles;
-        }
+        __syncthreads();  // planes staged
+        surface_extent<L>(planes, pb.N, ext);
     }
     __syncthreads();
 
@@ -780,7 +701,7 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
             // float-float; the term -C (e^y - 1 - y) (or -I0 e^{-O/Lambda} for
             // C = 0) in FP32, its product by C kept exact as a float-float.
             FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
-            march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, tb, pb.work ? &n_eval : nullptr,
+            march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, pb.work ? &n_eval : nullptr,
                                           [&](int l, unsigned long long tl) {
                 const FF n = ff_two_sum((float)(uint32_t)(tl >> 20) * 1048576.0f * 0x1p-23f,
                                         (float)(uint32_t)(tl & 0xFFFFFu) * 0x1p-23f);

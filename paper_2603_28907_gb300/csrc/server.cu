@@ -71,7 +71,7 @@ size_t footprint_of(const mt_request &r)
     b += rays * (16 + 16 + 8 * L + 24 + 24 + 8 + 8 + 8 + 8 + 4 + 8);  // ray table, counts
     b += C * ((rays + 4095) / 4096) * 8;            // partial sums
     b += L * N * 8 * 2;                             // prior mean, staging
-    if (N * L * 8 + MT_SMEM_STATIC_DX > MT_MAX_SMEM) b += C * N * L * 8;  // HBM (h, dx) planes
+    if (N * L * 8 + MT_SMEM_STATIC > MT_MAX_SMEM) b += C * N * L * 8;  // HBM (h, dx) planes
     if (r.kernel == MT_KERNEL_MALA) b += 3 * C * L * N * 8 + C * 8;
     b += rays * 16 + C * L * N * es;                // output staging
     return b + (8u << 20);                          // allocator slack
