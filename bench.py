@@ -43,7 +43,7 @@ FP32_PER_CLK_SM = 128    # FP32 lanes per SM (probe: 114.6 FMA/clk at the nomina
 # DRAM traffic of one k_march launch (read + write bytes) from the ncu capture
 # summarised in profiles/k_march_scenario_c128_ncu.md, scaled from 128 to 1024
 # chains; valid only for the kernel source it was measured on.
-MARCH_TRAFFIC = {"source_sha1": "fef326f82aac", "bytes": 72.0e6}
+MARCH_TRAFFIC = {"source_sha1": "6cc94c367900", "bytes": 73.0e6}
 
 
 def march_traffic():
@@ -51,6 +51,20 @@ def march_traffic():
     src = os.path.join(ROOT, "paper_2603_28907_gb300", "csrc", "march.cuh")
     h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
     return MARCH_TRAFFIC["bytes"] if h == MARCH_TRAFFIC["source_sha1"] else None
+
+
+# FP32 lane-ops per evaluated surface-sample of the FP32 march (two samples
+# per step: 19 paired FP32 instructions + 4 scalar x-lerp FMAs per 2 samples)
+EVAL_FP32_OPS = 21.0
+
+
+def march_peak_evaluated():
+    """Evaluated surface-samples per second the pipes allow for the march's
+    own op mix (21 FP32 lane-ops + ex2 + rcp per evaluated sample)."""
+    clk = SM_COUNT * SM_MAX_MHZ * 1e6
+    sfu = clk / (1.0 / EX2_PER_CLK_SM + 1.0 / RCP_PER_CLK_SM)
+    fp32 = clk * FP32_PER_CLK_SM / EVAL_FP32_OPS
+    return min(sfu, fp32)
 
 
 def march_peak(L):
@@ -580,12 +594,13 @@ def main():
                                        "128 FP32 lanes with 12+9L ops per sample",
                          "kernel": "k_march", "kernel_ms_avg": avg_launch_s * 1e3,
                          "launches": march_n,
-                         "evaluated_fraction": work_eval / work_total if work_total else None,
-                         "frac_evaluated_work": (achieved / peak) * (work_eval / work_total)
-                         if work_total else None,
-                         "note": "units are the method's surface-samples; samples at least 25 "
-                                 "log2 units from their surface are exactly 0/1 and added "
-                                 "without evaluation (bit-identical)"},
+                         "evaluated": evaluated_roofline(achieved, work_eval, work_total),
+                         "note": "units are the method's surface-samples (12+9L FP32 ops and "
+                                 "2L MUFU per sample); samples at least 25 log2 units from "
+                                 "their surface are exactly 0/1 and added without evaluation "
+                                 "(bit-identical), so frac can exceed 1; 'evaluated' rates the "
+                                 "samples the kernel did compute against the pipes' limit for "
+                                 "its own op mix"},
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -595,6 +610,19 @@ def main():
     if pg:
         pg.barrier()
         pg.destroy_process_group()
+
+
+def evaluated_roofline(achieved_t, work_eval, work_total):
+    """Roofline of the work the ray kernel actually did: evaluated
+    surface-samples per second against march_peak_evaluated()."""
+    if not work_total:
+        return None
+    frac_eval = work_eval / work_total
+    ach = achieved_t * frac_eval
+    peak = march_peak_evaluated() / 1e12
+    return {"fraction": frac_eval, "achieved": ach, "peak": peak, "frac": ach / peak,
+            "unit": "T evaluated surface-samples/s",
+            "ops_per_sample": f"{EVAL_FP32_OPS:g} FP32 lane-ops + ex2 + rcp"}
 
 
 def measure_e2e(ctx, H0np, stream, args, w, rays):
