@@ -91,6 +91,7 @@ struct mt_ctx {
     Prob pb{};
 
     double *d_mu = nullptr, *d_sensors = nullptr, *d_dirs = nullptr;
+    float2 *d_muff = nullptr;        // float-float prior mean (FP32-mode prior)
     float4 *d_o4 = nullptr, *d_s4 = nullptr;
     float *d_kz0 = nullptr;
     double *d_od = nullptr, *d_sd = nullptr, *d_dt = nullptr, *d_a = nullptr, *d_sumK = nullptr;
@@ -282,6 +283,11 @@ static void refresh_prob(mt_ctx *ctx)
         pb.ref[l] = (float)m;
     }
     pb.kz0 = ctx->d_kz0;
+    pb.mu_ff = ctx->d_muff;
+    pb.lz_f = (float)ctx->box[2];
+    if ((double)pb.lz_f > ctx->box[2]) pb.lz_f = nextafterf(pb.lz_f, -INFINITY);
+    pb.delta_ff = make_float2((float)ctx->cfg.min_thick,
+                              (float)(ctx->cfg.min_thick - (double)(float)ctx->cfg.min_thick));
     pb.perm = ctx->d_perm;
     pb.gnodes = nullptr;  // set per launch by ensure_nodes when the grid needs it
     pb.work = ctx->timing ? ctx->d_work : nullptr;
@@ -622,6 +628,7 @@ mt_status mt_destroy(mt_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     drop_chains(ctx);
     dfree(ctx->d_mu);
+    dfree(ctx->d_muff);
     dfree(ctx->d_sensors);
     dfree(ctx->d_dirs);
     dfree(ctx->d_o4);
@@ -687,6 +694,15 @@ mt_status mt_set_grid(mt_ctx *ctx, int n_layers, int n_rows, int n_cols, const d
     if (prior_mean) ctx->mu.assign(prior_mean, prior_mean + n);
     TRY(dalloc(ctx, &ctx->d_mu, n));
     CK(ctx, cudaMemcpyAsync(ctx->d_mu, ctx->mu.data(), n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<float2> muff(n);
+    for (size_t i = 0; i < n; ++i) {
+        const float hi = (float)ctx->mu[i];
+        muff[i] = make_float2(hi, (float)(ctx->mu[i] - (double)hi));
+    }
+    TRY(dalloc(ctx, &ctx->d_muff, n));
+    CK(ctx, cudaMemcpyAsync(ctx->d_muff, muff.data(), n * sizeof(float2), cudaMemcpyHostToDevice,
+                            ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));  // muff is a local host buffer
     ctx->have_grid = true;
     ctx->have_counts = false;
     refresh_prob(ctx);

@@ -54,6 +54,9 @@ struct Prob {
                                // planes in HBM, [chain][l][node] float2; else nullptr
     const int *perm;           // march order of the rays (ray table sorted by vertical
                                // step, then start height); nullptr = ray order
+    const float2 *mu_ff;       // [L][N] float-float of the prior mean (FP32-mode prior)
+    float lz_f;                // largest float <= box[2]
+    float2 delta_ff;           // float-float of the minimum thickness
     float2 grho_ff;            // float-float of G * rho_top
     float2 invL_ff;            // float-float of 1 / Lambda
 };

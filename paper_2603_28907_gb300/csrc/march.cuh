@@ -387,13 +387,32 @@ __device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, float2 kf2, f
     const float2 fy = add2(fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy), f2(0.5f));
     const int nA = (__float_as_int(ty.x) - 0x4B400000) * Q + (__float_as_int(tx.x) - 0x4B400000);
     const int nB = (__float_as_int(ty.y) - 0x4B400000) * Q + (__float_as_int(tx.y) - 0x4B400000);
-    if (nA != curA || nB != curB) {
+    if constexpr (GLOBAL) {
+        if (nA != curA || nB != curB) {
+            curA = nA;
+            curB = nB;
+            rA0 = __ldg(pl + nA);
+            rA1 = __ldg(pl + nA + Q);
+            rB0 = __ldg(pl + nB);
+            rB1 = __ldg(pl + nB + Q);
+        }
+    } else {
+        // reload both samples' corner records when either entered a new cell:
+        // predicated shared loads instead of a divergent branch
+        const uint32_t need = (uint32_t)((nA != curA) | (nB != curB));
         curA = nA;
         curB = nB;
-        rA0 = GLOBAL ? __ldg(pl + nA) : pl[nA];
-        rA1 = GLOBAL ? __ldg(pl + nA + Q) : pl[nA + Q];
-        rB0 = GLOBAL ? __ldg(pl + nB) : pl[nB];
-        rB1 = GLOBAL ? __ldg(pl + nB + Q) : pl[nB + Q];
+        const uint32_t base = (uint32_t)__cvta_generic_to_shared(pl);
+        const uint32_t aA0 = base + (uint32_t)nA * 8u, aA1 = aA0 + (uint32_t)Q * 8u;
+        const uint32_t aB0 = base + (uint32_t)nB * 8u, aB1 = aB0 + (uint32_t)Q * 8u;
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %8, 0;\n\t"
+                     "@p ld.shared.v2.f32 {%0, %1}, [%9];\n\t"
+                     "@p ld.shared.v2.f32 {%2, %3}, [%10];\n\t"
+                     "@p ld.shared.v2.f32 {%4, %5}, [%11];\n\t"
+                     "@p ld.shared.v2.f32 {%6, %7}, [%12];\n\t}"
+                     : "+f"(rA0.x), "+f"(rA0.y), "+f"(rA1.x), "+f"(rA1.y),
+                       "+f"(rB0.x), "+f"(rB0.y), "+f"(rB1.x), "+f"(rB1.y)
+                     : "r"(need), "r"(aA0), "r"(aA1), "r"(aB0), "r"(aB1));
     }
     const float2 a = make_float2(fmaf(fx.x, rA0.y, rA0.x), fmaf(fx.y, rB0.y, rB0.x));  // row r0
     const float2 b = make_float2(fmaf(fx.x, rA1.y, rA1.x), fmaf(fx.y, rB1.y, rB1.x));  // row r0 + 1

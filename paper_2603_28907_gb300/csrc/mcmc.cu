@@ -17,42 +17,107 @@ namespace mt {
 // lp = -tau/2 sum_l (h_l - mu_l)^T Q (h_l - mu_l), Q = diag(A 1) - r A on the
 // periodic 4-neighbour grid (Eq. def_CAR_precision, Fig. neighbors), and -inf
 // unless every height is in [0, Lz] and every thickness is >= delta (Sec.
-// 2.1.3, strictly positive thicknesses).  FP64, one block per chain.
-template <typename H>
-__global__ void __launch_bounds__(256) k_prior(Prob pb, HRef h, const double *mu, double *lp_out)
+// 2.1.3, strictly positive thicknesses).  With e = h - mu, the quadratic form
+// is sum_nodes e (4 e - r (e_up + e_down + e_right + e_left))
+//   = 4 sum e^2 - 2 r sum_nodes e (e_right + e_up)
+// (each neighbour pair appears twice in the first sum; the identity also holds
+// where a side of 2 or 1 nodes makes the wrap-around neighbours coincide).
+// One block per chain; each thread walks nodes i, i + 256, ... with its
+// (layer, row, col) stepped incrementally.
+constexpr int kPriorThreads = 256;
+
+struct NodeWalk {
+    int l, r, c, dr, dc;
+    __device__ NodeWalk(int i, int N, int Q) : l(i / N), r((i % N) / Q), c(i % Q), dr(kPriorThreads / Q), dc(kPriorThreads % Q) {}
+    __device__ void next(int R, int Q)
+    {
+        c += dc;
+        r += dr;
+        if (c >= Q) {
+            c -= Q;
+            ++r;
+        }
+        while (r >= R) {
+            r -= R;
+            ++l;
+        }
+    }
+};
+
+// FP64 heights (F64 mode): FP64 arithmetic.
+__global__ void __launch_bounds__(kPriorThreads) k_prior_f64(Prob pb, HRef h, const double *mu, double *lp_out)
 {
     const int c = blockIdx.x;
-    const H *Hc = chain_ptr<H>(h, c);
-    const int N = pb.N, Q = pb.Q, R = pb.R;
-    const int n = pb.L * N;
-    double quad = 0.0;
+    const double *Hc = chain_ptr<double>(h, c);
+    const int N = pb.N, Q = pb.Q, R = pb.R, n = pb.L * N;
+    double q1 = 0.0, q2 = 0.0;
     int bad = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int l = i / N, rc = i - l * N, r = rc / Q, cc = rc - r * Q;
-        const double hv = (double)Hc[i];
+    NodeWalk wk(threadIdx.x, N, Q);
+    for (int i = threadIdx.x; i < n; i += kPriorThreads, wk.next(R, Q)) {
+        const int base = wk.l * N, rt = wk.c + 1 == Q ? 0 : wk.c + 1, up = wk.r + 1 == R ? 0 : wk.r + 1;
+        const double hv = Hc[i];
         if (!(hv >= 0.0 && hv <= pb.box[2])) bad = 1;
-        if (l > 0 && !(hv - (double)Hc[i - N] >= pb.delta)) bad = 1;
-        const int up = r + 1 == R ? 0 : r + 1, dn = r == 0 ? R - 1 : r - 1;
-        const int rt = cc + 1 == Q ? 0 : cc + 1, lf = cc == 0 ? Q - 1 : cc - 1;
-        const H *hl = Hc + (size_t)l * N;
-        const double *ml = mu + (size_t)l * N;
-        const double e = hv - ml[rc];
-        const double nb = ((double)hl[up * Q + cc] - ml[up * Q + cc]) +
-                          ((double)hl[dn * Q + cc] - ml[dn * Q + cc]) +
-                          ((double)hl[r * Q + rt] - ml[r * Q + rt]) +
-                          ((double)hl[r * Q + lf] - ml[r * Q + lf]);
-        quad += e * (4.0 * e - pb.car_r * nb);
+        if (wk.l > 0 && !(hv - Hc[i - N] >= pb.delta)) bad = 1;
+        const int iR = base + wk.r * Q + rt, iU = base + up * Q + wk.c;
+        const double e = hv - mu[i];
+        const double t = (Hc[iR] - mu[iR]) + (Hc[iU] - mu[iU]);
+        q1 = fma(e, e, q1);
+        q2 = fma(e, t, q2);
     }
-    quad = block_sum(quad);
+    const double quad = block_sum(4.0 * q1 - 2.0 * pb.car_r * q2);
     bad = __syncthreads_or(bad);
     if (threadIdx.x == 0) lp_out[c] = bad ? -INFINITY : -0.5 * pb.tau * quad;
+}
+
+// e = h - mu as a float-float (h a float, mu = mu_ff.x + mu_ff.y).
+__device__ __forceinline__ FF ff_dev(float hv, float2 m)
+{
+    return ff_add(ff_two_sum(hv, -m.x), FF{-m.y, 0.f});
+}
+
+// FP32 heights: float-float arithmetic on the FP32 pipes (relative error
+// ~2^-44 of the quadratic form; FP64 runs at a small fraction of the FP32
+// rate here).  Bounds and thicknesses are decided exactly: h <= Lz as
+// h <= the largest float <= Lz, and h_l - h_{l-1} (exact as a float-float
+// two-sum) against delta as a float-float.
+__global__ void __launch_bounds__(kPriorThreads) k_prior_f32(Prob pb, HRef h, double *lp_out)
+{
+    const int c = blockIdx.x;
+    const float *Hc = chain_ptr<float>(h, c);
+    const float2 *mu = pb.mu_ff;
+    const int N = pb.N, Q = pb.Q, R = pb.R, n = pb.L * N;
+    FF q1 = {0.f, 0.f}, q2 = {0.f, 0.f};
+    int bad = 0;
+    NodeWalk wk(threadIdx.x, N, Q);
+    for (int i = threadIdx.x; i < n; i += kPriorThreads, wk.next(R, Q)) {
+        const int base = wk.l * N, rt = wk.c + 1 == Q ? 0 : wk.c + 1, up = wk.r + 1 == R ? 0 : wk.r + 1;
+        const float hv = Hc[i];
+        if (!(hv >= 0.0f && hv <= pb.lz_f)) bad = 1;
+        if (wk.l > 0) {
+            const FF d = ff_two_sum(hv, -Hc[i - N]);
+            if (d.hi < pb.delta_ff.x || (d.hi == pb.delta_ff.x && d.lo < pb.delta_ff.y)) bad = 1;
+        }
+        const int iR = base + wk.r * Q + rt, iU = base + up * Q + wk.c;
+        const FF e = ff_dev(hv, mu[i]);
+        const FF t = ff_add(ff_dev(Hc[iR], mu[iR]), ff_dev(Hc[iU], mu[iU]));
+        q1 = ff_add(q1, ff_mul(e, e));
+        q2 = ff_add(q2, ff_mul(e, t));
+    }
+    q1 = block_sum(q1);
+    __syncthreads();  // block_sum reuses its shared buffer
+    q2 = block_sum(q2);
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        const double quad = 4.0 * ((double)q1.hi + (double)q1.lo) - 2.0 * pb.car_r * ((double)q2.hi + (double)q2.lo);
+        lp_out[c] = bad ? -INFINITY : -0.5 * pb.tau * quad;
+    }
 }
 
 cudaError_t launch_prior(const Prob &pb, int mode, HRef h, const double *mu, int n_chains,
                          double *lp_out, cudaStream_t st)
 {
-    if (mode == MODE_F64) k_prior<double><<<n_chains, 256, 0, st>>>(pb, h, mu, lp_out);
-    else k_prior<float><<<n_chains, 256, 0, st>>>(pb, h, mu, lp_out);
+    if (mode == MODE_F64) k_prior_f64<<<n_chains, kPriorThreads, 0, st>>>(pb, h, mu, lp_out);
+    else k_prior_f32<<<n_chains, kPriorThreads, 0, st>>>(pb, h, lp_out);
     return cudaGetLastError();
 }
 
