@@ -596,7 +596,7 @@ def main():
                          "launches": march_n,
                          "evaluated": evaluated_roofline(achieved, work_eval, work_total),
                          "note": "units are the method's surface-samples (12+9L FP32 ops and "
-                                 "2L MUFU per sample); samples at least 25 log2 units from "
+                                 "2L MUFU per sample); samples at least 24.25 log2 units from "
                                  "their surface are exactly 0/1 and added without evaluation "
                                  "(bit-identical), so frac can exceed 1; 'evaluated' rates the "
                                  "samples the kernel did compute against the pipes' limit for "

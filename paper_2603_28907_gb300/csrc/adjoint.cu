@@ -9,13 +9,18 @@
 // from every sample k, with varsigma' = varsigma (1 - varsigma) / gamma and
 // w_n the bilinear weight of the node.  The log-prior adds -tau Q (h_l - mu_l).
 //
-// Each ray is marched twice by its thread: pass 1 gives O_p (the same
-// arithmetic as the forward kernel), pass 2 recomputes the samples and
-// scatters.  A lane sums its contributions per cell in FP32 registers (in
-// sample order) and adds each cell's sums to 64-bit fixed-point accumulators
-// (units of 2^-32) with integer atomics, so the gradient does not depend on
-// the order in which threads add and is reproducible bit for bit; a sum that
-// rounds to zero at that resolution is not added.
+// Each ray is marched twice by its thread, one surface at a time: pass 1
+// gives O_p with the forward kernel's arithmetic and exact saturation windows
+// (so O_p equals the FP32 forward kernel's bit for bit), pass 2 recomputes the
+// samples and scatters.  A lane sums its contributions per cell in FP32
+// registers (in sample order) and adds each cell's sums to 64-bit fixed-point
+// accumulators (units of 2^-32) with integer atomics, so the gradient does not
+// depend on the order in which threads add and is reproducible bit for bit; a
+// sum that rounds to zero at that resolution is not added.  Pass 2 visits only
+// the samples within log2|coef_l| + 10 log2 units of surface l (coef_l: the
+// sample weight in fixed-point units); every sample outside has
+// varsigma' <= 2^-(that), so all of them together move a cell's sum by less
+// than G * 2^-10 fixed-point units.
 #include <math.h>
 
 #include "march.cuh"
@@ -31,84 +36,159 @@ __device__ __forceinline__ void add_fixed(unsigned long long *p, float v)
     if (q != 0) atomicAdd(p, (unsigned long long)q);
 }
 
-// Flush one lane's per-cell sums (4 corners x L surfaces) to the accumulators.
+// Surface l's corner heights of the cell at `node` from node-major records.
 template <int L>
-__device__ __forceinline__ void flush_cell(unsigned long long *acc, int N, int Q, int node,
-                                           float (&c00)[L], float (&c01)[L], float (&c10)[L],
-                                           float (&c11)[L])
+__device__ __forceinline__ void cell_corners(const float *sh, int node, int Q, int l, float &h00,
+                                             float &d0, float &h10, float &d1)
 {
+    constexpr int LP = NodeLayout<float, L>::LP;
+    h00 = sh[node * LP + l];
+    d0 = sh[(node + 1) * LP + l] - h00;
+    h10 = sh[(node + Q) * LP + l];
+    d1 = sh[(node + Q + 1) * LP + l] - h10;
+}
+
+// Per-surface minimum / maximum of node-major records (block reduction into
+// ext[l], ext[L + l]); all threads call it after the records are staged.
+template <int L>
+__device__ __forceinline__ void node_extent(const float *sh, int N, float *ext)
+{
+    constexpr int LP = NodeLayout<float, L>::LP;
+    __shared__ float red[2 * MT_MAX_L][32];
+    float lo[L], hi[L];
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-        unsigned long long *al = acc + (size_t)l * N + node;
-        add_fixed(al, c00[l]);
-        add_fixed(al + 1, c01[l]);
-        add_fixed(al + Q, c10[l]);
-        add_fixed(al + Q + 1, c11[l]);
-        c00[l] = c01[l] = c10[l] = c11[l] = 0.f;
+        lo[l] = INFINITY;
+        hi[l] = -INFINITY;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const float v = sh[i * LP + l];
+            lo[l] = fminf(lo[l], v);
+            hi[l] = fmaxf(hi[l], v);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[l] = fminf(lo[l], __shfl_xor_sync(0xffffffffu, lo[l], o));
+            hi[l] = fmaxf(hi[l], __shfl_xor_sync(0xffffffffu, hi[l], o));
+        }
+        if (lane == 0) {
+            red[l][warp] = lo[l];
+            red[MT_MAX_L + l][warp] = hi[l];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < L) {
+        float a = INFINITY, b = -INFINITY;
+        for (int j = 0; j < nw; ++j) {
+            a = fminf(a, red[threadIdx.x][j]);
+            b = fmaxf(b, red[MT_MAX_L + threadIdx.x][j]);
+        }
+        ext[threadIdx.x] = a;
+        ext[L + threadIdx.x] = b;
     }
 }
 
-// Pass 2 for one ray: scatter coef_l * varsigma' * w_n into acc[l][node].  The
-// lane sums its contributions in registers while it stays in one cell (in
-// sample order) and adds them to the fixed-point accumulators when it leaves.
+// Pass 1 for surface l over samples [lo, he): the exact integer indicator sum
+// (units 2^-23) with the forward kernel's per-sample arithmetic.
 template <int L>
-__device__ __forceinline__ void scatter_ray(const Prob &pb, const float *sh, int ray,
-                                            const float (&coef)[L], unsigned long long *acc)
+__device__ __forceinline__ unsigned long long forward_surface(const Prob &pb, const float *sh, int l,
+                                                              float4 o, float4 st, float zh, float zl,
+                                                              int lo, int he)
 {
-    const float4 o = pb.o4[ray], st = pb.s4[ray];
-    float z0h[L], z0l[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-        z0h[l] = pb.kz0[(size_t)l * pb.n_rays + ray];
-        z0l[l] = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
-    }
     const float M = 12582912.0f;
     const float nkg = -pb.kg;
-    const int Q = pb.Q, N = pb.N;
-    float h00[L], h01[L], h10[L], h11[L];
-    float c00[L], c01[L], c10[L], c11[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) h00[l] = h01[l] = h10[l] = h11[l] = c00[l] = c01[l] = c10[l] = c11[l] = 0.f;
+    const int Q = pb.Q;
+    float h00 = 0.f, d0 = 0.f, h10 = 0.f, d1 = 0.f;
     int cur = -1;
-    float kf = 0.f;
-    for (int k = 0; k < pb.G; ++k, kf += 1.0f) {
+    float kf = (float)lo;
+    unsigned long long t = 0ull;
+    for (int k0 = lo; k0 < he; k0 += 256) {
+        const int kn = min(256, he - k0);
+        uint32_t acc = 0u;
+        for (int k = 0; k < kn; ++k, kf += 1.0f) {
+            const float gx = fmaf(kf, st.x, o.x), gy = fmaf(kf, st.y, o.y);
+            const float tx = gx + M, ty = gy + M;
+            const float fx = (gx - (tx - M)) + 0.5f, fy = (gy - (ty - M)) + 0.5f;
+            const int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
+            if (node != cur) {
+                cur = node;
+                cell_corners<L>(sh, node, Q, l, h00, d0, h10, d1);
+            }
+            const float a = fmaf(fx, d0, h00), b = fmaf(fx, d1, h10);
+            const float sl = fmaf(fy, fmaf(a, -1.0f, b), a);
+            const float zlv = fmaf(kf, st.w, fmaf(kf, st.z, zh) + zl);
+            const float arg = fmaf(nkg, sl, zlv);
+            acc += __float_as_uint(rcp_approx(1.0f + ex2_approx(arg)) + 1.0f);
+        }
+        t += (unsigned long long)(acc - (uint32_t)kn * 0x3F800000u);
+    }
+    return t;
+}
+
+// Pass 2 for surface l over samples [lo, he): scatter coef * varsigma' * w_n
+// into acc[l][node]; sums are kept per cell in registers and added to the
+// fixed-point accumulators when the sample leaves the cell.
+template <int L>
+__device__ __forceinline__ void scatter_surface(const Prob &pb, const float *sh, int l, float4 o,
+                                                float4 st, float zh, float zl, int lo, int he,
+                                                float coef, unsigned long long *acc)
+{
+    const float M = 12582912.0f;
+    const float nkg = -pb.kg;
+    const int Q = pb.Q;
+    unsigned long long *al = acc + (size_t)l * pb.N;
+    float h00 = 0.f, d0 = 0.f, h10 = 0.f, d1 = 0.f;
+    float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
+    int cur = -1;
+    float kf = (float)lo;
+    for (int k = lo; k < he; ++k, kf += 1.0f) {
         const float gx = fmaf(kf, st.x, o.x), gy = fmaf(kf, st.y, o.y);
         const float tx = gx + M, ty = gy + M;
         const float fx = (gx - (tx - M)) + 0.5f, fy = (gy - (ty - M)) + 0.5f;
         const int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
         if (node != cur) {
-            if (cur >= 0) flush_cell<L>(acc, N, Q, cur, c00, c01, c10, c11);
+            if (cur >= 0) {
+                add_fixed(al + cur, c00);
+                add_fixed(al + cur + 1, c01);
+                add_fixed(al + cur + Q, c10);
+                add_fixed(al + cur + Q + 1, c11);
+                c00 = c01 = c10 = c11 = 0.f;
+            }
             cur = node;
-            load_node<float, float, L>(sh, node, h00);
-            load_node<float, float, L>(sh, node + 1, h01);
-            load_node<float, float, L>(sh, node + Q, h10);
-            load_node<float, float, L>(sh, node + Q + 1, h11);
+            cell_corners<L>(sh, node, Q, l, h00, d0, h10, d1);
         }
-        const float w01 = fx * (1.0f - fy), w00 = (1.0f - fx) * (1.0f - fy);
-        const float w11 = fx * fy, w10 = (1.0f - fx) * fy;
-#pragma unroll
-        for (int l = 0; l < L; ++l) {
-            const float a = fmaf(fx, h01[l] - h00[l], h00[l]);
-            const float b = fmaf(fx, h11[l] - h10[l], h10[l]);
-            const float sl = fmaf(fy, b - a, a);
-            const float zl = fmaf(kf, st.w, fmaf(kf, st.z, z0h[l]) + z0l[l]);
-            // varsigma (1 - varsigma) = e / (1 + e)^2 is symmetric in the sign of
-            // the argument; with e = 2^-|arg| <= 1 nothing overflows
-            const float e = ex2_approx(-fabsf(fmaf(nkg, sl, zl)));
-            const float sg = rcp_approx(1.0f + e);
-            const float v = coef[l] * (e * sg * sg);
-            c00[l] = fmaf(v, w00, c00[l]);
-            c01[l] = fmaf(v, w01, c01[l]);
-            c10[l] = fmaf(v, w10, c10[l]);
-            c11[l] = fmaf(v, w11, c11[l]);
-        }
+        const float a = fmaf(fx, d0, h00), b = fmaf(fx, d1, h10);
+        const float sl = fmaf(fy, fmaf(a, -1.0f, b), a);
+        const float zlv = fmaf(kf, st.w, fmaf(kf, st.z, zh) + zl);
+        // varsigma (1 - varsigma) = e / (1 + e)^2 is symmetric in the sign of
+        // the argument; with e = 2^-|arg| <= 1 nothing overflows
+        const float e = ex2_approx(-fabsf(fmaf(nkg, sl, zlv)));
+        const float sg = rcp_approx(1.0f + e);
+        const float v = coef * (e * sg * sg);
+        const float vy = v * fy, vny = v - vy;  // v fy, v (1 - fy)
+        c00 = fmaf(-fx, vny, c00 + vny);        // v (1 - fx)(1 - fy)
+        c01 = fmaf(fx, vny, c01);               // v fx (1 - fy)
+        c10 = fmaf(-fx, vy, c10 + vy);          // v (1 - fx) fy
+        c11 = fmaf(fx, vy, c11);                // v fx fy
     }
-    if (cur >= 0) flush_cell<L>(acc, N, Q, cur, c00, c01, c10, c11);
+    if (cur >= 0) {
+        add_fixed(al + cur, c00);
+        add_fixed(al + cur + 1, c01);
+        add_fixed(al + cur + Q, c10);
+        add_fixed(al + cur + Q + 1, c11);
+    }
 }
 
-// One CTA = one chain x one block of rays.  SMEM: accumulate in shared memory
-// and flush once per CTA; otherwise add straight into global memory.
-constexpr int kAdjThreads = 512;  // one CTA per SM with the scenario's 192 KB of shared memory
+// One CTA = one chain x one block of ray slots (slot i -> ray perm[i]).  SMEM:
+// accumulate in shared memory and flush once per CTA; otherwise add straight
+// into global memory.
+constexpr int kAdjThreads = 1024;  // one CTA per SM with the scenario's 192 KB of shared memory
 
 template <int L, bool SMEM>
 __global__ void __launch_bounds__(kAdjThreads)
@@ -125,18 +205,33 @@ k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long lo
     stage_nodes<float, float, L>(sh, chain_ptr<float>(h, c), N, pb.ref);
     if constexpr (SMEM)
         for (int i = threadIdx.x; i < L * N; i += blockDim.x) acc_s[i] = 0ull;
+    __shared__ float ext[2 * MT_MAX_L];
+    __syncthreads();
+    node_extent<L>(sh, N, ext);
     __syncthreads();
     unsigned long long *acc = SMEM ? acc_s : gc;
+    const uint32_t q_one = __float_as_uint(rcp_approx(1.0f) + 1.0f) - 0x3F800000u;
 
     const int r_begin = blockIdx.x * rays_per_block;
     const int r_end = min(r_begin + rays_per_block, pb.n_rays);
     double ll = 0.0;
-    for (int ray = r_begin + threadIdx.x; ray < r_end; ray += blockDim.x) {
-        unsigned long long tot[L];
-        march_ray_f32<L, false, float>(pb, sh, ray, tot);
+    for (int slot = r_begin + threadIdx.x; slot < r_end; slot += blockDim.x) {
+        const int ray = pb.perm ? pb.perm[slot] : slot;
+        const float4 o = pb.o4[ray], st = pb.s4[ray];
+        const float rdz = rcp_approx(st.z);
         double S_ = 0.0;
-#pragma unroll
-        for (int l = 0; l < L; ++l) S_ = fma(pb.drho[l], (double)tot[l] * 0x1p-23, S_);
+#pragma unroll 1
+        for (int l = 0; l < L; ++l) {
+            const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
+            const float zl = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
+            int lo, hi;
+            transition_window(zh, st.z, rdz, pb.kg, ext[l], ext[L + l], pb.G, lo, hi);
+            lo = min(lo, pb.G);
+            const int he = max(hi + 1, lo);
+            const unsigned long long tl =
+                (unsigned long long)lo * q_one + forward_surface<L>(pb, sh, l, o, st, zh, zl, lo, he);
+            S_ = fma(pb.drho[l], (double)tl * 0x1p-23, S_);
+        }
         const double O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
         const int Cp = pb.cnt[ray];
         const double lam = pb.I0 * exp(-O * pb.inv_Lambda);
@@ -148,10 +243,21 @@ k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long lo
         }
         const double dO = (lam - (double)Cp) * pb.inv_Lambda;  // d ll / d O_p
         const double base = dO * pb.dt[ray] / pb.gamma * (double)kFix;
-        float coef[L];
-#pragma unroll
-        for (int l = 0; l < L; ++l) coef[l] = (float)(base * pb.drho[l]);
-        scatter_ray<L>(pb, sh, ray, coef, acc);
+#pragma unroll 1
+        for (int l = 0; l < L; ++l) {
+            const float coef = (float)(base * pb.drho[l]);
+            if (coef == 0.0f) continue;
+            // samples beyond log2|coef| + 10 log2 units from the surface add
+            // less than 2^-10 fixed-point units each
+            const float ka = fmaxf(log2f(fabsf(coef)) + 10.0f, 1.0f);
+            const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
+            const float zl = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
+            int lo, hi;
+            transition_window(zh, st.z, rdz, pb.kg, ext[l], ext[L + l], pb.G, lo, hi, ka);
+            lo = min(lo, pb.G);
+            const int he = max(hi + 1, lo);
+            scatter_surface<L>(pb, sh, l, o, st, zh, zl, lo, he, coef, acc);
+        }
     }
     ll = block_sum(ll);
     if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = ll;

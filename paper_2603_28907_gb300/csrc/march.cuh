@@ -466,23 +466,24 @@ __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, float4
 
 // Samples whose sigmoid argument is at least kSat (log2 units) from zero have
 // integer contributions known without evaluating them.  Above the surface
-// (arg >= kSat) sigma = rcp(1 + 2^arg) <= 2^-24, and sigma + 1 rounds to
-// exactly 1.0f (round to nearest even); below it (arg <= -kSat) 2^arg <=
-// 2^-24, 1 + 2^arg rounds to exactly 1.0f, and the sample adds rcp(1) + 1.
-// |arg| >= 24 suffices; kSat = 25 leaves a whole log2 unit for the relative
-// error of ex2.approx / rcp.approx (~2^-22) and for the FP32 rounding of the
-// argument and of the window bounds (~1e-5 log2 units).
-constexpr float kSat = 25.0f;
+// (arg >= kSat > 24) 2^arg > 2^24 even with ex2.approx's relative error
+// (~2^-22), so sigma = rcp(1 + 2^arg) < 2^-24 and sigma + 1 rounds to exactly
+// 1.0f; below it (arg <= -kSat) 2^arg < 2^-24, 1 + 2^arg rounds to exactly
+// 1.0f, and the sample adds rcp(1) + 1.  The margin 0.25 over 24 is four
+// orders of magnitude above the FP32 rounding of the argument and of the
+// window bounds (~2e-5 log2 units).
+constexpr float kSat = 24.25f;
 
 // Sample window [lo, hi] in which surface l can be transitional along a ray:
-// outside it |kg (z - s_l)| >= kSat for every height in [smin, smax] (offsets
+// outside it |kg (z - s_l)| >= ksat for every height in [smin, smax] (offsets
 // h - ref_l).  z_l(k) = z0 + k dz (scaled by kg); rdz ~ 1 / dz.  The sample
 // bounds are widened by 2^-20 (|k| + 1), many times the relative rounding
 // error of (bound - z0) * rdz, so the window never loses a sample.
 __device__ __forceinline__ void transition_window(float z0, float dz, float rdz, float kg, float smin,
-                                                  float smax, int G, int &lo, int &hi)
+                                                  float smax, int G, int &lo, int &hi,
+                                                  float ksat = kSat)
 {
-    const float a = kg * smin - kSat, b = kg * smax + kSat;  // z_l must lie in (a, b)
+    const float a = kg * smin - ksat, b = kg * smax + ksat;  // z_l must lie in (a, b)
     if (!(fabsf(dz) >= 1e-20f)) {
         const bool in = z0 > a && z0 < b;
         lo = in ? 0 : G;
