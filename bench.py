@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving mix instead of the Metropolis step benchmark")
     ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--diag", action="store_true",
+                    help="time the chain diagnostics (nested R-hat, interface std) on the scenario")
     ap.add_argument("--study", choices=["precision", "gradient"], default=None,
                     help="precision-mode or gradient/MALA study on the scenario data")
     ap.add_argument("--proposals", type=int, default=100000)
@@ -474,6 +476,56 @@ def run_gradient_study(args, local):
     print(json.dumps({"study": "gradient", "workload": w.name, **out}), flush=True)
 
 
+def run_diag(args, local):
+    """Nested R-hat over 1024 scenario chains (32 super-chains of 32; one and
+    ten stored draws) and the interface standard deviation over 1024 samples
+    at 150 levels, timed with CUDA events, the FP64 oracle beside them."""
+    import torch
+    from paper_2603_28907_gb300 import mt
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.scenario()
+    pr = W.problem(w)
+    ctx = mt.from_workload(pr, precision=mt.PREC_F32, device=local)
+    C, K, n_z = 1024, 32, 150
+    H = torch.tensor(W.init_chains(w, C).astype(np.float32), device=dev)
+    P = w.L * w.R * w.Q
+    r = torch.zeros(P, dtype=torch.float64, device=dev)
+    out = torch.zeros((w.L, n_z, w.R, w.Q), dtype=torch.float64, device=dev)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {}
+    for N in (1, 10):
+        d = (H[None] + 0.01 * torch.randn((N,) + tuple(H.shape), device=dev)).contiguous()
+        ms = timed(lambda: ctx.nested_rhat(d, K, r))
+        res[f"nested_rhat_draws_{N}"] = {"ms": ms, "bytes_read": 3 * d.numel() * 4,
+                                         "GB_per_s": 3 * d.numel() * 4 / ms / 1e6}
+    ms = timed(lambda: ctx.interface_std(H, n_z, out))
+    res["interface_std"] = {"ms": ms, "samples": C, "levels": n_z,
+                            "voxels": w.L * n_z * w.R * w.Q}
+    from oracle import diagnostics as D
+    hn = H.cpu().double().numpy()
+    t0 = time.perf_counter()
+    D.nested_rhat(hn.reshape(1, C, P), K)
+    res["oracle_nested_rhat_draws_1_ms"] = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    D.interface_std(hn[:128], w.box[2], n_z)
+    res["oracle_interface_std_128_samples_ms"] = (time.perf_counter() - t0) * 1e3
+    print(json.dumps({"diag": "chain diagnostics", "workload": w.name, "chains": C,
+                      "super_chains": K, **res}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -487,6 +539,10 @@ def main():
     if args.study == "gradient":
         if rank == 0:
             run_gradient_study(args, local)
+        return
+    if args.diag:
+        if rank == 0:
+            run_diag(args, local)
         return
     w = W.scenario()
     if args.chains:

@@ -98,7 +98,11 @@ typedef struct {
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
  * to run on (borrowed; NULL = the library creates and owns one).  *out is set
- * on success.  Errors: MT_EINVAL (bad config), MT_ECUDA, MT_ENOMEM. */
+ * on success.  Errors: MT_EINVAL (bad config), MT_ECUDA, MT_ENOMEM.
+ * Verification switch: if the environment variable MT_FULL_WINDOWS is set to
+ * a value other than "0" when the context is created, its FP32 ray kernels
+ * evaluate every sample instead of skipping the exactly saturated ones; the
+ * results are bit-identical, only slower. */
 MT_API mt_status mt_create(mt_ctx **out, int device, const mt_config *cfg, void *cuda_stream);
 
 /* Release every device buffer, graph and event of the context. NULL is a no-op. */
@@ -234,6 +238,37 @@ MT_API mt_status mt_get_work(mt_ctx *ctx, double *evaluated, double *total, int 
 /* Sizes of the loaded problem (any pointer nullable). */
 MT_API mt_status mt_get_sizes(const mt_ctx *ctx, int *n_layers, int *n_rows, int *n_cols,
                        int *n_sensors, int *n_pixels, int *n_chains);
+
+/* ------------------------------------------------------------------------
+ * Chain diagnostics.
+ *
+ * Nested R-hat (Sec. 3.2: chains grouped into super-chains that share a
+ * start, to detect chains stuck near it; statistic of Margossian et al. 2024)
+ * of every height over stored draws.  draws: [n_draws][n_chains][L][R][Q],
+ * host or device, FP64 in MT_PREC_F64 and FP32 otherwise (what
+ * mt_get_state returns).  Chains c = k*M .. k*M + M - 1 form super-chain k,
+ * M = n_chains / n_super.  Per height: B = variance of the super-chain means
+ * (divisor n_super - 1); W = mean over super-chains of the variance of their
+ * chain means (divisor M - 1, 0 if M = 1) plus the mean within-chain variance
+ * (divisor n_draws - 1, 0 if n_draws = 1); R = sqrt(1 + B / W), 1 if
+ * B = W = 0.  rhat_out: [L*R*Q] (host or device, nullable); rhat_max_out:
+ * host, nullable.  FP64.  Errors: MT_EINVAL (n_draws < 1, n_super < 2 or not
+ * dividing n_chains, null draws), MT_ESTATE (no grid). */
+MT_API mt_status mt_nested_rhat(mt_ctx *ctx, int n_draws, int n_chains, const void *draws, int n_super,
+                                double *rhat_out, double *rhat_max_out);
+
+/* Tomographic standard deviation of the below-interface indicators
+ * B^l_{ijk}(H) = eta(H_{l,i,j} - z_k), eta(0) = 1/2 (Eq.
+ * def_below_interface_indicator; Sec. 4, Fig. tomography_std_poisson) over
+ * n_samples height sets: voxel columns at the surface nodes, levels
+ * z_k = k * box[2] / n_z, k = 0 .. n_z - 1 (box as given to mt_set_grid;
+ * heights are measured from the box floor).  Population standard deviation
+ * sqrt(mean(B^2) - mean(B)^2), in [0, 1/2].  samples: [n_samples][L][R][Q],
+ * host or device, dtype as for mt_nested_rhat; std_out: [L][n_z][R][Q]
+ * doubles, host or device.  Errors: MT_EINVAL (n_samples < 1, n_z outside
+ * 1..4096, null pointers), MT_ESTATE (no grid). */
+MT_API mt_status mt_interface_std(mt_ctx *ctx, int n_samples, const void *samples, int n_z,
+                                  double *std_out);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of inversion requests on one GPU.

@@ -224,8 +224,8 @@ k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long lo
         for (int l = 0; l < L; ++l) {
             const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
             const float zl = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
-            int lo, hi;
-            transition_window(zh, st.z, rdz, pb.kg, ext[l], ext[L + l], pb.G, lo, hi);
+            int lo = 0, hi = pb.G - 1;
+            if (!pb.full_windows) transition_window(zh, st.z, rdz, pb.kg, ext[l], ext[L + l], pb.G, lo, hi);
             lo = min(lo, pb.G);
             const int he = max(hi + 1, lo);
             const unsigned long long tl =

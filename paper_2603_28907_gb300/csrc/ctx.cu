@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -114,6 +115,8 @@ struct mt_ctx {
     size_t gacc_cap = 0;
     void *d_tmp = nullptr;           // small per-chain scratch
     size_t tmp_cap = 0;
+    void *d_diag = nullptr;          // diagnostics scratch
+    size_t diag_cap = 0;
 
     void *d_part = nullptr;
     size_t part_cap = 0;
@@ -598,6 +601,8 @@ mt_status mt_create(mt_ctx **out, int device, const mt_config *cfg, void *cuda_s
     ctx->device = device;
     ctx->cfg = *cfg;
     ctx->mode = cfg->precision;
+    const char *fw = getenv("MT_FULL_WINDOWS");
+    ctx->pb.full_windows = (fw && fw[0] && fw[0] != '0') ? 1 : 0;
     e = cudaSetDevice(device);
     if (e == cudaSuccess) {
         if (cuda_stream) {
@@ -651,6 +656,7 @@ mt_status mt_destroy(mt_ctx *ctx)
     if (ctx->d_out) cudaFree(ctx->d_out);
     if (ctx->d_out2) cudaFree(ctx->d_out2);
     if (ctx->d_gacc) cudaFree(ctx->d_gacc);
+    if (ctx->d_diag) cudaFree(ctx->d_diag);
     if (ctx->d_nodes) cudaFree(ctx->d_nodes);
     if (ctx->d_tmp) cudaFree(ctx->d_tmp);
     for (int i = 0; i < 2; ++i)
@@ -1210,3 +1216,58 @@ mt_status mt_get_sizes(const mt_ctx *ctx, int *n_layers, int *n_rows, int *n_col
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- diagnostics
+mt_status mt_nested_rhat(mt_ctx *ctx, int n_draws, int n_chains, const void *draws, int n_super,
+                         double *rhat_out, double *rhat_max_out)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (!ctx->have_grid) return fail(ctx, MT_ESTATE, "mt_set_grid has not been called");
+    if (n_draws < 1 || n_super < 2 || n_super > 65535 || n_chains < n_super || n_chains % n_super ||
+        !draws)
+        return fail(ctx, MT_EINVAL,
+                    "mt_nested_rhat: need n_draws >= 1, 2 <= n_super <= 65535 dividing n_chains, "
+                    "and draws");
+    CK(ctx, cudaSetDevice(ctx->device));
+    const size_t P = n_per_chain(ctx);
+    const void *dd;
+    TRY(dev_in(ctx, draws, (size_t)n_draws * n_chains * P * elem_size(ctx), &dd));
+    OutBuf o;
+    TRY(dev_out(ctx, rhat_out, P * 8, &ctx->d_out, &ctx->out_cap, &o));
+    TRY(grow(ctx, &ctx->d_diag, &ctx->diag_cap, (2 * (size_t)n_super * P + 1) * 8));
+    double *sm = (double *)ctx->d_diag, *wk = sm + (size_t)n_super * P;
+    unsigned long long *mx = (unsigned long long *)(wk + (size_t)n_super * P);
+    CK(ctx, cudaMemsetAsync(mx, 0, 8, ctx->stream));
+    CK(ctx, launch_nested_rhat(ctx->mode, dd, n_draws, n_chains, (int)P, n_super, sm, wk,
+                               (double *)o.dev, mx, ctx->stream));
+    TRY(finish_out(ctx, &o));
+    if (rhat_max_out)
+        CK(ctx, cudaMemcpyAsync(rhat_max_out, mx, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MT_OK;
+}
+
+mt_status mt_interface_std(mt_ctx *ctx, int n_samples, const void *samples, int n_z, double *std_out)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (!ctx->have_grid) return fail(ctx, MT_ESTATE, "mt_set_grid has not been called");
+    if (n_samples < 1 || n_z < 1 || n_z > 4096 || !samples || !std_out)
+        return fail(ctx, MT_EINVAL,
+                    "mt_interface_std: need n_samples >= 1, 1 <= n_z <= 4096, samples and std_out");
+    CK(ctx, cudaSetDevice(ctx->device));
+    const size_t P = n_per_chain(ctx), N = (size_t)ctx->R * ctx->Q;
+    const void *ds;
+    TRY(dev_in(ctx, samples, (size_t)n_samples * P * elem_size(ctx), &ds));
+    OutBuf o;
+    TRY(dev_out(ctx, std_out, (size_t)ctx->L * n_z * N * 8, &ctx->d_out, &ctx->out_cap, &o));
+    std::vector<double> z(n_z);
+    const double dz = ctx->box[2] / n_z;
+    for (int k = 0; k < n_z; ++k) z[k] = k * dz;
+    TRY(grow(ctx, &ctx->d_diag, &ctx->diag_cap, (size_t)n_z * 8));
+    CK(ctx, cudaMemcpyAsync(ctx->d_diag, z.data(), (size_t)n_z * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, launch_interface_std(ctx->mode, ds, n_samples, ctx->L, (int)N, n_z,
+                                 (const double *)ctx->d_diag, (double *)o.dev, ctx->stream));
+    TRY(finish_out(ctx, &o));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));  // z is a local host buffer
+    return MT_OK;
+}

@@ -52,6 +52,7 @@ struct Prob {
                                // march (the rest were exactly saturated), else nullptr
     float *gnodes;             // grids too large for shared memory: per-chain (h, dx)
                                // planes in HBM, [chain][l][node] float2; else nullptr
+    int full_windows;          // FP32 march evaluates every sample (verification switch)
     const int *perm;           // march order of the rays (ray table sorted by vertical
                                // step, then start height); nullptr = ray order
     const float2 *mu_ff;       // [L][N] float-float of the prior mean (FP32-mode prior)
@@ -124,5 +125,10 @@ cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, lon
                                  double *extra, cudaStream_t st);
 cudaError_t launch_gather(int mode, HRef h, int n_chains, long long n_per_chain, void *out,
                           cudaStream_t st);
+cudaError_t launch_nested_rhat(int mode, const void *draws, int N, int C, int P, int K, double *sm,
+                               double *wk, double *rhat, unsigned long long *max_bits, cudaStream_t st);
+size_t interface_smem(int n_z);
+cudaError_t launch_interface_std(int mode, const void *samples, int S, int L, int N, int n_z,
+                                 const double *z, double *out, cudaStream_t st);
 
 }  // namespace mt

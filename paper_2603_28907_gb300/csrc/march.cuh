@@ -526,8 +526,8 @@ __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *plane
     for (int l = 0; l < L; ++l) {
         const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
         const float zl = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
-        int lo, hi;
-        transition_window(zh, st.z, rdz, pb.kg, ext[l], ext[L + l], G, lo, hi);
+        int lo = 0, hi = G - 1;
+        if (!pb.full_windows) transition_window(zh, st.z, rdz, pb.kg, ext[l], ext[L + l], G, lo, hi);
         lo = min(lo, G);
         int he = max(hi + 1, lo);
         if ((he - lo) & 1) {

@@ -83,6 +83,8 @@ SIGNATURES = {
     "mt_get_timing": [_vp, C.c_int, _dp, _lp, C.c_int],
     "mt_get_work": [_vp, _dp, _dp, C.c_int],
     "mt_get_sizes": [_vp, _ip, _ip, _ip, _ip, _ip, _ip],
+    "mt_nested_rhat": [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, _dp],
+    "mt_interface_std": [_vp, C.c_int, _vp, C.c_int, _vp],
     "mt_server_create": [C.POINTER(C.c_void_p), C.c_int, C.c_size_t, C.c_int],
     "mt_server_submit": [_vp, C.POINTER(Request), C.POINTER(C.c_int64)],
     "mt_server_wait": [_vp, C.c_int64, C.c_double, _vp, _vp, _vp, _vp, C.POINTER(RequestInfo)],
@@ -251,6 +253,19 @@ class Context:
         ev, tot = C.c_double(), C.c_double()
         self._ck("mt_get_work", self.lib.mt_get_work(self.h, C.byref(ev), C.byref(tot), int(reset)))
         return ev.value, tot.value
+
+    def nested_rhat(self, draws, n_super, rhat_out=None):
+        """mt_nested_rhat on draws [n_draws][n_chains][L][R][Q]; returns the maximum."""
+        mx = C.c_double()
+        self._ck("mt_nested_rhat", self.lib.mt_nested_rhat(
+            self.h, draws.shape[0], draws.shape[1], _ptr(draws), int(n_super), _ptr(rhat_out),
+            C.byref(mx)))
+        return mx.value
+
+    def interface_std(self, samples, n_z, std_out):
+        """mt_interface_std on samples [n_samples][L][R][Q] into std_out [L][n_z][R][Q]."""
+        self._ck("mt_interface_std", self.lib.mt_interface_std(
+            self.h, samples.shape[0], _ptr(samples), int(n_z), _ptr(std_out)))
 
     def get_timing(self, kernel_id, reset=False):
         ms, n = C.c_double(), C.c_int64()
