@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) k_rhat_final(const double *sm, const doub
         b += d * d;
     }
     b /= (K - 1);
-    const double r = w > 0.0 ? sqrt(1.0 + b / w) : (b == 0.0 ? 1.0 : INFINITY);
+    const double r = w > 0.0 ? sqrt(__dadd_rn(1.0, b / w)) : (b == 0.0 ? 1.0 : INFINITY);
     if (rhat) rhat[p] = r;
     atomicMax(max_bits, (unsigned long long)__double_as_longlong(r));
 }
@@ -132,7 +132,10 @@ __global__ void __launch_bounds__(256) k_interface_std(const H *samples, int S, 
             const unsigned long long t = hj[2 * k + 1];
             const double mean = (double)(2 * above + t) / (2.0 * S);
             const double mean2 = (double)(4 * above + t) / (4.0 * S);
-            out[((size_t)l * n_z + k) * N + n0 + jj] = sqrt(fmax(mean2 - mean * mean, 0.0));
+            // explicit roundings (no contraction into an FMA): the same
+            // operations as the plain definition sqrt(mean(B^2) - mean(B)^2)
+            const double var = __dsub_rn(mean2, __dmul_rn(mean, mean));
+            out[((size_t)l * n_z + k) * N + n0 + jj] = sqrt(fmax(var, 0.0));
             above += (unsigned long long)hj[2 * k] + hj[2 * k + 1];
         }
     }
