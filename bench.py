@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving mix instead of the Metropolis step benchmark")
     ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--copula", action="store_true",
+                    help="random-walk steps under the paper's copula prior on the scenario")
     ap.add_argument("--diag", action="store_true",
                     help="time the chain diagnostics (nested R-hat, interface std) on the scenario")
     ap.add_argument("--study", choices=["precision", "gradient"], default=None,
@@ -476,6 +478,60 @@ def run_gradient_study(args, local):
     print(json.dumps({"study": "gradient", "workload": w.name, **out}), flush=True)
 
 
+def run_copula(args, local):
+    """Random-walk Metropolis on the latents of the paper's copula prior
+    (1024 scenario chains, FP32): per step the proposal, the latent prior, the
+    latent -> heights transform, the ray kernel and the accept.  Also times
+    the transform alone."""
+    import torch
+    from paper_2603_28907_gb300 import mt
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    w = W.scenario()
+    pr = W.problem(w)
+    ctx = mt.from_workload(pr, precision=mt.PREC_F32, device=local, stream=stream.cuda_stream)
+    counts = torch.zeros((w.S, w.P), dtype=torch.int32, device=dev)
+    ctx.generate_data(pr["H_true"], w.seed_data, mt.COUNTS_POISSON, counts_out=counts)
+    ctx.sync(120.0)
+    ctx.set_prior(mt.PRIOR_COPULA)
+    C = 1024
+    rng = np.random.default_rng(7)
+    lat = 0.5 * rng.standard_normal((C, w.L, w.R, w.Q))
+    lat[:, w.L - 1] = 0.0
+    lat[:, w.L - 1, 0, :w.L - 1] = 0.9
+    L0 = torch.tensor(lat.astype(np.float32), device=dev)
+    ctx.init_chains(L0, w.seed_mcmc)
+    ctx.run(mt.KERNEL_RW, 0.002, args.warmup, 1)
+    ctx.sync(120.0)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.run(mt.KERNEL_RW, 0.002, args.steps, 1)
+        e1.record(stream)
+    ctx.sync(120.0)
+    ms = e0.elapsed_time(e1) / args.steps
+    H = torch.zeros_like(L0)
+    ctx.copula_heights(L0, H)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(5):
+        ctx.copula_heights(L0, H)
+    t1.record()
+    torch.cuda.synchronize()
+    acc = torch.zeros(C, dtype=torch.int64, device=dev)
+    ctx.get_state(accepts_out=acc)
+    rays = w.S * w.P
+    print(json.dumps({"copula": "random-walk Metropolis on copula-prior latents",
+                      "workload": w.name, "chains": C, "steps": args.steps,
+                      "ms_per_step": ms, "chain_ray_evals_per_s": C * rays / (ms / 1e3),
+                      "transform_ms_1024_chains": t0.elapsed_time(t1) / 5,
+                      "acceptance": float(acc.double().mean().item()) / (args.warmup + args.steps)}),
+          flush=True)
+    ctx.close()
+
+
 def run_diag(args, local):
     """Nested R-hat over 1024 scenario chains (32 super-chains of 32; one and
     ten stored draws) and the interface standard deviation over 1024 samples
@@ -543,6 +599,10 @@ def main():
     if args.diag:
         if rank == 0:
             run_diag(args, local)
+        return
+    if args.copula:
+        if rank == 0:
+            run_copula(args, local)
         return
     w = W.scenario()
     if args.chains:

@@ -240,6 +240,39 @@ MT_API mt_status mt_get_sizes(const mt_ctx *ctx, int *n_layers, int *n_rows, int
                        int *n_sensors, int *n_pixels, int *n_chains);
 
 /* ------------------------------------------------------------------------
+ * Prior.
+ *
+ * MT_PRIOR_CAR (the default): chain states are heights; the log-prior is the
+ * CAR quadratic form -tau/2 sum_l (h_l - mu_l)^T (4I - rA)(h_l - mu_l) with
+ * the hard ordering / bounds constraints (see mt_config).
+ *
+ * MT_PRIOR_COPULA: the paper's prior (Sec. 2.1.3).  Chain states are latents
+ * laid out like heights [L][R][Q]: planes 0 .. L-2 hold standard-normal
+ * fields z_l, the first L-1 entries of plane L-1 hold the spatial-dependence
+ * parameters r_l (prior U(0, 1)); the rest of plane L-1 is ignored.  Heights:
+ * x_l = Q(r_l)^-1/2 z_l with Q(r) = 4I - rA on the periodic grid (Eq.
+ * def_CAR_precision; the symmetric square root, applied with 2-D discrete
+ * Fourier transforms, where the paper uses a Cholesky factor: both give x the
+ * law N(0, Q^-1)), u_l = Phi(x_l / sqrt(Sigma_11)) (Eq. CAR_cdf_transform),
+ * H_l = H_{l-1} + u_l (T - H_{l-1}) with H_{-1} = 0 (Eq. indep_columns), and
+ * the top surface L-1 is the known terrain T = the prior mean's top plane.
+ * Log-prior in latent coordinates: -1/2 sum z^2 if every r_l is in (0, 1),
+ * else -inf.  mt_logpost, mt_ray_terms, mt_init_chains, mt_set_state and
+ * mt_get_state then take and return latents; random-walk steps move the
+ * latents.  Gradients, MALA and mt_logpost_noalloc need the CAR prior.
+ * Switching drops the chains; mt_set_grid resets the prior to MT_PRIOR_CAR.
+ * Errors: MT_EINVAL (kind, fewer than 2 surfaces, grids whose transform does
+ * not fit in shared memory: 4 R Q values of the height dtype), MT_ESTATE. */
+#define MT_PRIOR_CAR 0
+#define MT_PRIOR_COPULA 1
+MT_API mt_status mt_set_prior(mt_ctx *ctx, int kind);
+
+/* Heights [n][L][R][Q] (host or device, height dtype) of n latent states
+ * (same layout and dtype) under the copula prior.  MT_ESTATE unless the
+ * copula prior is set. */
+MT_API mt_status mt_copula_heights(mt_ctx *ctx, int n, const void *latent, void *heights_out);
+
+/* ------------------------------------------------------------------------
  * Chain diagnostics.
  *
  * Nested R-hat (Sec. 3.2: chains grouped into super-chains that share a

@@ -117,6 +117,10 @@ struct mt_ctx {
     size_t tmp_cap = 0;
     void *d_diag = nullptr;          // diagnostics scratch
     size_t diag_cap = 0;
+    bool copula = false;             // copula prior: chain states are latents (z, r)
+    void *d_terr = nullptr;          // copula prior: terrain (top surface), mode dtype
+    void *d_Hd = nullptr;            // copula prior: heights derived from latents
+    size_t hd_cap = 0;
 
     void *d_part = nullptr;
     size_t part_cap = 0;
@@ -507,10 +511,36 @@ static void ev_end(mt_ctx *ctx, int id, EvPair *p)
 }
 
 // log-likelihood + log-prior of n chains given by h, into device arrays.
+// Heights buffer for n chains' derived heights (copula prior).
+static mt_status ensure_derived(mt_ctx *ctx, int n)
+{
+    void *old = ctx->d_Hd;
+    TRY(grow(ctx, &ctx->d_Hd, &ctx->hd_cap, (size_t)n * n_per_chain(ctx) * elem_size(ctx)));
+    if (ctx->d_Hd != old) drop_graph(ctx);  // a captured graph holds the old pointer
+    return MT_OK;
+}
+
+// Log-prior of n chain states h into d_lp (nullable), and the heights the ray
+// kernel marches: the states themselves (CAR prior), or the heights derived
+// from latent states (copula prior).
+static mt_status prior_and_heights(mt_ctx *ctx, HRef h, int n, double *d_lp, HRef *hm)
+{
+    if (!ctx->copula) {
+        if (d_lp) CK(ctx, launch_prior(ctx->pb, ctx->mode, h, ctx->d_mu, n, d_lp, ctx->stream));
+        *hm = h;
+        return MT_OK;
+    }
+    if (d_lp) CK(ctx, launch_prior_latent(ctx->pb, ctx->mode, h, n, d_lp, ctx->stream));
+    TRY(ensure_derived(ctx, n));
+    CK(ctx, launch_copula(ctx->pb, ctx->mode, h, ctx->d_terr, ctx->d_Hd, n, ctx->stream));
+    *hm = HRef{ctx->d_Hd, (long long)n_per_chain(ctx), nullptr, 0, 0};
+    return MT_OK;
+}
+
 static mt_status eval_logpost(mt_ctx *ctx, HRef h, int n, double *d_ll, double *d_lp)
 {
     TRY(ensure_partials(ctx, n));
-    if (d_lp) CK(ctx, launch_prior(ctx->pb, ctx->mode, h, ctx->d_mu, n, d_lp, ctx->stream));
+    TRY(prior_and_heights(ctx, h, n, d_lp, &h));
     if (d_ll) {
         EvPair ep;
         if (ctx->timing) {
@@ -528,6 +558,8 @@ namespace mt {
 mt_status ctx_view(mt_ctx *ctx, CtxView *v)
 {
     TRY(need(ctx, true));
+    if (ctx->copula)
+        return fail(ctx, MT_EINVAL, "the copula prior derives heights into a library buffer; use mt_logpost");
     v->pb = ctx->pb;
     v->mode = ctx->mode;
     v->device = ctx->device;
@@ -560,6 +592,7 @@ static mt_status eval_grad(mt_ctx *ctx, HRef h, int n, double *d_grad, double *d
 
 static mt_status grad_ok(mt_ctx *ctx)
 {
+    if (ctx->copula) return fail(ctx, MT_EINVAL, "gradients need the CAR prior (mt_set_prior 0)");
     if (ctx->mode == MODE_F64)
         return fail(ctx, MT_EINVAL, "the adjoint computes in FP32: use an FP32 precision mode");
     if (adjoint_smem_bytes(ctx->pb, false) + MT_SMEM_STATIC > MT_MAX_SMEM)
@@ -657,6 +690,8 @@ mt_status mt_destroy(mt_ctx *ctx)
     if (ctx->d_out2) cudaFree(ctx->d_out2);
     if (ctx->d_gacc) cudaFree(ctx->d_gacc);
     if (ctx->d_diag) cudaFree(ctx->d_diag);
+    if (ctx->d_terr) cudaFree(ctx->d_terr);
+    if (ctx->d_Hd) cudaFree(ctx->d_Hd);
     if (ctx->d_nodes) cudaFree(ctx->d_nodes);
     if (ctx->d_tmp) cudaFree(ctx->d_tmp);
     for (int i = 0; i < 2; ++i)
@@ -690,6 +725,7 @@ mt_status mt_set_grid(mt_ctx *ctx, int n_layers, int n_rows, int n_cols, const d
         if (!(unit_density[u] >= 0.0)) return fail(ctx, MT_EINVAL, "unit_density[%d] < 0", u);
     CK(ctx, cudaSetDevice(ctx->device));
     drop_chains(ctx);
+    ctx->copula = false;
     ctx->L = n_layers;
     ctx->R = n_rows;
     ctx->Q = n_cols;
@@ -844,6 +880,7 @@ mt_status mt_ray_terms(mt_ctx *ctx, int n_chains, const void *heights, double *o
     TRY(dev_out(ctx, term_out, nr * 8, &ctx->d_out2, &ctx->out2_cap, &t));
     TRY(ensure_partials(ctx, n_chains));
     HRef h{dh, (long long)np, nullptr, 0, 0};
+    TRY(prior_and_heights(ctx, h, n_chains, nullptr, &h));
     CK(ctx, launch_march(ctx->pb, ctx->mode, h, n_chains, ctx->d_part, (double *)o.dev,
                          (double *)t.dev, ctx->stream));
     TRY(finish_out(ctx, &o));
@@ -974,7 +1011,7 @@ static mt_status enqueue_step(mt_ctx *ctx, int kernel, double step, int off)
     CK(ctx, launch_propose_rw(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_cur, ctx->C, step, ctx->seed,
                               ctx->d_step, off, ctx->stream));
     HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
-    CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
+    TRY(prior_and_heights(ctx, hp, ctx->C, ctx->d_lpp, &hp));
     EvPair ep;
     if (ctx->timing) {
         ev_begin(ctx, 0, &ep);
@@ -998,7 +1035,9 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
         return fail(ctx, MT_EINVAL, "kernel %d", kernel);
     if (!(step >= 0.0) || n_super < 0 || n_within < 1 || n_within > 4096)
         return fail(ctx, MT_EINVAL, "need step >= 0, n_super >= 0, 1 <= n_within <= 4096");
+    if (ctx->copula) TRY(ensure_derived(ctx, ctx->C));
     if (kernel == MT_KERNEL_MALA) {
+        if (ctx->copula) return fail(ctx, MT_EINVAL, "MALA needs the CAR prior (mt_set_prior 0)");
         TRY(grad_ok(ctx));
         if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA needs a step size eps > 0");
         TRY(ensure_chain_grads(ctx));
@@ -1269,5 +1308,54 @@ mt_status mt_interface_std(mt_ctx *ctx, int n_samples, const void *samples, int 
                                  (const double *)ctx->d_diag, (double *)o.dev, ctx->stream));
     TRY(finish_out(ctx, &o));
     CK(ctx, cudaStreamSynchronize(ctx->stream));  // z is a local host buffer
+    return MT_OK;
+}
+
+// ---------------------------------------------------------------- copula prior
+mt_status mt_set_prior(mt_ctx *ctx, int kind)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (!ctx->have_grid) return fail(ctx, MT_ESTATE, "mt_set_grid has not been called");
+    if (kind != MT_PRIOR_CAR && kind != MT_PRIOR_COPULA)
+        return fail(ctx, MT_EINVAL, "mt_set_prior: kind %d", kind);
+    CK(ctx, cudaSetDevice(ctx->device));
+    if (kind == MT_PRIOR_COPULA) {
+        if (ctx->L < 2) return fail(ctx, MT_EINVAL, "the copula prior needs >= 2 surfaces (the top is the terrain)");
+        const size_t smem = copula_smem_bytes(ctx->pb, ctx->mode);
+        if (smem + MT_SMEM_STATIC > MT_MAX_SMEM)
+            return fail(ctx, MT_EINVAL, "grid %d x %d too large for the copula transform (%zu bytes of shared memory)",
+                        ctx->R, ctx->Q, smem);
+        const size_t N = (size_t)ctx->R * ctx->Q, es = elem_size(ctx);
+        std::vector<double> t(ctx->mu.begin() + (ctx->L - 1) * N, ctx->mu.begin() + ctx->L * N);
+        std::vector<float> tf(N);
+        for (size_t i = 0; i < N; ++i) tf[i] = (float)t[i];
+        if (ctx->d_terr) cudaFree(ctx->d_terr);
+        ctx->d_terr = nullptr;
+        CK(ctx, cudaMalloc(&ctx->d_terr, N * es));
+        CK(ctx, cudaMemcpyAsync(ctx->d_terr, es == 8 ? (const void *)t.data() : (const void *)tf.data(),
+                                N * es, cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    drop_chains(ctx);
+    ctx->copula = kind == MT_PRIOR_COPULA;
+    return MT_OK;
+}
+
+mt_status mt_copula_heights(mt_ctx *ctx, int n, const void *latent, void *heights_out)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (!ctx->copula) return fail(ctx, MT_ESTATE, "mt_set_prior(ctx, MT_PRIOR_COPULA) first");
+    if (n < 1 || n > 65535 || !latent || !heights_out)
+        return fail(ctx, MT_EINVAL, "need 1 <= n <= 65535, latent and heights_out");
+    CK(ctx, cudaSetDevice(ctx->device));
+    const size_t bytes = (size_t)n * n_per_chain(ctx) * elem_size(ctx);
+    const void *dl;
+    TRY(dev_in(ctx, latent, bytes, &dl));
+    OutBuf o;
+    TRY(dev_out(ctx, heights_out, bytes, &ctx->d_out, &ctx->out_cap, &o));
+    HRef h{dl, (long long)n_per_chain(ctx), nullptr, 0, 0};
+    CK(ctx, launch_copula(ctx->pb, ctx->mode, h, ctx->d_terr, o.dev, n, ctx->stream));
+    TRY(finish_out(ctx, &o));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
     return MT_OK;
 }

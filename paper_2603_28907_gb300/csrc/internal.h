@@ -128,6 +128,11 @@ cudaError_t launch_gather(int mode, HRef h, int n_chains, long long n_per_chain,
 cudaError_t launch_nested_rhat(int mode, const void *draws, int N, int C, int P, int K, double *sm,
                                double *wk, double *rhat, unsigned long long *max_bits, cudaStream_t st);
 size_t interface_smem(int n_z);
+size_t copula_smem_bytes(const Prob &pb, int mode);
+cudaError_t launch_copula(const Prob &pb, int mode, HRef lat, const void *terrain, void *H, int n_chains,
+                          cudaStream_t st);
+cudaError_t launch_prior_latent(const Prob &pb, int mode, HRef lat, int n_chains, double *lp_out,
+                                cudaStream_t st);
 cudaError_t launch_interface_std(int mode, const void *samples, int S, int L, int N, int n_z,
                                  const double *z, double *out, cudaStream_t st);
 

@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmt.so")
 
 PREC_F64, PREC_F32, PREC_F32C, PREC_BF16 = 0, 1, 2, 3
+PRIOR_CAR, PRIOR_COPULA = 0, 1
 KERNEL_RW, KERNEL_MALA = 0, 1
 COUNTS_POISSON, COUNTS_ROUND = 0, 1
 
@@ -83,6 +84,8 @@ SIGNATURES = {
     "mt_get_timing": [_vp, C.c_int, _dp, _lp, C.c_int],
     "mt_get_work": [_vp, _dp, _dp, C.c_int],
     "mt_get_sizes": [_vp, _ip, _ip, _ip, _ip, _ip, _ip],
+    "mt_set_prior": [_vp, C.c_int],
+    "mt_copula_heights": [_vp, C.c_int, _vp, _vp],
     "mt_nested_rhat": [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, _dp],
     "mt_interface_std": [_vp, C.c_int, _vp, C.c_int, _vp],
     "mt_server_create": [C.POINTER(C.c_void_p), C.c_int, C.c_size_t, C.c_int],
@@ -253,6 +256,13 @@ class Context:
         ev, tot = C.c_double(), C.c_double()
         self._ck("mt_get_work", self.lib.mt_get_work(self.h, C.byref(ev), C.byref(tot), int(reset)))
         return ev.value, tot.value
+
+    def set_prior(self, kind):
+        self._ck("mt_set_prior", self.lib.mt_set_prior(self.h, int(kind)))
+
+    def copula_heights(self, latent, heights_out):
+        self._ck("mt_copula_heights", self.lib.mt_copula_heights(
+            self.h, latent.shape[0], _ptr(latent), _ptr(heights_out)))
 
     def nested_rhat(self, draws, n_super, rhat_out=None):
         """mt_nested_rhat on draws [n_draws][n_chains][L][R][Q]; returns the maximum."""
