@@ -246,7 +246,7 @@ MT_API mt_status mt_get_sizes(const mt_ctx *ctx, int *n_layers, int *n_rows, int
  * CAR quadratic form -tau/2 sum_l (h_l - mu_l)^T (4I - rA)(h_l - mu_l) with
  * the hard ordering / bounds constraints (see mt_config).
  *
- * MT_PRIOR_COPULA: the paper's prior (Sec. 2.1.3).  Chain states are latents
+ * MT_PRIOR_COPULA: the paper's prior (Sec. 2.2.1).  Chain states are latents
  * laid out like heights [L][R][Q]: planes 0 .. L-2 hold standard-normal
  * fields z_l, the first L-1 entries of plane L-1 hold the spatial-dependence
  * parameters r_l (prior U(0, 1)); the rest of plane L-1 is ignored.  Heights:

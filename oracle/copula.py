@@ -1,7 +1,7 @@
 """FP64 CPU oracle of the paper's copula prior over layer heights (test
 infrastructure; only ``tests/`` and ``bench.py``'s CPU legs may import it).
 
-Sec. 2.1.3 ("Constructing a prior for layer models"): per sampled surface l
+Sec. 2.2.1 ("Constructing a prior for layer models"): per sampled surface l
 (all but the top, which is the known terrain T) a standard-normal field z_l
 on the R x Q grid and a spatial-dependence parameter r_l ~ U(0, 1);
   x_l = U(r_l) z_l  with U U^T = Q(r_l)^-1,  Q(r) = 4 I - r A  (periodic

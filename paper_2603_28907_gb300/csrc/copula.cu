@@ -1,4 +1,4 @@
-// copula.cu -- the paper's copula prior over layer heights (Sec. 2.1.3).
+// copula.cu -- the paper's copula prior over layer heights (Sec. 2.2.1).
 //
 // Per chain the state is a latent array laid out like the heights
 // [L][R][Q]: planes 0 .. L-2 hold standard-normal fields z_l, the first L-1

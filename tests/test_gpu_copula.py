@@ -1,4 +1,4 @@
-"""The paper's copula prior (Sec. 2.1.3) on the GPU against the FP64 oracle.
+"""The paper's copula prior (Sec. 2.2.1) on the GPU against the FP64 oracle.
 
 Latent -> heights transform (oracle/copula.py: spectral Q^-1/2, Phi, stick
 breaking) in both height precisions and at the scenario size; log-posterior of

@@ -1,4 +1,4 @@
-"""Pins of the copula-prior oracle (oracle/copula.py; Sec. 2.1.3).
+"""Pins of the copula-prior oracle (oracle/copula.py; Sec. 2.2.1).
 
 The spectral square root against dense linear algebra (U U^T = Q^-1 with Q
 built node by node from the periodic 4-neighbour stencil, and against the
