@@ -446,13 +446,15 @@ def run_gradient_study(args, local):
     fd = np.array([(f[2 * j] - f[2 * j + 1]) / 2e-3 for j in range(16)])
     ga = np.array([g[ix] for ix in idx])
     out["grad_vs_fd_max_rel_err"] = float(np.max(np.abs(ga - fd) / np.maximum(np.abs(fd), 1e-3 * np.abs(g).max())))
-    # 3. MALA vs random walk on 1024 chains: ESS per second of the mean height of each surface
-    C, n_steps = 1024, 200
+    # 3. MALA and HMC vs random walk on 1024 chains: ESS per second of the mean height of each surface
+    C = 1024
     H0 = torch.tensor(np.stack([W.geometry(w, [w.seed_init, c]) for c in range(C)]).astype(np.float32), device=dev)
-    runs = {"rw_sigma_0.002": (mt.KERNEL_RW, 0.002), "mala_eps_0.5": (mt.KERNEL_MALA, 0.5),
-            "mala_eps_0.005": (mt.KERNEL_MALA, 0.005)}
+    runs = {"rw_sigma_0.002": (mt.KERNEL_RW, 0.002, 200), "mala_eps_0.5": (mt.KERNEL_MALA, 0.5, 200),
+            "mala_eps_0.005": (mt.KERNEL_MALA, 0.005, 200),
+            "hmc_eps_0.003_leapfrog_8": (mt.KERNEL_HMC, 0.003, 100)}
     cur = torch.zeros_like(H0)
-    for name, (kern, step) in runs.items():
+    c32.set_hmc(8)
+    for name, (kern, step, n_steps) in runs.items():
         c32.init_chains(H0, w.seed_mcmc)
         c32.run(kern, step, 1, 1)   # build the graph / initial gradients outside the timing
         c32.sync(600.0)

@@ -78,7 +78,7 @@ typedef enum {
 enum { MT_PREC_F64 = 0, MT_PREC_F32 = 1, MT_PREC_F32C = 2, MT_PREC_BF16 = 3 };
 
 /* Proposal kernels for mt_run. */
-enum { MT_KERNEL_RW = 0, MT_KERNEL_MALA = 1 };
+enum { MT_KERNEL_RW = 0, MT_KERNEL_MALA = 1, MT_KERNEL_HMC = 2 };
 
 /* Observed-count generation for mt_generate_data. */
 enum { MT_COUNTS_POISSON = 0, MT_COUNTS_ROUND = 1 };
@@ -192,12 +192,21 @@ MT_API mt_status mt_init_chains(mt_ctx *ctx, int n_chains, const void *heights0,
  * kernel MT_KERNEL_RW: H' = H + step * xi; MT_KERNEL_MALA: Langevin proposal
  * H' = H + (eps^2/2) grad(H) + eps xi with eps = step, the gradient from the
  * adjoint (FP32 precision modes, gamma > 0), and the Hastings correction
- * ln q(H|H') - ln q(H'|H) in the accept test.  Step k of chain c
- * draws xi from Philox stream 3 (RW) or 5 (MALA), counter {j, k, c}, and its
- * acceptance uniform from stream 4, counter {0, k, c}.  The n_within steps of
- * a super-step are one CUDA graph replay; the host only sees super-step
- * boundaries.  Asynchronous. */
+ * ln q(H|H') - ln q(H'|H) in the accept test; MT_KERNEL_HMC: Hamiltonian
+ * Monte Carlo (Sec. 3.1; unit mass matrix) with a leapfrog trajectory of
+ * mt_set_hmc's n_leapfrog steps of size eps = step: momentum p0 ~ N(0, I),
+ * p = p0 + eps/2 g, then n_leapfrog times H' += eps p and p += eps g(H')
+ * (eps/2 after the last), the trajectory carried in FP64 and each gradient
+ * taken at the stored (rounded) heights; accept term
+ * log pi(H') - log pi(H) + |p0|^2/2 - |p|^2/2 (same requirements as MALA).
+ * Step k of chain c draws xi from Philox stream 3 (RW), 5 (MALA) or 6 (HMC),
+ * counter {j, k, c}, and its acceptance uniform from stream 4, counter
+ * {0, k, c}.  The n_within steps of a super-step are one CUDA graph replay;
+ * the host only sees super-step boundaries.  Asynchronous. */
 MT_API mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within);
+
+/* Leapfrog steps per HMC proposal (1 .. 1024; default 8).  MT_EINVAL outside. */
+MT_API mt_status mt_set_hmc(mt_ctx *ctx, int n_leapfrog);
 
 /* Copy the chains' current state out (each pointer host or device, nullable):
  * heights [C][L][R][Q] storage type, loglik/logprior double [C], accepts

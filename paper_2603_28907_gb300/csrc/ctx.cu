@@ -117,6 +117,10 @@ struct mt_ctx {
     size_t tmp_cap = 0;
     void *d_diag = nullptr;          // diagnostics scratch
     size_t diag_cap = 0;
+    int hmc_leap = 8;                // leapfrog steps per HMC proposal
+    double *d_P = nullptr;           // HMC momentum [C][n]
+    double *d_Q64 = nullptr;         // HMC trajectory position in FP64 [C][n]
+    double *d_k0 = nullptr;          // HMC initial kinetic energy [C]
     bool copula = false;             // copula prior: chain states are latents (z, r)
     void *d_terr = nullptr;          // copula prior: terrain (top surface), mode dtype
     void *d_Hd = nullptr;            // copula prior: heights derived from latents
@@ -237,6 +241,9 @@ static void drop_chains(mt_ctx *ctx)
     dfree(ctx->d_accl);
     dfree(ctx->d_G);
     dfree(ctx->d_extra);
+    dfree(ctx->d_P);
+    dfree(ctx->d_Q64);
+    dfree(ctx->d_k0);
     ctx->g_valid = false;
     ctx->C = 0;
 }
@@ -1000,11 +1007,56 @@ static mt_status enqueue_mala(mt_ctx *ctx, double eps, int off)
     return MT_OK;
 }
 
+static mt_status ensure_hmc(mt_ctx *ctx)
+{
+    const size_t n = (size_t)ctx->C * n_per_chain(ctx);
+    if (!ctx->d_P) TRY(dalloc(ctx, &ctx->d_P, n));
+    if (!ctx->d_Q64) TRY(dalloc(ctx, &ctx->d_Q64, n));
+    if (!ctx->d_k0) TRY(dalloc(ctx, &ctx->d_k0, (size_t)ctx->C));
+    return MT_OK;
+}
+
+// One HMC step: momentum and the first drift, then per leapfrog step the
+// proposal's gradient (adjoint) and a kick + drift, a final half kick with
+// the kinetic-energy difference, the proposal's prior and the accept (the
+// last adjoint's forward pass gave the proposal's log-likelihood partials).
+static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
+{
+    const size_t np = n_per_chain(ctx);
+    const long long bs = (long long)ctx->C * np;
+    EvPair es;
+    if (ctx->timing) ev_begin(ctx, 1, &es);
+    CK(ctx, launch_hmc_start(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps,
+                             ctx->d_P, ctx->d_Q64, ctx->d_k0, ctx->seed, ctx->d_step, off, ctx->stream));
+    HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
+    for (int i = 0; i < ctx->hmc_leap; ++i) {
+        CK(ctx, cudaMemsetAsync(ctx->d_gacc, 0, (size_t)ctx->C * np * 8, ctx->stream));
+        CK(ctx, launch_adjoint(ctx->pb, hp, ctx->C, (double *)ctx->d_part,
+                               (unsigned long long *)ctx->d_gacc, ctx->stream));
+        CK(ctx, launch_grad_finish_sel(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C,
+                                       (const unsigned long long *)ctx->d_gacc, ctx->d_G, ctx->d_cur,
+                                       ctx->stream));
+        if (i + 1 < ctx->hmc_leap)
+            CK(ctx, launch_hmc_kick_drift(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C,
+                                          eps, ctx->d_P, ctx->d_Q64, ctx->stream));
+    }
+    CK(ctx, launch_hmc_finish(ctx->pb, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ctx->d_P, ctx->d_k0,
+                              ctx->d_extra, ctx->stream));
+    CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
+    CK(ctx, launch_accept_fused(ctx->pb, MODE_F32, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
+                                ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
+                                ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
+                                ctx->stream));
+    if (ctx->timing) ev_end(ctx, 1, &es);
+    return MT_OK;
+}
+
 static mt_status enqueue_step(mt_ctx *ctx, int kernel, double step, int off)
 {
     const size_t np = n_per_chain(ctx);
     const long long bs = (long long)ctx->C * np;
     if (kernel == MT_KERNEL_MALA) return enqueue_mala(ctx, step, off);
+    if (kernel == MT_KERNEL_HMC) return enqueue_hmc(ctx, step, off);
     if (kernel != MT_KERNEL_RW) return fail(ctx, MT_EINVAL, "kernel %d not available", kernel);
     EvPair es;
     if (ctx->timing) ev_begin(ctx, 1, &es);
@@ -1031,18 +1083,21 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
 {
     TRY(need(ctx, true));
     if (ctx->C < 1) return fail(ctx, MT_ESTATE, "mt_init_chains first");
-    if (kernel != MT_KERNEL_RW && kernel != MT_KERNEL_MALA)
+    if (kernel != MT_KERNEL_RW && kernel != MT_KERNEL_MALA && kernel != MT_KERNEL_HMC)
         return fail(ctx, MT_EINVAL, "kernel %d", kernel);
     if (!(step >= 0.0) || n_super < 0 || n_within < 1 || n_within > 4096)
         return fail(ctx, MT_EINVAL, "need step >= 0, n_super >= 0, 1 <= n_within <= 4096");
     if (ctx->copula) TRY(ensure_derived(ctx, ctx->C));
-    if (kernel == MT_KERNEL_MALA) {
-        if (ctx->copula) return fail(ctx, MT_EINVAL, "MALA needs the CAR prior (mt_set_prior 0)");
+    if (kernel == MT_KERNEL_MALA || kernel == MT_KERNEL_HMC) {
+        if (ctx->copula) return fail(ctx, MT_EINVAL, "MALA / HMC need the CAR prior (mt_set_prior 0)");
         TRY(grad_ok(ctx));
-        if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA needs a step size eps > 0");
+        if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA / HMC need a step size eps > 0");
         TRY(ensure_chain_grads(ctx));
+        if (kernel == MT_KERNEL_HMC) TRY(ensure_hmc(ctx));
     }
     TRY(ensure_partials(ctx, ctx->C));
+    // random-walk steps move the states without their gradients
+    if (kernel == MT_KERNEL_RW && n_super > 0) ctx->g_valid = false;
     if (ctx->timing) {
         for (int s = 0; s < n_super; ++s) {
             for (int i = 0; i < n_within; ++i) TRY(enqueue_step(ctx, kernel, step, i));
@@ -1357,5 +1412,14 @@ mt_status mt_copula_heights(mt_ctx *ctx, int n, const void *latent, void *height
     CK(ctx, launch_copula(ctx->pb, ctx->mode, h, ctx->d_terr, o.dev, n, ctx->stream));
     TRY(finish_out(ctx, &o));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MT_OK;
+}
+
+mt_status mt_set_hmc(mt_ctx *ctx, int n_leapfrog)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (n_leapfrog < 1 || n_leapfrog > 1024) return fail(ctx, MT_EINVAL, "n_leapfrog %d not in [1, 1024]", n_leapfrog);
+    if (ctx->hmc_leap != n_leapfrog) drop_graph(ctx);
+    ctx->hmc_leap = n_leapfrog;
     return MT_OK;
 }

@@ -22,7 +22,7 @@ namespace mt {
 
 enum { MODE_F64 = 0, MODE_F32 = 1, MODE_F32C = 2, MODE_BF16 = 3 };
 enum { STREAM_GEOM = 0, STREAM_DATA = 1, STREAM_INIT = 2, STREAM_PROP = 3, STREAM_ACC = 4,
-       STREAM_MALA = 5 };
+       STREAM_MALA = 5, STREAM_HMC = 6 };
 
 struct Prob {
     int L, R, Q, S, P, G, n_rays, N;  // N = R*Q nodes per surface
@@ -120,6 +120,16 @@ cudaError_t launch_propose_mala(const Prob &pb, int mode, void *hbuf, long long 
                                 const double *gbuf, const uint8_t *cur, int n_chains, double eps,
                                 uint64_t seed, const int64_t *step_base, int step_off,
                                 cudaStream_t st);
+cudaError_t launch_hmc_start(const Prob &pb, int mode, void *hbuf, long long buf_stride,
+                             const double *gbuf, const uint8_t *cur, int n_chains, double eps,
+                             double *pbuf, double *qbuf, double *k0, uint64_t seed,
+                             const int64_t *step_base, int step_off, cudaStream_t st);
+cudaError_t launch_hmc_kick_drift(const Prob &pb, int mode, void *hbuf, long long buf_stride,
+                                  const double *gbuf, const uint8_t *cur, int n_chains, double eps,
+                                  double *pbuf, double *qbuf, cudaStream_t st);
+cudaError_t launch_hmc_finish(const Prob &pb, long long buf_stride, const double *gbuf,
+                              const uint8_t *cur, int n_chains, double eps, double *pbuf,
+                              const double *k0, double *extra, cudaStream_t st);
 cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, long long buf_stride,
                                  const double *gbuf, const uint8_t *cur, int n_chains, double eps,
                                  double *extra, cudaStream_t st);

@@ -254,6 +254,120 @@ cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, lon
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- HMC
+// Hamiltonian Monte Carlo with a leapfrog trajectory (Sec. 3.1, the building
+// block of the paper's NUTS; unit mass matrix).  Momentum p0 ~ N(0, I) from
+// Philox stream HMC, counter {pair j, step, chain}; p = p0 + eps/2 g(q0);
+// n_leap times: q += eps p, then p += eps g(q) (eps/2 after the last drift).
+// The trajectory q is carried in FP64 (qbuf); the proposal buffer holds it
+// rounded to the height dtype, which is where the gradient and the
+// log-density are evaluated.  Gradients: G[1 - cur] (the proposal's), G[cur]
+// (the current state's), FP64 like the momentum.  The accept term is
+// K(p0) - K(p), K = |p|^2 / 2.
+template <typename H>
+__global__ void __launch_bounds__(256)
+k_hmc_start(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur, double eps,
+            double *pbuf, double *qbuf, double *k0, uint64_t seed, const int64_t *step_base, int step_off)
+{
+    const int c = blockIdx.x;
+    const uint32_t step = (uint32_t)(*step_base + step_off);
+    const int cs = cur[c];
+    const long long a = (long long)cs * bs + (long long)c * n;
+    const long long b = (long long)(1 - cs) * bs + (long long)c * n;
+    double kin = 0.0;
+    for (int j = threadIdx.x; 2 * j < n; j += blockDim.x) {
+        const uint4 w = draw4(seed, STREAM_HMC, (uint32_t)c, step, (uint32_t)j);
+        const double u1 = u01_f64(w.x, w.y), u2 = u01_f64(w.z, w.w);
+        const double rad = sqrt(-2.0 * log(u1));
+        double sn, cn;
+        sincospi(2.0 * u2, &sn, &cn);
+        const double xi[2] = {rad * cn, rad * sn};
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int i = 2 * j + t;
+            if (i >= n) break;
+            kin += 0.5 * xi[t] * xi[t];
+            const double p = xi[t] + 0.5 * eps * gbuf[a + i];
+            const double q = (double)hbuf[a + i] + eps * p;
+            pbuf[(size_t)c * n + i] = p;
+            qbuf[(size_t)c * n + i] = q;
+            hbuf[b + i] = (H)q;
+        }
+    }
+    kin = block_sum(kin);
+    if (threadIdx.x == 0) k0[c] = kin;
+}
+
+template <typename H>
+__global__ void __launch_bounds__(256)
+k_hmc_kick_drift(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur, double eps,
+                 double *pbuf, double *qbuf)
+{
+    const int c = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long b = (long long)(1 - cur[c]) * bs + (long long)c * n;
+    const size_t k = (size_t)c * n + i;
+    const double p = pbuf[k] + eps * gbuf[b + i];
+    const double q = qbuf[k] + eps * p;
+    pbuf[k] = p;
+    qbuf[k] = q;
+    hbuf[b + i] = (H)q;
+}
+
+__global__ void __launch_bounds__(256)
+k_hmc_finish(int n, long long bs, const double *gbuf, const uint8_t *cur, double eps,
+             const double *pbuf, const double *k0, double *extra)
+{
+    const int c = blockIdx.x;
+    const long long b = (long long)(1 - cur[c]) * bs + (long long)c * n;
+    double kin = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double p = pbuf[(size_t)c * n + i] + 0.5 * eps * gbuf[b + i];
+        kin += 0.5 * p * p;
+    }
+    kin = block_sum(kin);
+    if (threadIdx.x == 0) extra[c] = k0[c] - kin;
+}
+
+cudaError_t launch_hmc_start(const Prob &pb, int mode, void *hbuf, long long buf_stride,
+                             const double *gbuf, const uint8_t *cur, int n_chains, double eps,
+                             double *pbuf, double *qbuf, double *k0, uint64_t seed,
+                             const int64_t *step_base, int step_off, cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    if (mode == MODE_F64)
+        k_hmc_start<double><<<n_chains, 256, 0, st>>>(n, (double *)hbuf, buf_stride, gbuf, cur, eps, pbuf,
+                                                      qbuf, k0, seed, step_base, step_off);
+    else
+        k_hmc_start<float><<<n_chains, 256, 0, st>>>(n, (float *)hbuf, buf_stride, gbuf, cur, eps, pbuf,
+                                                     qbuf, k0, seed, step_base, step_off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hmc_kick_drift(const Prob &pb, int mode, void *hbuf, long long buf_stride,
+                                  const double *gbuf, const uint8_t *cur, int n_chains, double eps,
+                                  double *pbuf, double *qbuf, cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    dim3 grid((n + 255) / 256, n_chains);
+    if (mode == MODE_F64)
+        k_hmc_kick_drift<double><<<grid, 256, 0, st>>>(n, (double *)hbuf, buf_stride, gbuf, cur, eps,
+                                                       pbuf, qbuf);
+    else
+        k_hmc_kick_drift<float><<<grid, 256, 0, st>>>(n, (float *)hbuf, buf_stride, gbuf, cur, eps,
+                                                      pbuf, qbuf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hmc_finish(const Prob &pb, long long buf_stride, const double *gbuf,
+                              const uint8_t *cur, int n_chains, double eps, double *pbuf,
+                              const double *k0, double *extra, cudaStream_t st)
+{
+    k_hmc_finish<<<n_chains, 256, 0, st>>>(pb.L * pb.N, buf_stride, gbuf, cur, eps, pbuf, k0, extra);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- reduce
 // ll[c] = sum over data of the Poisson constants + the CTA partials of chain c
 // added in CTA order (deterministic).
