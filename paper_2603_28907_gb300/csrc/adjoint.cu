@@ -18,9 +18,9 @@
 // depend on the order in which threads add and is reproducible bit for bit; a
 // sum that rounds to zero at that resolution is not added.  Pass 2 visits only
 // the samples within log2|coef_l| + 10 log2 units of surface l (coef_l: the
-// sample weight in fixed-point units); every sample outside has
-// varsigma' <= 2^-(that), so all of them together move a cell's sum by less
-// than G * 2^-10 fixed-point units.
+// sample weight in fixed-point units; a warp uses its largest); every sample
+// outside has varsigma' <= 2^-(that), so all of them together move a cell's
+// sum by less than G * 2^-10 fixed-point units.
 #include <math.h>
 
 #include "march.cuh"
@@ -30,9 +30,22 @@ namespace mt {
 constexpr float kFix = 4294967296.0f;  // 2^32
 constexpr double kInvFix = 1.0 / 4294967296.0;
 
+// Add round(v) (to nearest, ties to even) to a fixed-point accumulator, with
+// FP32 and integer operations only (a 64-bit float -> integer conversion runs
+// on the FP64 pipe, which is slow on this part).
 __device__ __forceinline__ void add_fixed(unsigned long long *p, float v)
 {
-    const long long q = llrintf(v);
+    const float a = fabsf(v);
+    long long q;
+    if (a < 4194304.0f) {  // |v| < 2^22: adding 1.5 * 2^23 rounds to an integer
+        q = (long long)(__float_as_int(v + 12582912.0f) - 0x4B400000);
+    } else {               // |v| = m 2^(e - 150) with m the 24-bit significand
+        const uint32_t bits = __float_as_uint(a);
+        const uint32_t e = min(bits >> 23, 190u), m = (bits & 0x7FFFFFu) | 0x800000u;
+        const unsigned long long mag = e >= 150u ? (unsigned long long)m << (e - 150u)
+                                                 : (unsigned long long)((m >> 1) + (m & (m >> 1) & 1u));
+        q = v < 0.f ? -(long long)mag : (long long)mag;
+    }
     if (q != 0) atomicAdd(p, (unsigned long long)q);
 }
 
@@ -214,12 +227,14 @@ k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long lo
 
     const int r_begin = blockIdx.x * rays_per_block;
     const int r_end = min(r_begin + rays_per_block, pb.n_rays);
-    double ll = 0.0;
+    FF accf = {0.f, 0.f};
     for (int slot = r_begin + threadIdx.x; slot < r_end; slot += blockDim.x) {
         const int ray = pb.perm ? pb.perm[slot] : slot;
         const float4 o = pb.o4[ray], st = pb.s4[ray];
         const float rdz = rcp_approx(st.z);
-        double S_ = 0.0;
+        // O and y = a - O / Lambda in float-float, the Poisson term as in the
+        // forward kernel's FP32 modes (so the two give the same partials)
+        FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
 #pragma unroll 1
         for (int l = 0; l < L; ++l) {
             const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
@@ -230,26 +245,38 @@ k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long lo
             const int he = max(hi + 1, lo);
             const unsigned long long tl =
                 (unsigned long long)lo * q_one + forward_surface<L>(pb, sh, l, o, st, zh, zl, lo, he);
-            S_ = fma(pb.drho[l], (double)tl * 0x1p-23, S_);
+            const FF nl = ff_two_sum((float)(uint32_t)(tl >> 20) * 1048576.0f * 0x1p-23f,
+                                     (float)(uint32_t)(tl & 0xFFFFFu) * 0x1p-23f);
+            Sff = ff_add(Sff, ff_mul(FF{pb.drho_ff[l].x, pb.drho_ff[l].y}, nl));
         }
-        const double O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
+        const FF Off = ff_mul(FF{pb.dt_ff[ray].x, pb.dt_ff[ray].y}, Sff);
+        const FF OL = ff_mul(Off, FF{pb.invL_ff.x, pb.invL_ff.y});
         const int Cp = pb.cnt[ray];
-        const double lam = pb.I0 * exp(-O * pb.inv_Lambda);
+        const float invL = pb.invL_ff.x;
+        float dO;  // d ll / d O_p = (lambda - C) / Lambda
+        FF tf;
         if (Cp > 0) {
-            const double y = pb.a[ray] - O * pb.inv_Lambda;
-            ll += -(double)Cp * (double)g_f32((float)y);
+            const FF yff = ff_add(FF{pb.a_ff[ray].x, pb.a_ff[ray].y}, FF{-OL.hi, -OL.lo});
+            const float y = yff.hi + yff.lo, g = g_f32(y), cf = (float)Cp;
+            const float cg = cf * g;
+            tf = FF{-cg, -fmaf(cf, g, -cg)};
+            dO = cf * expm1f(y) * invL;          // lambda - C = C (e^y - 1)
         } else {
-            ll += -lam;
+            const float lam = (float)pb.I0 * expf(-(OL.hi + OL.lo));
+            tf = FF{-lam, 0.f};
+            dO = lam * invL;
         }
-        const double dO = (lam - (double)Cp) * pb.inv_Lambda;  // d ll / d O_p
-        const double base = dO * pb.dt[ray] / pb.gamma * (double)kFix;
+        accf = ff_add(accf, tf);
+        const float base = dO * pb.dt_ff[ray].x * (float)(1.0 / pb.gamma) * kFix;
 #pragma unroll 1
         for (int l = 0; l < L; ++l) {
-            const float coef = (float)(base * pb.drho[l]);
-            if (coef == 0.0f) continue;
+            const float coef = base * pb.drho_f[l];
             // samples beyond log2|coef| + 10 log2 units from the surface add
-            // less than 2^-10 fixed-point units each
-            const float ka = fmaxf(log2f(fabsf(coef)) + 10.0f, 1.0f);
+            // less than 2^-10 fixed-point units each; the warp takes its
+            // largest such width (its rays have near-equal windows) so that
+            // its lanes run loops of equal length
+            float ka = fmaxf(log2f(fabsf(coef) + 1e-30f) + 10.0f, 1.0f);
+            ka = __int_as_float(__reduce_max_sync(__activemask(), __float_as_int(ka)));
             const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
             const float zl = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
             int lo, hi;
@@ -259,8 +286,8 @@ k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long lo
             scatter_surface<L>(pb, sh, l, o, st, zh, zl, lo, he, coef, acc);
         }
     }
-    ll = block_sum(ll);
-    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = ll;
+    accf = block_sum(accf);
+    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = (double)accf.hi + (double)accf.lo;
     if constexpr (SMEM) {
         __syncthreads();
         for (int i = threadIdx.x; i < L * N; i += blockDim.x) {
