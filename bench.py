@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving mix instead of the Metropolis step benchmark")
     ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--linear", action="store_true",
+                    help="random-walk steps under the paper's linearised forward model on the scenario")
     ap.add_argument("--copula", action="store_true",
                     help="random-walk steps under the paper's copula prior on the scenario")
     ap.add_argument("--diag", action="store_true",
@@ -480,6 +482,56 @@ def run_gradient_study(args, local):
     print(json.dumps({"study": "gradient", "workload": w.name, **out}), flush=True)
 
 
+def run_linear(args, local):
+    """Random-walk Metropolis under the linearised forward model (1024
+    scenario chains, FP32, 75 levels of 2 m): per step the proposal, the
+    prior, the voxel densities, the batched sparse path-length product and
+    the accept.  Reports the set-up time, the matrix size and the
+    linearisation error of the log-likelihood at the chains' starts and at
+    the data-generating geometry."""
+    import torch
+    from paper_2603_28907_gb300 import mt
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    w = W.scenario()
+    pr = W.problem(w)
+    ctx = mt.from_workload(pr, precision=mt.PREC_F32, device=local, stream=stream.cuda_stream)
+    counts = torch.zeros((w.S, w.P), dtype=torch.int32, device=dev)
+    ctx.generate_data(pr["H_true"], w.seed_data, mt.COUNTS_POISSON, counts_out=counts)
+    ctx.sync(120.0)
+    C, nz = 1024, 75
+    H0 = torch.tensor(np.concatenate([pr["H_true"][None], W.init_chains(w, C - 1)]).astype(np.float32),
+                      device=dev)
+    ll_m = torch.zeros(C, dtype=torch.float64, device=dev)
+    ctx.logpost(H0, ll_m, None)
+    t0 = time.perf_counter()
+    ctx.set_forward(mt.FORWARD_LINEAR, nz)
+    setup_s = time.perf_counter() - t0
+    ll_l = torch.zeros_like(ll_m)
+    ctx.logpost(H0, ll_l, None)
+    torch.cuda.synchronize()
+    d = (ll_l - ll_m).abs().cpu().numpy()
+    ctx.init_chains(H0, w.seed_mcmc)
+    ctx.run(mt.KERNEL_RW, 0.002, args.warmup, 1)
+    ctx.sync(120.0)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.run(mt.KERNEL_RW, 0.002, args.steps, 1)
+        e1.record(stream)
+    ctx.sync(120.0)
+    ms = e0.elapsed_time(e1) / args.steps
+    rays = w.S * w.P
+    print(json.dumps({"linear": "random-walk Metropolis under the linearised forward model",
+                      "workload": w.name, "chains": C, "levels": nz,
+                      "voxels": (w.R - 1) * (w.Q - 1) * nz, "steps": args.steps, "ms_per_step": ms,
+                      "chain_ray_evals_per_s": C * rays / (ms / 1e3), "setup_s": setup_s,
+                      "linearisation_abs_dll_at_truth": float(d[0]),
+                      "linearisation_abs_dll_at_starts_median": float(np.median(d[1:]))}), flush=True)
+    ctx.close()
+
+
 def run_copula(args, local):
     """Random-walk Metropolis on the latents of the paper's copula prior
     (1024 scenario chains, FP32): per step the proposal, the latent prior, the
@@ -605,6 +657,10 @@ def main():
     if args.copula:
         if rank == 0:
             run_copula(args, local)
+        return
+    if args.linear:
+        if rank == 0:
+            run_linear(args, local)
         return
     w = W.scenario()
     if args.chains:

@@ -282,6 +282,30 @@ MT_API mt_status mt_set_prior(mt_ctx *ctx, int kind);
 MT_API mt_status mt_copula_heights(mt_ctx *ctx, int n, const void *latent, void *heights_out);
 
 /* ------------------------------------------------------------------------
+ * Forward model.
+ *
+ * MT_FORWARD_MARCH (the default): every ray is marched at n_grid samples.
+ * MT_FORWARD_LINEAR: the paper's linearised model (Sec. 2.1.2, Eqs.
+ * expected_counts_linearized / _approx) on a voxel density grid (Sec. 2.1.4,
+ * Eq. def_LM_density_grid_smooth): voxels are the (R-1) x (Q-1) cells of the
+ * surface grid times n_z levels of height box[2] / n_z; a voxel's density is
+ * rho_top + sum_l (rho_l - rho_{l+1}) varsigma(h_l - z_k) with h_l the mean of
+ * the cell's four corner heights and z_k the level's centre; L_pv = the
+ * length of ray p inside voxel v (built once on the host in FP64, stored in
+ * the height dtype); lambda_hat_p = lambda_p(R0) (1 - sum_v L_pv (R_v - R0_v)
+ * / Lambda) with R0 the densities of h_ref ([L][R][Q] host FP64; NULL = the
+ * prior mean).  The Poisson log-likelihood is -inf when some lambda_hat_p <=
+ * 0.  mt_logpost and random-walk steps then use it; mt_ray_terms, gradients,
+ * MALA, HMC and mt_logpost_noalloc need the march.  Live chains are
+ * re-evaluated.  mt_set_grid / mt_set_sensors / mt_set_pixels reset the
+ * model to the march.
+ * Errors: MT_EINVAL (kind, n_z outside 1..4096), MT_ESTATE (grid, sensors or
+ * pixels missing). */
+#define MT_FORWARD_MARCH 0
+#define MT_FORWARD_LINEAR 1
+MT_API mt_status mt_set_forward(mt_ctx *ctx, int kind, int n_z, const double *h_ref);
+
+/* ------------------------------------------------------------------------
  * Chain diagnostics.
  *
  * Nested R-hat (Sec. 3.2: chains grouped into super-chains that share a

@@ -117,6 +117,13 @@ struct mt_ctx {
     size_t tmp_cap = 0;
     void *d_diag = nullptr;          // diagnostics scratch
     size_t diag_cap = 0;
+    bool linear = false;             // linearised forward model instead of the march
+    int lin_nz = 0;
+    std::vector<double> lin_href;    // reference heights of the linearisation
+    int *d_lrow = nullptr, *d_lcol = nullptr;  // voxel path lengths (CSR by ray)
+    void *d_lval = nullptr, *d_R0 = nullptr, *d_dR = nullptr;  // d_R0: reference cell-centre heights
+    size_t dR_cap = 0;
+    double *d_lam0 = nullptr, *d_amc = nullptr;
     int hmc_leap = 8;                // leapfrog steps per HMC proposal
     double *d_P = nullptr;           // HMC momentum [C][n]
     double *d_Q64 = nullptr;         // HMC trajectory position in FP64 [C][n]
@@ -384,6 +391,8 @@ static mt_status counts_ready(mt_ctx *ctx)
     ctx->have_counts = true;
     refresh_prob(ctx);
     ctx->pb.sumK = sk;
+    if (ctx->linear)
+        CK(ctx, launch_lin_amc(ctx->pb.n_rays, ctx->d_lam0, ctx->d_cnt, ctx->d_amc, ctx->stream));
     drop_graph(ctx);
     ctx->g_valid = false;
     if (ctx->C > 0) {  // live chains: their log-likelihoods refer to the old counts
@@ -544,6 +553,33 @@ static mt_status prior_and_heights(mt_ctx *ctx, HRef h, int n, double *d_lp, HRe
     return MT_OK;
 }
 
+// Scratch of the linearised model for n chains (dR, [voxels][n padded to 32]).
+static mt_status ensure_lin(mt_ctx *ctx, int n)
+{
+    if (!ctx->linear) return MT_OK;
+    const size_t nvox = (size_t)ctx->lin_nz * (ctx->R - 1) * (ctx->Q - 1);
+    const size_t Cp = ((size_t)n + 31) / 32 * 32;
+    void *old = ctx->d_dR;
+    TRY(grow(ctx, &ctx->d_dR, &ctx->dR_cap, nvox * Cp * elem_size(ctx)));
+    if (ctx->d_dR != old) drop_graph(ctx);
+    return MT_OK;
+}
+
+// The per-(chain, CTA) log-likelihood partials of n chains' heights h:
+// the march, or the linearised model.
+static mt_status ray_kernel(mt_ctx *ctx, HRef h, int n)
+{
+    if (ctx->linear) {
+        TRY(ensure_lin(ctx, n));
+        CK(ctx, launch_lin(ctx->pb, ctx->mode, h, n, ctx->lin_nz, ctx->d_lrow, ctx->d_lcol, ctx->d_lval,
+                           ctx->d_R0, ctx->d_dR, ctx->d_lam0, ctx->d_amc, (double *)ctx->d_part,
+                           ctx->stream));
+        return MT_OK;
+    }
+    CK(ctx, launch_march(ctx->pb, ctx->mode, h, n, ctx->d_part, nullptr, nullptr, ctx->stream));
+    return MT_OK;
+}
+
 static mt_status eval_logpost(mt_ctx *ctx, HRef h, int n, double *d_ll, double *d_lp)
 {
     TRY(ensure_partials(ctx, n));
@@ -554,9 +590,10 @@ static mt_status eval_logpost(mt_ctx *ctx, HRef h, int n, double *d_ll, double *
             ev_begin(ctx, 0, &ep);
             count_work(ctx, n);
         }
-        CK(ctx, launch_march(ctx->pb, ctx->mode, h, n, ctx->d_part, nullptr, nullptr, ctx->stream));
+        TRY(ray_kernel(ctx, h, n));
         if (ctx->timing) ev_end(ctx, 0, &ep);
-        CK(ctx, launch_reduce_ll(ctx->pb, ctx->mode, n, ctx->d_part, d_ll, ctx->stream));
+        CK(ctx, launch_reduce_ll(ctx->pb, ctx->linear ? MODE_F32 : ctx->mode, n, ctx->d_part, d_ll,
+                                 ctx->stream));
     }
     return MT_OK;
 }
@@ -567,6 +604,8 @@ mt_status ctx_view(mt_ctx *ctx, CtxView *v)
     TRY(need(ctx, true));
     if (ctx->copula)
         return fail(ctx, MT_EINVAL, "the copula prior derives heights into a library buffer; use mt_logpost");
+    if (ctx->linear)
+        return fail(ctx, MT_EINVAL, "the linearised model needs a library buffer; use mt_logpost");
     v->pb = ctx->pb;
     v->mode = ctx->mode;
     v->device = ctx->device;
@@ -599,6 +638,7 @@ static mt_status eval_grad(mt_ctx *ctx, HRef h, int n, double *d_grad, double *d
 
 static mt_status grad_ok(mt_ctx *ctx)
 {
+    if (ctx->linear) return fail(ctx, MT_EINVAL, "gradients need the marched forward model");
     if (ctx->copula) return fail(ctx, MT_EINVAL, "gradients need the CAR prior (mt_set_prior 0)");
     if (ctx->mode == MODE_F64)
         return fail(ctx, MT_EINVAL, "the adjoint computes in FP32: use an FP32 precision mode");
@@ -698,6 +738,13 @@ mt_status mt_destroy(mt_ctx *ctx)
     if (ctx->d_gacc) cudaFree(ctx->d_gacc);
     if (ctx->d_diag) cudaFree(ctx->d_diag);
     if (ctx->d_terr) cudaFree(ctx->d_terr);
+    if (ctx->d_lrow) cudaFree(ctx->d_lrow);
+    if (ctx->d_lcol) cudaFree(ctx->d_lcol);
+    if (ctx->d_lval) cudaFree(ctx->d_lval);
+    if (ctx->d_R0) cudaFree(ctx->d_R0);
+    if (ctx->d_dR) cudaFree(ctx->d_dR);
+    if (ctx->d_lam0) cudaFree(ctx->d_lam0);
+    if (ctx->d_amc) cudaFree(ctx->d_amc);
     if (ctx->d_Hd) cudaFree(ctx->d_Hd);
     if (ctx->d_nodes) cudaFree(ctx->d_nodes);
     if (ctx->d_tmp) cudaFree(ctx->d_tmp);
@@ -733,6 +780,7 @@ mt_status mt_set_grid(mt_ctx *ctx, int n_layers, int n_rows, int n_cols, const d
     CK(ctx, cudaSetDevice(ctx->device));
     drop_chains(ctx);
     ctx->copula = false;
+    ctx->linear = false;
     ctx->L = n_layers;
     ctx->R = n_rows;
     ctx->Q = n_cols;
@@ -772,6 +820,7 @@ mt_status mt_set_sensors(mt_ctx *ctx, int n_sensors, const double *pos)
                 return fail(ctx, MT_EINVAL, "sensor %d is not strictly inside the box", s);
     CK(ctx, cudaSetDevice(ctx->device));
     drop_chains(ctx);
+    ctx->linear = false;
     ctx->S = n_sensors;
     TRY(dalloc(ctx, &ctx->d_sensors, 3 * (size_t)n_sensors));
     CK(ctx, cudaMemcpyAsync(ctx->d_sensors, pos, 24 * (size_t)n_sensors, cudaMemcpyHostToDevice,
@@ -798,6 +847,7 @@ mt_status mt_set_pixels(mt_ctx *ctx, int n_pixels, const double *dirs)
         return fail(ctx, MT_EINVAL, "too many rays");
     CK(ctx, cudaSetDevice(ctx->device));
     drop_chains(ctx);
+    ctx->linear = false;
     ctx->P = n_pixels;
     TRY(dalloc(ctx, &ctx->d_dirs, 3 * (size_t)n_pixels));
     CK(ctx, cudaMemcpyAsync(ctx->d_dirs, dirs, 24 * (size_t)n_pixels, cudaMemcpyHostToDevice,
@@ -876,6 +926,7 @@ mt_status mt_ray_terms(mt_ctx *ctx, int n_chains, const void *heights, double *o
                        double *term_out)
 {
     TRY(need(ctx, true));
+    if (ctx->linear) return fail(ctx, MT_EINVAL, "mt_ray_terms reports the marched forward model");
     if (n_chains < 1 || n_chains > 65535 || !heights)
         return fail(ctx, MT_EINVAL, "need 1 <= n_chains <= 65535 and heights");
     const size_t np = n_per_chain(ctx);
@@ -1069,9 +1120,9 @@ static mt_status enqueue_step(mt_ctx *ctx, int kernel, double step, int off)
         ev_begin(ctx, 0, &ep);
         count_work(ctx, ctx->C);
     }
-    CK(ctx, launch_march(ctx->pb, ctx->mode, hp, ctx->C, ctx->d_part, nullptr, nullptr, ctx->stream));
+    TRY(ray_kernel(ctx, hp, ctx->C));
     if (ctx->timing) ev_end(ctx, 0, &ep);
-    CK(ctx, launch_accept_fused(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, nullptr,
+    CK(ctx, launch_accept_fused(ctx->pb, ctx->linear ? MODE_F32 : ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, nullptr,
                                 ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
                                 ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
                                 ctx->stream));
@@ -1088,7 +1139,9 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
     if (!(step >= 0.0) || n_super < 0 || n_within < 1 || n_within > 4096)
         return fail(ctx, MT_EINVAL, "need step >= 0, n_super >= 0, 1 <= n_within <= 4096");
     if (ctx->copula) TRY(ensure_derived(ctx, ctx->C));
+    TRY(ensure_lin(ctx, ctx->C));
     if (kernel == MT_KERNEL_MALA || kernel == MT_KERNEL_HMC) {
+        if (ctx->linear) return fail(ctx, MT_EINVAL, "MALA / HMC need the marched forward model");
         if (ctx->copula) return fail(ctx, MT_EINVAL, "MALA / HMC need the CAR prior (mt_set_prior 0)");
         TRY(grad_ok(ctx));
         if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA / HMC need a step size eps > 0");
@@ -1385,6 +1438,13 @@ mt_status mt_set_prior(mt_ctx *ctx, int kind)
         std::vector<float> tf(N);
         for (size_t i = 0; i < N; ++i) tf[i] = (float)t[i];
         if (ctx->d_terr) cudaFree(ctx->d_terr);
+    if (ctx->d_lrow) cudaFree(ctx->d_lrow);
+    if (ctx->d_lcol) cudaFree(ctx->d_lcol);
+    if (ctx->d_lval) cudaFree(ctx->d_lval);
+    if (ctx->d_R0) cudaFree(ctx->d_R0);
+    if (ctx->d_dR) cudaFree(ctx->d_dR);
+    if (ctx->d_lam0) cudaFree(ctx->d_lam0);
+    if (ctx->d_amc) cudaFree(ctx->d_amc);
         ctx->d_terr = nullptr;
         CK(ctx, cudaMalloc(&ctx->d_terr, N * es));
         CK(ctx, cudaMemcpyAsync(ctx->d_terr, es == 8 ? (const void *)t.data() : (const void *)tf.data(),
@@ -1421,5 +1481,95 @@ mt_status mt_set_hmc(mt_ctx *ctx, int n_leapfrog)
     if (n_leapfrog < 1 || n_leapfrog > 1024) return fail(ctx, MT_EINVAL, "n_leapfrog %d not in [1, 1024]", n_leapfrog);
     if (ctx->hmc_leap != n_leapfrog) drop_graph(ctx);
     ctx->hmc_leap = n_leapfrog;
+    return MT_OK;
+}
+
+// ---------------------------------------------------------------- linearised forward model
+mt_status mt_set_forward(mt_ctx *ctx, int kind, int n_z, const double *h_ref)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (!(ctx->have_grid && ctx->have_sensors && ctx->have_pixels))
+        return fail(ctx, MT_ESTATE, "mt_set_forward needs grid, sensors and pixels");
+    if (kind != MT_FORWARD_MARCH && kind != MT_FORWARD_LINEAR)
+        return fail(ctx, MT_EINVAL, "mt_set_forward: kind %d", kind);
+    CK(ctx, cudaSetDevice(ctx->device));
+    drop_graph(ctx);
+    if (kind == MT_FORWARD_MARCH) {
+        ctx->linear = false;
+        if (ctx->C > 0 && ctx->have_counts) {  // live chains: re-evaluate under the march
+            const size_t np = n_per_chain(ctx);
+            HRef h{ctx->d_H, (long long)np, ctx->d_cur, (long long)(ctx->C * np), 0};
+            TRY(eval_logpost(ctx, h, ctx->C, ctx->d_ll, ctx->d_lp));
+            CK(ctx, cudaStreamSynchronize(ctx->stream));
+        }
+        ctx->g_valid = false;
+        return MT_OK;
+    }
+    if (n_z < 1 || n_z > 4096) return fail(ctx, MT_EINVAL, "n_z %d not in [1, 4096]", n_z);
+    const size_t N = (size_t)ctx->R * ctx->Q, np = n_per_chain(ctx);
+    ctx->lin_href.assign(h_ref ? h_ref : ctx->mu.data(), (h_ref ? h_ref : ctx->mu.data()) + np);
+    std::vector<double> sens(3 * (size_t)ctx->S), dirs(3 * (size_t)ctx->P);
+    CK(ctx, cudaMemcpyAsync(sens.data(), ctx->d_sensors, sens.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(dirs.data(), ctx->d_dirs, dirs.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    refresh_prob(ctx);
+    std::vector<int> row, col;
+    std::vector<double> val, R0;
+    lin_build_lengths(ctx->pb, sens, dirs, n_z, row, col, val);
+    lin_density_host(ctx->pb, ctx->lin_href.data(), n_z, R0);
+    const size_t nr = (size_t)ctx->pb.n_rays, nnz = col.size();
+    std::vector<double> lam0(nr);
+    for (size_t p = 0; p < nr; ++p) {
+        double O = 0.0;
+        for (int e = row[p]; e < row[p + 1]; ++e) O += val[e] * R0[col[e]];
+        lam0[p] = ctx->cfg.I0 * exp(-O / ctx->cfg.atten);
+    }
+    // the reference's cell-centre heights [L][cells] (the density kernel
+    // differences the chains' indicators against them)
+    const int nx = ctx->Q - 1, ny = ctx->R - 1;
+    std::vector<double> h0c((size_t)ctx->L * nx * ny);
+    for (int l = 0; l < ctx->L; ++l)
+        for (int i = 0; i < ny; ++i)
+            for (int j = 0; j < nx; ++j) {
+                const double *hl = ctx->lin_href.data() + (size_t)l * N;
+                h0c[((size_t)l * ny + i) * nx + j] =
+                    0.25 * ((hl[i * ctx->Q + j] + hl[i * ctx->Q + j + 1]) + (hl[(i + 1) * ctx->Q + j] + hl[(i + 1) * ctx->Q + j + 1]));
+            }
+    const size_t es = elem_size(ctx);
+    std::vector<float> valf, h0f;
+    if (es == 4) {
+        valf.assign(val.begin(), val.end());
+        h0f.assign(h0c.begin(), h0c.end());
+    }
+    for (void **p : {(void **)&ctx->d_lrow, (void **)&ctx->d_lcol, &ctx->d_lval, &ctx->d_R0,
+                     (void **)&ctx->d_lam0, (void **)&ctx->d_amc}) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+    CK(ctx, cudaMalloc((void **)&ctx->d_lrow, row.size() * 4));
+    CK(ctx, cudaMalloc((void **)&ctx->d_lcol, nnz * 4 + 16));
+    CK(ctx, cudaMalloc(&ctx->d_lval, nnz * es + 16));
+    CK(ctx, cudaMalloc(&ctx->d_R0, h0c.size() * es));
+    CK(ctx, cudaMalloc((void **)&ctx->d_lam0, nr * 8));
+    CK(ctx, cudaMalloc((void **)&ctx->d_amc, nr * 8));
+    CK(ctx, cudaMemcpyAsync(ctx->d_lrow, row.data(), row.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->d_lcol, col.data(), nnz * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->d_lval, es == 4 ? (const void *)valf.data() : (const void *)val.data(),
+                            nnz * es, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->d_R0, es == 4 ? (const void *)h0f.data() : (const void *)h0c.data(),
+                            h0c.size() * es, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->d_lam0, lam0.data(), nr * 8, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->lin_nz = n_z;
+    ctx->linear = true;
+    if (ctx->have_counts)
+        CK(ctx, launch_lin_amc((int)nr, ctx->d_lam0, ctx->d_cnt, ctx->d_amc, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));  // host vectors go out of scope
+    (void)N;
+    if (ctx->C > 0 && ctx->have_counts) {  // live chains: re-evaluate under the new forward model
+        HRef h{ctx->d_H, (long long)np, ctx->d_cur, (long long)(ctx->C * np), 0};
+        TRY(eval_logpost(ctx, h, ctx->C, ctx->d_ll, ctx->d_lp));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    ctx->g_valid = false;
     return MT_OK;
 }

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/mt.h"
 
 #define MT_MAX_L 8
@@ -74,6 +76,12 @@ struct HRef {
 
 // What a context holds for a call that must not allocate (filled by ctx_view,
 // which also checks that grid, sensors, pixels and counts are set).
+// Host side of the linearised forward model (linear.cu).
+void lin_build_lengths(const Prob &pb, const std::vector<double> &sensors,
+                       const std::vector<double> &dirs, int nz, std::vector<int> &row,
+                       std::vector<int> &col, std::vector<double> &val);
+void lin_density_host(const Prob &pb, const double *H, int nz, std::vector<double> &R);
+
 struct CtxView {
     Prob pb;
     int mode;
@@ -139,6 +147,10 @@ cudaError_t launch_nested_rhat(int mode, const void *draws, int N, int C, int P,
                                double *wk, double *rhat, unsigned long long *max_bits, cudaStream_t st);
 size_t interface_smem(int n_z);
 size_t copula_smem_bytes(const Prob &pb, int mode);
+cudaError_t launch_lin(const Prob &pb, int mode, HRef h, int n_chains, int nz, const int *row,
+                       const int *col, const void *val, const void *h0c, void *dR, const double *lam0,
+                       const double *amc, double *partial, cudaStream_t st);
+cudaError_t launch_lin_amc(int n, const double *lam0, const int32_t *cnt, double *amc, cudaStream_t st);
 cudaError_t launch_copula(const Prob &pb, int mode, HRef lat, const void *terrain, void *H, int n_chains,
                           cudaStream_t st);
 cudaError_t launch_prior_latent(const Prob &pb, int mode, HRef lat, int n_chains, double *lp_out,

@@ -1,0 +1,267 @@
+// linear.cu -- the paper's linearised forward model (Sec. 2.1.2, Eqs.
+// expected_counts_linearized / _approx) on the voxel density grid of
+// Sec. 2.1.4 (Eq. def_LM_density_grid_smooth).
+//
+// Voxels: the (R-1) x (Q-1) cells of the surface grid times n_z levels of
+// height dz = Lz / n_z, flat index v = (k ny + i) nx + j.  Density at the
+// voxel centre: R_v = rho_top + sum_l (rho_l - rho_{l+1}) varsigma(h_l - z_k),
+// h_l = mean of the cell's four corner heights, z_k = (k + 1/2) dz.
+// L_pv = length of ray p inside voxel v (its in-box segment), a sparse
+// matrix in CSR by ray, built once on the host in FP64.  With lambda0_p =
+// I0 exp(-O_p(R0) / Lambda) at the reference density R0 = R(H_ref):
+//   lambda_hat_p(R) = lambda0_p (1 - sum_v L_pv (R_v - R0_v) / Lambda).
+// Per evaluation: k_lin_density writes dR = R - R0 for every voxel and
+// chain, [v][chain] (chains fastest, padded to 32), as differences of the
+// indicators; k_lin_ll gives each warp
+// one ray at a time for 32 chains (lane = chain), sums L_pv dR_v over the
+// ray's voxels and adds the Poisson term, C (ln(lambda_hat / C) - (lambda_hat
+// - C) / C) = -C (x - log1p(x)), x = (lambda_hat - C) / C, or -lambda_hat
+// for C = 0 (-inf where lambda_hat <= 0).
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "march.cuh"
+
+namespace mt {
+
+// ---------------------------------------------------------------- host
+static double slab_exit(const double o[3], const double d[3], const double box[3])
+{
+    double te = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        double ta = INFINITY;
+        if (d[a] > 0.0) ta = (box[a] - o[a]) / d[a];
+        else if (d[a] < 0.0) ta = (0.0 - o[a]) / d[a];
+        te = fmin(te, ta);
+    }
+    return te;
+}
+
+// Voxel path lengths of every ray (ray = s * P + p), appended in CSR order.
+void lin_build_lengths(const Prob &pb, const std::vector<double> &sensors,
+                       const std::vector<double> &dirs, int nz, std::vector<int> &row,
+                       std::vector<int> &col, std::vector<double> &val)
+{
+    const int nx = pb.Q - 1, ny = pb.R - 1;
+    const int n[3] = {nx, ny, nz};
+    const double h[3] = {pb.box[0] / nx, pb.box[1] / ny, pb.box[2] / nz};
+    row.assign(1, 0);
+    col.clear();
+    val.clear();
+    std::vector<double> ts;
+    std::vector<std::pair<int, double>> seg;
+    for (int s = 0; s < pb.S; ++s)
+        for (int p = 0; p < pb.P; ++p) {
+            const double *o = &sensors[3 * s], *d = &dirs[3 * p];
+            const double te = slab_exit(o, d, pb.box);
+            ts.assign({0.0, te});
+            for (int a = 0; a < 3; ++a)
+                if (d[a] != 0.0)
+                    for (int b = 0; b <= n[a]; ++b) {
+                        const double t = (b * h[a] - o[a]) / d[a];
+                        if (t > 0.0 && t < te) ts.push_back(t);
+                    }
+            std::sort(ts.begin(), ts.end());
+            seg.clear();
+            for (size_t q = 0; q + 1 < ts.size(); ++q) {
+                const double t0 = ts[q], t1 = ts[q + 1];
+                if (!(t1 > t0)) continue;
+                const double tm = 0.5 * (t0 + t1);
+                const int j = std::min((int)((o[0] + tm * d[0]) / h[0]), nx - 1);
+                const int i = std::min((int)((o[1] + tm * d[1]) / h[1]), ny - 1);
+                const int k = std::min((int)((o[2] + tm * d[2]) / h[2]), nz - 1);
+                seg.push_back({(k * ny + std::max(i, 0)) * nx + std::max(j, 0), t1 - t0});
+            }
+            std::sort(seg.begin(), seg.end());
+            for (size_t q = 0; q < seg.size(); ++q) {
+                if (q > 0 && seg[q].first == seg[q - 1].first) {
+                    val.back() += seg[q].second;  // the same voxel entered twice (a grazing edge)
+                } else {
+                    col.push_back(seg[q].first);
+                    val.push_back(seg[q].second);
+                }
+            }
+            row.push_back((int)col.size());
+        }
+}
+
+// Voxel densities of heights H [L][R][Q] (FP64).
+void lin_density_host(const Prob &pb, const double *H, int nz, std::vector<double> &R)
+{
+    const int nx = pb.Q - 1, ny = pb.R - 1, Q = pb.Q, N = pb.N;
+    R.assign((size_t)nz * ny * nx, pb.rho_top);
+    const double dz = pb.box[2] / nz;
+    for (int i = 0; i < ny; ++i)
+        for (int j = 0; j < nx; ++j)
+            for (int l = 0; l < pb.L; ++l) {
+                const double *h = H + (size_t)l * N;
+                const double hc = 0.25 * (h[i * Q + j] + h[i * Q + j + 1] + h[(i + 1) * Q + j] + h[(i + 1) * Q + j + 1]);
+                for (int k = 0; k < nz; ++k) {
+                    const double u = hc - (k + 0.5) * dz;
+                    const double s = pb.gamma == 0.0 ? (u > 0 ? 1.0 : (u < 0 ? 0.0 : 0.5))
+                                                     : 1.0 / (1.0 + exp(-u / pb.gamma));
+                    R[((size_t)k * ny + i) * nx + j] += pb.drho[l] * s;
+                }
+            }
+}
+
+// ---------------------------------------------------------------- device
+// sigma(a) - sigma(b) for the logistic sigma, with relative accuracy also
+// when a and b are close: sigma(a) (1 - sigma(b)) (1 - e^{-(a-b)}).
+template <typename T> __device__ __forceinline__ T dsigma(T a, T b)
+{
+    if (fabs(a - b) < (T)1) {
+        const T sa = (T)1 / ((T)1 + exp(-a)), snb = (T)1 / ((T)1 + exp(b));  // sigma(a), 1 - sigma(b)
+        return -sa * snb * expm1(b - a);
+    }
+    return (T)1 / ((T)1 + exp(-a)) - (T)1 / ((T)1 + exp(-b));
+}
+
+template <typename T> __device__ __forceinline__ T eta(T u) { return u > (T)0 ? (T)1 : (u < (T)0 ? (T)0 : (T)0.5); }
+
+// dR[v][c] = R_v(H_c) - R_v(H_ref), formed per surface as the difference of
+// the two indicators (so it is accurate relative to itself, and exactly 0 at
+// the reference); h0c = the reference's cell-centre heights [L][cells].
+// Threads = 32 chains x 8 cells per block, cells along x.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lin_density(Prob pb, HRef h, int n_chains, int Cp, int nz,
+                                                     const T *h0c, T *dR)
+{
+    const int lane = threadIdx.x & 31, cw = threadIdx.x >> 5;
+    const int nx = pb.Q - 1, ny = pb.R - 1;
+    const int colv = blockIdx.x * 8 + cw;  // cell index i * nx + j
+    const int c = blockIdx.y * 32 + lane;
+    if (colv >= nx * ny) return;
+    const int i = colv / nx, j = colv - i * nx;
+    const size_t ncell = (size_t)nx * ny;
+    if (c >= n_chains) {
+        for (int k = 0; k < nz; ++k) dR[((size_t)k * ncell + colv) * Cp + c] = (T)0;
+        return;
+    }
+    const T *Hc = chain_ptr<T>(h, c);
+    T hc[MT_MAX_L], hr[MT_MAX_L];
+#pragma unroll
+    for (int l = 0; l < MT_MAX_L; ++l) {
+        if (l < pb.L) {
+            const T *hl = Hc + (size_t)l * pb.N;
+            hc[l] = (T)0.25 * ((hl[i * pb.Q + j] + hl[i * pb.Q + j + 1]) + (hl[(i + 1) * pb.Q + j] + hl[(i + 1) * pb.Q + j + 1]));
+            hr[l] = h0c[(size_t)l * ncell + colv];
+        }
+    }
+    const T dz = (T)(pb.box[2] / nz), inv_g = pb.gamma > 0.0 ? (T)(1.0 / pb.gamma) : (T)0;
+    for (int k = 0; k < nz; ++k) {
+        const T z = ((T)k + (T)0.5) * dz;
+        T r = (T)0;
+#pragma unroll
+        for (int l = 0; l < MT_MAX_L; ++l) {
+            if (l < pb.L) {
+                const T d = pb.gamma == 0.0 ? eta<T>(hc[l] - z) - eta<T>(hr[l] - z)
+                                            : dsigma<T>((hc[l] - z) * inv_g, (hr[l] - z) * inv_g);
+                r += (T)pb.drho[l] * d;
+            }
+        }
+        dR[((size_t)k * ncell + colv) * Cp + c] = r;
+    }
+}
+
+// x - log1p(x) without cancellation for small |x| (its series x^2/2 - x^3/3
+// + x^4/4 - ...).
+template <typename T> __device__ __forceinline__ T x_minus_log1p(T x)
+{
+    if (fabs(x) < (T)0.125) {
+        T t = x, s = (T)0;
+#pragma unroll
+        for (int n = 2; n <= 24; ++n) {
+            t *= x;
+            s += ((n & 1) ? -t : t) / (T)n;
+        }
+        return s;
+    }
+    return x - log1p(x);
+}
+
+// One warp = one ray at a time for 32 chains (lane = chain); a CTA = its 32
+// warps over the block's rays for one tile of 32 chains.  Per chain the
+// CTA's terms are summed (float-float for FP32, FP64 for F64) and written as
+// partial[c][block]; -inf if any of them had lambda_hat <= 0.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_lin_ll(Prob pb, int n_chains, int Cp, int rays_per_block,
+                                                 const int *row, const int *col, const T *val,
+                                                 const T *dR, const double *lam0, const double *amc,
+                                                 double *partial)
+{
+    __shared__ double red[32][33];
+    __shared__ int bad[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c = blockIdx.y * 32 + lane;
+    if (threadIdx.x < 32) bad[threadIdx.x] = 0;
+    __syncthreads();
+    const int r_begin = blockIdx.x * rays_per_block;
+    const int r_end = min(r_begin + rays_per_block, pb.n_rays);
+    const T invL = (T)pb.inv_Lambda;
+    double acc_d = 0.0;
+    FF acc_f = {0.f, 0.f};
+    int neg = 0;
+    for (int p = r_begin + wid; p < r_end; p += nw) {
+        T dO = (T)0;
+        for (int e = row[p]; e < row[p + 1]; ++e) dO += val[e] * dR[(size_t)col[e] * Cp + c];
+        const int Cn = pb.cnt[p];
+        const T l0 = (T)lam0[p];
+        const T lh = l0 * ((T)1 - dO * invL);
+        neg |= !(lh > (T)0);
+        T term;
+        if (Cn > 0) {
+            const T x = ((T)amc[p] - l0 * dO * invL) / (T)Cn;  // (lambda_hat - C) / C
+            term = -(T)Cn * x_minus_log1p<T>(x);
+        } else {
+            term = -lh;
+        }
+        if constexpr (sizeof(T) == 8) acc_d += (double)term;
+        else acc_f = ff_add(acc_f, FF{(float)term, 0.f});
+    }
+    red[wid][lane] = sizeof(T) == 8 ? acc_d : (double)acc_f.hi + (double)acc_f.lo;
+    if (neg) atomicOr(&bad[lane], 1);
+    __syncthreads();
+    if (wid == 0 && c < n_chains) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[w][lane];
+        partial[(size_t)c * gridDim.x + blockIdx.x] = bad[lane] ? -INFINITY : s;
+    }
+}
+
+__global__ void k_lin_amc(int n, const double *lam0, const int32_t *cnt, double *amc)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) amc[p] = lam0[p] - (double)cnt[p];
+}
+
+cudaError_t launch_lin_amc(int n, const double *lam0, const int32_t *cnt, double *amc, cudaStream_t st)
+{
+    k_lin_amc<<<(n + 255) / 256, 256, 0, st>>>(n, lam0, cnt, amc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lin(const Prob &pb, int mode, HRef h, int n_chains, int nz, const int *row,
+                       const int *col, const void *val, const void *h0c, void *dR, const double *lam0,
+                       const double *amc, double *partial, cudaStream_t st)
+{
+    const int Cp = (n_chains + 31) / 32 * 32;
+    const int ncol = (pb.Q - 1) * (pb.R - 1);
+    dim3 gd((ncol + 7) / 8, Cp / 32);
+    const int rpb = march_rays_per_block(pb);
+    dim3 gl((pb.n_rays + rpb - 1) / rpb, Cp / 32);
+    if (mode == MODE_F64) {
+        k_lin_density<double><<<gd, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const double *)h0c, (double *)dR);
+        k_lin_ll<double><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, rpb, row, col, (const double *)val,
+                                              (const double *)dR, lam0, amc, partial);
+    } else {
+        k_lin_density<float><<<gd, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const float *)h0c, (float *)dR);
+        k_lin_ll<float><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, rpb, row, col, (const float *)val,
+                                             (const float *)dR, lam0, amc, partial);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mt

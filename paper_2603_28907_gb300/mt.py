@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libmt.so")
 
 PREC_F64, PREC_F32, PREC_F32C, PREC_BF16 = 0, 1, 2, 3
 PRIOR_CAR, PRIOR_COPULA = 0, 1
+FORWARD_MARCH, FORWARD_LINEAR = 0, 1
 KERNEL_RW, KERNEL_MALA, KERNEL_HMC = 0, 1, 2
 COUNTS_POISSON, COUNTS_ROUND = 0, 1
 
@@ -86,6 +87,7 @@ SIGNATURES = {
     "mt_get_sizes": [_vp, _ip, _ip, _ip, _ip, _ip, _ip],
     "mt_set_prior": [_vp, C.c_int],
     "mt_set_hmc": [_vp, C.c_int],
+    "mt_set_forward": [_vp, C.c_int, C.c_int, _vp],
     "mt_copula_heights": [_vp, C.c_int, _vp, _vp],
     "mt_nested_rhat": [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, _dp],
     "mt_interface_std": [_vp, C.c_int, _vp, C.c_int, _vp],
@@ -257,6 +259,10 @@ class Context:
         ev, tot = C.c_double(), C.c_double()
         self._ck("mt_get_work", self.lib.mt_get_work(self.h, C.byref(ev), C.byref(tot), int(reset)))
         return ev.value, tot.value
+
+    def set_forward(self, kind, n_z=0, h_ref=None):
+        h = None if h_ref is None else np.ascontiguousarray(h_ref, np.float64)
+        self._ck("mt_set_forward", self.lib.mt_set_forward(self.h, int(kind), int(n_z), _ptr(h)))
 
     def set_hmc(self, n_leapfrog):
         self._ck("mt_set_hmc", self.lib.mt_set_hmc(self.h, int(n_leapfrog)))

@@ -1,0 +1,97 @@
+"""The paper's linearised forward model (Sec. 2.1.2) on the GPU against the
+FP64 oracle (oracle/linear.py): log-likelihoods of several geometries in
+both height precisions (the path lengths, voxel densities and linearisation
+of the oracle, evaluated independently), the exact value at the reference
+geometry, -inf once lambda_hat turns non-positive, random-walk steps under
+the model, and the calls that need the march refusing it."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import linear as LN
+from paper_2603_28907_gb300 import mt, workloads as W
+from tests.gpu_common import DEV, setup
+
+pytestmark = pytest.mark.gpu
+
+
+def _dtype(precision):
+    return torch.float64 if precision == mt.PREC_F64 else torch.float32
+
+
+# FP64: 1e-10 relative.  FP32: 1e-3 absolute at the reference and the
+# data-generating geometry; for geometries far from the reference the FP32
+# sums over a ray's voxels and the per-ray Poisson terms leave ~1e-7 relative
+# per ray, 1e-6 relative of the chain's log-likelihood.
+@pytest.mark.parametrize("precision,rtol,atol_near", [(mt.PREC_F64, 1e-10, 1e-6), (mt.PREC_F32, 1e-6, 1e-3)])
+def test_linear_loglik_matches_oracle(precision, rtol, atol_near):
+    w = W.tiny()
+    pr, ctx, op, counts, _ = setup(w, precision=precision)
+    nz = 30
+    ctx.set_forward(mt.FORWARD_LINEAR, nz)
+    rays = LN.lengths(pr, nz)
+    C = counts.cpu().numpy()
+    Hs = np.concatenate([pr["mu"][None], pr["H_true"][None], W.init_chains(w, 3)])
+    H = torch.tensor(Hs, dtype=_dtype(precision), device=DEV).contiguous()
+    ll = torch.zeros(H.shape[0], dtype=torch.float64, device=DEV)
+    lp = torch.zeros_like(ll)
+    ctx.logpost(H, ll, lp)
+    torch.cuda.synchronize()
+    Hn = H.cpu().double().numpy()
+    for c in range(H.shape[0]):
+        ref = LN.loglik(Hn[c], pr, C, rays, nz, pr["mu"])
+        if math.isinf(ref):
+            assert ll[c].item() == -math.inf
+        elif c < 2:
+            assert abs(ll[c].item() - ref) <= atol_near, (c, ll[c].item(), ref)
+        else:
+            assert abs(ll[c].item() - ref) <= rtol * abs(ref), (c, ll[c].item(), ref)
+        assert abs(lp[c].item() - op.logprior(Hn[c])) <= 1e-9 * max(1.0, abs(op.logprior(Hn[c])))
+    ctx.close()
+
+
+def test_linear_negative_lambda_is_minus_inf():
+    w = W.tiny()
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F64)
+    ctx.set_forward(mt.FORWARD_LINEAR, 30)
+    H = np.array(pr["mu"])
+    H[0] = 1.0                                            # far below the reference: opacity drops
+    H[1] = 2.0                                            # by far more than Lambda on many rays
+    H[2] = 3.0
+    Ht = torch.tensor(H[None], dtype=torch.float64, device=DEV).contiguous()
+    ll = torch.zeros(1, dtype=torch.float64, device=DEV)
+    ctx.logpost(Ht, ll, None)
+    torch.cuda.synchronize()
+    assert ll[0].item() == LN.loglik(H, pr, counts.cpu().numpy(), LN.lengths(pr, 30), 30, pr["mu"])
+    ctx.close()
+
+
+def test_linear_random_walk_and_refusals():
+    w = W.tiny()
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    nz = 30
+    ctx.set_forward(mt.FORWARD_LINEAR, nz)
+    H0 = torch.tensor(W.init_chains(w), dtype=torch.float32, device=DEV).contiguous()
+    ctx.init_chains(H0, w.seed_mcmc)
+    ctx.run(mt.KERNEL_RW, 0.05, 2, 5)
+    H = torch.zeros_like(H0)
+    ll = torch.zeros(w.n_chains, dtype=torch.float64, device=DEV)
+    ctx.get_state(H, ll)
+    torch.cuda.synchronize()
+    rays = LN.lengths(pr, nz)
+    Hn = H.cpu().double().numpy()
+    for c in range(w.n_chains):
+        ref = LN.loglik(Hn[c], pr, counts.cpu().numpy(), rays, nz, pr["mu"])
+        assert abs(ll[c].item() - ref) <= 1e-6 * abs(ref)
+    g = torch.zeros((1, w.L, w.R, w.Q), dtype=torch.float64, device=DEV)
+    with pytest.raises(mt.MtError):
+        ctx.grad(H0[:1].contiguous(), g)
+    O = torch.zeros((1, w.S * w.P), dtype=torch.float64, device=DEV)
+    with pytest.raises(mt.MtError):
+        ctx.ray_terms(H0[:1].contiguous(), O)
+    ctx.set_forward(mt.FORWARD_MARCH)                    # back to the march: chains re-usable
+    ctx.run(mt.KERNEL_RW, 0.05, 1, 1)
+    ctx.sync(60.0)
+    ctx.close()
