@@ -1438,13 +1438,6 @@ mt_status mt_set_prior(mt_ctx *ctx, int kind)
         std::vector<float> tf(N);
         for (size_t i = 0; i < N; ++i) tf[i] = (float)t[i];
         if (ctx->d_terr) cudaFree(ctx->d_terr);
-    if (ctx->d_lrow) cudaFree(ctx->d_lrow);
-    if (ctx->d_lcol) cudaFree(ctx->d_lcol);
-    if (ctx->d_lval) cudaFree(ctx->d_lval);
-    if (ctx->d_R0) cudaFree(ctx->d_R0);
-    if (ctx->d_dR) cudaFree(ctx->d_dR);
-    if (ctx->d_lam0) cudaFree(ctx->d_lam0);
-    if (ctx->d_amc) cudaFree(ctx->d_amc);
         ctx->d_terr = nullptr;
         CK(ctx, cudaMalloc(&ctx->d_terr, N * es));
         CK(ctx, cudaMemcpyAsync(ctx->d_terr, es == 8 ? (const void *)t.data() : (const void *)tf.data(),
@@ -1564,7 +1557,6 @@ mt_status mt_set_forward(mt_ctx *ctx, int kind, int n_z, const double *h_ref)
     if (ctx->have_counts)
         CK(ctx, launch_lin_amc((int)nr, ctx->d_lam0, ctx->d_cnt, ctx->d_amc, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));  // host vectors go out of scope
-    (void)N;
     if (ctx->C > 0 && ctx->have_counts) {  // live chains: re-evaluate under the new forward model
         HRef h{ctx->d_H, (long long)np, ctx->d_cur, (long long)(ctx->C * np), 0};
         TRY(eval_logpost(ctx, h, ctx->C, ctx->d_ll, ctx->d_lp));

@@ -95,3 +95,28 @@ def test_linear_random_walk_and_refusals():
     ctx.run(mt.KERNEL_RW, 0.05, 1, 1)
     ctx.sync(60.0)
     ctx.close()
+
+
+def test_linear_model_with_the_copula_prior():
+    """Both switches together: latents -> heights -> linearised likelihood;
+    setting the prior after the forward model keeps the model's buffers."""
+    from oracle import copula as K
+    w = W.tiny()
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F64)
+    nz = 30
+    ctx.set_forward(mt.FORWARD_LINEAR, nz)
+    ctx.set_prior(mt.PRIOR_COPULA)
+    rng = np.random.default_rng(6)
+    lat = 0.3 * rng.standard_normal((2, w.L, w.R, w.Q))
+    lat[:, w.L - 1] = 0.0
+    lat[:, w.L - 1, 0, :w.L - 1] = 0.8
+    Lt = torch.tensor(lat, dtype=torch.float64, device=DEV).contiguous()
+    ll = torch.zeros(2, dtype=torch.float64, device=DEV)
+    ctx.logpost(Lt, ll, None)
+    torch.cuda.synchronize()
+    rays = LN.lengths(pr, nz)
+    for c in range(2):
+        H = K.heights(lat[c], pr["mu"][w.L - 1])
+        ref = LN.loglik(H, pr, counts.cpu().numpy(), rays, nz, pr["mu"])
+        assert abs(ll[c].item() - ref) <= 1e-9 * abs(ref)
+    ctx.close()
