@@ -121,7 +121,9 @@ struct mt_ctx {
     int lin_nz = 0;
     std::vector<double> lin_href;    // reference heights of the linearisation
     int *d_lrow = nullptr, *d_lcol = nullptr;  // voxel path lengths (CSR by ray)
-    void *d_lval = nullptr, *d_R0 = nullptr, *d_dR = nullptr;  // d_R0: reference cell-centre heights
+    void *d_lval = nullptr, *d_R0 = nullptr, *d_dR = nullptr;  // d_R0: reference voxel densities
+    double *d_fine = nullptr;        // linearised model: fine-block partial sums
+    size_t fine_cap = 0;
     size_t dR_cap = 0;
     double *d_lam0 = nullptr, *d_amc = nullptr;
     int hmc_leap = 8;                // leapfrog steps per HMC proposal
@@ -559,9 +561,10 @@ static mt_status ensure_lin(mt_ctx *ctx, int n)
     if (!ctx->linear) return MT_OK;
     const size_t nvox = (size_t)ctx->lin_nz * (ctx->R - 1) * (ctx->Q - 1);
     const size_t Cp = ((size_t)n + 31) / 32 * 32;
-    void *old = ctx->d_dR;
+    void *old = ctx->d_dR, *old_f = ctx->d_fine;
     TRY(grow(ctx, &ctx->d_dR, &ctx->dR_cap, nvox * Cp * elem_size(ctx)));
-    if (ctx->d_dR != old) drop_graph(ctx);
+    TRY(grow(ctx, (void **)&ctx->d_fine, &ctx->fine_cap, lin_fine_partials(ctx->pb, n) * 8));
+    if (ctx->d_dR != old || (void *)ctx->d_fine != old_f) drop_graph(ctx);
     return MT_OK;
 }
 
@@ -572,8 +575,8 @@ static mt_status ray_kernel(mt_ctx *ctx, HRef h, int n)
     if (ctx->linear) {
         TRY(ensure_lin(ctx, n));
         CK(ctx, launch_lin(ctx->pb, ctx->mode, h, n, ctx->lin_nz, ctx->d_lrow, ctx->d_lcol, ctx->d_lval,
-                           ctx->d_R0, ctx->d_dR, ctx->d_lam0, ctx->d_amc, (double *)ctx->d_part,
-                           ctx->stream));
+                           ctx->d_R0, ctx->d_dR, ctx->d_lam0, ctx->d_amc, ctx->d_fine,
+                           (double *)ctx->d_part, ctx->stream));
         return MT_OK;
     }
     CK(ctx, launch_march(ctx->pb, ctx->mode, h, n, ctx->d_part, nullptr, nullptr, ctx->stream));
@@ -745,6 +748,7 @@ mt_status mt_destroy(mt_ctx *ctx)
     if (ctx->d_dR) cudaFree(ctx->d_dR);
     if (ctx->d_lam0) cudaFree(ctx->d_lam0);
     if (ctx->d_amc) cudaFree(ctx->d_amc);
+    if (ctx->d_fine) cudaFree(ctx->d_fine);
     if (ctx->d_Hd) cudaFree(ctx->d_Hd);
     if (ctx->d_nodes) cudaFree(ctx->d_nodes);
     if (ctx->d_tmp) cudaFree(ctx->d_tmp);
@@ -1499,7 +1503,7 @@ mt_status mt_set_forward(mt_ctx *ctx, int kind, int n_z, const double *h_ref)
         return MT_OK;
     }
     if (n_z < 1 || n_z > 4096) return fail(ctx, MT_EINVAL, "n_z %d not in [1, 4096]", n_z);
-    const size_t N = (size_t)ctx->R * ctx->Q, np = n_per_chain(ctx);
+    const size_t np = n_per_chain(ctx);
     ctx->lin_href.assign(h_ref ? h_ref : ctx->mu.data(), (h_ref ? h_ref : ctx->mu.data()) + np);
     std::vector<double> sens(3 * (size_t)ctx->S), dirs(3 * (size_t)ctx->P);
     CK(ctx, cudaMemcpyAsync(sens.data(), ctx->d_sensors, sens.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1517,23 +1521,10 @@ mt_status mt_set_forward(mt_ctx *ctx, int kind, int n_z, const double *h_ref)
         for (int e = row[p]; e < row[p + 1]; ++e) O += val[e] * R0[col[e]];
         lam0[p] = ctx->cfg.I0 * exp(-O / ctx->cfg.atten);
     }
-    // the reference's cell-centre heights [L][cells] (the density kernel
-    // differences the chains' indicators against them)
-    const int nx = ctx->Q - 1, ny = ctx->R - 1;
-    std::vector<double> h0c((size_t)ctx->L * nx * ny);
-    for (int l = 0; l < ctx->L; ++l)
-        for (int i = 0; i < ny; ++i)
-            for (int j = 0; j < nx; ++j) {
-                const double *hl = ctx->lin_href.data() + (size_t)l * N;
-                h0c[((size_t)l * ny + i) * nx + j] =
-                    0.25 * ((hl[i * ctx->Q + j] + hl[i * ctx->Q + j + 1]) + (hl[(i + 1) * ctx->Q + j] + hl[(i + 1) * ctx->Q + j + 1]));
-            }
     const size_t es = elem_size(ctx);
-    std::vector<float> valf, h0f;
-    if (es == 4) {
-        valf.assign(val.begin(), val.end());
-        h0f.assign(h0c.begin(), h0c.end());
-    }
+    std::vector<float> valf;
+    if (es == 4) valf.assign(val.begin(), val.end());
+    const size_t nvox = R0.size();
     for (void **p : {(void **)&ctx->d_lrow, (void **)&ctx->d_lcol, &ctx->d_lval, &ctx->d_R0,
                      (void **)&ctx->d_lam0, (void **)&ctx->d_amc}) {
         if (*p) cudaFree(*p);
@@ -1542,15 +1533,25 @@ mt_status mt_set_forward(mt_ctx *ctx, int kind, int n_z, const double *h_ref)
     CK(ctx, cudaMalloc((void **)&ctx->d_lrow, row.size() * 4));
     CK(ctx, cudaMalloc((void **)&ctx->d_lcol, nnz * 4 + 16));
     CK(ctx, cudaMalloc(&ctx->d_lval, nnz * es + 16));
-    CK(ctx, cudaMalloc(&ctx->d_R0, h0c.size() * es));
+    CK(ctx, cudaMalloc(&ctx->d_R0, nvox * es));
     CK(ctx, cudaMalloc((void **)&ctx->d_lam0, nr * 8));
     CK(ctx, cudaMalloc((void **)&ctx->d_amc, nr * 8));
     CK(ctx, cudaMemcpyAsync(ctx->d_lrow, row.data(), row.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->d_lcol, col.data(), nnz * 4, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->d_lval, es == 4 ? (const void *)valf.data() : (const void *)val.data(),
                             nnz * es, cudaMemcpyHostToDevice, ctx->stream));
-    CK(ctx, cudaMemcpyAsync(ctx->d_R0, es == 4 ? (const void *)h0f.data() : (const void *)h0c.data(),
-                            h0c.size() * es, cudaMemcpyHostToDevice, ctx->stream));
+    // reference densities with the device's own arithmetic (so that the
+    // densities of the reference itself differ from them by exactly 0)
+    {
+        std::vector<float> hf;
+        if (es == 4) hf.assign(ctx->lin_href.begin(), ctx->lin_href.end());
+        TRY(grow(ctx, &ctx->d_in, &ctx->in_cap, np * es));
+        CK(ctx, cudaMemcpyAsync(ctx->d_in, es == 4 ? (const void *)hf.data() : (const void *)ctx->lin_href.data(),
+                                np * es, cudaMemcpyHostToDevice, ctx->stream));
+        HRef hr{ctx->d_in, (long long)np, nullptr, 0, 0};
+        CK(ctx, launch_lin_reference(ctx->pb, ctx->mode, hr, n_z, ctx->d_R0, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
     CK(ctx, cudaMemcpyAsync(ctx->d_lam0, lam0.data(), nr * 8, cudaMemcpyHostToDevice, ctx->stream));
     ctx->lin_nz = n_z;
     ctx->linear = true;

@@ -148,8 +148,10 @@ cudaError_t launch_nested_rhat(int mode, const void *draws, int N, int C, int P,
 size_t interface_smem(int n_z);
 size_t copula_smem_bytes(const Prob &pb, int mode);
 cudaError_t launch_lin(const Prob &pb, int mode, HRef h, int n_chains, int nz, const int *row,
-                       const int *col, const void *val, const void *h0c, void *dR, const double *lam0,
-                       const double *amc, double *partial, cudaStream_t st);
+                       const int *col, const void *val, const void *R0, void *dR, const double *lam0,
+                       const double *amc, double *fine, double *partial, cudaStream_t st);
+cudaError_t launch_lin_reference(const Prob &pb, int mode, HRef h, int nz, void *R0, cudaStream_t st);
+size_t lin_fine_partials(const Prob &pb, int n_chains);
 cudaError_t launch_lin_amc(int n, const double *lam0, const int32_t *cnt, double *amc, cudaStream_t st);
 cudaError_t launch_copula(const Prob &pb, int mode, HRef lat, const void *terrain, void *H, int n_chains,
                           cudaStream_t st);

@@ -108,26 +108,16 @@ void lin_density_host(const Prob &pb, const double *H, int nz, std::vector<doubl
 }
 
 // ---------------------------------------------------------------- device
-// sigma(a) - sigma(b) for the logistic sigma, with relative accuracy also
-// when a and b are close: sigma(a) (1 - sigma(b)) (1 - e^{-(a-b)}).
-template <typename T> __device__ __forceinline__ T dsigma(T a, T b)
-{
-    if (fabs(a - b) < (T)1) {
-        const T sa = (T)1 / ((T)1 + exp(-a)), snb = (T)1 / ((T)1 + exp(b));  // sigma(a), 1 - sigma(b)
-        return -sa * snb * expm1(b - a);
-    }
-    return (T)1 / ((T)1 + exp(-a)) - (T)1 / ((T)1 + exp(-b));
-}
-
 template <typename T> __device__ __forceinline__ T eta(T u) { return u > (T)0 ? (T)1 : (u < (T)0 ? (T)0 : (T)0.5); }
 
-// dR[v][c] = R_v(H_c) - R_v(H_ref), formed per surface as the difference of
-// the two indicators (so it is accurate relative to itself, and exactly 0 at
-// the reference); h0c = the reference's cell-centre heights [L][cells].
-// Threads = 32 chains x 8 cells per block, cells along x.
+// Voxel densities R_v(H_c) - R0_v of n_chains heights, [v][chain] (chains
+// fastest, padded to Cp); with R0 == nullptr the densities themselves (used
+// once for the reference, so that R and R0 come from the same arithmetic and
+// dR is exactly 0 at the reference).  Threads = 32 chains x 8 cells per
+// block, cells along x.
 template <typename T>
 __global__ void __launch_bounds__(256) k_lin_density(Prob pb, HRef h, int n_chains, int Cp, int nz,
-                                                     const T *h0c, T *dR)
+                                                     const T *R0, T *dR)
 {
     const int lane = threadIdx.x & 31, cw = threadIdx.x >> 5;
     const int nx = pb.Q - 1, ny = pb.R - 1;
@@ -141,28 +131,28 @@ __global__ void __launch_bounds__(256) k_lin_density(Prob pb, HRef h, int n_chai
         return;
     }
     const T *Hc = chain_ptr<T>(h, c);
-    T hc[MT_MAX_L], hr[MT_MAX_L];
+    T hc[MT_MAX_L];
 #pragma unroll
     for (int l = 0; l < MT_MAX_L; ++l) {
         if (l < pb.L) {
             const T *hl = Hc + (size_t)l * pb.N;
             hc[l] = (T)0.25 * ((hl[i * pb.Q + j] + hl[i * pb.Q + j + 1]) + (hl[(i + 1) * pb.Q + j] + hl[(i + 1) * pb.Q + j + 1]));
-            hr[l] = h0c[(size_t)l * ncell + colv];
         }
     }
     const T dz = (T)(pb.box[2] / nz), inv_g = pb.gamma > 0.0 ? (T)(1.0 / pb.gamma) : (T)0;
     for (int k = 0; k < nz; ++k) {
         const T z = ((T)k + (T)0.5) * dz;
-        T r = (T)0;
+        T r = (T)pb.rho_top;
 #pragma unroll
         for (int l = 0; l < MT_MAX_L; ++l) {
             if (l < pb.L) {
-                const T d = pb.gamma == 0.0 ? eta<T>(hc[l] - z) - eta<T>(hr[l] - z)
-                                            : dsigma<T>((hc[l] - z) * inv_g, (hr[l] - z) * inv_g);
-                r += (T)pb.drho[l] * d;
+                const T u = hc[l] - z;
+                const T sg = pb.gamma == 0.0 ? eta<T>(u) : (T)1 / ((T)1 + exp(-u * inv_g));
+                r += (T)pb.drho[l] * sg;
             }
         }
-        dR[((size_t)k * ncell + colv) * Cp + c] = r;
+        const size_t v = (size_t)k * ncell + colv;
+        dR[v * Cp + c] = R0 ? r - R0[v] : r;
     }
 }
 
@@ -183,8 +173,10 @@ template <typename T> __device__ __forceinline__ T x_minus_log1p(T x)
 }
 
 // One warp = one ray at a time for 32 chains (lane = chain); a CTA = its 32
-// warps over the block's rays for one tile of 32 chains.  Per chain the
-// CTA's terms are summed (float-float for FP32, FP64 for F64) and written as
+// warps over the block's rays for one tile of 32 chains.  Blocks are small
+// and the grid runs ray blocks fastest, so the CTAs in flight share one or
+// two chain tiles and their gathers hit L2.  Per chain the CTA's terms are
+// summed (float-float for FP32, FP64 for F64) and written as
 // partial[c][block]; -inf if any of them had lambda_hat <= 0.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_lin_ll(Prob pb, int n_chains, int Cp, int rays_per_block,
@@ -206,7 +198,17 @@ __global__ void __launch_bounds__(1024) k_lin_ll(Prob pb, int n_chains, int Cp, 
     int neg = 0;
     for (int p = r_begin + wid; p < r_end; p += nw) {
         T dO = (T)0;
-        for (int e = row[p]; e < row[p + 1]; ++e) dO += val[e] * dR[(size_t)col[e] * Cp + c];
+        const int e1 = row[p + 1];
+        int e = row[p];
+        for (; e + 4 <= e1; e += 4) {  // four gathers in flight
+            const T d0 = dR[(size_t)col[e] * Cp + c], d1 = dR[(size_t)col[e + 1] * Cp + c];
+            const T d2 = dR[(size_t)col[e + 2] * Cp + c], d3 = dR[(size_t)col[e + 3] * Cp + c];
+            dO += val[e] * d0;
+            dO += val[e + 1] * d1;
+            dO += val[e + 2] * d2;
+            dO += val[e + 3] * d3;
+        }
+        for (; e < e1; ++e) dO += val[e] * dR[(size_t)col[e] * Cp + c];
         const int Cn = pb.cnt[p];
         const T l0 = (T)lam0[p];
         const T lh = l0 * ((T)1 - dO * invL);
@@ -231,6 +233,17 @@ __global__ void __launch_bounds__(1024) k_lin_ll(Prob pb, int n_chains, int Cp, 
     }
 }
 
+// part[c][b] = sum of the f consecutive fine partials of block b, in order.
+__global__ void k_lin_fold(int n_chains, int n_fine, int n_blk, int f, const double *fine, double *part)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_chains * n_blk) return;
+    const int c = idx / n_blk, b = idx - c * n_blk;
+    double s = 0.0;
+    for (int q = b * f; q < min((b + 1) * f, n_fine); ++q) s += fine[(size_t)c * n_fine + q];
+    part[(size_t)c * n_blk + b] = s;
+}
+
 __global__ void k_lin_amc(int n, const double *lam0, const int32_t *cnt, double *amc)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -243,24 +256,44 @@ cudaError_t launch_lin_amc(int n, const double *lam0, const int32_t *cnt, double
     return cudaGetLastError();
 }
 
+constexpr int kLinRays = 512;  // rays per k_lin_ll block (divides the march's 8192)
+
+size_t lin_fine_partials(const Prob &pb, int n_chains)
+{
+    return (size_t)n_chains * ((pb.n_rays + kLinRays - 1) / kLinRays);
+}
+
+cudaError_t launch_lin_reference(const Prob &pb, int mode, HRef h, int nz, void *R0, cudaStream_t st)
+{
+    const int ncol = (pb.Q - 1) * (pb.R - 1);
+    dim3 gd((ncol + 7) / 8, 1);
+    if (mode == MODE_F64) k_lin_density<double><<<gd, 256, 0, st>>>(pb, h, 1, 1, nz, nullptr, (double *)R0);
+    else k_lin_density<float><<<gd, 256, 0, st>>>(pb, h, 1, 1, nz, nullptr, (float *)R0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_lin(const Prob &pb, int mode, HRef h, int n_chains, int nz, const int *row,
-                       const int *col, const void *val, const void *h0c, void *dR, const double *lam0,
-                       const double *amc, double *partial, cudaStream_t st)
+                       const int *col, const void *val, const void *R0, void *dR, const double *lam0,
+                       const double *amc, double *fine, double *partial, cudaStream_t st)
 {
     const int Cp = (n_chains + 31) / 32 * 32;
     const int ncol = (pb.Q - 1) * (pb.R - 1);
     dim3 gd((ncol + 7) / 8, Cp / 32);
-    const int rpb = march_rays_per_block(pb);
-    dim3 gl((pb.n_rays + rpb - 1) / rpb, Cp / 32);
+    const int n_fine = (pb.n_rays + kLinRays - 1) / kLinRays;
+    dim3 gl(n_fine, Cp / 32);
     if (mode == MODE_F64) {
-        k_lin_density<double><<<gd, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const double *)h0c, (double *)dR);
-        k_lin_ll<double><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, rpb, row, col, (const double *)val,
-                                              (const double *)dR, lam0, amc, partial);
+        k_lin_density<double><<<gd, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const double *)R0, (double *)dR);
+        k_lin_ll<double><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, kLinRays, row, col, (const double *)val,
+                                              (const double *)dR, lam0, amc, fine);
     } else {
-        k_lin_density<float><<<gd, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const float *)h0c, (float *)dR);
-        k_lin_ll<float><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, rpb, row, col, (const float *)val,
-                                             (const float *)dR, lam0, amc, partial);
+        k_lin_density<float><<<gd, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const float *)R0, (float *)dR);
+        k_lin_ll<float><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, kLinRays, row, col, (const float *)val,
+                                             (const float *)dR, lam0, amc, fine);
     }
+    const int rpb = march_rays_per_block(pb);
+    const int n_blk = (pb.n_rays + rpb - 1) / rpb;
+    const int f = (rpb + kLinRays - 1) / kLinRays;
+    k_lin_fold<<<(n_chains * n_blk + 255) / 256, 256, 0, st>>>(n_chains, n_fine, n_blk, f, fine, partial);
     return cudaGetLastError();
 }
 
