@@ -131,24 +131,30 @@ __global__ void __launch_bounds__(256) k_lin_density(Prob pb, HRef h, int n_chai
         return;
     }
     const T *Hc = chain_ptr<T>(h, c);
-    T hc[MT_MAX_L];
+    T hc[MT_MAX_L], dr[MT_MAX_L];
 #pragma unroll
     for (int l = 0; l < MT_MAX_L; ++l) {
         if (l < pb.L) {
             const T *hl = Hc + (size_t)l * pb.N;
             hc[l] = (T)0.25 * ((hl[i * pb.Q + j] + hl[i * pb.Q + j + 1]) + (hl[(i + 1) * pb.Q + j] + hl[(i + 1) * pb.Q + j + 1]));
+            dr[l] = (T)pb.drho[l];
         }
     }
     const T dz = (T)(pb.box[2] / nz), inv_g = pb.gamma > 0.0 ? (T)(1.0 / pb.gamma) : (T)0;
+    const T rtop = (T)pb.rho_top;
+    const bool hard = pb.gamma == 0.0;
     for (int k = 0; k < nz; ++k) {
         const T z = ((T)k + (T)0.5) * dz;
-        T r = (T)pb.rho_top;
+        T r = rtop;
 #pragma unroll
         for (int l = 0; l < MT_MAX_L; ++l) {
             if (l < pb.L) {
                 const T u = hc[l] - z;
-                const T sg = pb.gamma == 0.0 ? eta<T>(u) : (T)1 / ((T)1 + exp(-u * inv_g));
-                r += (T)pb.drho[l] * sg;
+                T sg;
+                if (hard) sg = eta<T>(u);
+                else if constexpr (sizeof(T) == 4) sg = __frcp_rn(1.0f + expf(-u * inv_g));
+                else sg = 1.0 / (1.0 + exp(-u * inv_g));
+                r += dr[l] * sg;
             }
         }
         const size_t v = (size_t)k * ncell + colv;
@@ -160,12 +166,15 @@ __global__ void __launch_bounds__(256) k_lin_density(Prob pb, HRef h, int n_chai
 // + x^4/4 - ...).
 template <typename T> __device__ __forceinline__ T x_minus_log1p(T x)
 {
+    // |x| < 1/8: the series to x^11 (FP32) or x^22 (FP64) leaves less than
+    // 8^-9 (resp. 8^-20) of x^2/2
+    constexpr int NT = sizeof(T) == 4 ? 11 : 22;
     if (fabs(x) < (T)0.125) {
         T t = x, s = (T)0;
 #pragma unroll
-        for (int n = 2; n <= 24; ++n) {
+        for (int n = 2; n <= NT; ++n) {
             t *= x;
-            s += ((n & 1) ? -t : t) / (T)n;
+            s += ((n & 1) ? -t : t) * ((T)1 / (T)n);
         }
         return s;
     }
@@ -174,8 +183,8 @@ template <typename T> __device__ __forceinline__ T x_minus_log1p(T x)
 
 // One warp = one ray at a time for 32 chains (lane = chain); a CTA = its 32
 // warps over the block's rays for one tile of 32 chains.  Blocks are small
-// and the grid runs ray blocks fastest, so the CTAs in flight share one or
-// two chain tiles and their gathers hit L2.  Per chain the CTA's terms are
+// and the grid runs ray blocks fastest, so the CTAs in flight work on one
+// chain tile and their gathers hit L2.  Per chain the CTA's terms are
 // summed (float-float for FP32, FP64 for F64) and written as
 // partial[c][block]; -inf if any of them had lambda_hat <= 0.
 template <typename T>
@@ -256,7 +265,9 @@ cudaError_t launch_lin_amc(int n, const double *lam0, const int32_t *cnt, double
     return cudaGetLastError();
 }
 
-constexpr int kLinRays = 512;  // rays per k_lin_ll block (divides the march's 8192)
+// rays per k_lin_ll block (divides the march's 8192): two per warp, so that
+// one 32-chain tile fills the GPU and the CTAs in flight share its dR in L2
+constexpr int kLinRays = 64;
 
 size_t lin_fine_partials(const Prob &pb, int n_chains)
 {
