@@ -29,8 +29,10 @@ def nvcc() -> str:
 
 
 def _flags(verbose_ptxas: bool) -> list:
-    f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-         "--expt-relaxed-constexpr", "-Xcompiler", "-fvisibility=hidden"]
+    # host code: no fused multiply-add contraction, so that it rounds alike
+    # on x86 and Arm hosts
+    f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr", "-Xcompiler", "-fvisibility=hidden"]
     if verbose_ptxas:
         f += ["-Xptxas", "-v"]
     return ARCH + f
@@ -42,7 +44,7 @@ def _sources() -> list:
 
 def _deps() -> list:
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) \
-        + glob.glob(os.path.join(INCLUDE, "*.h"))
+        + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:

@@ -109,6 +109,10 @@ void lin_density_host(const Prob &pb, const double *H, int nz, std::vector<doubl
 
 // ---------------------------------------------------------------- device
 template <typename T> __device__ __forceinline__ T eta(T u) { return u > (T)0 ? (T)1 : (u < (T)0 ? (T)0 : (T)0.5); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 
 // Voxel densities R_v(H_c) - R0_v of n_chains heights, [v][chain] (chains
 // fastest, padded to Cp); with R0 == nullptr the densities themselves (used
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(256) k_lin_density(Prob pb, HRef h, int n_chai
     const int nx = pb.Q - 1, ny = pb.R - 1;
     const int colv = blockIdx.x * 8 + cw;  // cell index i * nx + j
     const int c = blockIdx.y * 32 + lane;
-    if (colv >= nx * ny) return;
+    if (colv >= nx * ny || c >= Cp) return;  // the reference launch has Cp = 1
     const int i = colv / nx, j = colv - i * nx;
     const size_t ncell = (size_t)nx * ny;
     if (c >= n_chains) {
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(256) k_lin_density(Prob pb, HRef h, int n_chai
     for (int l = 0; l < MT_MAX_L; ++l) {
         if (l < pb.L) {
             const T *hl = Hc + (size_t)l * pb.N;
-            hc[l] = (T)0.25 * ((hl[i * pb.Q + j] + hl[i * pb.Q + j + 1]) + (hl[(i + 1) * pb.Q + j] + hl[(i + 1) * pb.Q + j + 1]));
+            hc[l] = (T)0.25 * (((hl[i * pb.Q + j] + hl[i * pb.Q + j + 1]) + hl[(i + 1) * pb.Q + j]) + hl[(i + 1) * pb.Q + j + 1]);
             dr[l] = (T)pb.drho[l];
         }
     }
@@ -144,12 +148,15 @@ __global__ void __launch_bounds__(256) k_lin_density(Prob pb, HRef h, int n_chai
     const T rtop = (T)pb.rho_top;
     const bool hard = pb.gamma == 0.0;
     for (int k = 0; k < nz; ++k) {
-        const T z = ((T)k + (T)0.5) * dz;
+        // z_k and h - z_k each rounded on their own (no fused multiply-add):
+        // a surface exactly at a voxel centre gives u = 0 and the hard
+        // indicator its midpoint value, as in the host's reference densities
+        const T z = mul_rn((T)k + (T)0.5, dz);
         T r = rtop;
 #pragma unroll
         for (int l = 0; l < MT_MAX_L; ++l) {
             if (l < pb.L) {
-                const T u = hc[l] - z;
+                const T u = sub_rn(hc[l], z);
                 T sg;
                 if (hard) sg = eta<T>(u);
                 else if constexpr (sizeof(T) == 4) sg = __frcp_rn(1.0f + expf(-u * inv_g));

@@ -153,3 +153,25 @@ def test_copula_refuses_car_only_calls():
     H = torch.tensor(W.init_chains(w, 2), dtype=torch.float32, device=DEV).contiguous()
     ctx.grad(H, g)
     ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(mt.PREC_F64, 1e-9), (mt.PREC_F32, 2e-3)])
+def test_copula_heights_odd_grid(precision, tol):
+    """A 5 x 7 grid (neither side a power of two; the DFT passes are direct
+    sums over any size) with 3 surfaces and several r, including r near 0."""
+    w = W.small(R=5, Q=7, bases=(40.0, 75.0, 110.0), rho=(2.65, 1.9, 0.0012, 2.65), n_chains=4)
+    pr = W.problem(w)
+    ctx = mt.from_workload(pr, precision=precision)
+    ctx.set_prior(mt.PRIOR_COPULA)
+    lat = latents(w, 4, 9)
+    for c, r in enumerate((1e-6, 0.3, 0.9, 0.999)):
+        lat[c, w.L - 1].reshape(-1)[:w.L - 1] = r
+    Lt = torch.tensor(lat, dtype=_dtype(precision), device=DEV).contiguous()
+    H = torch.zeros_like(Lt)
+    ctx.copula_heights(Lt, H)
+    torch.cuda.synchronize()
+    T = pr["mu"][w.L - 1]
+    Ln, Hg = Lt.cpu().double().numpy(), H.cpu().double().numpy()
+    for c in range(4):
+        assert np.max(np.abs(Hg[c] - K.heights(Ln[c], T))) <= tol
+    ctx.close()
