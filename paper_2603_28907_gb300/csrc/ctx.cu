@@ -25,7 +25,7 @@ cudaError_t launch_accept_fused(const Prob &pb, int mode, int n_chains, const vo
                                 double *lp, double *ll_prop_out, uint8_t *cur, uint8_t *prop_sel,
                                 int64_t *accepts, int32_t *acc_last, double *logu_out,
                                 uint64_t seed, const int64_t *step_base, int step_off,
-                                cudaStream_t st);
+                                cudaStream_t st, double *alpha_out = nullptr);
 size_t nodes_bytes_f64(int L, int N);
 
 int march_rays_per_block(const Prob &pb)
@@ -127,6 +127,12 @@ struct mt_ctx {
     size_t dR_cap = 0;
     double *d_lam0 = nullptr, *d_amc = nullptr;
     int hmc_leap = 8;                // leapfrog steps per HMC proposal
+    // step-size adaptation of MALA / HMC (mt_set_adapt): target acceptance,
+    // number of adapted steps (0 = off), state not yet initialised
+    double adapt_target = 0.8;
+    int adapt_n = 0;
+    bool adapt_pending = false;
+    double *d_eps = nullptr, *d_da = nullptr, *d_alpha = nullptr;
     double *d_P = nullptr;           // HMC momentum [C][n]
     double *d_Q64 = nullptr;         // HMC trajectory position in FP64 [C][n]
     double *d_k0 = nullptr;          // HMC initial kinetic energy [C]
@@ -253,6 +259,10 @@ static void drop_chains(mt_ctx *ctx)
     dfree(ctx->d_P);
     dfree(ctx->d_Q64);
     dfree(ctx->d_k0);
+    dfree(ctx->d_eps);
+    dfree(ctx->d_da);
+    dfree(ctx->d_alpha);
+    ctx->adapt_pending = ctx->adapt_n > 0;  // new chains adapt from the start
     ctx->g_valid = false;
     ctx->C = 0;
 }
@@ -999,6 +1009,7 @@ mt_status mt_init_chains(mt_ctx *ctx, int n_chains, const void *heights0, uint64
     }
     drop_graph(ctx);
     ctx->g_valid = false;
+    ctx->adapt_pending = ctx->adapt_n > 0;  // new chains adapt their step sizes from the start
     ctx->seed = seed;
     CK(ctx, cudaMemcpyAsync(ctx->d_H, heights0, (size_t)n_chains * np * es, cudaMemcpyDefault,
                             ctx->stream));
@@ -1038,7 +1049,8 @@ static mt_status enqueue_mala(mt_ctx *ctx, double eps, int off)
     const long long bs = (long long)ctx->C * np;
     EvPair es;
     if (ctx->timing) ev_begin(ctx, 1, &es);
-    CK(ctx, launch_propose_mala(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps,
+    const double *ec = ctx->adapt_n > 0 ? ctx->d_eps : nullptr;
+    CK(ctx, launch_propose_mala(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec,
                                 ctx->seed, ctx->d_step, off, ctx->stream));
     HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
     CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
@@ -1052,12 +1064,15 @@ static mt_status enqueue_mala(mt_ctx *ctx, double eps, int off)
     CK(ctx, launch_grad_finish_sel(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C,
                                    (const unsigned long long *)ctx->d_gacc, ctx->d_G, ctx->d_cur,
                                    ctx->stream));
-    CK(ctx, launch_mala_hastings(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps,
+    CK(ctx, launch_mala_hastings(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec,
                                  ctx->d_extra, ctx->stream));
     CK(ctx, launch_accept_fused(ctx->pb, MODE_F32, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
                                 ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
                                 ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
-                                ctx->stream));
+                                ctx->stream, ec ? ctx->d_alpha : nullptr));
+    if (ec)
+        CK(ctx, launch_adapt(ctx->C, ctx->adapt_target, ctx->adapt_n, ctx->d_alpha, ctx->d_da, ctx->d_eps,
+                             ctx->stream));
     if (ctx->timing) ev_end(ctx, 1, &es);
     return MT_OK;
 }
@@ -1071,6 +1086,26 @@ static mt_status ensure_hmc(mt_ctx *ctx)
     return MT_OK;
 }
 
+// Step-size adaptation buffers; on the first gradient-sampler run after
+// mt_set_adapt (or after new chains) every chain starts at eps0.
+static mt_status ensure_adapt(mt_ctx *ctx, double eps0)
+{
+    const size_t C = (size_t)ctx->C;
+    if (!ctx->d_eps || !ctx->d_da || !ctx->d_alpha) {
+        drop_graph(ctx);
+        TRY(dalloc(ctx, &ctx->d_eps, C));
+        TRY(dalloc(ctx, &ctx->d_da, 4 * C));
+        TRY(dalloc(ctx, &ctx->d_alpha, C));
+        CK(ctx, cudaMemsetAsync(ctx->d_alpha, 0, C * 8, ctx->stream));
+        ctx->adapt_pending = true;
+    }
+    if (ctx->adapt_pending) {
+        CK(ctx, launch_adapt_init(ctx->C, eps0, ctx->d_da, ctx->d_eps, ctx->stream));
+        ctx->adapt_pending = false;
+    }
+    return MT_OK;
+}
+
 // One HMC step: momentum and the first drift, then per leapfrog step the
 // proposal's gradient (adjoint) and a kick + drift, a final half kick with
 // the kinetic-energy difference, the proposal's prior and the accept (the
@@ -1081,7 +1116,8 @@ static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
     const long long bs = (long long)ctx->C * np;
     EvPair es;
     if (ctx->timing) ev_begin(ctx, 1, &es);
-    CK(ctx, launch_hmc_start(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps,
+    const double *ec = ctx->adapt_n > 0 ? ctx->d_eps : nullptr;
+    CK(ctx, launch_hmc_start(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec,
                              ctx->d_P, ctx->d_Q64, ctx->d_k0, ctx->seed, ctx->d_step, off, ctx->stream));
     HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
     for (int i = 0; i < ctx->hmc_leap; ++i) {
@@ -1093,15 +1129,18 @@ static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
                                        ctx->stream));
         if (i + 1 < ctx->hmc_leap)
             CK(ctx, launch_hmc_kick_drift(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C,
-                                          eps, ctx->d_P, ctx->d_Q64, ctx->stream));
+                                          eps, ec, ctx->d_P, ctx->d_Q64, ctx->stream));
     }
-    CK(ctx, launch_hmc_finish(ctx->pb, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ctx->d_P, ctx->d_k0,
+    CK(ctx, launch_hmc_finish(ctx->pb, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec, ctx->d_P, ctx->d_k0,
                               ctx->d_extra, ctx->stream));
     CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
     CK(ctx, launch_accept_fused(ctx->pb, MODE_F32, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
                                 ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
                                 ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
-                                ctx->stream));
+                                ctx->stream, ec ? ctx->d_alpha : nullptr));
+    if (ec)
+        CK(ctx, launch_adapt(ctx->C, ctx->adapt_target, ctx->adapt_n, ctx->d_alpha, ctx->d_da, ctx->d_eps,
+                             ctx->stream));
     if (ctx->timing) ev_end(ctx, 1, &es);
     return MT_OK;
 }
@@ -1151,6 +1190,7 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
         if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA / HMC need a step size eps > 0");
         TRY(ensure_chain_grads(ctx));
         if (kernel == MT_KERNEL_HMC) TRY(ensure_hmc(ctx));
+        if (ctx->adapt_n > 0) TRY(ensure_adapt(ctx, step));
     }
     TRY(ensure_partials(ctx, ctx->C));
     // random-walk steps move the states without their gradients
@@ -1478,6 +1518,39 @@ mt_status mt_set_hmc(mt_ctx *ctx, int n_leapfrog)
     if (n_leapfrog < 1 || n_leapfrog > 1024) return fail(ctx, MT_EINVAL, "n_leapfrog %d not in [1, 1024]", n_leapfrog);
     if (ctx->hmc_leap != n_leapfrog) drop_graph(ctx);
     ctx->hmc_leap = n_leapfrog;
+    return MT_OK;
+}
+
+mt_status mt_set_adapt(mt_ctx *ctx, double target_accept, int n_adapt)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (!(target_accept > 0.0 && target_accept < 1.0) || n_adapt < 0)
+        return fail(ctx, MT_EINVAL, "mt_set_adapt: need 0 < target_accept < 1 and n_adapt >= 0");
+    CK(ctx, cudaSetDevice(ctx->device));
+    drop_graph(ctx);
+    ctx->adapt_target = target_accept;
+    ctx->adapt_n = n_adapt;
+    ctx->adapt_pending = n_adapt > 0;
+    if (n_adapt == 0) {
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(ctx->d_eps);
+        dfree(ctx->d_da);
+        dfree(ctx->d_alpha);
+    }
+    return MT_OK;
+}
+
+mt_status mt_get_adapt(mt_ctx *ctx, double *eps_out, double *accept_prob_out)
+{
+    TRY(need(ctx, false));
+    if (ctx->C < 1) return fail(ctx, MT_ESTATE, "mt_init_chains first");
+    if (ctx->adapt_n == 0 || ctx->adapt_pending || !ctx->d_eps)
+        return fail(ctx, MT_ESTATE, "no adapted step sizes: mt_set_adapt, then a MALA / HMC mt_run");
+    const size_t C = ctx->C;
+    if (eps_out) CK(ctx, cudaMemcpyAsync(eps_out, ctx->d_eps, C * 8, cudaMemcpyDefault, ctx->stream));
+    if (accept_prob_out)
+        CK(ctx, cudaMemcpyAsync(accept_prob_out, ctx->d_alpha, C * 8, cudaMemcpyDefault, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
     return MT_OK;
 }
 

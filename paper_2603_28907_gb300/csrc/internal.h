@@ -124,23 +124,29 @@ cudaError_t launch_grad_finish_sel(const Prob &pb, int mode, HRef h, const doubl
                                    cudaStream_t st);
 cudaError_t launch_scatter_sel(int n_chains, long long n, const double *src, const uint8_t *cur,
                                double *G, cudaStream_t st);
+// The gradient samplers take the step size eps, or per chain eps_c[c] when
+// eps_c is not null (step-size adaptation).
 cudaError_t launch_propose_mala(const Prob &pb, int mode, void *hbuf, long long buf_stride,
                                 const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                                uint64_t seed, const int64_t *step_base, int step_off,
-                                cudaStream_t st);
+                                const double *eps_c, uint64_t seed, const int64_t *step_base,
+                                int step_off, cudaStream_t st);
 cudaError_t launch_hmc_start(const Prob &pb, int mode, void *hbuf, long long buf_stride,
                              const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                             double *pbuf, double *qbuf, double *k0, uint64_t seed,
-                             const int64_t *step_base, int step_off, cudaStream_t st);
+                             const double *eps_c, double *pbuf, double *qbuf, double *k0,
+                             uint64_t seed, const int64_t *step_base, int step_off, cudaStream_t st);
 cudaError_t launch_hmc_kick_drift(const Prob &pb, int mode, void *hbuf, long long buf_stride,
                                   const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                                  double *pbuf, double *qbuf, cudaStream_t st);
+                                  const double *eps_c, double *pbuf, double *qbuf, cudaStream_t st);
 cudaError_t launch_hmc_finish(const Prob &pb, long long buf_stride, const double *gbuf,
-                              const uint8_t *cur, int n_chains, double eps, double *pbuf,
-                              const double *k0, double *extra, cudaStream_t st);
+                              const uint8_t *cur, int n_chains, double eps, const double *eps_c,
+                              double *pbuf, const double *k0, double *extra, cudaStream_t st);
 cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, long long buf_stride,
                                  const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                                 double *extra, cudaStream_t st);
+                                 const double *eps_c, double *extra, cudaStream_t st);
+// Dual-averaging step-size adaptation (mcmc.cu): state da [C][4], step sizes eps [C]
+cudaError_t launch_adapt_init(int n_chains, double eps0, double *da, double *eps, cudaStream_t st);
+cudaError_t launch_adapt(int n_chains, double target, int n_adapt, const double *alpha, double *da,
+                         double *eps, cudaStream_t st);
 cudaError_t launch_gather(int mode, HRef h, int n_chains, long long n_per_chain, void *out,
                           cudaStream_t st);
 cudaError_t launch_nested_rhat(int mode, const void *draws, int N, int C, int P, int K, double *sm,

@@ -177,9 +177,10 @@ cudaError_t launch_propose_rw(const Prob &pb, int mode, void *hbuf, long long bu
 template <typename H>
 __global__ void __launch_bounds__(256)
 k_propose_mala(int n, H *hbuf, long long buf_stride, const double *gbuf, const uint8_t *cur,
-               double eps, uint64_t seed, const int64_t *step_base, int step_off)
+               double eps0, const double *eps_c, uint64_t seed, const int64_t *step_base, int step_off)
 {
     const int c = blockIdx.y;
+    const double eps = eps_c ? eps_c[c] : eps0;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (2 * j >= n) return;
     const uint32_t step = (uint32_t)(*step_base + step_off);
@@ -200,17 +201,17 @@ k_propose_mala(int n, H *hbuf, long long buf_stride, const double *gbuf, const u
 
 cudaError_t launch_propose_mala(const Prob &pb, int mode, void *hbuf, long long buf_stride,
                                 const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                                uint64_t seed, const int64_t *step_base, int step_off,
-                                cudaStream_t st)
+                                const double *eps_c, uint64_t seed, const int64_t *step_base,
+                                int step_off, cudaStream_t st)
 {
     const int n = pb.L * pb.N;
     dim3 grid((n / 2 + 1 + 255) / 256, n_chains);
     if (mode == MODE_F64)
         k_propose_mala<double><<<grid, 256, 0, st>>>(n, (double *)hbuf, buf_stride, gbuf, cur, eps,
-                                                     seed, step_base, step_off);
+                                                     eps_c, seed, step_base, step_off);
     else
         k_propose_mala<float><<<grid, 256, 0, st>>>(n, (float *)hbuf, buf_stride, gbuf, cur, eps,
-                                                    seed, step_base, step_off);
+                                                    eps_c, seed, step_base, step_off);
     return cudaGetLastError();
 }
 
@@ -219,9 +220,10 @@ cudaError_t launch_propose_mala(const Prob &pb, int mode, void *hbuf, long long 
 template <typename H>
 __global__ void __launch_bounds__(256)
 k_mala_hastings(int n, const H *hbuf, long long buf_stride, const double *gbuf, const uint8_t *cur,
-                double eps, double *extra)
+                double eps0, const double *eps_c, double *extra)
 {
     const int c = blockIdx.x;
+    const double eps = eps_c ? eps_c[c] : eps0;
     const int cs = cur[c];
     const long long a = (long long)cs * buf_stride + (long long)c * n;       // current
     const long long b = (long long)(1 - cs) * buf_stride + (long long)c * n; // proposal
@@ -242,15 +244,15 @@ k_mala_hastings(int n, const H *hbuf, long long buf_stride, const double *gbuf, 
 
 cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, long long buf_stride,
                                  const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                                 double *extra, cudaStream_t st)
+                                 const double *eps_c, double *extra, cudaStream_t st)
 {
     const int n = pb.L * pb.N;
     if (mode == MODE_F64)
         k_mala_hastings<double><<<n_chains, 256, 0, st>>>(n, (const double *)hbuf, buf_stride, gbuf,
-                                                          cur, eps, extra);
+                                                          cur, eps, eps_c, extra);
     else
         k_mala_hastings<float><<<n_chains, 256, 0, st>>>(n, (const float *)hbuf, buf_stride, gbuf,
-                                                         cur, eps, extra);
+                                                         cur, eps, eps_c, extra);
     return cudaGetLastError();
 }
 
@@ -266,10 +268,12 @@ cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, lon
 // K(p0) - K(p), K = |p|^2 / 2.
 template <typename H>
 __global__ void __launch_bounds__(256)
-k_hmc_start(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur, double eps,
-            double *pbuf, double *qbuf, double *k0, uint64_t seed, const int64_t *step_base, int step_off)
+k_hmc_start(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur, double eps0,
+            const double *eps_c, double *pbuf, double *qbuf, double *k0, uint64_t seed,
+            const int64_t *step_base, int step_off)
 {
     const int c = blockIdx.x;
+    const double eps = eps_c ? eps_c[c] : eps0;
     const uint32_t step = (uint32_t)(*step_base + step_off);
     const int cs = cur[c];
     const long long a = (long long)cs * bs + (long long)c * n;
@@ -300,12 +304,13 @@ k_hmc_start(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur
 
 template <typename H>
 __global__ void __launch_bounds__(256)
-k_hmc_kick_drift(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur, double eps,
-                 double *pbuf, double *qbuf)
+k_hmc_kick_drift(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur, double eps0,
+                 const double *eps_c, double *pbuf, double *qbuf)
 {
     const int c = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double eps = eps_c ? eps_c[c] : eps0;
     const long long b = (long long)(1 - cur[c]) * bs + (long long)c * n;
     const size_t k = (size_t)c * n + i;
     const double p = pbuf[k] + eps * gbuf[b + i];
@@ -316,10 +321,11 @@ k_hmc_kick_drift(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t
 }
 
 __global__ void __launch_bounds__(256)
-k_hmc_finish(int n, long long bs, const double *gbuf, const uint8_t *cur, double eps,
-             const double *pbuf, const double *k0, double *extra)
+k_hmc_finish(int n, long long bs, const double *gbuf, const uint8_t *cur, double eps0,
+             const double *eps_c, const double *pbuf, const double *k0, double *extra)
 {
     const int c = blockIdx.x;
+    const double eps = eps_c ? eps_c[c] : eps0;
     const long long b = (long long)(1 - cur[c]) * bs + (long long)c * n;
     double kin = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -332,39 +338,40 @@ k_hmc_finish(int n, long long bs, const double *gbuf, const uint8_t *cur, double
 
 cudaError_t launch_hmc_start(const Prob &pb, int mode, void *hbuf, long long buf_stride,
                              const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                             double *pbuf, double *qbuf, double *k0, uint64_t seed,
-                             const int64_t *step_base, int step_off, cudaStream_t st)
+                             const double *eps_c, double *pbuf, double *qbuf, double *k0,
+                             uint64_t seed, const int64_t *step_base, int step_off, cudaStream_t st)
 {
     const int n = pb.L * pb.N;
     if (mode == MODE_F64)
-        k_hmc_start<double><<<n_chains, 256, 0, st>>>(n, (double *)hbuf, buf_stride, gbuf, cur, eps, pbuf,
-                                                      qbuf, k0, seed, step_base, step_off);
+        k_hmc_start<double><<<n_chains, 256, 0, st>>>(n, (double *)hbuf, buf_stride, gbuf, cur, eps, eps_c,
+                                                      pbuf, qbuf, k0, seed, step_base, step_off);
     else
-        k_hmc_start<float><<<n_chains, 256, 0, st>>>(n, (float *)hbuf, buf_stride, gbuf, cur, eps, pbuf,
-                                                     qbuf, k0, seed, step_base, step_off);
+        k_hmc_start<float><<<n_chains, 256, 0, st>>>(n, (float *)hbuf, buf_stride, gbuf, cur, eps, eps_c,
+                                                     pbuf, qbuf, k0, seed, step_base, step_off);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hmc_kick_drift(const Prob &pb, int mode, void *hbuf, long long buf_stride,
                                   const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                                  double *pbuf, double *qbuf, cudaStream_t st)
+                                  const double *eps_c, double *pbuf, double *qbuf, cudaStream_t st)
 {
     const int n = pb.L * pb.N;
     dim3 grid((n + 255) / 256, n_chains);
     if (mode == MODE_F64)
         k_hmc_kick_drift<double><<<grid, 256, 0, st>>>(n, (double *)hbuf, buf_stride, gbuf, cur, eps,
-                                                       pbuf, qbuf);
+                                                       eps_c, pbuf, qbuf);
     else
         k_hmc_kick_drift<float><<<grid, 256, 0, st>>>(n, (float *)hbuf, buf_stride, gbuf, cur, eps,
-                                                      pbuf, qbuf);
+                                                      eps_c, pbuf, qbuf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hmc_finish(const Prob &pb, long long buf_stride, const double *gbuf,
-                              const uint8_t *cur, int n_chains, double eps, double *pbuf,
-                              const double *k0, double *extra, cudaStream_t st)
+                              const uint8_t *cur, int n_chains, double eps, const double *eps_c,
+                              double *pbuf, const double *k0, double *extra, cudaStream_t st)
 {
-    k_hmc_finish<<<n_chains, 256, 0, st>>>(pb.L * pb.N, buf_stride, gbuf, cur, eps, pbuf, k0, extra);
+    k_hmc_finish<<<n_chains, 256, 0, st>>>(pb.L * pb.N, buf_stride, gbuf, cur, eps, eps_c, pbuf, k0,
+                                           extra);
     return cudaGetLastError();
 }
 
@@ -407,7 +414,7 @@ __global__ void k_accept(int n_chains, int mode, const void *partial, int n_blk,
                          const double *lp_prop, const double *extra, double *ll, double *lp,
                          double *ll_prop_out, uint8_t *cur, uint8_t *prop_sel, int64_t *accepts,
                          int32_t *acc_last, double *logu_out, uint64_t seed,
-                         const int64_t *step_base, int step_off)
+                         const int64_t *step_base, int step_off, double *alpha_out)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_chains) return;
@@ -419,6 +426,9 @@ __global__ void k_accept(int n_chains, int mode, const void *partial, int n_blk,
     double delta = (lln + lpn) - (ll[c] + lp[c]);
     if (extra) delta += extra[c];
     const int acc = (lpn > -INFINITY) && (logu < delta);
+    // acceptance probability min(1, e^delta) of the proposal (0 where it is
+    // outside the prior's support or delta is not a number)
+    if (alpha_out) alpha_out[c] = (lpn > -INFINITY && delta == delta) ? (delta >= 0.0 ? 1.0 : exp(delta)) : 0.0;
     const uint8_t cs = cur[c];
     prop_sel[c] = (uint8_t)(1 - cs);
     if (acc) {
@@ -437,13 +447,13 @@ cudaError_t launch_accept_fused(const Prob &pb, int mode, int n_chains, const vo
                                 double *lp, double *ll_prop_out, uint8_t *cur, uint8_t *prop_sel,
                                 int64_t *accepts, int32_t *acc_last, double *logu_out,
                                 uint64_t seed, const int64_t *step_base, int step_off,
-                                cudaStream_t st)
+                                cudaStream_t st, double *alpha_out)
 {
     const int n_blk = (pb.n_rays + march_rays_per_block(pb) - 1) / march_rays_per_block(pb);
     k_accept<<<(n_chains + 127) / 128, 128, 0, st>>>(n_chains, mode, partial, n_blk, pb.sumK,
                                                      lp_prop, extra, ll, lp, ll_prop_out, cur,
                                                      prop_sel, accepts, acc_last, logu_out, seed,
-                                                     step_base, step_off);
+                                                     step_base, step_off, alpha_out);
     return cudaGetLastError();
 }
 
@@ -455,6 +465,61 @@ __global__ void k_advance(int64_t *step, int n)
 cudaError_t launch_advance(int64_t *step, int n, cudaStream_t st)
 {
     k_advance<<<1, 32, 0, st>>>(step, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- step-size adaptation
+// Per-chain dual averaging of log eps toward a target acceptance probability
+// delta (Sec. 3.1: the step size is tuned in the warm-up toward 0.8; the
+// scheme is Hoffman & Gelman's, J. Mach. Learn. Res. 15 (2014), Sec. 3.2.1,
+// with gamma = 0.05, t0 = 10, kappa = 0.75 and mu = log(10 eps0)).  After the
+// m-th adapted step with acceptance probability alpha_m:
+//   Hbar_m = (1 - 1/(m + t0)) Hbar_{m-1} + (delta - alpha_m) / (m + t0)
+//   log eps_m = mu - sqrt(m) / gamma * Hbar_m
+//   log epsbar_m = m^-kappa log eps_m + (1 - m^-kappa) log epsbar_{m-1}
+// (Hbar_0 = 0, log epsbar_0 = 0); the next step runs with eps_m, and after
+// the last adapted step every chain keeps epsbar.  State per chain:
+// da[4c..4c+3] = {log epsbar, Hbar, mu, m}.
+__global__ void k_adapt_init(int n_chains, double eps0, double *da, double *eps)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chains) return;
+    eps[c] = eps0;
+    da[4 * c + 0] = 0.0;
+    da[4 * c + 1] = 0.0;
+    da[4 * c + 2] = log(10.0 * eps0);
+    da[4 * c + 3] = 0.0;
+}
+
+__global__ void k_adapt(int n_chains, double target, int n_adapt, const double *alpha, double *da,
+                        double *eps)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chains) return;
+    const double m = da[4 * c + 3] + 1.0;
+    if (m > (double)n_adapt) return;  // adaptation over: eps stays at epsbar
+    const double t0 = 10.0, gamma = 0.05, kappa = 0.75;
+    const double w = 1.0 / (m + t0);
+    const double hbar = (1.0 - w) * da[4 * c + 1] + w * (target - alpha[c]);
+    const double log_eps = da[4 * c + 2] - sqrt(m) / gamma * hbar;
+    const double eta = pow(m, -kappa);
+    const double log_bar = eta * log_eps + (1.0 - eta) * da[4 * c + 0];
+    da[4 * c + 0] = log_bar;
+    da[4 * c + 1] = hbar;
+    da[4 * c + 3] = m;
+    eps[c] = exp(m < (double)n_adapt ? log_eps : log_bar);
+}
+
+cudaError_t launch_adapt_init(int n_chains, double eps0, double *da, double *eps, cudaStream_t st)
+{
+    k_adapt_init<<<(n_chains + 127) / 128, 128, 0, st>>>(n_chains, eps0, da, eps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adapt(int n_chains, double target, int n_adapt, const double *alpha, double *da,
+                         double *eps, cudaStream_t st)
+{
+    k_adapt<<<(n_chains + 127) / 128, 128, 0, st>>>(n_chains, target, n_adapt, alpha, da, eps);
     return cudaGetLastError();
 }
 

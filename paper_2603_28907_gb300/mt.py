@@ -87,6 +87,8 @@ SIGNATURES = {
     "mt_get_sizes": [_vp, _ip, _ip, _ip, _ip, _ip, _ip],
     "mt_set_prior": [_vp, C.c_int],
     "mt_set_hmc": [_vp, C.c_int],
+    "mt_set_adapt": [_vp, C.c_double, C.c_int],
+    "mt_get_adapt": [_vp, _vp, _vp],
     "mt_set_forward": [_vp, C.c_int, C.c_int, _vp],
     "mt_copula_heights": [_vp, C.c_int, _vp, _vp],
     "mt_nested_rhat": [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, _dp],
@@ -266,6 +268,12 @@ class Context:
 
     def set_hmc(self, n_leapfrog):
         self._ck("mt_set_hmc", self.lib.mt_set_hmc(self.h, int(n_leapfrog)))
+
+    def set_adapt(self, target_accept, n_adapt):
+        self._ck("mt_set_adapt", self.lib.mt_set_adapt(self.h, float(target_accept), int(n_adapt)))
+
+    def get_adapt(self, eps_out=None, accept_prob_out=None):
+        self._ck("mt_get_adapt", self.lib.mt_get_adapt(self.h, _ptr(eps_out), _ptr(accept_prob_out)))
 
     def set_prior(self, kind):
         self._ck("mt_set_prior", self.lib.mt_set_prior(self.h, int(kind)))
