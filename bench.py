@@ -451,15 +451,25 @@ def run_gradient_study(args, local):
     # 3. MALA and HMC vs random walk on 1024 chains: ESS per second of the mean height of each surface
     C = 1024
     H0 = torch.tensor(np.stack([W.geometry(w, [w.seed_init, c]) for c in range(C)]).astype(np.float32), device=dev)
-    runs = {"rw_sigma_0.002": (mt.KERNEL_RW, 0.002, 200), "mala_eps_0.5": (mt.KERNEL_MALA, 0.5, 200),
-            "mala_eps_0.005": (mt.KERNEL_MALA, 0.005, 200),
-            "hmc_eps_0.003_leapfrog_8": (mt.KERNEL_HMC, 0.003, 100)}
+    # name: (kernel, step, measured steps, adapted warm-up steps toward a target acceptance)
+    runs = {"rw_sigma_0.002": (mt.KERNEL_RW, 0.002, 200, 0), "mala_eps_0.5": (mt.KERNEL_MALA, 0.5, 200, 0),
+            "mala_eps_0.005": (mt.KERNEL_MALA, 0.005, 200, 0),
+            "hmc_eps_0.003_leapfrog_8": (mt.KERNEL_HMC, 0.003, 100, 0),
+            "hmc_adapted_to_0.8_leapfrog_8": (mt.KERNEL_HMC, 0.003, 60, 30)}
     cur = torch.zeros_like(H0)
     c32.set_hmc(8)
-    for name, (kern, step, n_steps) in runs.items():
+    for name, (kern, step, n_steps, n_adapt) in runs.items():
+        c32.set_adapt(0.8, n_adapt)
         c32.init_chains(H0, w.seed_mcmc)
-        c32.run(kern, step, 1, 1)   # build the graph / initial gradients outside the timing
+        c32.run(kern, step, 1, max(1, n_adapt))   # graph, initial gradients, warm-up: untimed
         c32.sync(600.0)
+        acc0 = torch.zeros(C, dtype=torch.int64, device=dev)
+        c32.get_state(accepts_out=acc0)
+        eps_c = None
+        if n_adapt:
+            e = torch.zeros(C, dtype=torch.float64, device=dev)
+            c32.get_adapt(e)
+            eps_c = np.percentile(e.cpu().numpy(), [0, 50, 100]).tolist()
         trace = np.zeros((n_steps, C, w.L))
         t_gpu = 0.0
         for k in range(n_steps):
@@ -476,9 +486,12 @@ def run_gradient_study(args, local):
         c32.get_state(accepts_out=acc)
         burn = n_steps // 2
         ess = np.array([[_ess(trace[burn:, c, l]) for l in range(w.L)] for c in range(C)])
-        out[name] = dict(acceptance=float(acc.double().mean().item()) / (n_steps + 1),
+        out[name] = dict(acceptance=float((acc - acc0).double().mean().item()) / n_steps,
                          step_ms=t_gpu / n_steps * 1e3, ess_per_chain_mean=float(ess.mean()),
                          ess_per_s_total=float(ess.sum(0).mean() / (t_gpu * (n_steps - burn) / n_steps)))
+        if eps_c is not None:
+            out[name].update(adapted_steps=n_adapt, eps_min_median_max=eps_c)
+    c32.set_adapt(0.8, 0)
     print(json.dumps({"study": "gradient", "workload": w.name, **out}), flush=True)
 
 

@@ -177,7 +177,7 @@ MT_API mt_status mt_ray_terms(mt_ctx *ctx, int n_chains, const void *heights, do
  * (differentiable forward model, Sec. 2.1.4; the hand-written adjoint of the
  * ray march plus -tau Q (h - mu) from the prior): grad_out host or device
  * double [n_chains][L][R][Q]; logpost_out (nullable) double [n_chains].
- * FP32 march arithmetic with 64-bit fixed-point (2^-32) accumulation, so the
+ * FP32 march arithmetic with 64-bit fixed-point (2^-24) accumulation, so the
  * result is reproducible bit for bit.  Needs gamma > 0 and an FP32 precision
  * mode (MT_EINVAL otherwise); heights as for mt_logpost. */
 MT_API mt_status mt_grad(mt_ctx *ctx, int n_chains, const void *heights, double *grad_out,

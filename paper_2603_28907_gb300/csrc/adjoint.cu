@@ -14,21 +14,25 @@
 // (so O_p equals the FP32 forward kernel's bit for bit), pass 2 recomputes the
 // samples and scatters.  A lane sums its contributions per cell in FP32
 // registers (in sample order) and adds each cell's sums to 64-bit fixed-point
-// accumulators (units of 2^-32) with integer atomics, so the gradient does not
+// accumulators (units of 2^-24) with integer atomics, so the gradient does not
 // depend on the order in which threads add and is reproducible bit for bit; a
-// sum that rounds to zero at that resolution is not added.  Pass 2 visits only
-// the samples within log2|coef_l| + 10 log2 units of surface l (coef_l: the
-// sample weight in fixed-point units; a warp uses its largest); every sample
-// outside has varsigma' <= 2^-(that), so all of them together move a cell's
-// sum by less than G * 2^-10 fixed-point units.
+// sum that rounds to zero at that resolution is not added.  The unit is at or
+// below the FP32 rounding of any cell sum of magnitude >= 1 (and of the SFU
+// approximations' ~1e-7 relative error in each term).  Pass 2 visits only the
+// samples within log2|coef_l| + 4 log2 units of surface l (coef_l: the sample
+// weight in fixed-point units; a warp uses its largest); every sample outside
+// has varsigma' <= 2^-(that) and adds less than 2^-4 units; varsigma' falls
+// off geometrically along the ray, so all of them together add less than
+// 2^-4 / (1 - 2^-s) units per cell and side (s: the ray's vertical step per
+// sample in log2 units), and never more than G 2^-4.
 #include <math.h>
 
 #include "march.cuh"
 
 namespace mt {
 
-constexpr float kFix = 4294967296.0f;  // 2^32
-constexpr double kInvFix = 1.0 / 4294967296.0;
+constexpr float kFix = 16777216.0f;  // 2^24
+constexpr double kInvFix = 1.0 / 16777216.0;
 
 // Add round(v) (to nearest, ties to even) to a fixed-point accumulator, with
 // FP32 and integer operations only (a 64-bit float -> integer conversion runs
@@ -144,9 +148,23 @@ __device__ __forceinline__ unsigned long long forward_surface(const Prob &pb, co
     return t;
 }
 
+// The four corner sums of a cell into the fixed-point accumulators.
+__device__ __forceinline__ void flush_cell(unsigned long long *al, int cell, int Q, float c00, float c01,
+                                           float c10, float c11)
+{
+    add_fixed(al + cell, c00);
+    add_fixed(al + cell + 1, c01);
+    add_fixed(al + cell + Q, c10);
+    add_fixed(al + cell + Q + 1, c11);
+}
+
 // Pass 2 for surface l over samples [lo, he): scatter coef * varsigma' * w_n
-// into acc[l][node]; sums are kept per cell in registers and added to the
-// fixed-point accumulators when the sample leaves the cell.
+// into acc[l][node].  Sums are kept per cell in registers; when a sample
+// leaves its cell the cell's sums move to a pending slot, and the pending
+// slots of all the warp's lanes are added to the fixed-point accumulators
+// together, only when some lane needs its slot again (so the atomics run
+// with most lanes active instead of one lane at every cell change; integer
+// adds commute, so the result does not depend on when they happen).
 template <int L>
 __device__ __forceinline__ void scatter_surface(const Prob &pb, const float *sh, int l, float4 o,
                                                 float4 st, float zh, float zl, int lo, int he,
@@ -158,21 +176,28 @@ __device__ __forceinline__ void scatter_surface(const Prob &pb, const float *sh,
     unsigned long long *al = acc + (size_t)l * pb.N;
     float h00 = 0.f, d0 = 0.f, h10 = 0.f, d1 = 0.f;
     float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
-    int cur = -1;
+    float p00 = 0.f, p01 = 0.f, p10 = 0.f, p11 = 0.f;
+    int cur = -1, pend = -1;  // current cell; cell of the pending sums (-1: none)
     float kf = (float)lo;
     for (int k = lo; k < he; ++k, kf += 1.0f) {
         const float gx = fmaf(kf, st.x, o.x), gy = fmaf(kf, st.y, o.y);
         const float tx = gx + M, ty = gy + M;
         const float fx = (gx - (tx - M)) + 0.5f, fy = (gy - (ty - M)) + 0.5f;
         const int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
-        if (node != cur) {
-            if (cur >= 0) {
-                add_fixed(al + cur, c00);
-                add_fixed(al + cur + 1, c01);
-                add_fixed(al + cur + Q, c10);
-                add_fixed(al + cur + Q + 1, c11);
-                c00 = c01 = c10 = c11 = 0.f;
+        const bool chg = node != cur;
+        if (__any_sync(__activemask(), chg && pend >= 0)) {
+            if (pend >= 0) {
+                flush_cell(al, pend, Q, p00, p01, p10, p11);
+                pend = -1;
             }
+        }
+        if (chg) {
+            pend = cur;
+            p00 = c00;
+            p01 = c01;
+            p10 = c10;
+            p11 = c11;
+            c00 = c01 = c10 = c11 = 0.f;
             cur = node;
             cell_corners<L>(sh, node, Q, l, h00, d0, h10, d1);
         }
@@ -190,12 +215,8 @@ __device__ __forceinline__ void scatter_surface(const Prob &pb, const float *sh,
         c10 = fmaf(-fx, vy, c10 + vy);          // v (1 - fx) fy
         c11 = fmaf(fx, vy, c11);                // v fx fy
     }
-    if (cur >= 0) {
-        add_fixed(al + cur, c00);
-        add_fixed(al + cur + 1, c01);
-        add_fixed(al + cur + Q, c10);
-        add_fixed(al + cur + Q + 1, c11);
-    }
+    if (pend >= 0) flush_cell(al, pend, Q, p00, p01, p10, p11);
+    if (cur >= 0) flush_cell(al, cur, Q, c00, c01, c10, c11);
 }
 
 // One CTA = one chain x one block of ray slots (slot i -> ray perm[i]).  SMEM:
@@ -271,11 +292,11 @@ k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long lo
 #pragma unroll 1
         for (int l = 0; l < L; ++l) {
             const float coef = base * pb.drho_f[l];
-            // samples beyond log2|coef| + 10 log2 units from the surface add
-            // less than 2^-10 fixed-point units each; the warp takes its
+            // samples beyond log2|coef| + 4 log2 units from the surface add
+            // less than 2^-4 fixed-point units each; the warp takes its
             // largest such width (its rays have near-equal windows) so that
             // its lanes run loops of equal length
-            float ka = fmaxf(log2f(fabsf(coef) + 1e-30f) + 10.0f, 1.0f);
+            float ka = fmaxf(log2f(fabsf(coef) + 1e-30f) + 4.0f, 1.0f);
             ka = __int_as_float(__reduce_max_sync(__activemask(), __float_as_int(ka)));
             const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
             const float zl = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
@@ -343,7 +364,7 @@ cudaError_t launch_adjoint(const Prob &pb, HRef h, int n_chains, double *partial
     }
 }
 
-// grad[c][i] = gacc * 2^-32 - tau (Q (h - mu))_i, and logpost = ll + lp.
+// grad[c][i] = gacc * 2^-24 - tau (Q (h - mu))_i, and logpost = ll + lp.
 template <typename H>
 __global__ void k_grad_finish(Prob pb, HRef h, const double *mu, const unsigned long long *gacc,
                               double *grad)

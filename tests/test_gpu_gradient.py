@@ -1,7 +1,7 @@
 """Adjoint gradient, autograd wrapper and MALA against the FP64 oracle.
 
 Tolerances: the GPU gradient is FP32 march arithmetic accumulated in 64-bit
-fixed point (2^-32) and FP64; it must match the oracle's analytic FP64 gradient
+fixed point (2^-24) and FP64; it must match the oracle's analytic FP64 gradient
 (itself pinned by central differences) within 1e-3 of the largest component,
 and be bit-identical from call to call.
 """
