@@ -9,16 +9,16 @@
 // from every sample k, with varsigma' = varsigma (1 - varsigma) / gamma and
 // w_n the bilinear weight of the node.  The log-prior adds -tau Q (h_l - mu_l).
 //
-// Each ray is marched twice by its thread, one surface at a time: pass 1
-// gives O_p with the forward kernel's arithmetic and exact saturation windows
-// (so O_p equals the FP32 forward kernel's bit for bit), pass 2 recomputes the
-// samples and scatters.  A lane sums its contributions per cell in FP32
-// registers (in sample order) and adds each cell's sums to 64-bit fixed-point
+// The forward kernel (an FP32-mode march of the same heights) writes each
+// ray's d ll / d O_p; this kernel then marches every ray once more, one
+// surface at a time, over the samples near the surface, and scatters.  A
+// lane sums its contributions per cell in FP32 registers (in sample order)
+// and adds each cell's sums to 64-bit fixed-point
 // accumulators (units of 2^-24) with integer atomics, so the gradient does not
 // depend on the order in which threads add and is reproducible bit for bit; a
 // sum that rounds to zero at that resolution is not added.  The unit is at or
 // below the FP32 rounding of any cell sum of magnitude >= 1 (and of the SFU
-// approximations' ~1e-7 relative error in each term).  Pass 2 visits only the
+// approximations' ~1e-7 relative error in each term).  The scatter visits only the
 // samples within log2|coef_l| + 4 log2 units of surface l (coef_l: the sample
 // weight in fixed-point units; a warp uses its largest); every sample outside
 // has varsigma' <= 2^-(that) and adds less than 2^-4 units; varsigma' falls
@@ -111,43 +111,6 @@ __device__ __forceinline__ void node_extent(const float *sh, int N, float *ext)
     }
 }
 
-// Pass 1 for surface l over samples [lo, he): the exact integer indicator sum
-// (units 2^-23) with the forward kernel's per-sample arithmetic.
-template <int L>
-__device__ __forceinline__ unsigned long long forward_surface(const Prob &pb, const float *sh, int l,
-                                                              float4 o, float4 st, float zh, float zl,
-                                                              int lo, int he)
-{
-    const float M = 12582912.0f;
-    const float nkg = -pb.kg;
-    const int Q = pb.Q;
-    float h00 = 0.f, d0 = 0.f, h10 = 0.f, d1 = 0.f;
-    int cur = -1;
-    float kf = (float)lo;
-    unsigned long long t = 0ull;
-    for (int k0 = lo; k0 < he; k0 += 256) {
-        const int kn = min(256, he - k0);
-        uint32_t acc = 0u;
-        for (int k = 0; k < kn; ++k, kf += 1.0f) {
-            const float gx = fmaf(kf, st.x, o.x), gy = fmaf(kf, st.y, o.y);
-            const float tx = gx + M, ty = gy + M;
-            const float fx = (gx - (tx - M)) + 0.5f, fy = (gy - (ty - M)) + 0.5f;
-            const int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
-            if (node != cur) {
-                cur = node;
-                cell_corners<L>(sh, node, Q, l, h00, d0, h10, d1);
-            }
-            const float a = fmaf(fx, d0, h00), b = fmaf(fx, d1, h10);
-            const float sl = fmaf(fy, fmaf(a, -1.0f, b), a);
-            const float zlv = fmaf(kf, st.w, fmaf(kf, st.z, zh) + zl);
-            const float arg = fmaf(nkg, sl, zlv);
-            acc += __float_as_uint(rcp_approx(1.0f + ex2_approx(arg)) + 1.0f);
-        }
-        t += (unsigned long long)(acc - (uint32_t)kn * 0x3F800000u);
-    }
-    return t;
-}
-
 // The four corner sums of a cell into the fixed-point accumulators.
 __device__ __forceinline__ void flush_cell(unsigned long long *al, int cell, int Q, float c00, float c01,
                                            float c10, float c11)
@@ -158,7 +121,7 @@ __device__ __forceinline__ void flush_cell(unsigned long long *al, int cell, int
     add_fixed(al + cell + Q + 1, c11);
 }
 
-// Pass 2 for surface l over samples [lo, he): scatter coef * varsigma' * w_n
+// Surface l over samples [lo, he): scatter coef * varsigma' * w_n
 // into acc[l][node].  Sums are kept per cell in registers; when a sample
 // leaves its cell the cell's sums move to a pending slot, and the pending
 // slots of all the warp's lanes are added to the fixed-point accumulators
@@ -226,7 +189,7 @@ constexpr int kAdjThreads = 1024;  // one CTA per SM with the scenario's 192 KB 
 
 template <int L, bool SMEM>
 __global__ void __launch_bounds__(kAdjThreads)
-k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long long *gacc)
+k_adjoint(Prob pb, HRef h, int rays_per_block, unsigned long long *gacc)
 {
     using NL = NodeLayout<float, L>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -244,50 +207,14 @@ k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long lo
     node_extent<L>(sh, N, ext);
     __syncthreads();
     unsigned long long *acc = SMEM ? acc_s : gc;
-    const uint32_t q_one = __float_as_uint(rcp_approx(1.0f) + 1.0f) - 0x3F800000u;
 
     const int r_begin = blockIdx.x * rays_per_block;
     const int r_end = min(r_begin + rays_per_block, pb.n_rays);
-    FF accf = {0.f, 0.f};
     for (int slot = r_begin + threadIdx.x; slot < r_end; slot += blockDim.x) {
         const int ray = pb.perm ? pb.perm[slot] : slot;
         const float4 o = pb.o4[ray], st = pb.s4[ray];
         const float rdz = rcp_approx(st.z);
-        // O and y = a - O / Lambda in float-float, the Poisson term as in the
-        // forward kernel's FP32 modes (so the two give the same partials)
-        FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
-#pragma unroll 1
-        for (int l = 0; l < L; ++l) {
-            const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
-            const float zl = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
-            int lo = 0, hi = pb.G - 1;
-            if (!pb.full_windows) transition_window(zh, st.z, rdz, pb.kg, ext[l], ext[L + l], pb.G, lo, hi);
-            lo = min(lo, pb.G);
-            const int he = max(hi + 1, lo);
-            const unsigned long long tl =
-                (unsigned long long)lo * q_one + forward_surface<L>(pb, sh, l, o, st, zh, zl, lo, he);
-            const FF nl = ff_two_sum((float)(uint32_t)(tl >> 20) * 1048576.0f * 0x1p-23f,
-                                     (float)(uint32_t)(tl & 0xFFFFFu) * 0x1p-23f);
-            Sff = ff_add(Sff, ff_mul(FF{pb.drho_ff[l].x, pb.drho_ff[l].y}, nl));
-        }
-        const FF Off = ff_mul(FF{pb.dt_ff[ray].x, pb.dt_ff[ray].y}, Sff);
-        const FF OL = ff_mul(Off, FF{pb.invL_ff.x, pb.invL_ff.y});
-        const int Cp = pb.cnt[ray];
-        const float invL = pb.invL_ff.x;
-        float dO;  // d ll / d O_p = (lambda - C) / Lambda
-        FF tf;
-        if (Cp > 0) {
-            const FF yff = ff_add(FF{pb.a_ff[ray].x, pb.a_ff[ray].y}, FF{-OL.hi, -OL.lo});
-            const float y = yff.hi + yff.lo, g = g_f32(y), cf = (float)Cp;
-            const float cg = cf * g;
-            tf = FF{-cg, -fmaf(cf, g, -cg)};
-            dO = cf * expm1f(y) * invL;          // lambda - C = C (e^y - 1)
-        } else {
-            const float lam = (float)pb.I0 * expf(-(OL.hi + OL.lo));
-            tf = FF{-lam, 0.f};
-            dO = lam * invL;
-        }
-        accf = ff_add(accf, tf);
+        const float dO = pb.dO[(size_t)c * pb.n_rays + ray];  // d ll / d O_p from the march
         const float base = dO * pb.dt_ff[ray].x * (float)(1.0 / pb.gamma) * kFix;
 #pragma unroll 1
         for (int l = 0; l < L; ++l) {
@@ -307,8 +234,6 @@ k_adjoint(Prob pb, HRef h, int rays_per_block, double *partial, unsigned long lo
             scatter_surface<L>(pb, sh, l, o, st, zh, zl, lo, he, coef, acc);
         }
     }
-    accf = block_sum(accf);
-    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = (double)accf.hi + (double)accf.lo;
     if constexpr (SMEM) {
         __syncthreads();
         for (int i = threadIdx.x; i < L * N; i += blockDim.x) {
@@ -327,14 +252,13 @@ size_t adjoint_smem_bytes(const Prob &pb, bool with_acc)
 }
 
 template <int L>
-static cudaError_t adj_l(const Prob &pb, HRef h, int n_chains, int rpb, double *partial,
-                         unsigned long long *gacc, cudaStream_t st)
+static cudaError_t adj_l(const Prob &pb, HRef h, int n_chains, int rpb, unsigned long long *gacc,
+                         cudaStream_t st)
 {
     const size_t with = adjoint_smem_bytes(pb, true);
     const bool smem_acc = with + MT_SMEM_STATIC <= MT_MAX_SMEM;
     const size_t bytes = smem_acc ? with : adjoint_smem_bytes(pb, false);
-    void (*fn)(Prob, HRef, int, double *, unsigned long long *) =
-        smem_acc ? k_adjoint<L, true> : k_adjoint<L, false>;
+    void (*fn)(Prob, HRef, int, unsigned long long *) = smem_acc ? k_adjoint<L, true> : k_adjoint<L, false>;
     static size_t set[2] = {0, 0};
     if (bytes > 48 * 1024 && bytes > set[smem_acc]) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -342,24 +266,24 @@ static cudaError_t adj_l(const Prob &pb, HRef h, int n_chains, int rpb, double *
         set[smem_acc] = bytes;
     }
     dim3 grid((pb.n_rays + rpb - 1) / rpb, n_chains);
-    fn<<<grid, kAdjThreads, bytes, st>>>(pb, h, rpb, partial, gacc);
+    fn<<<grid, kAdjThreads, bytes, st>>>(pb, h, rpb, gacc);
     return cudaGetLastError();
 }
 
-// gacc: [n_chains][L][N] zeroed by the caller; partial: [n_chains][blocks].
-cudaError_t launch_adjoint(const Prob &pb, HRef h, int n_chains, double *partial,
-                           unsigned long long *gacc, cudaStream_t st)
+// gacc: [n_chains][L][N] zeroed by the caller; pb.dO: [n_chains][n_rays].
+cudaError_t launch_adjoint(const Prob &pb, HRef h, int n_chains, unsigned long long *gacc, cudaStream_t st)
 {
+    if (!pb.dO) return cudaErrorInvalidValue;
     const int rpb = march_rays_per_block(pb);
     switch (pb.L) {
-        case 1: return adj_l<1>(pb, h, n_chains, rpb, partial, gacc, st);
-        case 2: return adj_l<2>(pb, h, n_chains, rpb, partial, gacc, st);
-        case 3: return adj_l<3>(pb, h, n_chains, rpb, partial, gacc, st);
-        case 4: return adj_l<4>(pb, h, n_chains, rpb, partial, gacc, st);
-        case 5: return adj_l<5>(pb, h, n_chains, rpb, partial, gacc, st);
-        case 6: return adj_l<6>(pb, h, n_chains, rpb, partial, gacc, st);
-        case 7: return adj_l<7>(pb, h, n_chains, rpb, partial, gacc, st);
-        case 8: return adj_l<8>(pb, h, n_chains, rpb, partial, gacc, st);
+        case 1: return adj_l<1>(pb, h, n_chains, rpb, gacc, st);
+        case 2: return adj_l<2>(pb, h, n_chains, rpb, gacc, st);
+        case 3: return adj_l<3>(pb, h, n_chains, rpb, gacc, st);
+        case 4: return adj_l<4>(pb, h, n_chains, rpb, gacc, st);
+        case 5: return adj_l<5>(pb, h, n_chains, rpb, gacc, st);
+        case 6: return adj_l<6>(pb, h, n_chains, rpb, gacc, st);
+        case 7: return adj_l<7>(pb, h, n_chains, rpb, gacc, st);
+        case 8: return adj_l<8>(pb, h, n_chains, rpb, gacc, st);
         default: return cudaErrorInvalidValue;
     }
 }

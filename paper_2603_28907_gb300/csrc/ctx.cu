@@ -113,6 +113,8 @@ struct mt_ctx {
     double *d_extra = nullptr;       // [C] Hastings terms
     void *d_gacc = nullptr;          // adjoint fixed-point accumulators
     size_t gacc_cap = 0;
+    void *d_dO = nullptr;            // per-ray d ll / d O_p of gradient evaluations
+    size_t dO_cap = 0;
     void *d_tmp = nullptr;           // small per-chain scratch
     size_t tmp_cap = 0;
     void *d_diag = nullptr;          // diagnostics scratch
@@ -323,6 +325,7 @@ static void refresh_prob(mt_ctx *ctx)
                               (float)(ctx->cfg.min_thick - (double)(float)ctx->cfg.min_thick));
     pb.perm = ctx->d_perm;
     pb.gnodes = nullptr;  // set per launch by ensure_nodes when the grid needs it
+    pb.dO = nullptr;      // set in the copies that gradient launches use
     pb.work = ctx->timing ? ctx->d_work : nullptr;
     pb.o4 = ctx->d_o4;
     pb.s4 = ctx->d_s4;
@@ -630,19 +633,39 @@ mt_status ctx_view(mt_ctx *ctx, CtxView *v)
 mt_status ctx_fail(mt_ctx *ctx, mt_status st, const char *msg) { return fail(ctx, st, "%s", msg); }
 }  // namespace mt
 
+// Buffers of a gradient evaluation of n chains: fixed-point accumulators and
+// the per-ray d ll / d O_p.
+static mt_status ensure_grad_bufs(mt_ctx *ctx, int n)
+{
+    const size_t np = n_per_chain(ctx);
+    void *old_g = ctx->d_gacc, *old_d = ctx->d_dO;
+    TRY(grow(ctx, &ctx->d_gacc, &ctx->gacc_cap, (size_t)n * np * 8));
+    TRY(grow(ctx, &ctx->d_dO, &ctx->dO_cap, (size_t)n * ctx->pb.n_rays * 4));
+    if (ctx->d_gacc != old_g || ctx->d_dO != old_d) drop_graph(ctx);
+    return MT_OK;
+}
+
+// Forward march (log-likelihood partials and each ray's d ll / d O_p) and the
+// adjoint's scatter into the zeroed accumulators, for n chains given by h.
+static mt_status enqueue_forward_adjoint(mt_ctx *ctx, HRef h, int n)
+{
+    Prob pg = ctx->pb;
+    pg.dO = (float *)ctx->d_dO;
+    pg.work = nullptr;
+    CK(ctx, cudaMemsetAsync(ctx->d_gacc, 0, (size_t)n * n_per_chain(ctx) * 8, ctx->stream));
+    CK(ctx, launch_march(pg, ctx->mode, h, n, ctx->d_part, nullptr, nullptr, ctx->stream));
+    CK(ctx, launch_adjoint(pg, h, n, (unsigned long long *)ctx->d_gacc, ctx->stream));
+    return MT_OK;
+}
+
 // Gradient of the log-posterior (and its value) of n chains given by h, into
 // device arrays grad [n][L][R][Q] and (nullable) ll / lp.  FP32 arithmetic.
 static mt_status eval_grad(mt_ctx *ctx, HRef h, int n, double *d_grad, double *d_ll, double *d_lp)
 {
-    const size_t np = n_per_chain(ctx);
-    void *old_g = ctx->d_gacc;
-    TRY(grow(ctx, &ctx->d_gacc, &ctx->gacc_cap, (size_t)n * np * 8));
-    if (ctx->d_gacc != old_g) drop_graph(ctx);
+    TRY(ensure_grad_bufs(ctx, n));
     TRY(ensure_partials(ctx, n));
-    CK(ctx, cudaMemsetAsync(ctx->d_gacc, 0, (size_t)n * np * 8, ctx->stream));
-    CK(ctx, launch_adjoint(ctx->pb, h, n, (double *)ctx->d_part, (unsigned long long *)ctx->d_gacc,
-                           ctx->stream));
-    if (d_ll) CK(ctx, launch_reduce_ll(ctx->pb, MODE_F32, n, ctx->d_part, d_ll, ctx->stream));
+    TRY(enqueue_forward_adjoint(ctx, h, n));
+    if (d_ll) CK(ctx, launch_reduce_ll(ctx->pb, ctx->mode, n, ctx->d_part, d_ll, ctx->stream));
     if (d_lp) CK(ctx, launch_prior(ctx->pb, ctx->mode, h, ctx->d_mu, n, d_lp, ctx->stream));
     CK(ctx, launch_grad_finish(ctx->pb, ctx->mode, h, ctx->d_mu, n,
                                (const unsigned long long *)ctx->d_gacc, d_grad, ctx->stream));
@@ -749,6 +772,7 @@ mt_status mt_destroy(mt_ctx *ctx)
     if (ctx->d_out) cudaFree(ctx->d_out);
     if (ctx->d_out2) cudaFree(ctx->d_out2);
     if (ctx->d_gacc) cudaFree(ctx->d_gacc);
+    if (ctx->d_dO) cudaFree(ctx->d_dO);
     if (ctx->d_diag) cudaFree(ctx->d_diag);
     if (ctx->d_terr) cudaFree(ctx->d_terr);
     if (ctx->d_lrow) cudaFree(ctx->d_lrow);
@@ -1032,8 +1056,7 @@ static mt_status ensure_chain_grads(mt_ctx *ctx)
     if (!ctx->d_G) TRY(dalloc(ctx, &ctx->d_G, 2 * (size_t)ctx->C * np));
     if (!ctx->d_extra) TRY(dalloc(ctx, &ctx->d_extra, (size_t)ctx->C));
     // gradients of the current heights into G[cur]; the current log-likelihoods
-    // are refreshed with the adjoint's forward pass so that the proposals'
-    // (computed by the same pass) are compared against the same arithmetic
+    // are refreshed by the gradient's forward pass, which the proposals' use too
     HRef hc{ctx->d_H, (long long)np, ctx->d_cur, (long long)(ctx->C * np), 0};
     TRY(grow(ctx, &ctx->d_out, &ctx->out_cap, (size_t)ctx->C * np * 8));
     TRY(eval_grad(ctx, hc, ctx->C, (double *)ctx->d_out, ctx->d_ll, nullptr));
@@ -1056,9 +1079,7 @@ static mt_status enqueue_mala(mt_ctx *ctx, double eps, int off)
     CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
     EvPair ep;
     if (ctx->timing) ev_begin(ctx, 0, &ep);
-    CK(ctx, cudaMemsetAsync(ctx->d_gacc, 0, (size_t)ctx->C * np * 8, ctx->stream));
-    CK(ctx, launch_adjoint(ctx->pb, hp, ctx->C, (double *)ctx->d_part,
-                           (unsigned long long *)ctx->d_gacc, ctx->stream));
+    TRY(enqueue_forward_adjoint(ctx, hp, ctx->C));
     if (ctx->timing) ev_end(ctx, 0, &ep);
     // gradient of the proposals into G[1 - cur]
     CK(ctx, launch_grad_finish_sel(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C,
@@ -1066,7 +1087,7 @@ static mt_status enqueue_mala(mt_ctx *ctx, double eps, int off)
                                    ctx->stream));
     CK(ctx, launch_mala_hastings(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec,
                                  ctx->d_extra, ctx->stream));
-    CK(ctx, launch_accept_fused(ctx->pb, MODE_F32, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
+    CK(ctx, launch_accept_fused(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
                                 ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
                                 ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
                                 ctx->stream, ec ? ctx->d_alpha : nullptr));
@@ -1121,9 +1142,7 @@ static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
                              ctx->d_P, ctx->d_Q64, ctx->d_k0, ctx->seed, ctx->d_step, off, ctx->stream));
     HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
     for (int i = 0; i < ctx->hmc_leap; ++i) {
-        CK(ctx, cudaMemsetAsync(ctx->d_gacc, 0, (size_t)ctx->C * np * 8, ctx->stream));
-        CK(ctx, launch_adjoint(ctx->pb, hp, ctx->C, (double *)ctx->d_part,
-                               (unsigned long long *)ctx->d_gacc, ctx->stream));
+        TRY(enqueue_forward_adjoint(ctx, hp, ctx->C));
         CK(ctx, launch_grad_finish_sel(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C,
                                        (const unsigned long long *)ctx->d_gacc, ctx->d_G, ctx->d_cur,
                                        ctx->stream));
@@ -1134,7 +1153,7 @@ static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
     CK(ctx, launch_hmc_finish(ctx->pb, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec, ctx->d_P, ctx->d_k0,
                               ctx->d_extra, ctx->stream));
     CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
-    CK(ctx, launch_accept_fused(ctx->pb, MODE_F32, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
+    CK(ctx, launch_accept_fused(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
                                 ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
                                 ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
                                 ctx->stream, ec ? ctx->d_alpha : nullptr));
@@ -1189,6 +1208,7 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
         TRY(grad_ok(ctx));
         if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA / HMC need a step size eps > 0");
         TRY(ensure_chain_grads(ctx));
+        TRY(ensure_grad_bufs(ctx, ctx->C));
         if (kernel == MT_KERNEL_HMC) TRY(ensure_hmc(ctx));
         if (ctx->adapt_n > 0) TRY(ensure_adapt(ctx, step));
     }

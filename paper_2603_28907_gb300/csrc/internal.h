@@ -62,6 +62,9 @@ struct Prob {
     float2 delta_ff;           // float-float of the minimum thickness
     float2 grho_ff;            // float-float of G * rho_top
     float2 invL_ff;            // float-float of 1 / Lambda
+    float *dO;                 // FP32 modes: the march also writes d ll / d O_p = (lambda_p -
+                               // C_p) / Lambda per ray, [chain][ray]; the adjoint reads it
+                               // (nullptr: not written)
 };
 
 // Where chain c's heights live: base + sel[c] * sel_stride + c * chain_stride
@@ -114,8 +117,10 @@ cudaError_t launch_propose_rw(const Prob &pb, int mode, void *hbuf, long long bu
                               const int64_t *step_base, int step_off, cudaStream_t st);
 cudaError_t launch_advance(int64_t *step, int n, cudaStream_t st);
 size_t adjoint_smem_bytes(const Prob &pb, bool with_acc);
-cudaError_t launch_adjoint(const Prob &pb, HRef h, int n_chains, double *partial,
-                           unsigned long long *gacc, cudaStream_t st);
+// The adjoint's scatter of pb.dO (written by an FP32-mode march of the same
+// heights) into gacc [n_chains][L][N] (zeroed by the caller).
+cudaError_t launch_adjoint(const Prob &pb, HRef h, int n_chains, unsigned long long *gacc,
+                           cudaStream_t st);
 cudaError_t launch_grad_finish(const Prob &pb, int mode, HRef h, const double *mu, int n_chains,
                                const unsigned long long *gacc, double *grad, cudaStream_t st);
 cudaError_t launch_add(int n, const double *a, const double *b, double *out, cudaStream_t st);

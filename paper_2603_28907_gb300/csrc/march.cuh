@@ -730,14 +730,20 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
             const FF Off = ff_mul(FF{pb.dt_ff[ray].x, pb.dt_ff[ray].y}, Sff);
             const FF OL = ff_mul(Off, FF{pb.invL_ff.x, pb.invL_ff.y});
             FF tf;
+            float dO;  // d ll / d O_p = (lambda - C) / Lambda, for the adjoint
             if (Cp > 0) {
                 const FF yff = ff_add(FF{pb.a_ff[ray].x, pb.a_ff[ray].y}, FF{-OL.hi, -OL.lo});
-                const float g = g_f32(yff.hi + yff.lo), cf = (float)Cp;
+                const float y = yff.hi + yff.lo;
+                const float g = g_f32(y), cf = (float)Cp;
                 const float cg = cf * g;
                 tf = FF{-cg, -fmaf(cf, g, -cg)};
+                dO = cf * expm1f(y) * pb.invL_ff.x;  // lambda - C = C (e^y - 1)
             } else {
-                tf = FF{-(float)pb.I0 * expf(-(OL.hi + OL.lo)), 0.f};
+                const float lam = (float)pb.I0 * expf(-(OL.hi + OL.lo));
+                tf = FF{-lam, 0.f};
+                dO = lam * pb.invL_ff.x;
             }
+            if (pb.dO) pb.dO[(size_t)c * pb.n_rays + ray] = dO;
             accf = ff_add(accf, tf);
             if (ray_O) ray_O[(size_t)c * pb.n_rays + ray] = (double)Off.hi + (double)Off.lo;
             if (ray_term)
