@@ -13,6 +13,7 @@ import oracle
 from paper_2603_28907_gb300 import autograd as AG
 from paper_2603_28907_gb300 import mt, workloads as W
 from tests.gpu_common import DEV, heights, logpost, setup
+from tests.test_gpu_parity import fp32_loglik_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -140,3 +141,40 @@ def test_mala_lockstep():
                 stats["accepted"] += 1
     assert stats["mismatch"] == 0, stats
     assert stats["accepted"] > 0, stats
+
+
+def test_grad_large_grid_global_paths():
+    """A 100 x 100 grid with 4 surfaces: the march reads its (h, dx) records from
+    HBM and the adjoint adds straight into global fixed-point accumulators (its
+    records fit in shared memory, the accumulators do not); the gradient must
+    still match the oracle's, and a MALA step runs on those paths."""
+    w = W.small(R=100, Q=100, bases=(40.0, 70.0, 110.0, 140.0),
+                rho=(2.65, 1.9, 0.0012, 2.65, 0.0012), G=64, n_zenith=6, n_azimuth=9,
+                n_sensors=2)
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    Hs = np.stack([W.perturbed(pr["H_true"], 1.0, [4]), W.init_chains(w, 1)[0]])
+    H = heights(Hs, mt.PREC_F32)
+    g = torch.zeros(H.shape, dtype=torch.float64, device=DEV)
+    lp = torch.zeros(2, dtype=torch.float64, device=DEV)
+    ctx.grad(H, g, lp)
+    torch.cuda.synchronize()
+    g = g.cpu().numpy()
+    Hn = H.double().cpu().numpy()
+    for c in range(2):
+        ref = op.grad_loglik(Hn[c]) + op.grad_logprior(Hn[c])
+        scale = np.abs(ref).max()
+        assert np.max(np.abs(g[c] - ref)) <= 1e-3 * scale, (c, np.max(np.abs(g[c] - ref)), scale)
+        ref_lp = op.loglik(Hn[c]) + op.logprior(Hn[c])
+        if np.isinf(ref_lp):                             # a node above the box top
+            assert lp[c].item() == ref_lp
+        else:
+            assert abs(lp[c].item() - ref_lp) <= fp32_loglik_tol(pr, op, Hn[c]) + 1e-9 * abs(ref_lp)
+    H = heights(np.stack([W.init_chains(w, 2)[c] for c in range(2)]), mt.PREC_F32)
+    ctx.init_chains(H, 5)
+    ctx.run(mt.KERNEL_MALA, 0.005, 1, 2)
+    ll = torch.zeros(2, dtype=torch.float64, device=DEV)
+    Hs2 = torch.zeros_like(H)
+    ctx.get_state(Hs2, ll)
+    H2 = Hs2.double().cpu().numpy()
+    for c in range(2):
+        assert abs(ll[c].item() - op.loglik(H2[c])) <= fp32_loglik_tol(pr, op, H2[c])
