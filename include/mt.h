@@ -223,6 +223,30 @@ MT_API mt_status mt_set_hmc(mt_ctx *ctx, int n_leapfrog);
  * MT_EINVAL.  Random-walk steps neither use nor change the step sizes. */
 MT_API mt_status mt_set_adapt(mt_ctx *ctx, double target_accept, int n_adapt);
 
+/* Diagonal preconditioner of HMC adapted in the same warm-up (Sec. 3.1: the
+ * warm-up tunes a diagonal preconditioner together with the step size).
+ * With on = 1 the n_adapt warm-up steps armed by mt_set_adapt (n_adapt >= 20,
+ * HMC only; MALA runs are refused while it is on) follow a windowed
+ * schedule: an initial buffer, slow windows of doubling length and a
+ * terminal buffer (75 / 25 / 50 steps, or 15 % / 75 % / 10 % of n_adapt when
+ * those do not fit; the last slow window is stretched to the terminal buffer
+ * when the next one would cross it).  During each slow window every chain
+ * accumulates the mean and variance of each height of its post-step states
+ * (Welford, FP64); at the window's end its inverse metric becomes
+ * (n/(n+5)) var + shrink 5/(n+5) (n the window length) and the step-size
+ * averaging restarts from mu = log(10 eps).  HMC then draws momenta
+ * p ~ N(0, M) with M = diag(1 / inverse metric), drifts H += eps M^-1 p and
+ * takes the kinetic energy p^T M^-1 p / 2; the adapted metric is kept after
+ * the warm-up.  on = 0: unit metric.  shrink >= 0 (m^2; 1e-3 is the usual
+ * default of that schedule).  Re-arms the warm-up (the next HMC run starts
+ * it over).  MT_EINVAL on bad arguments. */
+MT_API mt_status mt_set_metric_adapt(mt_ctx *ctx, int on, double shrink);
+
+/* Each chain's diagonal inverse metric, host or device double
+ * [n_chains][L][R][Q].  Synchronous.  MT_ESTATE before the first HMC run of
+ * an armed warm-up with the metric adapted. */
+MT_API mt_status mt_get_metric(mt_ctx *ctx, double *inv_metric_out);
+
 /* The per-chain step sizes the next MALA / HMC step uses and the
  * acceptance probability of each chain's last adapted step, host or device
  * double [n_chains] each (nullable).  Synchronous.  MT_ESTATE before the

@@ -23,13 +23,16 @@ import oracle
 STREAM_HMC = 6
 
 
-def leapfrog(q0, p0, eps, n_leap, grad, state=np.float64):
+def leapfrog(q0, p0, eps, n_leap, grad, state=np.float64, inv_metric=None):
     """(q, p) after n_leap leapfrog steps; grad(x) is evaluated at x rounded
-    to `state`.  Returns the rounded final position and the final momentum."""
+    to `state`.  With a diagonal inverse metric m (mass matrix diag(1/m)) each
+    drift moves q by eps * m * p.  Returns the rounded final position and the
+    final momentum."""
+    m = 1.0 if inv_metric is None else np.asarray(inv_metric, np.float64)
     q = np.asarray(q0, np.float64).copy()
     p = np.asarray(p0, np.float64) + 0.5 * eps * grad(np.asarray(q, state).astype(np.float64))
     for i in range(n_leap):
-        q = q + eps * p
+        q = q + eps * (m * p)
         g = grad(np.asarray(q, state).astype(np.float64))
         p = p + (eps if i < n_leap - 1 else 0.5 * eps) * g
     return np.asarray(q, state).astype(np.float64), p
@@ -40,10 +43,17 @@ def momentum(seed, chain, step, shape):
     return oracle.normals(seed, STREAM_HMC, chain, step, n).reshape(shape)
 
 
-def propose(op, H, eps, n_leap, seed, chain, step, state=np.float32):
+def propose(op, H, eps, n_leap, seed, chain, step, state=np.float32, inv_metric=None):
     """One HMC proposal of chain `chain` at step `step` from heights H for the
-    oracle problem `op` (log pi = loglik + logprior).  Returns (q', K0 - K1)."""
+    oracle problem `op` (log pi = loglik + logprior).  Returns (q', K0 - K1)
+    with K(p) = p^T M^-1 p / 2.  With a diagonal inverse metric m the momentum
+    is p0 = xi / sqrt(m) for the standard normals xi, so K(p0) = |xi|^2 / 2."""
     grad = lambda x: op.grad_loglik(x) + op.grad_logprior(x)
-    p0 = momentum(seed, chain, step, np.shape(H))
-    q, p = leapfrog(H, p0, eps, n_leap, grad, state)
-    return q, 0.5 * float(np.sum(p0 * p0)) - 0.5 * float(np.sum(p * p))
+    xi = momentum(seed, chain, step, np.shape(H))
+    if inv_metric is None:
+        p0, m = xi, 1.0
+    else:
+        m = np.asarray(inv_metric, np.float64)
+        p0 = xi / np.sqrt(m)
+    q, p = leapfrog(H, p0, eps, n_leap, grad, state, inv_metric)
+    return q, 0.5 * float(np.sum(xi * xi)) - 0.5 * float(np.sum(m * p * p))

@@ -135,6 +135,11 @@ struct mt_ctx {
     int adapt_n = 0;
     bool adapt_pending = false;
     double *d_eps = nullptr, *d_da = nullptr, *d_alpha = nullptr;
+    // diagonal inverse metric of HMC adapted in the same warm-up
+    // (mt_set_metric_adapt): Welford mean / M2 and the metric, [C][n] each
+    bool metric_on = false;
+    double metric_shrink = 1e-3;
+    double *d_minv = nullptr, *d_wmean = nullptr, *d_wm2 = nullptr;
     double *d_P = nullptr;           // HMC momentum [C][n]
     double *d_Q64 = nullptr;         // HMC trajectory position in FP64 [C][n]
     double *d_k0 = nullptr;          // HMC initial kinetic energy [C]
@@ -264,6 +269,9 @@ static void drop_chains(mt_ctx *ctx)
     dfree(ctx->d_eps);
     dfree(ctx->d_da);
     dfree(ctx->d_alpha);
+    dfree(ctx->d_minv);
+    dfree(ctx->d_wmean);
+    dfree(ctx->d_wm2);
     ctx->adapt_pending = ctx->adapt_n > 0;  // new chains adapt from the start
     ctx->g_valid = false;
     ctx->C = 0;
@@ -1092,7 +1100,7 @@ static mt_status enqueue_mala(mt_ctx *ctx, double eps, int off)
                                 ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
                                 ctx->stream, ec ? ctx->d_alpha : nullptr));
     if (ec)
-        CK(ctx, launch_adapt(ctx->C, ctx->adapt_target, ctx->adapt_n, ctx->d_alpha, ctx->d_da, ctx->d_eps,
+        CK(ctx, launch_adapt(ctx->C, ctx->adapt_target, ctx->adapt_n, 0, ctx->d_alpha, ctx->d_da, ctx->d_eps,
                              ctx->stream));
     if (ctx->timing) ev_end(ctx, 1, &es);
     return MT_OK;
@@ -1107,21 +1115,30 @@ static mt_status ensure_hmc(mt_ctx *ctx)
     return MT_OK;
 }
 
-// Step-size adaptation buffers; on the first gradient-sampler run after
-// mt_set_adapt (or after new chains) every chain starts at eps0.
+// Warm-up adaptation buffers; on the first gradient-sampler run after
+// mt_set_adapt (or after new chains) every chain starts at eps0 (and, with
+// the metric adapted, at the unit metric with empty accumulators).
 static mt_status ensure_adapt(mt_ctx *ctx, double eps0)
 {
-    const size_t C = (size_t)ctx->C;
+    const size_t C = (size_t)ctx->C, nm = C * n_per_chain(ctx);
     if (!ctx->d_eps || !ctx->d_da || !ctx->d_alpha) {
         drop_graph(ctx);
         TRY(dalloc(ctx, &ctx->d_eps, C));
-        TRY(dalloc(ctx, &ctx->d_da, 4 * C));
+        TRY(dalloc(ctx, &ctx->d_da, (size_t)kDAStride * C));
         TRY(dalloc(ctx, &ctx->d_alpha, C));
         CK(ctx, cudaMemsetAsync(ctx->d_alpha, 0, C * 8, ctx->stream));
         ctx->adapt_pending = true;
     }
+    if (ctx->metric_on && (!ctx->d_minv || !ctx->d_wmean || !ctx->d_wm2)) {
+        drop_graph(ctx);
+        TRY(dalloc(ctx, &ctx->d_minv, nm));
+        TRY(dalloc(ctx, &ctx->d_wmean, nm));
+        TRY(dalloc(ctx, &ctx->d_wm2, nm));
+        ctx->adapt_pending = true;
+    }
     if (ctx->adapt_pending) {
         CK(ctx, launch_adapt_init(ctx->C, eps0, ctx->d_da, ctx->d_eps, ctx->stream));
+        if (ctx->metric_on) CK(ctx, launch_metric_init(nm, ctx->d_wmean, ctx->d_wm2, ctx->d_minv, ctx->stream));
         ctx->adapt_pending = false;
     }
     return MT_OK;
@@ -1138,7 +1155,9 @@ static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
     EvPair es;
     if (ctx->timing) ev_begin(ctx, 1, &es);
     const double *ec = ctx->adapt_n > 0 ? ctx->d_eps : nullptr;
-    CK(ctx, launch_hmc_start(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec,
+    const bool metric = ec && ctx->metric_on;
+    const double *mi = metric ? ctx->d_minv : nullptr;
+    CK(ctx, launch_hmc_start(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec, mi,
                              ctx->d_P, ctx->d_Q64, ctx->d_k0, ctx->seed, ctx->d_step, off, ctx->stream));
     HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
     for (int i = 0; i < ctx->hmc_leap; ++i) {
@@ -1148,18 +1167,22 @@ static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
                                        ctx->stream));
         if (i + 1 < ctx->hmc_leap)
             CK(ctx, launch_hmc_kick_drift(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C,
-                                          eps, ec, ctx->d_P, ctx->d_Q64, ctx->stream));
+                                          eps, ec, mi, ctx->d_P, ctx->d_Q64, ctx->stream));
     }
-    CK(ctx, launch_hmc_finish(ctx->pb, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec, ctx->d_P, ctx->d_k0,
+    CK(ctx, launch_hmc_finish(ctx->pb, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec, mi, ctx->d_P, ctx->d_k0,
                               ctx->d_extra, ctx->stream));
     CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
     CK(ctx, launch_accept_fused(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
                                 ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
                                 ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
                                 ctx->stream, ec ? ctx->d_alpha : nullptr));
+    if (metric)  // the post-step states into the slow window's accumulators
+        CK(ctx, launch_metric(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_cur, ctx->C, ctx->adapt_n,
+                              ctx->metric_shrink, ctx->d_da, ctx->d_wmean, ctx->d_wm2, ctx->d_minv,
+                              ctx->stream));
     if (ec)
-        CK(ctx, launch_adapt(ctx->C, ctx->adapt_target, ctx->adapt_n, ctx->d_alpha, ctx->d_da, ctx->d_eps,
-                             ctx->stream));
+        CK(ctx, launch_adapt(ctx->C, ctx->adapt_target, ctx->adapt_n, metric ? 1 : 0, ctx->d_alpha, ctx->d_da,
+                             ctx->d_eps, ctx->stream));
     if (ctx->timing) ev_end(ctx, 1, &es);
     return MT_OK;
 }
@@ -1207,6 +1230,10 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
         if (ctx->copula) return fail(ctx, MT_EINVAL, "MALA / HMC need the CAR prior (mt_set_prior 0)");
         TRY(grad_ok(ctx));
         if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA / HMC need a step size eps > 0");
+        if (ctx->metric_on && ctx->adapt_n > 0 && kernel == MT_KERNEL_MALA)
+            return fail(ctx, MT_EINVAL, "the adapted metric is for HMC: mt_set_metric_adapt(ctx, 0, ...) for MALA");
+        if (ctx->metric_on && ctx->adapt_n > 0 && ctx->adapt_n < 20)
+            return fail(ctx, MT_EINVAL, "metric adaptation needs n_adapt >= 20 warm-up steps");
         TRY(ensure_chain_grads(ctx));
         TRY(ensure_grad_bufs(ctx, ctx->C));
         if (kernel == MT_KERNEL_HMC) TRY(ensure_hmc(ctx));
@@ -1556,7 +1583,42 @@ mt_status mt_set_adapt(mt_ctx *ctx, double target_accept, int n_adapt)
         dfree(ctx->d_eps);
         dfree(ctx->d_da);
         dfree(ctx->d_alpha);
+        dfree(ctx->d_minv);
+        dfree(ctx->d_wmean);
+        dfree(ctx->d_wm2);
     }
+    return MT_OK;
+}
+
+mt_status mt_set_metric_adapt(mt_ctx *ctx, int on, double shrink)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if ((on != 0 && on != 1) || !(shrink >= 0.0))
+        return fail(ctx, MT_EINVAL, "mt_set_metric_adapt: need on in {0, 1} and shrink >= 0");
+    CK(ctx, cudaSetDevice(ctx->device));
+    drop_graph(ctx);
+    ctx->metric_on = on != 0;
+    ctx->metric_shrink = shrink;
+    ctx->adapt_pending = ctx->adapt_n > 0;  // the warm-up starts over
+    if (!on) {
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(ctx->d_minv);
+        dfree(ctx->d_wmean);
+        dfree(ctx->d_wm2);
+    }
+    return MT_OK;
+}
+
+mt_status mt_get_metric(mt_ctx *ctx, double *inv_metric_out)
+{
+    TRY(need(ctx, false));
+    if (ctx->C < 1) return fail(ctx, MT_ESTATE, "mt_init_chains first");
+    if (!inv_metric_out) return fail(ctx, MT_EINVAL, "need inv_metric_out");
+    if (!ctx->metric_on || ctx->adapt_n == 0 || ctx->adapt_pending || !ctx->d_minv)
+        return fail(ctx, MT_ESTATE, "no adapted metric: mt_set_metric_adapt, mt_set_adapt, then an HMC mt_run");
+    const size_t n = (size_t)ctx->C * n_per_chain(ctx);
+    CK(ctx, cudaMemcpyAsync(inv_metric_out, ctx->d_minv, n * 8, cudaMemcpyDefault, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
     return MT_OK;
 }
 

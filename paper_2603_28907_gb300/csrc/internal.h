@@ -135,23 +135,34 @@ cudaError_t launch_propose_mala(const Prob &pb, int mode, void *hbuf, long long 
                                 const double *gbuf, const uint8_t *cur, int n_chains, double eps,
                                 const double *eps_c, uint64_t seed, const int64_t *step_base,
                                 int step_off, cudaStream_t st);
+// HMC with a diagonal inverse metric minv [C][n] (nullptr: unit).
 cudaError_t launch_hmc_start(const Prob &pb, int mode, void *hbuf, long long buf_stride,
                              const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                             const double *eps_c, double *pbuf, double *qbuf, double *k0,
-                             uint64_t seed, const int64_t *step_base, int step_off, cudaStream_t st);
+                             const double *eps_c, const double *minv, double *pbuf, double *qbuf,
+                             double *k0, uint64_t seed, const int64_t *step_base, int step_off,
+                             cudaStream_t st);
 cudaError_t launch_hmc_kick_drift(const Prob &pb, int mode, void *hbuf, long long buf_stride,
                                   const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                                  const double *eps_c, double *pbuf, double *qbuf, cudaStream_t st);
+                                  const double *eps_c, const double *minv, double *pbuf, double *qbuf,
+                                  cudaStream_t st);
 cudaError_t launch_hmc_finish(const Prob &pb, long long buf_stride, const double *gbuf,
                               const uint8_t *cur, int n_chains, double eps, const double *eps_c,
-                              double *pbuf, const double *k0, double *extra, cudaStream_t st);
+                              const double *minv, double *pbuf, const double *k0, double *extra,
+                              cudaStream_t st);
 cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, long long buf_stride,
                                  const double *gbuf, const uint8_t *cur, int n_chains, double eps,
                                  const double *eps_c, double *extra, cudaStream_t st);
-// Dual-averaging step-size adaptation (mcmc.cu): state da [C][4], step sizes eps [C]
+// Warm-up adaptation (mcmc.cu): dual-averaging state da [C][6], step sizes
+// eps [C]; with metric != 0 the windowed diagonal-metric schedule (Welford
+// mean / m2 and the inverse metric minv, [C][n] each).
+constexpr int kDAStride = 6;
 cudaError_t launch_adapt_init(int n_chains, double eps0, double *da, double *eps, cudaStream_t st);
-cudaError_t launch_adapt(int n_chains, double target, int n_adapt, const double *alpha, double *da,
-                         double *eps, cudaStream_t st);
+cudaError_t launch_adapt(int n_chains, double target, int n_adapt, int metric, const double *alpha,
+                         double *da, double *eps, cudaStream_t st);
+cudaError_t launch_metric_init(size_t n, double *mean, double *m2, double *minv, cudaStream_t st);
+cudaError_t launch_metric(const Prob &pb, int mode, const void *hbuf, long long buf_stride,
+                          const uint8_t *cur, int n_chains, int n_adapt, double shrink,
+                          const double *da, double *mean, double *m2, double *minv, cudaStream_t st);
 cudaError_t launch_gather(int mode, HRef h, int n_chains, long long n_per_chain, void *out,
                           cudaStream_t st);
 cudaError_t launch_nested_rhat(int mode, const void *draws, int N, int C, int P, int K, double *sm,

@@ -269,7 +269,7 @@ cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, lon
 template <typename H>
 __global__ void __launch_bounds__(256)
 k_hmc_start(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur, double eps0,
-            const double *eps_c, double *pbuf, double *qbuf, double *k0, uint64_t seed,
+            const double *eps_c, const double *minv, double *pbuf, double *qbuf, double *k0, uint64_t seed,
             const int64_t *step_base, int step_off)
 {
     const int c = blockIdx.x;
@@ -290,9 +290,10 @@ k_hmc_start(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur
         for (int t = 0; t < 2; ++t) {
             const int i = 2 * j + t;
             if (i >= n) break;
-            kin += 0.5 * xi[t] * xi[t];
-            const double p = xi[t] + 0.5 * eps * gbuf[a + i];
-            const double q = (double)hbuf[a + i] + eps * p;
+            kin += 0.5 * xi[t] * xi[t];  // K(p0) = p0^2 minv / 2 with p0 = xi / sqrt(minv)
+            const double mi = minv ? minv[(size_t)c * n + i] : 1.0;
+            const double p = (minv ? xi[t] / sqrt(mi) : xi[t]) + 0.5 * eps * gbuf[a + i];
+            const double q = (double)hbuf[a + i] + eps * (mi * p);
             pbuf[(size_t)c * n + i] = p;
             qbuf[(size_t)c * n + i] = q;
             hbuf[b + i] = (H)q;
@@ -305,7 +306,7 @@ k_hmc_start(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur
 template <typename H>
 __global__ void __launch_bounds__(256)
 k_hmc_kick_drift(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur, double eps0,
-                 const double *eps_c, double *pbuf, double *qbuf)
+                 const double *eps_c, const double *minv, double *pbuf, double *qbuf)
 {
     const int c = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -314,7 +315,7 @@ k_hmc_kick_drift(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t
     const long long b = (long long)(1 - cur[c]) * bs + (long long)c * n;
     const size_t k = (size_t)c * n + i;
     const double p = pbuf[k] + eps * gbuf[b + i];
-    const double q = qbuf[k] + eps * p;
+    const double q = qbuf[k] + eps * ((minv ? minv[k] : 1.0) * p);
     pbuf[k] = p;
     qbuf[k] = q;
     hbuf[b + i] = (H)q;
@@ -322,7 +323,7 @@ k_hmc_kick_drift(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t
 
 __global__ void __launch_bounds__(256)
 k_hmc_finish(int n, long long bs, const double *gbuf, const uint8_t *cur, double eps0,
-             const double *eps_c, const double *pbuf, const double *k0, double *extra)
+             const double *eps_c, const double *minv, const double *pbuf, const double *k0, double *extra)
 {
     const int c = blockIdx.x;
     const double eps = eps_c ? eps_c[c] : eps0;
@@ -330,7 +331,7 @@ k_hmc_finish(int n, long long bs, const double *gbuf, const uint8_t *cur, double
     double kin = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const double p = pbuf[(size_t)c * n + i] + 0.5 * eps * gbuf[b + i];
-        kin += 0.5 * p * p;
+        kin += 0.5 * (minv ? minv[(size_t)c * n + i] : 1.0) * p * p;
     }
     kin = block_sum(kin);
     if (threadIdx.x == 0) extra[c] = k0[c] - kin;
@@ -338,39 +339,42 @@ k_hmc_finish(int n, long long bs, const double *gbuf, const uint8_t *cur, double
 
 cudaError_t launch_hmc_start(const Prob &pb, int mode, void *hbuf, long long buf_stride,
                              const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                             const double *eps_c, double *pbuf, double *qbuf, double *k0,
-                             uint64_t seed, const int64_t *step_base, int step_off, cudaStream_t st)
+                             const double *eps_c, const double *minv, double *pbuf, double *qbuf,
+                             double *k0, uint64_t seed, const int64_t *step_base, int step_off,
+                             cudaStream_t st)
 {
     const int n = pb.L * pb.N;
     if (mode == MODE_F64)
         k_hmc_start<double><<<n_chains, 256, 0, st>>>(n, (double *)hbuf, buf_stride, gbuf, cur, eps, eps_c,
-                                                      pbuf, qbuf, k0, seed, step_base, step_off);
+                                                      minv, pbuf, qbuf, k0, seed, step_base, step_off);
     else
         k_hmc_start<float><<<n_chains, 256, 0, st>>>(n, (float *)hbuf, buf_stride, gbuf, cur, eps, eps_c,
-                                                     pbuf, qbuf, k0, seed, step_base, step_off);
+                                                     minv, pbuf, qbuf, k0, seed, step_base, step_off);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hmc_kick_drift(const Prob &pb, int mode, void *hbuf, long long buf_stride,
                                   const double *gbuf, const uint8_t *cur, int n_chains, double eps,
-                                  const double *eps_c, double *pbuf, double *qbuf, cudaStream_t st)
+                                  const double *eps_c, const double *minv, double *pbuf, double *qbuf,
+                                  cudaStream_t st)
 {
     const int n = pb.L * pb.N;
     dim3 grid((n + 255) / 256, n_chains);
     if (mode == MODE_F64)
         k_hmc_kick_drift<double><<<grid, 256, 0, st>>>(n, (double *)hbuf, buf_stride, gbuf, cur, eps,
-                                                       eps_c, pbuf, qbuf);
+                                                       eps_c, minv, pbuf, qbuf);
     else
         k_hmc_kick_drift<float><<<grid, 256, 0, st>>>(n, (float *)hbuf, buf_stride, gbuf, cur, eps,
-                                                      eps_c, pbuf, qbuf);
+                                                      eps_c, minv, pbuf, qbuf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hmc_finish(const Prob &pb, long long buf_stride, const double *gbuf,
                               const uint8_t *cur, int n_chains, double eps, const double *eps_c,
-                              double *pbuf, const double *k0, double *extra, cudaStream_t st)
+                              const double *minv, double *pbuf, const double *k0, double *extra,
+                              cudaStream_t st)
 {
-    k_hmc_finish<<<n_chains, 256, 0, st>>>(pb.L * pb.N, buf_stride, gbuf, cur, eps, eps_c, pbuf, k0,
+    k_hmc_finish<<<n_chains, 256, 0, st>>>(pb.L * pb.N, buf_stride, gbuf, cur, eps, eps_c, minv, pbuf, k0,
                                            extra);
     return cudaGetLastError();
 }
@@ -468,46 +472,145 @@ cudaError_t launch_advance(int64_t *step, int n, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- step-size adaptation
+// ---------------------------------------------------------------- warm-up adaptation
 // Per-chain dual averaging of log eps toward a target acceptance probability
 // delta (Sec. 3.1: the step size is tuned in the warm-up toward 0.8; the
 // scheme is Hoffman & Gelman's, J. Mach. Learn. Res. 15 (2014), Sec. 3.2.1,
 // with gamma = 0.05, t0 = 10, kappa = 0.75 and mu = log(10 eps0)).  After the
-// m-th adapted step with acceptance probability alpha_m:
+// m-th dual-averaging step with acceptance probability alpha_m:
 //   Hbar_m = (1 - 1/(m + t0)) Hbar_{m-1} + (delta - alpha_m) / (m + t0)
 //   log eps_m = mu - sqrt(m) / gamma * Hbar_m
 //   log epsbar_m = m^-kappa log eps_m + (1 - m^-kappa) log epsbar_{m-1}
 // (Hbar_0 = 0, log epsbar_0 = 0); the next step runs with eps_m, and after
-// the last adapted step every chain keeps epsbar.  State per chain:
-// da[4c..4c+3] = {log epsbar, Hbar, mu, m}.
+// the last of the W adapted steps every chain keeps epsbar.
+//
+// With the metric adapted too (HMC; Sec. 3.1: the warm-up also tunes a
+// diagonal preconditioner), the adapted steps t = 0 .. W-1 are split into an
+// initial buffer, slow windows of doubling length and a terminal buffer
+// (75 / 25 / 50 steps, or 15 % / 75 % / 10 % of W when those do not fit; the
+// last slow window is stretched to the terminal buffer when the next one
+// would cross it).  In a slow window every chain accumulates the mean and M2
+// of each coordinate of its post-step state (Welford); at the window's last
+// step its inverse metric becomes (n/(n+5)) var + s 5/(n+5) (var = M2/(n-1),
+// n the window length, s the shrinkage target), the accumulators restart and
+// the dual averaging restarts from mu = log(10 eps), Hbar = 0,
+// log epsbar = 0, m = 0.
+//
+// State per chain: da[6c .. 6c+5] = {log epsbar, Hbar, mu, m, t, unused}
+// (kDAStride = 6).
+
+// Slow window of adapted step t (of W): returns whether t lies in one, with
+// the window's first step and whether t is its last.
+__host__ __device__ inline bool slow_window(int W, int t, int &start, bool &last)
+{
+    int init = 75, term = 50, base = 25;
+    if (init + base + term > W) {
+        init = (int)(0.15 * W);
+        term = (int)(0.1 * W);
+        base = W - (init + term);
+    }
+    const int stop = W - term;
+    if (t < init || t >= stop || base < 1) return false;
+    int s0 = init, size = base;
+    while (s0 < stop) {
+        int end = s0 + size;
+        if (end + 2 * size > stop) end = stop;
+        if (t < end) {
+            start = s0;
+            last = t == end - 1;
+            return true;
+        }
+        s0 = end;
+        size *= 2;
+    }
+    return false;
+}
+
 __global__ void k_adapt_init(int n_chains, double eps0, double *da, double *eps)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_chains) return;
     eps[c] = eps0;
-    da[4 * c + 0] = 0.0;
-    da[4 * c + 1] = 0.0;
-    da[4 * c + 2] = log(10.0 * eps0);
-    da[4 * c + 3] = 0.0;
+    double *d = da + kDAStride * c;
+    d[0] = 0.0;
+    d[1] = 0.0;
+    d[2] = log(10.0 * eps0);
+    d[3] = 0.0;
+    d[4] = 0.0;
+    d[5] = 0.0;
 }
 
-__global__ void k_adapt(int n_chains, double target, int n_adapt, const double *alpha, double *da,
-                        double *eps)
+__global__ void k_adapt(int n_chains, double target, int n_adapt, int metric, const double *alpha,
+                        double *da, double *eps)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_chains) return;
-    const double m = da[4 * c + 3] + 1.0;
-    if (m > (double)n_adapt) return;  // adaptation over: eps stays at epsbar
+    double *d = da + kDAStride * c;
+    const int t = (int)d[4];
+    if (t >= n_adapt) return;  // adaptation over: eps stays at epsbar
+    const double m = d[3] + 1.0;
     const double t0 = 10.0, gamma = 0.05, kappa = 0.75;
     const double w = 1.0 / (m + t0);
-    const double hbar = (1.0 - w) * da[4 * c + 1] + w * (target - alpha[c]);
-    const double log_eps = da[4 * c + 2] - sqrt(m) / gamma * hbar;
+    const double hbar = (1.0 - w) * d[1] + w * (target - alpha[c]);
+    const double log_eps = d[2] - sqrt(m) / gamma * hbar;
     const double eta = pow(m, -kappa);
-    const double log_bar = eta * log_eps + (1.0 - eta) * da[4 * c + 0];
-    da[4 * c + 0] = log_bar;
-    da[4 * c + 1] = hbar;
-    da[4 * c + 3] = m;
-    eps[c] = exp(m < (double)n_adapt ? log_eps : log_bar);
+    const double log_bar = eta * log_eps + (1.0 - eta) * d[0];
+    const double e = exp(t + 1 < n_adapt ? log_eps : log_bar);
+    eps[c] = e;
+    int s0;
+    bool last = false;
+    if (metric && slow_window(n_adapt, t, s0, last) && last) {
+        d[0] = 0.0;  // the metric changed: dual averaging starts over from eps
+        d[1] = 0.0;
+        d[2] = log(10.0 * e);
+        d[3] = 0.0;
+    } else {
+        d[0] = log_bar;
+        d[1] = hbar;
+        d[3] = m;
+    }
+    d[4] = (double)(t + 1);
+}
+
+// Welford accumulation of the chains' post-step states during slow windows
+// and the inverse metric at each window's end; grid (coordinate blocks,
+// chains).  Reads the step index t before k_adapt advances it.
+template <typename H>
+__global__ void __launch_bounds__(256)
+k_metric(int n, const H *hbuf, long long bs, const uint8_t *cur, int n_adapt, double shrink,
+         const double *da, double *mean, double *m2, double *minv)
+{
+    const int c = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int t = (int)da[kDAStride * c + 4];
+    int s0;
+    bool last = false;
+    if (t >= n_adapt || !slow_window(n_adapt, t, s0, last)) return;
+    const size_t k = (size_t)c * n + i;
+    const double x = (double)hbuf[(long long)cur[c] * bs + (long long)c * n + i];
+    const double cnt = (double)(t - s0 + 1);
+    const double dx = x - mean[k];
+    const double mu = mean[k] + dx / cnt;
+    const double q = m2[k] + dx * (x - mu);
+    if (last) {
+        const double var = cnt > 1.0 ? q / (cnt - 1.0) : 0.0;
+        minv[k] = (cnt / (cnt + 5.0)) * var + shrink * (5.0 / (cnt + 5.0));
+        mean[k] = 0.0;
+        m2[k] = 0.0;
+    } else {
+        mean[k] = mu;
+        m2[k] = q;
+    }
+}
+
+__global__ void k_metric_init(size_t n, double *mean, double *m2, double *minv)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        mean[i] = 0.0;
+        m2[i] = 0.0;
+        minv[i] = 1.0;
+    }
 }
 
 cudaError_t launch_adapt_init(int n_chains, double eps0, double *da, double *eps, cudaStream_t st)
@@ -516,10 +619,31 @@ cudaError_t launch_adapt_init(int n_chains, double eps0, double *da, double *eps
     return cudaGetLastError();
 }
 
-cudaError_t launch_adapt(int n_chains, double target, int n_adapt, const double *alpha, double *da,
-                         double *eps, cudaStream_t st)
+cudaError_t launch_adapt(int n_chains, double target, int n_adapt, int metric, const double *alpha,
+                         double *da, double *eps, cudaStream_t st)
 {
-    k_adapt<<<(n_chains + 127) / 128, 128, 0, st>>>(n_chains, target, n_adapt, alpha, da, eps);
+    k_adapt<<<(n_chains + 127) / 128, 128, 0, st>>>(n_chains, target, n_adapt, metric, alpha, da, eps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_metric_init(size_t n, double *mean, double *m2, double *minv, cudaStream_t st)
+{
+    k_metric_init<<<1024, 256, 0, st>>>(n, mean, m2, minv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_metric(const Prob &pb, int mode, const void *hbuf, long long buf_stride,
+                          const uint8_t *cur, int n_chains, int n_adapt, double shrink,
+                          const double *da, double *mean, double *m2, double *minv, cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    dim3 grid((n + 255) / 256, n_chains);
+    if (mode == MODE_F64)
+        k_metric<double><<<grid, 256, 0, st>>>(n, (const double *)hbuf, buf_stride, cur, n_adapt, shrink, da,
+                                               mean, m2, minv);
+    else
+        k_metric<float><<<grid, 256, 0, st>>>(n, (const float *)hbuf, buf_stride, cur, n_adapt, shrink, da,
+                                              mean, m2, minv);
     return cudaGetLastError();
 }
 

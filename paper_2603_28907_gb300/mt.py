@@ -89,6 +89,8 @@ SIGNATURES = {
     "mt_set_hmc": [_vp, C.c_int],
     "mt_set_adapt": [_vp, C.c_double, C.c_int],
     "mt_get_adapt": [_vp, _vp, _vp],
+    "mt_set_metric_adapt": [_vp, C.c_int, C.c_double],
+    "mt_get_metric": [_vp, _vp],
     "mt_set_forward": [_vp, C.c_int, C.c_int, _vp],
     "mt_copula_heights": [_vp, C.c_int, _vp, _vp],
     "mt_nested_rhat": [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, _dp],
@@ -274,6 +276,12 @@ class Context:
 
     def get_adapt(self, eps_out=None, accept_prob_out=None):
         self._ck("mt_get_adapt", self.lib.mt_get_adapt(self.h, _ptr(eps_out), _ptr(accept_prob_out)))
+
+    def set_metric_adapt(self, on, shrink=1e-3):
+        self._ck("mt_set_metric_adapt", self.lib.mt_set_metric_adapt(self.h, int(on), float(shrink)))
+
+    def get_metric(self, inv_metric_out):
+        self._ck("mt_get_metric", self.lib.mt_get_metric(self.h, _ptr(inv_metric_out)))
 
     def set_prior(self, kind):
         self._ck("mt_set_prior", self.lib.mt_set_prior(self.h, int(kind)))

@@ -156,3 +156,93 @@ def test_adapt_settings_and_restart():
         ctx.get_adapt(e1)
     ctx.sync(60.0)
     ctx.close()
+
+
+def test_hmc_metric_warmup_lockstep():
+    """Windowed warm-up of the step size and a diagonal inverse metric (HMC):
+    each step's proposal against the oracle's with the chain's own eps and
+    metric, the acceptance probability within the FP32 band, and the next eps
+    and metric against the oracle's warm-up fed with the GPU's acceptance
+    probabilities and post-step states (metric: FP64 Welford on the same FP32
+    states, 1e-9 relative).  The metric changes once, at the end of the only
+    slow window of a 40-step warm-up (steps 6 .. 35), and stays fixed after."""
+    w = W.small(R=5, Q=7, bases=(40.0, 75.0), G=24, n_zenith=6, n_azimuth=7, n_chains=2)
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    C, eps0, n_leap, Wn, shrink = 2, 0.002, 2, 40, 1e-6
+    ctx.set_hmc(n_leap)
+    ctx.set_adapt(0.8, Wn)
+    ctx.set_metric_adapt(1, shrink)
+    H0 = torch.tensor(W.init_chains(w, C), dtype=torch.float32, device=DEV).contiguous()
+    ctx.init_chains(H0, 21)
+    minv_t = torch.zeros((C,) + tuple(H0.shape[1:]), dtype=torch.float64, device=DEV)
+    with pytest.raises(mt.MtError):
+        ctx.get_metric(minv_t)
+    cur = H0.double().cpu().numpy()
+    prop, llp, lpp, acc, logu = _buffers(H0, C)
+    eps_t = torch.zeros(C, dtype=torch.float64, device=DEV)
+    alpha_t = torch.zeros_like(eps_t)
+    st = torch.zeros_like(H0)
+    wus = [A.Warmup(eps0, 0.8, Wn, cur[c].shape, shrink) for c in range(C)]
+    eps_used, minv_used = np.full(C, eps0), np.ones(cur.shape)
+    logpi = lambda H: op.loglik(H) + op.logprior(H)
+    lp_cur = np.array([logpi(cur[c]) for c in range(C)])
+    band = 0
+    for k in range(Wn + 3):
+        ctx.run(mt.KERNEL_HMC, eps0, 1, 1)
+        ctx.get_last_step(prop, llp, lpp, acc, logu)
+        ctx.get_adapt(eps_t, alpha_t)
+        ctx.get_metric(minv_t)
+        ctx.get_state(st)
+        P, S = prop.double().cpu().numpy(), st.double().cpu().numpy()
+        eps_next, alpha, minv = eps_t.cpu().numpy(), alpha_t.cpu().numpy(), minv_t.cpu().numpy()
+        for c in range(C):
+            q, dk = hmc.propose(op, cur[c], eps_used[c], n_leap, 21, c, k, state=np.float32,
+                                inv_metric=minv_used[c])
+            # the FP32 gradients' error moves the trajectory in proportion to
+            # its length (the adapted eps and metric can make steps of metres)
+            disp = float(np.max(np.abs(q - cur[c])))
+            err = float(np.max(np.abs(P[c] - q)))
+            assert err <= 1e-4 + 1e-4 * disp, (k, c, err, disp, eps_used[c])
+            lq = logpi(P[c]) if np.isfinite(op.logprior(P[c])) else -np.inf
+            a_ref = A.accept_prob(lq - lp_cur[c] + dk, bool(np.isfinite(lq)))
+            band += abs(alpha[c] - a_ref) > 1e-3
+            assert abs(alpha[c] - a_ref) <= 5e-2, (k, c, alpha[c], a_ref)
+            ref = wus[c].update(float(alpha[c]), S[c])
+            assert abs(eps_next[c] - ref) <= 1e-12 * ref, (k, c, eps_next[c], ref)
+            np.testing.assert_allclose(minv[c], wus[c].inv_metric, rtol=1e-9, atol=0)
+            if acc[c].item():
+                lp_cur[c] = lq
+            cur[c] = S[c]
+        if k < 35:
+            assert np.all(minv == 1.0)
+        eps_used, minv_used = eps_next, minv
+    assert not np.all(minv_used == 1.0)
+    ctx.close()
+
+
+def test_metric_settings():
+    w = W.tiny()
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    for bad in ((2, 1e-3), (1, -1.0)):
+        with pytest.raises(mt.MtError):
+            ctx.set_metric_adapt(*bad)
+    ctx.set_adapt(0.8, 10)
+    ctx.set_metric_adapt(1)
+    H0 = torch.tensor(W.init_chains(w), dtype=torch.float32, device=DEV).contiguous()
+    ctx.init_chains(H0, 3)
+    with pytest.raises(mt.MtError):                      # fewer than 20 warm-up steps
+        ctx.run(mt.KERNEL_HMC, 0.002, 1, 1)
+    ctx.set_adapt(0.8, 30)
+    with pytest.raises(mt.MtError):                      # the metric is for HMC
+        ctx.run(mt.KERNEL_MALA, 0.002, 1, 1)
+    ctx.set_hmc(1)
+    ctx.run(mt.KERNEL_HMC, 0.002, 1, 1)
+    m = np.zeros((w.n_chains, w.L, w.R, w.Q))
+    ctx.get_metric(m)
+    assert np.all(m == 1.0)                              # still in the initial buffer
+    ctx.set_metric_adapt(0)
+    ctx.run(mt.KERNEL_HMC, 0.002, 1, 1)
+    with pytest.raises(mt.MtError):
+        ctx.get_metric(m)
+    ctx.sync(60.0)
+    ctx.close()
