@@ -451,15 +451,20 @@ def run_gradient_study(args, local):
     # 3. MALA and HMC vs random walk on 1024 chains: ESS per second of the mean height of each surface
     C = 1024
     H0 = torch.tensor(np.stack([W.geometry(w, [w.seed_init, c]) for c in range(C)]).astype(np.float32), device=dev)
-    # name: (kernel, step, measured steps, adapted warm-up steps toward a target acceptance)
-    runs = {"rw_sigma_0.002": (mt.KERNEL_RW, 0.002, 200, 0), "mala_eps_0.5": (mt.KERNEL_MALA, 0.5, 200, 0),
-            "mala_eps_0.005": (mt.KERNEL_MALA, 0.005, 200, 0),
-            "hmc_eps_0.003_leapfrog_8": (mt.KERNEL_HMC, 0.003, 100, 0),
-            "hmc_adapted_to_0.8_leapfrog_8": (mt.KERNEL_HMC, 0.003, 60, 30)}
+    # name: (kernel, step, measured steps, adapted warm-up steps toward a
+    # target acceptance, diagonal metric adapted in that warm-up)
+    runs = {"rw_sigma_0.002": (mt.KERNEL_RW, 0.002, 200, 0, False),
+            "mala_eps_0.5": (mt.KERNEL_MALA, 0.5, 200, 0, False),
+            "mala_eps_0.005": (mt.KERNEL_MALA, 0.005, 200, 0, False),
+            "hmc_eps_0.003_leapfrog_8": (mt.KERNEL_HMC, 0.003, 100, 0, False),
+            "hmc_adapted_to_0.8_leapfrog_8": (mt.KERNEL_HMC, 0.003, 60, 30, False),
+            "hmc_adapted_to_0.8_with_metric_leapfrog_8": (mt.KERNEL_HMC, 0.003, 60, 100, True)}
     cur = torch.zeros_like(H0)
     c32.set_hmc(8)
-    for name, (kern, step, n_steps, n_adapt) in runs.items():
+    for name, (kern, step, n_steps, n_adapt, metric) in runs.items():
         c32.set_adapt(0.8, n_adapt)
+        # shrinkage target of the metric: (1 mm)^2, the scale of this posterior
+        c32.set_metric_adapt(1 if metric else 0, 1e-6)
         c32.init_chains(H0, w.seed_mcmc)
         c32.run(kern, step, 1, max(1, n_adapt))   # graph, initial gradients, warm-up: untimed
         c32.sync(600.0)
@@ -491,7 +496,13 @@ def run_gradient_study(args, local):
                          ess_per_s_total=float(ess.sum(0).mean() / (t_gpu * (n_steps - burn) / n_steps)))
         if eps_c is not None:
             out[name].update(adapted_steps=n_adapt, eps_min_median_max=eps_c)
+        if metric:
+            m = torch.zeros((C,) + tuple(H0.shape[1:]), dtype=torch.float64, device=dev)
+            c32.get_metric(m)
+            out[name]["inv_metric_sqrt_percentiles_1_50_99_m"] = \
+                np.percentile(m.sqrt().cpu().numpy(), [1, 50, 99]).tolist()
     c32.set_adapt(0.8, 0)
+    c32.set_metric_adapt(0)
     print(json.dumps({"study": "gradient", "workload": w.name, **out}), flush=True)
 
 
