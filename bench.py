@@ -200,6 +200,15 @@ def cpu_baseline(pr, counts, Hs, n_chains_sample):
                       f"{dt:.2f} s wall"}
 
 
+def bench_config(w, C, world):
+    """The workload description both arms print."""
+    return {"workload": w.name, "chains_per_gpu": C, "surfaces": w.L,
+            "grid": [w.R, w.Q], "sensors": w.S, "pixels": w.P, "n_grid": w.G,
+            "precision": "f32 march, f64 reduction", "sampler": "random-walk",
+            "rw_sigma_m": w.rw_sigma, "l2": "flushed (256 MB write) between steps",
+            "parallelism": f"chains sharded, {world} independent rank(s)"}
+
+
 def run_reference(args, w, rank):
     """--impl reference: the FP64 oracle, timed on the host cores, same metric."""
     if rank != 0:
@@ -239,7 +248,7 @@ def run_reference(args, w, rank):
         "unit": "chain-ray/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "chains": w.n_chains, "sampler": "rw"},
+        "config": bench_config(w, w.n_chains, args.gpus),
         "cpu_baseline": {"value": value, "unit": "chain-ray/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "chain-ray/s", "h2d_bytes_per_step": 0,
@@ -776,11 +785,7 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "chains_per_gpu": C, "surfaces": w.L,
-                       "grid": [w.R, w.Q], "sensors": w.S, "pixels": w.P, "n_grid": w.G,
-                       "precision": "f32 march, f64 reduction", "sampler": "random-walk",
-                       "rw_sigma_m": w.rw_sigma, "l2": "flushed (256 MB write) between steps",
-                       "parallelism": f"chains sharded, {world} independent rank(s)"},
+            "config": bench_config(w, C, world),
             "mcmc_chain_steps_per_s": C * world * args.steps / (ms / 1e3),
             "acceptance": float(acc.double().mean().item()) / (args.warmup + args.steps),
             "gpu_launches": 5 * args.steps,
