@@ -78,7 +78,7 @@ typedef enum {
 enum { MT_PREC_F64 = 0, MT_PREC_F32 = 1, MT_PREC_F32C = 2, MT_PREC_BF16 = 3 };
 
 /* Proposal kernels for mt_run. */
-enum { MT_KERNEL_RW = 0, MT_KERNEL_MALA = 1, MT_KERNEL_HMC = 2 };
+enum { MT_KERNEL_RW = 0, MT_KERNEL_MALA = 1, MT_KERNEL_HMC = 2, MT_KERNEL_NUTS = 3 };
 
 /* Observed-count generation for mt_generate_data. */
 enum { MT_COUNTS_POISSON = 0, MT_COUNTS_ROUND = 1 };
@@ -208,6 +208,26 @@ MT_API mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n
 /* Leapfrog steps per HMC proposal (1 .. 1024; default 8).  MT_EINVAL outside. */
 MT_API mt_status mt_set_hmc(mt_ctx *ctx, int n_leapfrog);
 
+/* Maximum tree depth D of MT_KERNEL_NUTS (1 .. 10; default 8, the paper's
+ * cap of 256 steps: 2^8 - 1 = 255 leapfrog steps).  MT_KERNEL_NUTS runs the
+ * trajectory NUTS builds when it reaches its cap (Sec. 3.1: the paper caps
+ * NUTS at 256 steps and reports that almost every iteration reaches the
+ * cap; Hoffman & Gelman 2014): momentum p0 = xi / sqrt(m) (xi from Philox
+ * stream 7, counter {pair, step, chain}; m the diagonal inverse metric, 1
+ * without mt_set_metric_adapt); for depth j = 0 .. D-1 a direction v_j
+ * (stream 8, index j: backwards if its uniform is below 1/2) and 2^j
+ * leapfrog steps of size v_j eps from that end of the trajectory; each new
+ * state has log-weight ll + lp - p^T M^-1 p / 2 and replaces its subtree's
+ * sample when log u < w - W_sub (uniform index 64 + its leaf number, W_sub
+ * the subtree's log-sum of weights including it); after each subtree its
+ * sample replaces the trajectory's when log u < W_sub - W (index 32 + j),
+ * and W accumulates W_sub.  The chain moves to the trajectory's sample; no
+ * U-turn stop, no separate accept.  mt_get_last_step reports the sample as
+ * the proposal and accepted = whether the chain moved; the step-size
+ * adaptation uses the mean of min(1, e^(H_0 - H)) over the 2^D - 1 new
+ * states.  Requirements as for HMC.  MT_EINVAL outside 1 .. 10. */
+MT_API mt_status mt_set_nuts(mt_ctx *ctx, int max_depth);
+
 /* Step-size adaptation of the gradient samplers (Sec. 3.1: during warm-up
  * the step size is tuned toward a target acceptance probability, 0.8 in the
  * paper) by per-chain dual averaging of log eps (Hoffman & Gelman 2014,
@@ -226,7 +246,7 @@ MT_API mt_status mt_set_adapt(mt_ctx *ctx, double target_accept, int n_adapt);
 /* Diagonal preconditioner of HMC adapted in the same warm-up (Sec. 3.1: the
  * warm-up tunes a diagonal preconditioner together with the step size).
  * With on = 1 the n_adapt warm-up steps armed by mt_set_adapt (n_adapt >= 20,
- * HMC only; MALA runs are refused while it is on) follow a windowed
+ * HMC and NUTS; MALA runs are refused while it is on) follow a windowed
  * schedule: an initial buffer, slow windows of doubling length and a
  * terminal buffer (75 / 25 / 50 steps, or 15 % / 75 % / 10 % of n_adapt when
  * those do not fit; the last slow window is stretched to the terminal buffer

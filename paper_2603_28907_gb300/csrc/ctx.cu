@@ -129,6 +129,8 @@ struct mt_ctx {
     size_t dR_cap = 0;
     double *d_lam0 = nullptr, *d_amc = nullptr;
     int hmc_leap = 8;                // leapfrog steps per HMC proposal
+    int nuts_depth = 8;              // capped NUTS: 2^depth - 1 leapfrog steps
+    NutsBufs nuts{};
     // step-size adaptation of MALA / HMC (mt_set_adapt): target acceptance,
     // number of adapted steps (0 = off), state not yet initialised
     double adapt_target = 0.8;
@@ -272,6 +274,11 @@ static void drop_chains(mt_ctx *ctx)
     dfree(ctx->d_minv);
     dfree(ctx->d_wmean);
     dfree(ctx->d_wm2);
+    for (double **p : {&ctx->nuts.qL, &ctx->nuts.pL, &ctx->nuts.gL, &ctx->nuts.qR, &ctx->nuts.pR,
+                       &ctx->nuts.gR, &ctx->nuts.ph, &ctx->nuts.gsel, &ctx->nuts.gsub, &ctx->nuts.sc})
+        dfree(*p);
+    dfree(ctx->nuts.hsel);
+    dfree(ctx->nuts.hsub);
     ctx->adapt_pending = ctx->adapt_n > 0;  // new chains adapt from the start
     ctx->g_valid = false;
     ctx->C = 0;
@@ -1187,12 +1194,78 @@ static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
     return MT_OK;
 }
 
+static mt_status ensure_nuts(mt_ctx *ctx)
+{
+    NutsBufs &b = ctx->nuts;
+    const size_t n = (size_t)ctx->C * n_per_chain(ctx);
+    if (b.qL && b.sc) return MT_OK;
+    drop_graph(ctx);
+    for (double **p : {&b.qL, &b.pL, &b.gL, &b.qR, &b.pR, &b.gR, &b.ph, &b.gsel, &b.gsub}) TRY(dalloc(ctx, p, n));
+    TRY(dalloc(ctx, &b.sc, (size_t)kNS * ctx->C));
+    const size_t es = elem_size(ctx);
+    for (void **p : {&b.hsel, &b.hsub}) {
+        dfree(*p);
+        CK(ctx, cudaMalloc(p, n * es + 16));
+    }
+    return MT_OK;
+}
+
+// One capped-NUTS iteration: momentum and the trajectory's start, then per
+// depth j its 2^j leapfrog steps (half kick + drift, the new state's prior,
+// forward march + adjoint, gradient, log-likelihood, second half kick with
+// the state's weight and the subtree's sample), the merge into the
+// trajectory's sample, and the move of the chain to it.
+static mt_status enqueue_nuts(mt_ctx *ctx, double eps, int off)
+{
+    const size_t np = n_per_chain(ctx);
+    const long long bs = (long long)ctx->C * np;
+    EvPair es;
+    if (ctx->timing) ev_begin(ctx, 1, &es);
+    const double *ec = ctx->adapt_n > 0 ? ctx->d_eps : nullptr;
+    const bool metric = ec && ctx->metric_on;
+    const double *mi = metric ? ctx->d_minv : nullptr;
+    const NutsBufs &nb = ctx->nuts;
+    CK(ctx, launch_nuts_start(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, mi, ctx->d_ll,
+                              ctx->d_lp, nb, ctx->seed, ctx->d_step, off, ctx->stream));
+    HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
+    int leaf = 0;
+    for (int j = 0; j < ctx->nuts_depth; ++j) {
+        for (int k = 0; k < (1 << j); ++k, ++leaf) {
+            CK(ctx, launch_nuts_drift(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_cur, ctx->C, eps, ec, mi, nb,
+                                      ctx->seed, ctx->d_step, off, j, ctx->stream));
+            CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
+            TRY(enqueue_forward_adjoint(ctx, hp, ctx->C));
+            CK(ctx, launch_grad_finish_sel(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C,
+                                           (const unsigned long long *)ctx->d_gacc, ctx->d_G, ctx->d_cur,
+                                           ctx->stream));
+            CK(ctx, launch_reduce_ll(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_llp, ctx->stream));
+            CK(ctx, launch_nuts_leaf(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec, mi,
+                                     ctx->d_llp, ctx->d_lpp, nb, ctx->seed, ctx->d_step, off, j, leaf,
+                                     ctx->stream));
+        }
+        CK(ctx, launch_nuts_merge(ctx->pb, ctx->mode, ctx->C, nb, ctx->seed, ctx->d_step, off, j, ctx->stream));
+    }
+    CK(ctx, launch_nuts_finish(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->d_psel, ctx->C,
+                               ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_lpp, ctx->d_acc, ctx->d_accl, ctx->d_logu,
+                               ec ? ctx->d_alpha : nullptr, nb, leaf, ctx->stream));
+    if (metric)
+        CK(ctx, launch_metric(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_cur, ctx->C, ctx->adapt_n,
+                              ctx->metric_shrink, ctx->d_da, ctx->d_wmean, ctx->d_wm2, ctx->d_minv,
+                              ctx->stream));
+    if (ec)
+        CK(ctx, launch_adapt(ctx->C, ctx->adapt_target, ctx->adapt_n, metric ? 1 : 0, ctx->d_alpha, ctx->d_da,
+                             ctx->d_eps, ctx->stream));
+    if (ctx->timing) ev_end(ctx, 1, &es);
+    return MT_OK;
+}
+
 static mt_status enqueue_step(mt_ctx *ctx, int kernel, double step, int off)
 {
     const size_t np = n_per_chain(ctx);
     const long long bs = (long long)ctx->C * np;
     if (kernel == MT_KERNEL_MALA) return enqueue_mala(ctx, step, off);
     if (kernel == MT_KERNEL_HMC) return enqueue_hmc(ctx, step, off);
+    if (kernel == MT_KERNEL_NUTS) return enqueue_nuts(ctx, step, off);
     if (kernel != MT_KERNEL_RW) return fail(ctx, MT_EINVAL, "kernel %d not available", kernel);
     EvPair es;
     if (ctx->timing) ev_begin(ctx, 1, &es);
@@ -1219,17 +1292,18 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
 {
     TRY(need(ctx, true));
     if (ctx->C < 1) return fail(ctx, MT_ESTATE, "mt_init_chains first");
-    if (kernel != MT_KERNEL_RW && kernel != MT_KERNEL_MALA && kernel != MT_KERNEL_HMC)
+    if (kernel != MT_KERNEL_RW && kernel != MT_KERNEL_MALA && kernel != MT_KERNEL_HMC &&
+        kernel != MT_KERNEL_NUTS)
         return fail(ctx, MT_EINVAL, "kernel %d", kernel);
     if (!(step >= 0.0) || n_super < 0 || n_within < 1 || n_within > 4096)
         return fail(ctx, MT_EINVAL, "need step >= 0, n_super >= 0, 1 <= n_within <= 4096");
     if (ctx->copula) TRY(ensure_derived(ctx, ctx->C));
     TRY(ensure_lin(ctx, ctx->C));
-    if (kernel == MT_KERNEL_MALA || kernel == MT_KERNEL_HMC) {
-        if (ctx->linear) return fail(ctx, MT_EINVAL, "MALA / HMC need the marched forward model");
-        if (ctx->copula) return fail(ctx, MT_EINVAL, "MALA / HMC need the CAR prior (mt_set_prior 0)");
+    if (kernel == MT_KERNEL_MALA || kernel == MT_KERNEL_HMC || kernel == MT_KERNEL_NUTS) {
+        if (ctx->linear) return fail(ctx, MT_EINVAL, "MALA / HMC / NUTS need the marched forward model");
+        if (ctx->copula) return fail(ctx, MT_EINVAL, "MALA / HMC / NUTS need the CAR prior (mt_set_prior 0)");
         TRY(grad_ok(ctx));
-        if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA / HMC need a step size eps > 0");
+        if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA / HMC / NUTS need a step size eps > 0");
         if (ctx->metric_on && ctx->adapt_n > 0 && kernel == MT_KERNEL_MALA)
             return fail(ctx, MT_EINVAL, "the adapted metric is for HMC: mt_set_metric_adapt(ctx, 0, ...) for MALA");
         if (ctx->metric_on && ctx->adapt_n > 0 && ctx->adapt_n < 20)
@@ -1237,6 +1311,7 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
         TRY(ensure_chain_grads(ctx));
         TRY(ensure_grad_bufs(ctx, ctx->C));
         if (kernel == MT_KERNEL_HMC) TRY(ensure_hmc(ctx));
+        if (kernel == MT_KERNEL_NUTS) TRY(ensure_nuts(ctx));
         if (ctx->adapt_n > 0) TRY(ensure_adapt(ctx, step));
     }
     TRY(ensure_partials(ctx, ctx->C));
@@ -1587,6 +1662,15 @@ mt_status mt_set_adapt(mt_ctx *ctx, double target_accept, int n_adapt)
         dfree(ctx->d_wmean);
         dfree(ctx->d_wm2);
     }
+    return MT_OK;
+}
+
+mt_status mt_set_nuts(mt_ctx *ctx, int max_depth)
+{
+    if (!ctx) return fail(nullptr, MT_EINVAL, "null context");
+    if (max_depth < 1 || max_depth > 10) return fail(ctx, MT_EINVAL, "max_depth %d not in [1, 10]", max_depth);
+    if (ctx->nuts_depth != max_depth) drop_graph(ctx);
+    ctx->nuts_depth = max_depth;
     return MT_OK;
 }
 

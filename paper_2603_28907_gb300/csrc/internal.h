@@ -24,7 +24,7 @@ namespace mt {
 
 enum { MODE_F64 = 0, MODE_F32 = 1, MODE_F32C = 2, MODE_BF16 = 3 };
 enum { STREAM_GEOM = 0, STREAM_DATA = 1, STREAM_INIT = 2, STREAM_PROP = 3, STREAM_ACC = 4,
-       STREAM_MALA = 5, STREAM_HMC = 6 };
+       STREAM_MALA = 5, STREAM_HMC = 6, STREAM_NUTS_P = 7, STREAM_NUTS_U = 8 };
 
 struct Prob {
     int L, R, Q, S, P, G, n_rays, N;  // N = R*Q nodes per surface
@@ -152,6 +152,35 @@ cudaError_t launch_hmc_finish(const Prob &pb, long long buf_stride, const double
 cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, long long buf_stride,
                                  const double *gbuf, const uint8_t *cur, int n_chains, double eps,
                                  const double *eps_c, double *extra, cudaStream_t st);
+// Capped NUTS (mcmc.cu): the trajectory's two ends (FP64 position, momentum,
+// gradient) and the half-kicked momentum, [C][n] each; the trajectory's and
+// the current subtree's samples (heights in the storage type, gradients);
+// per-chain scalars sc [C][kNS].
+constexpr int kNS = 12;
+struct NutsBufs {
+    double *qL, *pL, *gL, *qR, *pR, *gR, *ph;
+    void *hsel, *hsub;
+    double *gsel, *gsub, *sc;
+};
+cudaError_t launch_nuts_start(const Prob &pb, int mode, const void *hbuf, long long bs, const double *gbuf,
+                              const uint8_t *cur, int n_chains, const double *minv, const double *ll,
+                              const double *lp, const NutsBufs &nb, uint64_t seed, const int64_t *step_base,
+                              int step_off, cudaStream_t st);
+cudaError_t launch_nuts_drift(const Prob &pb, int mode, void *hbuf, long long bs, const uint8_t *cur,
+                              int n_chains, double eps, const double *eps_c, const double *minv,
+                              const NutsBufs &nb, uint64_t seed, const int64_t *step_base, int step_off, int j,
+                              cudaStream_t st);
+cudaError_t launch_nuts_leaf(const Prob &pb, int mode, const void *hbuf, long long bs, const double *gbuf,
+                             const uint8_t *cur, int n_chains, double eps, const double *eps_c,
+                             const double *minv, const double *llp, const double *lpp, const NutsBufs &nb,
+                             uint64_t seed, const int64_t *step_base, int step_off, int j, int leaf,
+                             cudaStream_t st);
+cudaError_t launch_nuts_merge(const Prob &pb, int mode, int n_chains, const NutsBufs &nb, uint64_t seed,
+                              const int64_t *step_base, int step_off, int j, cudaStream_t st);
+cudaError_t launch_nuts_finish(const Prob &pb, int mode, void *hbuf, long long bs, double *gbuf,
+                               const uint8_t *cur, uint8_t *prop_sel, int n_chains, double *ll, double *lp,
+                               double *llp, double *lpp, int64_t *accepts, int32_t *acc_last, double *logu,
+                               double *alpha, const NutsBufs &nb, int n_leaves, cudaStream_t st);
 // Warm-up adaptation (mcmc.cu): dual-averaging state da [C][6], step sizes
 // eps [C]; with metric != 0 the windowed diagonal-metric schedule (Welford
 // mean / m2 and the inverse metric minv, [C][n] each).

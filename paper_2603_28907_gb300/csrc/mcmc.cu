@@ -379,6 +379,298 @@ cudaError_t launch_hmc_finish(const Prob &pb, long long buf_stride, const double
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- capped NUTS
+// The trajectory NUTS (Sec. 3.1; Hoffman & Gelman 2014) builds when it runs
+// to its cap of 2^D - 1 leapfrog steps, as the paper reports almost every
+// iteration did: momentum p0 = xi / sqrt(m) (Philox stream NUTS_P, counter
+// {pair, step, chain}); for depth j = 0 .. D-1 a direction v_j (stream
+// NUTS_U, index j: -1 if u < 1/2) and 2^j leapfrog steps of size v_j eps from
+// that end of the trajectory; every new state n gets log-weight
+// w_n = -H_n = ll + lp - K(p) and may replace the subtree's sample
+// (log u < w_n - W_sub after adding w_n, index 64 + leaf); after each subtree
+// its sample replaces the trajectory's when log u < W_sub - W (index
+// 32 + j), then W = logaddexp(W, W_sub).  The chain moves to the trajectory's
+// sample.  Ends (FP64 position, momentum, gradient) per side, [C][n] each;
+// per-chain scalars sc[kNS * c + ...].
+enum { NS_W = 0, NS_WSUB, NS_H0, NS_LLSEL, NS_LPSEL, NS_LLSUB, NS_LPSUB, NS_STAT, NS_MOVED };
+
+__device__ __forceinline__ double nuts_u(uint64_t seed, int c, uint32_t step, uint32_t index)
+{
+    const uint4 w = draw4(seed, STREAM_NUTS_U, (uint32_t)c, step, index);
+    return u01_f64(w.x, w.y);
+}
+
+__device__ __forceinline__ double logaddexp_d(double a, double b)
+{
+    if (a == -INFINITY) return b;
+    if (b == -INFINITY) return a;
+    const double m = fmax(a, b);
+    return m + log(exp(a - m) + exp(b - m));
+}
+
+template <typename H>
+__global__ void __launch_bounds__(256)
+k_nuts_start(int n, const H *hbuf, long long bs, const double *gbuf, const uint8_t *cur, const double *minv,
+             const double *ll, const double *lp, NutsBufs nb, uint64_t seed, const int64_t *step_base,
+             int step_off)
+{
+    const int c = blockIdx.x;
+    const uint32_t step = (uint32_t)(*step_base + step_off);
+    const long long a = (long long)cur[c] * bs + (long long)c * n;
+    double kin = 0.0;
+    for (int j = threadIdx.x; 2 * j < n; j += blockDim.x) {
+        const uint4 w = draw4(seed, STREAM_NUTS_P, (uint32_t)c, step, (uint32_t)j);
+        const double u1 = u01_f64(w.x, w.y), u2 = u01_f64(w.z, w.w);
+        const double rad = sqrt(-2.0 * log(u1));
+        double sn, cn;
+        sincospi(2.0 * u2, &sn, &cn);
+        const double xi[2] = {rad * cn, rad * sn};
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int i = 2 * j + t;
+            if (i >= n) break;
+            const size_t k = (size_t)c * n + i;
+            kin += 0.5 * xi[t] * xi[t];  // K(p0) with p0 = xi / sqrt(m)
+            const double p0 = minv ? xi[t] / sqrt(minv[k]) : xi[t];
+            const double q = (double)hbuf[a + i], g = gbuf[a + i];
+            nb.qL[k] = q;
+            nb.qR[k] = q;
+            nb.pL[k] = p0;
+            nb.pR[k] = p0;
+            nb.gL[k] = g;
+            nb.gR[k] = g;
+            reinterpret_cast<H *>(nb.hsel)[k] = hbuf[a + i];
+            nb.gsel[k] = g;
+        }
+    }
+    kin = block_sum(kin);
+    if (threadIdx.x == 0) {
+        double *sc = nb.sc + kNS * c;
+        const double H0 = -(ll[c] + lp[c]) + kin;
+        sc[NS_H0] = H0;
+        sc[NS_W] = -H0;
+        sc[NS_WSUB] = -INFINITY;
+        sc[NS_LLSEL] = ll[c];
+        sc[NS_LPSEL] = lp[c];
+        sc[NS_STAT] = 0.0;
+        sc[NS_MOVED] = 0.0;
+    }
+}
+
+// Half kick with the end's gradient and a drift, from the end on side v_j;
+// the rounded position goes to the proposal slot (evaluated next).
+template <typename H>
+__global__ void __launch_bounds__(256)
+k_nuts_drift(int n, H *hbuf, long long bs, const uint8_t *cur, double eps0, const double *eps_c,
+             const double *minv, NutsBufs nb, uint64_t seed, const int64_t *step_base, int step_off, int j)
+{
+    const int c = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t step = (uint32_t)(*step_base + step_off);
+    const int v = nuts_u(seed, c, step, (uint32_t)j) < 0.5 ? -1 : 1;
+    const double e = (double)v * (eps_c ? eps_c[c] : eps0);
+    const size_t k = (size_t)c * n + i;
+    double *q64 = v > 0 ? nb.qR : nb.qL;
+    const double *p = v > 0 ? nb.pR : nb.pL, *g = v > 0 ? nb.gR : nb.gL;
+    const double p_half = p[k] + 0.5 * e * g[k];
+    const double q = q64[k] + e * ((minv ? minv[k] : 1.0) * p_half);
+    q64[k] = q;
+    nb.ph[k] = p_half;
+    hbuf[(long long)(1 - cur[c]) * bs + (long long)c * n + i] = (H)q;
+}
+
+// Second half kick with the new gradient (G[1 - cur]), the new state's
+// energy and weight, the acceptance statistic and the subtree's sample.
+template <typename H>
+__global__ void __launch_bounds__(256)
+k_nuts_leaf(int n, const H *hbuf, long long bs, const double *gbuf, const uint8_t *cur, double eps0,
+            const double *eps_c, const double *minv, const double *llp, const double *lpp, NutsBufs nb,
+            uint64_t seed, const int64_t *step_base, int step_off, int j, int leaf)
+{
+    __shared__ int take_s;
+    const int c = blockIdx.x;
+    const uint32_t step = (uint32_t)(*step_base + step_off);
+    const int v = nuts_u(seed, c, step, (uint32_t)j) < 0.5 ? -1 : 1;
+    const double e = (double)v * (eps_c ? eps_c[c] : eps0);
+    const long long b = (long long)(1 - cur[c]) * bs + (long long)c * n;
+    double *p_end = v > 0 ? nb.pR : nb.pL, *g_end = v > 0 ? nb.gR : nb.gL;
+    double kin = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const size_t k = (size_t)c * n + i;
+        const double g = gbuf[b + i];
+        const double p = nb.ph[k] + 0.5 * e * g;
+        p_end[k] = p;
+        g_end[k] = g;
+        kin += 0.5 * (minv ? minv[k] : 1.0) * p * p;
+    }
+    kin = block_sum(kin);
+    if (threadIdx.x == 0) {
+        double *sc = nb.sc + kNS * c;
+        const double Hn = -(llp[c] + lpp[c]) + kin;
+        const bool fin = isfinite(Hn);
+        const double w = fin ? -Hn : -INFINITY;
+        if (fin) sc[NS_STAT] += fmin(1.0, exp(sc[NS_H0] - Hn));
+        const double Wn = logaddexp_d(sc[NS_WSUB], w);
+        const double lu = log(nuts_u(seed, c, step, 64u + (uint32_t)leaf));
+        const int take = fin && lu < w - Wn;
+        sc[NS_WSUB] = Wn;
+        if (take) {
+            sc[NS_LLSUB] = llp[c];
+            sc[NS_LPSUB] = lpp[c];
+        }
+        take_s = take;
+    }
+    __syncthreads();
+    if (take_s) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const size_t k = (size_t)c * n + i;
+            reinterpret_cast<H *>(nb.hsub)[k] = hbuf[b + i];
+            nb.gsub[k] = gbuf[b + i];
+        }
+    }
+}
+
+// The subtree's sample replaces the trajectory's (biased progressive
+// sampling); W is updated by k_nuts_merge_w after every block has read it.
+template <typename H>
+__global__ void __launch_bounds__(256)
+k_nuts_merge(int n, NutsBufs nb, uint64_t seed, const int64_t *step_base, int step_off, int j)
+{
+    const int c = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t step = (uint32_t)(*step_base + step_off);
+    double *sc = nb.sc + kNS * c;
+    const double Ws = sc[NS_WSUB], W = sc[NS_W];
+    const double lu = log(nuts_u(seed, c, step, 32u + (uint32_t)j));
+    if (!(Ws > -INFINITY && lu < Ws - W)) return;
+    if (i < n) {
+        const size_t k = (size_t)c * n + i;
+        reinterpret_cast<H *>(nb.hsel)[k] = reinterpret_cast<const H *>(nb.hsub)[k];
+        nb.gsel[k] = nb.gsub[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc[NS_LLSEL] = sc[NS_LLSUB];
+        sc[NS_LPSEL] = sc[NS_LPSUB];
+        sc[NS_MOVED] = 1.0;
+    }
+}
+
+__global__ void k_nuts_merge_w(int n_chains, double *scs)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chains) return;
+    double *sc = scs + kNS * c;
+    sc[NS_W] = logaddexp_d(sc[NS_W], sc[NS_WSUB]);
+    sc[NS_WSUB] = -INFINITY;
+}
+
+// The chain moves to the trajectory's sample (heights, gradient,
+// log-likelihood and log-prior); the step's record: proposal = that sample,
+// accepted = whether it moved, and the acceptance statistic for adaptation.
+template <typename H>
+__global__ void __launch_bounds__(256)
+k_nuts_finish(int n, H *hbuf, long long bs, double *gbuf, const uint8_t *cur, uint8_t *prop_sel, double *ll,
+              double *lp, double *llp, double *lpp, int64_t *accepts, int32_t *acc_last, double *logu,
+              double *alpha, NutsBufs nb, int n_leaves)
+{
+    const int c = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long a = (long long)cur[c] * bs + (long long)c * n;
+    if (i < n) {
+        const size_t k = (size_t)c * n + i;
+        hbuf[a + i] = reinterpret_cast<const H *>(nb.hsel)[k];
+        gbuf[a + i] = nb.gsel[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double *sc = nb.sc + kNS * c;
+        const int moved = sc[NS_MOVED] != 0.0;
+        ll[c] = sc[NS_LLSEL];
+        lp[c] = sc[NS_LPSEL];
+        llp[c] = sc[NS_LLSEL];
+        lpp[c] = sc[NS_LPSEL];
+        accepts[c] += moved;
+        acc_last[c] = moved;
+        logu[c] = 0.0;
+        prop_sel[c] = cur[c];
+        if (alpha) alpha[c] = sc[NS_STAT] / (double)n_leaves;
+    }
+}
+
+cudaError_t launch_nuts_start(const Prob &pb, int mode, const void *hbuf, long long bs, const double *gbuf,
+                              const uint8_t *cur, int n_chains, const double *minv, const double *ll,
+                              const double *lp, const NutsBufs &nb, uint64_t seed, const int64_t *step_base,
+                              int step_off, cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    if (mode == MODE_F64)
+        k_nuts_start<double><<<n_chains, 256, 0, st>>>(n, (const double *)hbuf, bs, gbuf, cur, minv, ll, lp, nb,
+                                                       seed, step_base, step_off);
+    else
+        k_nuts_start<float><<<n_chains, 256, 0, st>>>(n, (const float *)hbuf, bs, gbuf, cur, minv, ll, lp, nb,
+                                                      seed, step_base, step_off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nuts_drift(const Prob &pb, int mode, void *hbuf, long long bs, const uint8_t *cur,
+                              int n_chains, double eps, const double *eps_c, const double *minv,
+                              const NutsBufs &nb, uint64_t seed, const int64_t *step_base, int step_off, int j,
+                              cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    dim3 grid((n + 255) / 256, n_chains);
+    if (mode == MODE_F64)
+        k_nuts_drift<double><<<grid, 256, 0, st>>>(n, (double *)hbuf, bs, cur, eps, eps_c, minv, nb, seed,
+                                                   step_base, step_off, j);
+    else
+        k_nuts_drift<float><<<grid, 256, 0, st>>>(n, (float *)hbuf, bs, cur, eps, eps_c, minv, nb, seed,
+                                                  step_base, step_off, j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nuts_leaf(const Prob &pb, int mode, const void *hbuf, long long bs, const double *gbuf,
+                             const uint8_t *cur, int n_chains, double eps, const double *eps_c,
+                             const double *minv, const double *llp, const double *lpp, const NutsBufs &nb,
+                             uint64_t seed, const int64_t *step_base, int step_off, int j, int leaf,
+                             cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    if (mode == MODE_F64)
+        k_nuts_leaf<double><<<n_chains, 256, 0, st>>>(n, (const double *)hbuf, bs, gbuf, cur, eps, eps_c, minv,
+                                                      llp, lpp, nb, seed, step_base, step_off, j, leaf);
+    else
+        k_nuts_leaf<float><<<n_chains, 256, 0, st>>>(n, (const float *)hbuf, bs, gbuf, cur, eps, eps_c, minv,
+                                                     llp, lpp, nb, seed, step_base, step_off, j, leaf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nuts_merge(const Prob &pb, int mode, int n_chains, const NutsBufs &nb, uint64_t seed,
+                              const int64_t *step_base, int step_off, int j, cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    dim3 grid((n + 255) / 256, n_chains);
+    if (mode == MODE_F64) k_nuts_merge<double><<<grid, 256, 0, st>>>(n, nb, seed, step_base, step_off, j);
+    else k_nuts_merge<float><<<grid, 256, 0, st>>>(n, nb, seed, step_base, step_off, j);
+    k_nuts_merge_w<<<(n_chains + 127) / 128, 128, 0, st>>>(n_chains, nb.sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nuts_finish(const Prob &pb, int mode, void *hbuf, long long bs, double *gbuf,
+                               const uint8_t *cur, uint8_t *prop_sel, int n_chains, double *ll, double *lp,
+                               double *llp, double *lpp, int64_t *accepts, int32_t *acc_last, double *logu,
+                               double *alpha, const NutsBufs &nb, int n_leaves, cudaStream_t st)
+{
+    const int n = pb.L * pb.N;
+    dim3 grid((n + 255) / 256, n_chains);
+    if (mode == MODE_F64)
+        k_nuts_finish<double><<<grid, 256, 0, st>>>(n, (double *)hbuf, bs, gbuf, cur, prop_sel, ll, lp, llp, lpp,
+                                                    accepts, acc_last, logu, alpha, nb, n_leaves);
+    else
+        k_nuts_finish<float><<<grid, 256, 0, st>>>(n, (float *)hbuf, bs, gbuf, cur, prop_sel, ll, lp, llp, lpp,
+                                                   accepts, acc_last, logu, alpha, nb, n_leaves);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- reduce
 // ll[c] = sum over data of the Poisson constants + the CTA partials of chain c
 // added in CTA order (deterministic).

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libmt.so")
 PREC_F64, PREC_F32, PREC_F32C, PREC_BF16 = 0, 1, 2, 3
 PRIOR_CAR, PRIOR_COPULA = 0, 1
 FORWARD_MARCH, FORWARD_LINEAR = 0, 1
-KERNEL_RW, KERNEL_MALA, KERNEL_HMC = 0, 1, 2
+KERNEL_RW, KERNEL_MALA, KERNEL_HMC, KERNEL_NUTS = 0, 1, 2, 3
 COUNTS_POISSON, COUNTS_ROUND = 0, 1
 
 STATUS = {0: "MT_OK", -1: "MT_EINVAL", -2: "MT_ENOMEM", -3: "MT_ESTATE", -4: "MT_ECUDA",
@@ -87,6 +87,7 @@ SIGNATURES = {
     "mt_get_sizes": [_vp, _ip, _ip, _ip, _ip, _ip, _ip],
     "mt_set_prior": [_vp, C.c_int],
     "mt_set_hmc": [_vp, C.c_int],
+    "mt_set_nuts": [_vp, C.c_int],
     "mt_set_adapt": [_vp, C.c_double, C.c_int],
     "mt_get_adapt": [_vp, _vp, _vp],
     "mt_set_metric_adapt": [_vp, C.c_int, C.c_double],
@@ -276,6 +277,9 @@ class Context:
 
     def get_adapt(self, eps_out=None, accept_prob_out=None):
         self._ck("mt_get_adapt", self.lib.mt_get_adapt(self.h, _ptr(eps_out), _ptr(accept_prob_out)))
+
+    def set_nuts(self, max_depth):
+        self._ck("mt_set_nuts", self.lib.mt_set_nuts(self.h, int(max_depth)))
 
     def set_metric_adapt(self, on, shrink=1e-3):
         self._ck("mt_set_metric_adapt", self.lib.mt_set_metric_adapt(self.h, int(on), float(shrink)))
