@@ -467,9 +467,11 @@ def run_gradient_study(args, local):
             "mala_eps_0.005": (mt.KERNEL_MALA, 0.005, 200, 0, False),
             "hmc_eps_0.003_leapfrog_8": (mt.KERNEL_HMC, 0.003, 100, 0, False),
             "hmc_adapted_to_0.8_leapfrog_8": (mt.KERNEL_HMC, 0.003, 60, 30, False),
-            "hmc_adapted_to_0.8_with_metric_leapfrog_8": (mt.KERNEL_HMC, 0.003, 60, 100, True)}
+            "hmc_adapted_to_0.8_with_metric_leapfrog_8": (mt.KERNEL_HMC, 0.003, 60, 100, True),
+            "nuts_depth_4_adapted_to_0.8_with_metric": (mt.KERNEL_NUTS, 0.003, 30, 40, True)}
     cur = torch.zeros_like(H0)
     c32.set_hmc(8)
+    c32.set_nuts(4)
     for name, (kern, step, n_steps, n_adapt, metric) in runs.items():
         c32.set_adapt(0.8, n_adapt)
         # shrinkage target of the metric: (1 mm)^2, the scale of this posterior
