@@ -385,9 +385,9 @@ __device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, float2 kf2, f
     const float2 tx = add2(gx, M2), ty = add2(gy, M2);
     const float2 fx = add2(fma2(add2(tx, f2(-12582912.0f)), f2(-1.0f), gx), f2(0.5f));  // in [0, 1]
     const float2 fy = add2(fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy), f2(0.5f));
-    const int nA = (__float_as_int(ty.x) - 0x4B400000) * Q + (__float_as_int(tx.x) - 0x4B400000);
-    const int nB = (__float_as_int(ty.y) - 0x4B400000) * Q + (__float_as_int(tx.y) - 0x4B400000);
     if constexpr (GLOBAL) {
+        const int nA = (__float_as_int(ty.x) - 0x4B400000) * Q + (__float_as_int(tx.x) - 0x4B400000);
+        const int nB = (__float_as_int(ty.y) - 0x4B400000) * Q + (__float_as_int(tx.y) - 0x4B400000);
         if (nA != curA || nB != curB) {
             curA = nA;
             curB = nB;
@@ -398,13 +398,19 @@ __device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, float2 kf2, f
         }
     } else {
         // reload both samples' corner records when either entered a new cell:
-        // predicated shared loads instead of a divergent branch
-        const uint32_t need = (uint32_t)((nA != curA) | (nB != curB));
-        curA = nA;
-        curB = nB;
+        // predicated shared loads instead of a divergent branch.  The record's
+        // byte address 8 (Q iy + ix) + base comes straight from the float bits
+        // (ix = bits(tx) - 0x4B400000, likewise iy), modulo 2^32; the current
+        // cells are tracked by address (-1 is never one).
         const uint32_t base = (uint32_t)__cvta_generic_to_shared(pl);
-        const uint32_t aA0 = base + (uint32_t)nA * 8u, aA1 = aA0 + (uint32_t)Q * 8u;
-        const uint32_t aB0 = base + (uint32_t)nB * 8u, aB1 = aB0 + (uint32_t)Q * 8u;
+        const uint32_t k0 = base - 8u * 0x4B400000u * (uint32_t)(Q + 1);
+        const uint32_t rowb = 8u * (uint32_t)Q;
+        const uint32_t aA0 = (uint32_t)__float_as_int(ty.x) * rowb + ((uint32_t)__float_as_int(tx.x) * 8u + k0);
+        const uint32_t aB0 = (uint32_t)__float_as_int(ty.y) * rowb + ((uint32_t)__float_as_int(tx.y) * 8u + k0);
+        const uint32_t aA1 = aA0 + rowb, aB1 = aB0 + rowb;
+        const uint32_t need = (uint32_t)(((int)aA0 != curA) | ((int)aB0 != curB));
+        curA = (int)aA0;
+        curB = (int)aB0;
         asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %8, 0;\n\t"
                      "@p ld.shared.v2.f32 {%0, %1}, [%9];\n\t"
                      "@p ld.shared.v2.f32 {%2, %3}, [%10];\n\t"
