@@ -193,13 +193,16 @@ MT_API mt_status mt_init_chains(mt_ctx *ctx, int n_chains, const void *heights0,
  * H' = H + (eps^2/2) grad(H) + eps xi with eps = step, the gradient from the
  * adjoint (FP32 precision modes, gamma > 0), and the Hastings correction
  * ln q(H|H') - ln q(H'|H) in the accept test; MT_KERNEL_HMC: Hamiltonian
- * Monte Carlo (Sec. 3.1; unit mass matrix) with a leapfrog trajectory of
- * mt_set_hmc's n_leapfrog steps of size eps = step: momentum p0 ~ N(0, I),
- * p = p0 + eps/2 g, then n_leapfrog times H' += eps p and p += eps g(H')
- * (eps/2 after the last), the trajectory carried in FP64 and each gradient
- * taken at the stored (rounded) heights; accept term
- * log pi(H') - log pi(H) + |p0|^2/2 - |p|^2/2 (same requirements as MALA).
- * Step k of chain c draws xi from Philox stream 3 (RW), 5 (MALA) or 6 (HMC),
+ * Monte Carlo (Sec. 3.1) with a leapfrog trajectory of mt_set_hmc's
+ * n_leapfrog steps of size eps = step: momentum p0 = xi / sqrt(m) with
+ * xi ~ N(0, I) and m the diagonal inverse metric (1 unless adapted, see
+ * mt_set_metric_adapt), p = p0 + eps/2 g, then n_leapfrog times
+ * H' += eps m p and p += eps g(H') (eps/2 after the last), the trajectory
+ * carried in FP64 and each gradient taken at the stored (rounded) heights;
+ * accept term log pi(H') - log pi(H) + K(p0) - K(p), K = p^T m p / 2 (same
+ * requirements as MALA); MT_KERNEL_NUTS: the capped NUTS trajectory of
+ * mt_set_nuts.  Step k of chain c draws xi from Philox stream 3 (RW), 5
+ * (MALA), 6 (HMC) or 7 (NUTS),
  * counter {j, k, c}, and its acceptance uniform from stream 4, counter
  * {0, k, c}.  The n_within steps of a super-step are one CUDA graph replay;
  * the host only sees super-step boundaries.  Asynchronous. */

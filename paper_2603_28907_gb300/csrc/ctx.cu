@@ -1154,7 +1154,7 @@ static mt_status ensure_adapt(mt_ctx *ctx, double eps0)
 // One HMC step: momentum and the first drift, then per leapfrog step the
 // proposal's gradient (adjoint) and a kick + drift, a final half kick with
 // the kinetic-energy difference, the proposal's prior and the accept (the
-// last adjoint's forward pass gave the proposal's log-likelihood partials).
+// last gradient's forward march gave the proposal's log-likelihood partials).
 static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
 {
     const size_t np = n_per_chain(ctx);

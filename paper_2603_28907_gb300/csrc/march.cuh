@@ -261,7 +261,7 @@ __device__ __forceinline__ float2 load_group(const S *sh, int node, int l0)
 }
 
 // March one surface group over every sample of a ray from node-major
-// records (BF16 mode and the adjoint's forward pass) and add its integer
+// records (BF16 mode) and add its integer
 // indicator sums (units 2^-23) to t0 (surface l0) and t1 (l0 + 1).
 template <int L, int NS, bool HARD, typename S>
 __device__ __forceinline__ void march_group(const Prob &pb, const S *sh, float4 o, float4 st,

@@ -258,14 +258,15 @@ cudaError_t launch_mala_hastings(const Prob &pb, int mode, const void *hbuf, lon
 
 // ---------------------------------------------------------------- HMC
 // Hamiltonian Monte Carlo with a leapfrog trajectory (Sec. 3.1, the building
-// block of the paper's NUTS; unit mass matrix).  Momentum p0 ~ N(0, I) from
-// Philox stream HMC, counter {pair j, step, chain}; p = p0 + eps/2 g(q0);
-// n_leap times: q += eps p, then p += eps g(q) (eps/2 after the last drift).
+// block of the paper's NUTS).  Momentum p0 = xi / sqrt(m), xi ~ N(0, I) from
+// Philox stream HMC, counter {pair j, step, chain}, m the diagonal inverse
+// metric (1 unless adapted); p = p0 + eps/2 g(q0); n_leap times:
+// q += eps m p, then p += eps g(q) (eps/2 after the last drift).
 // The trajectory q is carried in FP64 (qbuf); the proposal buffer holds it
 // rounded to the height dtype, which is where the gradient and the
 // log-density are evaluated.  Gradients: G[1 - cur] (the proposal's), G[cur]
 // (the current state's), FP64 like the momentum.  The accept term is
-// K(p0) - K(p), K = |p|^2 / 2.
+// K(p0) - K(p), K = p^T m p / 2.
 template <typename H>
 __global__ void __launch_bounds__(256)
 k_hmc_start(int n, H *hbuf, long long bs, const double *gbuf, const uint8_t *cur, double eps0,
