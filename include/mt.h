@@ -57,7 +57,8 @@ typedef enum {
                            chains not set yet                               */
     MT_ECUDA = -4,      /* a CUDA runtime call failed                       */
     MT_ETIMEDOUT = -5,  /* mt_sync deadline passed, work still in flight    */
-    MT_EDEVFLAG = -6    /* a kernel latched a failure in the status word    */
+    MT_EDEVFLAG = -6,   /* a kernel latched a failure in the status word    */
+    MT_ECANCELED = -7   /* a served request was cancelled (mt_server_cancel) */
 } mt_status;
 
 /* Arithmetic of the ray march and the per-chain reduction.
@@ -472,6 +473,13 @@ MT_API mt_status mt_server_submit(mt_server *s, const mt_request *req, int64_t *
 MT_API mt_status mt_server_wait(mt_server *s, int64_t id, double timeout_s, void *heights_out,
                                 double *loglik_out, double *logprior_out, int64_t *accepts_out,
                                 mt_request_info *info);
+
+/* Cancel request `id`: a queued request is dropped at once; a running one
+ * stops at its next super-step boundary (no kernel is interrupted) and
+ * releases its device memory.  Either way mt_server_wait then returns
+ * MT_ECANCELED.  MT_ESTATE if the request had already finished, MT_EINVAL
+ * for an unknown id. */
+MT_API mt_status mt_server_cancel(mt_server *s, int64_t id);
 
 /* Aggregate latency and throughput of the requests finished so far. */
 MT_API mt_status mt_server_stats(mt_server *s, mt_server_stats_t *out);

@@ -146,7 +146,13 @@ __device__ __forceinline__ void scatter_surface(const Prob &pb, const float *sh,
         const float gx = fmaf(kf, st.x, o.x), gy = fmaf(kf, st.y, o.y);
         const float tx = gx + M, ty = gy + M;
         const float fx = (gx - (tx - M)) + 0.5f, fy = (gy - (ty - M)) + 0.5f;
-        const int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
+        int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
+#ifdef MT_BOUNDS_CHECK
+        if (!cell_ok(__float_as_int(tx) - 0x4B400000, __float_as_int(ty) - 0x4B400000, Q - 1, pb.R - 1)) {
+            atomicOr(pb.flag, 4);
+            node = 0;
+        }
+#endif
         const bool chg = node != cur;
         if (__any_sync(__activemask(), chg && pend >= 0)) {
             if (pend >= 0) {

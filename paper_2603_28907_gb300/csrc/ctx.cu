@@ -14,6 +14,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 namespace mt {
@@ -341,6 +343,7 @@ static void refresh_prob(mt_ctx *ctx)
     pb.perm = ctx->d_perm;
     pb.gnodes = nullptr;  // set per launch by ensure_nodes when the grid needs it
     pb.dO = nullptr;      // set in the copies that gradient launches use
+    pb.flag = ctx->d_flag;
     pb.work = ctx->timing ? ctx->d_work : nullptr;
     pb.o4 = ctx->d_o4;
     pb.s4 = ctx->d_s4;
@@ -1357,7 +1360,19 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
         ctx->g_nw = n_within;
         ctx->g_C = ctx->C;
     }
-    for (int s = 0; s < n_super; ++s) CK(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
+    // one NVTX range per super-step on the host timeline (a profiler that
+    // traces NVTX shows the graph launch and its kernels under it)
+    static const char *names[] = {"mt_run RW super-step", "mt_run MALA super-step", "mt_run HMC super-step",
+                                  "mt_run NUTS super-step"};
+    for (int s = 0; s < n_super; ++s) {
+        nvtxRangePushA(names[kernel]);
+        const cudaError_t e = cudaGraphLaunch(ctx->gexec, ctx->stream);
+        nvtxRangePop();
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, MT_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+        }
+    }
     return MT_OK;
 }
 
@@ -1451,8 +1466,10 @@ mt_status mt_sync(mt_ctx *ctx, double timeout_s)
     CK(ctx, cudaMemcpy(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
         CK(ctx, cudaMemset(ctx->d_flag, 0, sizeof(int)));
-        return fail(ctx, MT_EDEVFLAG, "a kernel latched device status %d (Poisson draw ran out of "
-                                      "attempts)", flag);
+        return fail(ctx, MT_EDEVFLAG,
+                    "a kernel latched device status %d (1: a Poisson draw ran out of attempts; 2: a "
+                    "ray's samples left the grid; 4: a cell index out of range, MT_BOUNDS_CHECK builds)",
+                    flag);
     }
     return MT_OK;
 }

@@ -62,6 +62,8 @@ struct Prob {
     float2 delta_ff;           // float-float of the minimum thickness
     float2 grho_ff;            // float-float of G * rho_top
     float2 invL_ff;            // float-float of 1 / Lambda
+    int *flag;                 // device status word (bit 4: a cell index out of range, in
+                               // builds with MT_BOUNDS_CHECK)
     float *dO;                 // FP32 modes: the march also writes d ll / d O_p = (lambda_p -
                                // C_p) / Lambda per ray, [chain][ray]; the adjoint reads it
                                // (nullptr: not written)

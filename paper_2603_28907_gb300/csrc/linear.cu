@@ -195,7 +195,7 @@ template <typename T> __device__ __forceinline__ T x_minus_log1p(T x)
 // summed (float-float for FP32, FP64 for F64) and written as
 // partial[c][block]; -inf if any of them had lambda_hat <= 0.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_lin_ll(Prob pb, int n_chains, int Cp, int rays_per_block,
+__global__ void __launch_bounds__(1024) k_lin_ll(Prob pb, int n_chains, int Cp, int rays_per_block, int nvox,
                                                  const int *row, const int *col, const T *val,
                                                  const T *dR, const double *lam0, const double *amc,
                                                  double *partial)
@@ -214,8 +214,16 @@ __global__ void __launch_bounds__(1024) k_lin_ll(Prob pb, int n_chains, int Cp, 
     int neg = 0;
     for (int p = r_begin + wid; p < r_end; p += nw) {
         T dO = (T)0;
-        const int e1 = row[p + 1];
+        int e1 = row[p + 1];
         int e = row[p];
+#ifdef MT_BOUNDS_CHECK
+        for (int q = row[p]; q < e1; ++q)
+            if ((unsigned)col[q] >= (unsigned)nvox) {
+                atomicOr(pb.flag, 4);
+                e1 = row[p];  // skip the ray's gathers
+                break;
+            }
+#endif
         for (; e + 4 <= e1; e += 4) {  // four gathers in flight
             const T d0 = dR[(size_t)col[e] * Cp + c], d1 = dR[(size_t)col[e + 1] * Cp + c];
             const T d2 = dR[(size_t)col[e + 2] * Cp + c], d3 = dR[(size_t)col[e + 3] * Cp + c];
@@ -301,11 +309,11 @@ cudaError_t launch_lin(const Prob &pb, int mode, HRef h, int n_chains, int nz, c
     dim3 gl(n_fine, Cp / 32);
     if (mode == MODE_F64) {
         k_lin_density<double><<<gd, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const double *)R0, (double *)dR);
-        k_lin_ll<double><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, kLinRays, row, col, (const double *)val,
+        k_lin_ll<double><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, kLinRays, nz * ncol, row, col, (const double *)val,
                                               (const double *)dR, lam0, amc, fine);
     } else {
         k_lin_density<float><<<gd, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const float *)R0, (float *)dR);
-        k_lin_ll<float><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, kLinRays, row, col, (const float *)val,
+        k_lin_ll<float><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, kLinRays, nz * ncol, row, col, (const float *)val,
                                              (const float *)dR, lam0, amc, fine);
     }
     const int rpb = march_rays_per_block(pb);

@@ -250,6 +250,16 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
+// Builds with MT_BOUNDS_CHECK verify every cell index the kernels form from
+// the ray table against the grid's cells [0, Q-1) x [0, R-1): an index out
+// of range latches bit 4 of the device status word and is replaced by cell
+// 0, so nothing is read or written out of bounds.  Other builds compile the
+// checks away (the ray table keeps every sample inside the grid).
+__device__ __forceinline__ bool cell_ok(int ix, int iy, int nxc, int nyc)
+{
+    return (unsigned)ix < (unsigned)nxc && (unsigned)iy < (unsigned)nyc;
+}
+
 // Corner heights of one surface group at a node: a pair (NS = 2) or the odd
 // last surface (NS = 1), from node-major records.
 template <int L, int NS, typename S, bool GLOBAL>
@@ -282,7 +292,13 @@ __device__ __forceinline__ void march_group(const Prob &pb, const S *sh, float4 
             const float gx = fmaf(kf, st.x, o.x), gy = fmaf(kf, st.y, o.y);
             const float tx = gx + M, ty = gy + M;
             const float fxs = (gx - (tx - M)) + 0.5f, fys = (gy - (ty - M)) + 0.5f;  // in [0, 1]
-            const int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
+            int node = (__float_as_int(ty) - 0x4B400000) * Q + (__float_as_int(tx) - 0x4B400000);
+#ifdef MT_BOUNDS_CHECK
+            if (!cell_ok(__float_as_int(tx) - 0x4B400000, __float_as_int(ty) - 0x4B400000, Q - 1, pb.R - 1)) {
+                atomicOr(pb.flag, 4);
+                node = 0;
+            }
+#endif
             if (node != cur) {
                 cur = node;
                 h00 = load_group<L, NS, S, false>(sh, node, l0);
@@ -375,8 +391,8 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
 // sample enters a new cell; the corner records of both samples are cached
 // and reloaded when either sample enters a new cell.
 template <bool HARD, bool GLOBAL>
-__device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, float2 kf2, float2 ox2, float2 oy2,
-                                          float2 sx2, float2 sy2, float2 szh2, float2 szl2,
+__device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, int R, int *flag, float2 kf2, float2 ox2,
+                                          float2 oy2, float2 sx2, float2 sy2, float2 szh2, float2 szl2,
                                           float2 zh2, float2 zl2, float2 nkg2, int &curA, int &curB,
                                           float2 &rA0, float2 &rA1, float2 &rB0, float2 &rB1)  // (h, dx): A/B x row r0/r0+1
 {
@@ -385,9 +401,17 @@ __device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, float2 kf2, f
     const float2 tx = add2(gx, M2), ty = add2(gy, M2);
     const float2 fx = add2(fma2(add2(tx, f2(-12582912.0f)), f2(-1.0f), gx), f2(0.5f));  // in [0, 1]
     const float2 fy = add2(fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy), f2(0.5f));
+#ifdef MT_BOUNDS_CHECK
+    const bool in_grid = cell_ok(__float_as_int(tx.x) - 0x4B400000, __float_as_int(ty.x) - 0x4B400000, Q - 1, R - 1) &&
+                         cell_ok(__float_as_int(tx.y) - 0x4B400000, __float_as_int(ty.y) - 0x4B400000, Q - 1, R - 1);
+    if (!in_grid) atomicOr(flag, 4);
+#endif
     if constexpr (GLOBAL) {
-        const int nA = (__float_as_int(ty.x) - 0x4B400000) * Q + (__float_as_int(tx.x) - 0x4B400000);
-        const int nB = (__float_as_int(ty.y) - 0x4B400000) * Q + (__float_as_int(tx.y) - 0x4B400000);
+        int nA = (__float_as_int(ty.x) - 0x4B400000) * Q + (__float_as_int(tx.x) - 0x4B400000);
+        int nB = (__float_as_int(ty.y) - 0x4B400000) * Q + (__float_as_int(tx.y) - 0x4B400000);
+#ifdef MT_BOUNDS_CHECK
+        if (!in_grid) nA = nB = 0;
+#endif
         if (nA != curA || nB != curB) {
             curA = nA;
             curB = nB;
@@ -405,8 +429,11 @@ __device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, float2 kf2, f
         const uint32_t base = (uint32_t)__cvta_generic_to_shared(pl);
         const uint32_t k0 = base - 8u * 0x4B400000u * (uint32_t)(Q + 1);
         const uint32_t rowb = 8u * (uint32_t)Q;
-        const uint32_t aA0 = (uint32_t)__float_as_int(ty.x) * rowb + ((uint32_t)__float_as_int(tx.x) * 8u + k0);
-        const uint32_t aB0 = (uint32_t)__float_as_int(ty.y) * rowb + ((uint32_t)__float_as_int(tx.y) * 8u + k0);
+        uint32_t aA0 = (uint32_t)__float_as_int(ty.x) * rowb + ((uint32_t)__float_as_int(tx.x) * 8u + k0);
+        uint32_t aB0 = (uint32_t)__float_as_int(ty.y) * rowb + ((uint32_t)__float_as_int(tx.y) * 8u + k0);
+#ifdef MT_BOUNDS_CHECK
+        if (!in_grid) aA0 = aB0 = base;
+#endif
         const uint32_t aA1 = aA0 + rowb, aB1 = aB0 + rowb;
         const uint32_t need = (uint32_t)(((int)aA0 != curA) | ((int)aB0 != curB));
         curA = (int)aA0;
@@ -440,7 +467,7 @@ __device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, float2 kf2, f
 // 2^-23) to t.  An odd count ends with one sample evaluated in both lanes and
 // counted once.
 template <bool HARD, bool GLOBAL>
-__device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, float4 o, float4 st,
+__device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, int R, int *flag, float4 o, float4 st,
                                                  float nkg, float zh, float zl, int lo, int he,
                                                  unsigned long long &t)
 {
@@ -455,7 +482,7 @@ __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, float4
         uint32_t acc = 0u;
 #pragma unroll 4
         for (int j = 0; j < jn; ++j) {
-            const float2 v = dx_pair<HARD, GLOBAL>(pl, Q, kf2, ox2, oy2, sx2, sy2, szh2, szl2, zh2, zl2,
+            const float2 v = dx_pair<HARD, GLOBAL>(pl, Q, R, flag, kf2, ox2, oy2, sx2, sy2, szh2, szl2, zh2, zl2,
                                                    nkg2, curA, curB, rA0, rA1, rB0, rB1);
             acc += __float_as_uint(v.x) + __float_as_uint(v.y);
             kf2 = add2(kf2, f2(2.0f));
@@ -464,7 +491,7 @@ __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, float4
     }
     if ((he - lo) & 1) {
         kf2 = f2((float)(he - 1));
-        const float2 v = dx_pair<HARD, GLOBAL>(pl, Q, kf2, ox2, oy2, sx2, sy2, szh2, szl2, zh2, zl2,
+        const float2 v = dx_pair<HARD, GLOBAL>(pl, Q, R, flag, kf2, ox2, oy2, sx2, sy2, szh2, szl2, zh2, zl2,
                                                nkg2, curA, curB, rA0, rA1, rB0, rB1);
         t += (unsigned long long)(__float_as_uint(v.x) - 0x3F800000u);
     }
@@ -542,7 +569,8 @@ __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *plane
         }
         if (evaluated) *evaluated += (unsigned long long)(he - lo);
         unsigned long long t = (unsigned long long)lo * q_one;  // samples below the window
-        march_surface_dx<HARD, GLOBAL>(planes + (size_t)l * pb.N, pb.Q, o, st, -pb.kg, zh, zl, lo, he, t);
+        march_surface_dx<HARD, GLOBAL>(planes + (size_t)l * pb.N, pb.Q, pb.R, pb.flag, o, st, -pb.kg, zh, zl, lo,
+                                       he, t);
         emit(l, t);
     }
 }

@@ -47,6 +47,7 @@ struct Request {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     bool inflight = false;
+    std::atomic<bool> cancel{false};
     int supers_done = 0;
     std::vector<float> superstep_ms;
     // results
@@ -252,6 +253,10 @@ static void worker_loop(mt_server *s)
                     r->supers_done += 1;
                 }
             }
+            if (r->status == MT_OK && r->cancel.load()) {
+                r->status = MT_ECANCELED;
+                r->error = "request cancelled";
+            }
             if (r->status != MT_OK || r->supers_done >= r->spec.n_super) {
                 finish_request(s, r);
                 s->active.erase(s->active.begin() + (long)i);
@@ -368,6 +373,30 @@ MT_API mt_status mt_server_wait(mt_server *s, int64_t id, double timeout_s, void
     if (loglik_out) memcpy(loglik_out, r->ll.data(), r->ll.size() * 8);
     if (logprior_out) memcpy(logprior_out, r->lp.data(), r->lp.size() * 8);
     if (accepts_out) memcpy(accepts_out, r->accepts.data(), r->accepts.size() * 8);
+    return MT_OK;
+}
+
+MT_API mt_status mt_server_cancel(mt_server *s, int64_t id)
+{
+    if (!s) return srv_fail(nullptr, MT_EINVAL, "null server");
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return srv_fail(s, MT_EINVAL, "unknown request id");
+    auto r = it->second;
+    if (r->done) return srv_fail(s, MT_ESTATE, "request already finished");
+    for (auto p = s->pending.begin(); p != s->pending.end(); ++p) {
+        if (p->get() != r.get()) continue;
+        // never admitted: nothing on the device to release
+        s->pending.erase(p);
+        r->status = MT_ECANCELED;
+        r->error = "request cancelled";
+        r->t_done = now_s(s->t0);
+        s->n_done += 1;
+        r->done = true;
+        s->cv_done.notify_all();
+        return MT_OK;
+    }
+    r->cancel.store(true);  // admitted: the scheduler stops it at a super-step boundary
     return MT_OK;
 }
 

@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmt.so")
+# MT_CHECKED=1 loads the bounds-checked build (libmt_checked.so, built by
+# build.build(checked=True)); it has the same ABI
+LIB_PATH = os.path.join(HERE, "libmt_checked.so" if os.environ.get("MT_CHECKED") == "1" else "libmt.so")
 
 PREC_F64, PREC_F32, PREC_F32C, PREC_BF16 = 0, 1, 2, 3
 PRIOR_CAR, PRIOR_COPULA = 0, 1
@@ -22,7 +24,7 @@ KERNEL_RW, KERNEL_MALA, KERNEL_HMC, KERNEL_NUTS = 0, 1, 2, 3
 COUNTS_POISSON, COUNTS_ROUND = 0, 1
 
 STATUS = {0: "MT_OK", -1: "MT_EINVAL", -2: "MT_ENOMEM", -3: "MT_ESTATE", -4: "MT_ECUDA",
-          -5: "MT_ETIMEDOUT", -6: "MT_EDEVFLAG"}
+          -5: "MT_ETIMEDOUT", -6: "MT_EDEVFLAG", -7: "MT_ECANCELED"}
 
 
 class MtError(RuntimeError):
@@ -100,6 +102,7 @@ SIGNATURES = {
     "mt_server_submit": [_vp, C.POINTER(Request), C.POINTER(C.c_int64)],
     "mt_server_wait": [_vp, C.c_int64, C.c_double, _vp, _vp, _vp, _vp, C.POINTER(RequestInfo)],
     "mt_server_stats": [_vp, C.POINTER(ServerStats)],
+    "mt_server_cancel": [_vp, C.c_int64],
     "mt_server_destroy": [_vp],
 }
 
@@ -391,6 +394,9 @@ class Server:
                                                            C.byref(info)))
         return dict(heights=H, loglik=ll, logprior=lp, accepts=acc,
                     info={k: getattr(info, k) for k, _ in RequestInfo._fields_})
+
+    def cancel(self, rid):
+        self._ck("mt_server_cancel", self.lib.mt_server_cancel(self.h, int(rid)))
 
     def stats(self):
         st = ServerStats()

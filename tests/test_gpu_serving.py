@@ -83,3 +83,39 @@ def test_budget_and_bad_requests():
         _submit_all(srv, [w], pace=False)
     assert e.value.status == -2
     srv.close()
+
+
+def test_cancel_queued_and_running_requests():
+    """One slot: request A runs (many super-steps), B waits in the queue.
+    Cancelling B drops it at once; cancelling A stops it at a super-step
+    boundary and frees its slot, so C then runs and equals C served alone."""
+    reqs = W.serving_mix(3, seed=9, small_scale=True)
+    a, b, c = reqs
+    srv = mt.Server(hbm_budget_bytes=1 << 30, max_active=1)
+    pa = W.problem(a)
+    ida = srv.submit(pa, W.init_chains(a).astype(np.float32), data_seed=a.seed_data, seed=a.seed_mcmc,
+                     step=0.02, n_super=100000, n_within=1)
+    idb, = _submit_all(srv, [b], pace=False)
+    time.sleep(0.2)
+    srv.cancel(idb)
+    with pytest.raises(mt.MtError) as e:
+        srv.wait(idb, 10.0)
+    assert e.value.status == -7
+    srv.cancel(ida)
+    with pytest.raises(mt.MtError) as e:
+        srv.wait(ida, 60.0)
+    assert e.value.status == -7
+    idc, = _submit_all(srv, [c], pace=False)
+    got = srv.wait(idc, 120.0)
+    with pytest.raises(mt.MtError) as e:                # already finished
+        srv.cancel(idc)
+    assert e.value.status == -3
+    with pytest.raises(mt.MtError):
+        srv.cancel(12345)
+    srv.close()
+    alone = mt.Server(hbm_budget_bytes=1 << 30, max_active=1)
+    idc2, = _submit_all(alone, [c], pace=False)
+    ref = alone.wait(idc2, 120.0)
+    alone.close()
+    np.testing.assert_array_equal(got["heights"], ref["heights"])
+    np.testing.assert_array_equal(got["loglik"], ref["loglik"])
