@@ -93,15 +93,17 @@ __device__ __forceinline__ void stage_nodes(S *sh, const H *Hc, int N, const flo
 }
 
 // FP32 node records, one plane per surface: plane l holds for every node
-// {h - ref_l, dx} with dx = h(r, c+1) - h(r, c) (0 in the last column), so a
-// cell needs the 8-byte records of its two left corners only.  A chain's
-// planes take 8 L N bytes, [l][node].
+// {hm, dx} with h = H - ref_l, dx = h(r, c+1) - h(r, c) (0 in the last
+// column) and hm = h + dx / 2, the height halfway along the row segment: the
+// x-lerp at the cell fraction f in [-1/2, 1/2] around the midpoint is then
+// hm + f dx, one multiply-add, and a cell needs the 8-byte records of its
+// two left corners only.  A chain's planes take 8 L N bytes, [l][node].
 template <typename H>
 __device__ __forceinline__ float2 dx_record(const H *Hc, int N, int Q, float ref, int l, int i)
 {
     const float h = (float)Hc[(size_t)l * N + i] - ref;
     const float d = (i % Q) == Q - 1 ? 0.f : ((float)Hc[(size_t)l * N + i + 1] - ref) - h;
-    return make_float2(h, d);
+    return make_float2(fmaf(0.5f, d, h), d);
 }
 
 template <typename H, int L>
@@ -113,9 +115,10 @@ __device__ __forceinline__ void stage_planes_dx(float2 *sh, const H *Hc, int N, 
     }
 }
 
-// Per-surface minimum and maximum of the staged offsets h - ref_l (planes in
-// shared memory or HBM): ext[l] = min, ext[L + l] = max.  All threads must
-// call it, after the planes are complete and visible.
+// Per-surface minimum and maximum of the node offsets h - ref_l, from the
+// staged records (planes in shared memory or HBM): ext[l] = min,
+// ext[L + l] = max.  All threads must call it, after the planes are complete
+// and visible.
 template <int L>
 __device__ __forceinline__ void surface_extent(const float2 *planes, int N, float *ext)
 {
@@ -129,9 +132,12 @@ __device__ __forceinline__ void surface_extent(const float2 *planes, int N, floa
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
 #pragma unroll
         for (int l = 0; l < L; ++l) {
-            const float v = planes[(size_t)l * N + i].x;
-            lo[l] = fminf(lo[l], v);
-            hi[l] = fmaxf(hi[l], v);
+            // the segment's two end nodes, hm -+ dx / 2 (their rounding is far
+            // inside the saturation threshold's margin)
+            const float2 r = planes[(size_t)l * N + i];
+            const float half = 0.5f * fabsf(r.y);
+            lo[l] = fminf(lo[l], r.x - half);
+            hi[l] = fmaxf(hi[l], r.x + half);
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -399,7 +405,7 @@ __device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, int R, int *f
     const float2 M2 = f2(12582912.0f);  // 1.5 * 2^23: adding it rounds to an integer
     const float2 gx = fma2(kf2, sx2, ox2), gy = fma2(kf2, sy2, oy2);
     const float2 tx = add2(gx, M2), ty = add2(gy, M2);
-    const float2 fx = add2(fma2(add2(tx, f2(-12582912.0f)), f2(-1.0f), gx), f2(0.5f));  // in [0, 1]
+    const float2 fx = fma2(add2(tx, f2(-12582912.0f)), f2(-1.0f), gx);  // in [-1/2, 1/2] about the midpoint
     const float2 fy = add2(fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy), f2(0.5f));
 #ifdef MT_BOUNDS_CHECK
     const bool in_grid = cell_ok(__float_as_int(tx.x) - 0x4B400000, __float_as_int(ty.x) - 0x4B400000, Q - 1, R - 1) &&
