@@ -75,3 +75,13 @@ def test_null_context_calls_return_einval(lib):
                                ctypes.c_void_p]
     assert lib.mt_logpost(None, 1, None, None, None) == -1
     assert lib.mt_destroy(None) == 0
+
+
+def test_bounds_checked_variant_builds_with_the_same_abi(lib):
+    """libmt_checked.so (MT_BOUNDS_CHECK) compiles, loads without a GPU and
+    exports the same symbols as the production library."""
+    path = B.build(checked=True)
+    assert path == B.OUT_CHECKED and path != B.OUT
+    chk = ctypes.CDLL(path)
+    for n in declared_symbols():
+        assert hasattr(chk, n), n
