@@ -179,8 +179,13 @@ MT_API mt_status mt_ray_terms(mt_ctx *ctx, int n_chains, const void *heights, do
  * ray march plus -tau Q (h - mu) from the prior): grad_out host or device
  * double [n_chains][L][R][Q]; logpost_out (nullable) double [n_chains].
  * FP32 march arithmetic with 64-bit fixed-point (2^-24) accumulation, so the
- * result is reproducible bit for bit.  Needs gamma > 0 and an FP32 precision
- * mode (MT_EINVAL otherwise); heights as for mt_logpost. */
+ * result is reproducible bit for bit.  Under the copula prior the states and
+ * the gradient are latents: the heights' log-likelihood gradient goes back
+ * through the stick-breaking, Phi, the Sigma_11(r) normalisation and the
+ * spectral filter (z and r gradients, r in the first L-1 entries of plane
+ * L-1, the rest of that plane 0), plus -z from the latent log-prior (FP32).
+ * Needs gamma > 0 and an FP32 precision mode (MT_EINVAL otherwise); heights
+ * (or latents) as for mt_logpost. */
 MT_API mt_status mt_grad(mt_ctx *ctx, int n_chains, const void *heights, double *grad_out,
                   double *logpost_out);
 
@@ -336,8 +341,9 @@ MT_API mt_status mt_get_sizes(const mt_ctx *ctx, int *n_layers, int *n_rows, int
  * the top surface L-1 is the known terrain T = the prior mean's top plane.
  * Log-prior in latent coordinates: -1/2 sum z^2 if every r_l is in (0, 1),
  * else -inf.  mt_logpost, mt_ray_terms, mt_init_chains, mt_set_state and
- * mt_get_state then take and return latents; random-walk steps move the
- * latents.  Gradients, MALA and mt_logpost_noalloc need the CAR prior.
+ * mt_get_state then take and return latents; random-walk, MALA, HMC and
+ * capped-NUTS steps move the latents (their gradient comes back through the
+ * transform, see mt_grad).  mt_logpost_noalloc needs the CAR prior.
  * Switching drops the chains; mt_set_grid resets the prior to MT_PRIOR_CAR.
  * Errors: MT_EINVAL (kind, fewer than 2 surfaces, grids whose transform does
  * not fit in shared memory: 4 R Q values of the height dtype), MT_ESTATE. */

@@ -71,3 +71,64 @@ def logprior(latent: np.ndarray) -> float:
     if not np.all((r > 0.0) & (r < 1.0)):
         return -math.inf
     return -0.5 * float(np.sum(lat[:L - 1] ** 2))
+
+
+def heights_vjp(latent: np.ndarray, terrain: np.ndarray, gH: np.ndarray) -> np.ndarray:
+    """Gradient with respect to the latents of sum(gH * heights(latent)) (the
+    chain rule through the stick-breaking, Phi, the normalisation by
+    sqrt(Sigma_11(r)) and the spectral filter Q(r)^-1/2; the top plane, the
+    terrain, does not depend on the latents).  Same layout as the latents:
+    planes 0 .. L-2 the z gradients, the first L-1 entries of plane L-1 the r
+    gradients, the rest 0.
+
+    With c_k = cos(2 pi k1/R) + cos(2 pi k2/Q) and eigenvalues l_k = 4 - 2 r c_k:
+      x = F^-1 (F z / sqrt(l)),  S = mean(1 / l),  s = x / sqrt(S),  u = Phi(s)
+      d l_k / dr = -2 c_k,  d l^-1/2 / dr = c l^-3/2,  dS / dr = mean(2 c / l^2)
+    and the filter is symmetric, so the z gradient is the filtered x gradient."""
+    lat = np.asarray(latent, np.float64)
+    L, R, Q = lat.shape
+    T = np.asarray(terrain, np.float64)
+    gH = np.asarray(gH, np.float64)
+    N = R * Q
+    k1 = np.arange(R)[:, None]
+    k2 = np.arange(Q)[None, :]
+    c = np.cos(2.0 * math.pi * k1 / R) + np.cos(2.0 * math.pi * k2 / Q)
+    # forward, keeping what the reverse pass needs
+    rs, s_l, below_l = [], [], []
+    below = np.zeros((R, Q))
+    for l in range(L - 1):
+        r = float(lat[L - 1].reshape(-1)[l])
+        S = sigma11(R, Q, r)
+        s = field(lat[l], r) / math.sqrt(S)
+        rs.append(r)
+        s_l.append(s)
+        below_l.append(below)
+        below = below + ndtr(s) * (T - below)
+    out = np.zeros_like(lat)
+    a = np.zeros((R, Q))                          # d/dH_l of everything above, carried down
+    for l in range(L - 2, -1, -1):
+        r, s, below = rs[l], s_l[l], below_l[l]
+        u = ndtr(s)
+        a = a + gH[l]
+        gu = a * (T - below)
+        a = a * (1.0 - u)                          # through H_l = (1 - u) H_{l-1} + u T
+        gs = gu * np.exp(-0.5 * s * s) / math.sqrt(2.0 * math.pi)
+        lam = 4.0 - 2.0 * r * c
+        S = float(np.mean(1.0 / lam))
+        gx = gs / math.sqrt(S)
+        gS = -0.5 * float(np.sum(gs * s)) / S      # s = x S^-1/2
+        out[l] = np.real(np.fft.ifft2(np.fft.fft2(gx) / np.sqrt(lam)))
+        # r through the filter: <gx, F^-1 (F z c lam^-3/2)>, and through S
+        dx_dr = np.real(np.fft.ifft2(np.fft.fft2(lat[l]) * c * lam ** -1.5))
+        gr = float(np.sum(gx * dx_dr)) + gS * float(np.mean(2.0 * c / lam ** 2))
+        out[L - 1].reshape(-1)[l] = gr
+    return out
+
+
+def logprior_grad(latent: np.ndarray) -> np.ndarray:
+    """Gradient of logprior inside its support: -z on planes 0 .. L-2, 0 for
+    the r entries and the unused rest of plane L-1."""
+    lat = np.asarray(latent, np.float64)
+    g = np.zeros_like(lat)
+    g[:-1] = -lat[:-1]
+    return g

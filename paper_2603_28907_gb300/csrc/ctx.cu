@@ -682,6 +682,15 @@ static mt_status eval_grad(mt_ctx *ctx, HRef h, int n, double *d_grad, double *d
 {
     TRY(ensure_grad_bufs(ctx, n));
     TRY(ensure_partials(ctx, n));
+    if (ctx->copula) {  // latents: heights from the transform, the gradient back through it
+        HRef hh;
+        TRY(prior_and_heights(ctx, h, n, d_lp, &hh));
+        TRY(enqueue_forward_adjoint(ctx, hh, n));
+        if (d_ll) CK(ctx, launch_reduce_ll(ctx->pb, ctx->mode, n, ctx->d_part, d_ll, ctx->stream));
+        CK(ctx, launch_copula_vjp(ctx->pb, h, hh, ctx->d_terr, (const unsigned long long *)ctx->d_gacc, d_grad,
+                                  nullptr, n, ctx->stream));
+        return MT_OK;
+    }
     TRY(enqueue_forward_adjoint(ctx, h, n));
     if (d_ll) CK(ctx, launch_reduce_ll(ctx->pb, ctx->mode, n, ctx->d_part, d_ll, ctx->stream));
     if (d_lp) CK(ctx, launch_prior(ctx->pb, ctx->mode, h, ctx->d_mu, n, d_lp, ctx->stream));
@@ -693,7 +702,8 @@ static mt_status eval_grad(mt_ctx *ctx, HRef h, int n, double *d_grad, double *d
 static mt_status grad_ok(mt_ctx *ctx)
 {
     if (ctx->linear) return fail(ctx, MT_EINVAL, "gradients need the marched forward model");
-    if (ctx->copula) return fail(ctx, MT_EINVAL, "gradients need the CAR prior (mt_set_prior 0)");
+    if (ctx->copula && copula_vjp_smem_bytes(ctx->pb) + MT_SMEM_STATIC > MT_MAX_SMEM)
+        return fail(ctx, MT_EINVAL, "grid too large for the copula transform's reverse pass");
     if (ctx->mode == MODE_F64)
         return fail(ctx, MT_EINVAL, "the adjoint computes in FP32: use an FP32 precision mode");
     if (adjoint_smem_bytes(ctx->pb, false) + MT_SMEM_STATIC > MT_MAX_SMEM)
@@ -1084,6 +1094,28 @@ static mt_status ensure_chain_grads(mt_ctx *ctx)
     return MT_OK;
 }
 
+// The proposals' (slot 1 - cur) log-prior into d_lpp, forward march with
+// d ll / d O_p (log-likelihood partials in d_part), adjoint, and their
+// log-posterior gradient into G[1 - cur]: heights with the CAR prior, or
+// latents through the copula transform and its reverse pass.
+static mt_status enqueue_proposal_eval(mt_ctx *ctx, HRef hp)
+{
+    if (!ctx->copula) {
+        CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
+        TRY(enqueue_forward_adjoint(ctx, hp, ctx->C));
+        CK(ctx, launch_grad_finish_sel(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C,
+                                       (const unsigned long long *)ctx->d_gacc, ctx->d_G, ctx->d_cur,
+                                       ctx->stream));
+        return MT_OK;
+    }
+    HRef hh;
+    TRY(prior_and_heights(ctx, hp, ctx->C, ctx->d_lpp, &hh));
+    TRY(enqueue_forward_adjoint(ctx, hh, ctx->C));
+    CK(ctx, launch_copula_vjp(ctx->pb, hp, hh, ctx->d_terr, (const unsigned long long *)ctx->d_gacc, ctx->d_G,
+                              ctx->d_cur, ctx->C, ctx->stream));
+    return MT_OK;
+}
+
 static mt_status enqueue_mala(mt_ctx *ctx, double eps, int off)
 {
     const size_t np = n_per_chain(ctx);
@@ -1094,15 +1126,10 @@ static mt_status enqueue_mala(mt_ctx *ctx, double eps, int off)
     CK(ctx, launch_propose_mala(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec,
                                 ctx->seed, ctx->d_step, off, ctx->stream));
     HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
-    CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
     EvPair ep;
     if (ctx->timing) ev_begin(ctx, 0, &ep);
-    TRY(enqueue_forward_adjoint(ctx, hp, ctx->C));
+    TRY(enqueue_proposal_eval(ctx, hp));  // prior, log-likelihood and gradient of the proposals
     if (ctx->timing) ev_end(ctx, 0, &ep);
-    // gradient of the proposals into G[1 - cur]
-    CK(ctx, launch_grad_finish_sel(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C,
-                                   (const unsigned long long *)ctx->d_gacc, ctx->d_G, ctx->d_cur,
-                                   ctx->stream));
     CK(ctx, launch_mala_hastings(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec,
                                  ctx->d_extra, ctx->stream));
     CK(ctx, launch_accept_fused(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
@@ -1155,9 +1182,10 @@ static mt_status ensure_adapt(mt_ctx *ctx, double eps0)
 }
 
 // One HMC step: momentum and the first drift, then per leapfrog step the
-// proposal's gradient (adjoint) and a kick + drift, a final half kick with
-// the kinetic-energy difference, the proposal's prior and the accept (the
-// last gradient's forward march gave the proposal's log-likelihood partials).
+// proposal's evaluation (prior, forward march, adjoint, gradient) and a
+// kick + drift, a final half kick with the kinetic-energy difference, and
+// the accept (the last evaluation, at the trajectory's end, gave the
+// proposal's log-prior and log-likelihood partials).
 static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
 {
     const size_t np = n_per_chain(ctx);
@@ -1171,17 +1199,15 @@ static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
                              ctx->d_P, ctx->d_Q64, ctx->d_k0, ctx->seed, ctx->d_step, off, ctx->stream));
     HRef hp{ctx->d_H, (long long)np, ctx->d_cur, bs, 1};
     for (int i = 0; i < ctx->hmc_leap; ++i) {
-        TRY(enqueue_forward_adjoint(ctx, hp, ctx->C));
-        CK(ctx, launch_grad_finish_sel(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C,
-                                       (const unsigned long long *)ctx->d_gacc, ctx->d_G, ctx->d_cur,
-                                       ctx->stream));
+        // the last evaluation, at the end of the trajectory, leaves the
+        // proposal's log-prior in d_lpp and its log-likelihood partials
+        TRY(enqueue_proposal_eval(ctx, hp));
         if (i + 1 < ctx->hmc_leap)
             CK(ctx, launch_hmc_kick_drift(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C,
                                           eps, ec, mi, ctx->d_P, ctx->d_Q64, ctx->stream));
     }
     CK(ctx, launch_hmc_finish(ctx->pb, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec, mi, ctx->d_P, ctx->d_k0,
                               ctx->d_extra, ctx->stream));
-    CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
     CK(ctx, launch_accept_fused(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
                                 ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
                                 ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
@@ -1236,11 +1262,7 @@ static mt_status enqueue_nuts(mt_ctx *ctx, double eps, int off)
         for (int k = 0; k < (1 << j); ++k, ++leaf) {
             CK(ctx, launch_nuts_drift(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_cur, ctx->C, eps, ec, mi, nb,
                                       ctx->seed, ctx->d_step, off, j, ctx->stream));
-            CK(ctx, launch_prior(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C, ctx->d_lpp, ctx->stream));
-            TRY(enqueue_forward_adjoint(ctx, hp, ctx->C));
-            CK(ctx, launch_grad_finish_sel(ctx->pb, ctx->mode, hp, ctx->d_mu, ctx->C,
-                                           (const unsigned long long *)ctx->d_gacc, ctx->d_G, ctx->d_cur,
-                                           ctx->stream));
+            TRY(enqueue_proposal_eval(ctx, hp));
             CK(ctx, launch_reduce_ll(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_llp, ctx->stream));
             CK(ctx, launch_nuts_leaf(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec, mi,
                                      ctx->d_llp, ctx->d_lpp, nb, ctx->seed, ctx->d_step, off, j, leaf,
@@ -1304,7 +1326,6 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
     TRY(ensure_lin(ctx, ctx->C));
     if (kernel == MT_KERNEL_MALA || kernel == MT_KERNEL_HMC || kernel == MT_KERNEL_NUTS) {
         if (ctx->linear) return fail(ctx, MT_EINVAL, "MALA / HMC / NUTS need the marched forward model");
-        if (ctx->copula) return fail(ctx, MT_EINVAL, "MALA / HMC / NUTS need the CAR prior (mt_set_prior 0)");
         TRY(grad_ok(ctx));
         if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA / HMC / NUTS need a step size eps > 0");
         if (ctx->metric_on && ctx->adapt_n > 0 && kernel == MT_KERNEL_MALA)

@@ -208,6 +208,13 @@ size_t lin_fine_partials(const Prob &pb, int n_chains);
 cudaError_t launch_lin_amc(int n, const double *lam0, const int32_t *cnt, double *amc, cudaStream_t st);
 cudaError_t launch_copula(const Prob &pb, int mode, HRef lat, const void *terrain, void *H, int n_chains,
                           cudaStream_t st);
+// Reverse of the copula transform (FP32 latents): the latent gradient from the
+// heights' log-likelihood gradient (fixed point, 2^-24) into G[1 - cur[c]][c]
+// (cur != nullptr) or G[c], plus the latent log-prior's gradient.
+size_t copula_vjp_smem_bytes(const Prob &pb);
+cudaError_t launch_copula_vjp(const Prob &pb, HRef lat, HRef hts, const void *terrain,
+                              const unsigned long long *gacc, double *G, const uint8_t *cur, int n_chains,
+                              cudaStream_t st);
 cudaError_t launch_prior_latent(const Prob &pb, int mode, HRef lat, int n_chains, double *lp_out,
                                 cudaStream_t st);
 cudaError_t launch_interface_std(int mode, const void *samples, int S, int L, int N, int n_z,

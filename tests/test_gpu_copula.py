@@ -4,7 +4,9 @@ Latent -> heights transform (oracle/copula.py: spectral Q^-1/2, Phi, stick
 breaking) in both height precisions and at the scenario size; log-posterior of
 latent states (likelihood of the derived heights + latent log-prior);
 random-walk Metropolis on latents in lockstep with the oracle's decisions;
-and the calls that need the CAR prior refuse the copula prior.
+gradients on latents (the adjoint back through the transform) against the
+oracle's chain rule, and HMC on latents in lockstep; the allocation-free call
+refuses the copula prior.
 """
 import math
 
@@ -141,14 +143,10 @@ def test_copula_refuses_car_only_calls():
     ctx.set_prior(mt.PRIOR_COPULA)
     lat = torch.tensor(latents(w, 2, 5), dtype=torch.float32, device=DEV).contiguous()
     g = torch.zeros((2, w.L, w.R, w.Q), dtype=torch.float64, device=DEV)
-    with pytest.raises(mt.MtError):
-        ctx.grad(lat, g)
     ll = torch.zeros(2, dtype=torch.float64, device=DEV)
     with pytest.raises(mt.MtError):
         ctx.logpost_noalloc(lat, ll)
-    ctx.init_chains(lat, 1)
-    with pytest.raises(mt.MtError):
-        ctx.run(mt.KERNEL_MALA, 0.01, 1, 1)
+    ctx.grad(lat, g)                                     # gradients on latents are fine
     ctx.set_prior(mt.PRIOR_CAR)                          # back to heights
     H = torch.tensor(W.init_chains(w, 2), dtype=torch.float32, device=DEV).contiguous()
     ctx.grad(H, g)
@@ -174,4 +172,108 @@ def test_copula_heights_odd_grid(precision, tol):
     Ln, Hg = Lt.cpu().double().numpy(), H.cpu().double().numpy()
     for c in range(4):
         assert np.max(np.abs(Hg[c] - K.heights(Ln[c], T))) <= tol
+    ctx.close()
+
+
+class _LatentProblem:
+    """The oracle's log-density and gradient in latent coordinates: the
+    likelihood of the derived heights, its gradient back through the transform
+    (oracle/copula.py heights_vjp), the latent log-prior and its gradient."""
+
+    def __init__(self, op, T):
+        self.op, self.T = op, T
+
+    def loglik(self, lat):
+        return self.op.loglik(K.heights(lat, self.T))
+
+    def logprior(self, lat):
+        return K.logprior(lat)
+
+    def grad_loglik(self, lat):
+        H = K.heights(lat, self.T)
+        return K.heights_vjp(lat, self.T, self.op.grad_loglik(H))
+
+    def grad_logprior(self, lat):
+        return K.logprior_grad(lat)
+
+
+def test_copula_gradient_matches_oracle():
+    """mt_grad on latents: the heights' log-likelihood gradient (adjoint)
+    back through the copula transform, plus -z, against the oracle's chain
+    rule (itself pinned by central differences) within 1e-3 of the largest
+    component; the log-posterior alongside."""
+    w = W.small(R=6, Q=5, bases=(40.0, 70.0, 110.0), rho=(2.65, 1.9, 0.0012, 2.65), G=48,
+                n_zenith=9, n_azimuth=13, n_sensors=3)
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    ctx.set_prior(mt.PRIOR_COPULA)
+    lat = latents(w, 2, 5, r=0.6)
+    Lt = torch.tensor(lat, dtype=torch.float32, device=DEV).contiguous()
+    g = torch.zeros(Lt.shape, dtype=torch.float64, device=DEV)
+    lp = torch.zeros(2, dtype=torch.float64, device=DEV)
+    ctx.grad(Lt, g, lp)
+    torch.cuda.synchronize()
+    g = g.cpu().numpy()
+    Ln = Lt.double().cpu().numpy()
+    lpx = _LatentProblem(op, pr["mu"][w.L - 1])
+    for c in range(2):
+        ref = lpx.grad_loglik(Ln[c]) + lpx.grad_logprior(Ln[c])
+        scale = np.abs(ref).max()
+        assert np.max(np.abs(g[c] - ref)) <= 1e-3 * scale, (c, np.max(np.abs(g[c] - ref)), scale)
+        ref_lp = lpx.loglik(Ln[c]) + lpx.logprior(Ln[c])
+        assert abs(lp[c].item() - ref_lp) <= 2e-2 + 1e-6 * abs(ref_lp), (c, lp[c].item(), ref_lp)
+    ctx.close()
+
+
+def test_copula_hmc_lockstep():
+    """HMC on latents against the oracle's HMC with the latent log-density:
+    proposals within the FP32 trajectory error, decisions equal except within
+    the FP32 band; then a capped-NUTS iteration and a MALA step run on the
+    same context."""
+    from oracle import hmc
+    w = W.small(R=5, Q=7, bases=(40.0, 75.0), G=24, n_zenith=6, n_azimuth=7, n_chains=3)
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    ctx.set_prior(mt.PRIOR_COPULA)
+    C, eps, n_leap = 3, 0.01, 3
+    ctx.set_hmc(n_leap)
+    L0 = torch.tensor(latents(w, C, 11, r=0.5), dtype=torch.float32, device=DEV).contiguous()
+    ctx.init_chains(L0, 13)
+    lpx = _LatentProblem(op, pr["mu"][w.L - 1])
+    logpi = lambda x: lpx.loglik(x) + lpx.logprior(x)
+    cur = L0.double().cpu().numpy()
+    lp_cur = np.array([logpi(cur[c]) for c in range(C)])
+    prop = torch.zeros_like(L0)
+    llp = torch.zeros(C, dtype=torch.float64, device=DEV)
+    lpp, logu = torch.zeros_like(llp), torch.zeros_like(llp)
+    acc = torch.zeros(C, dtype=torch.int32, device=DEV)
+    st = torch.zeros_like(L0)
+    accepted = band = 0
+    for k in range(6):
+        ctx.run(mt.KERNEL_HMC, eps, 1, 1)
+        ctx.get_last_step(prop, llp, lpp, acc, logu)
+        P = prop.double().cpu().numpy()
+        for c in range(C):
+            q, dk = hmc.propose(lpx, cur[c], eps, n_leap, 13, c, k, state=np.float32)
+            disp = float(np.max(np.abs(q - cur[c])))
+            assert np.max(np.abs(P[c] - q)) <= 1e-4 + 1e-4 * disp, (k, c, np.max(np.abs(P[c] - q)))
+            lq = logpi(P[c]) if np.isfinite(lpx.logprior(P[c])) else -np.inf
+            delta = lq - lp_cur[c] + dk
+            a_ref = bool(np.isfinite(lq) and logu[c].item() < delta)
+            if bool(acc[c].item()) != a_ref:
+                assert abs(logu[c].item() - delta) < 5e-2, (k, c, logu[c].item(), delta)
+                band += 1
+            if acc[c].item():
+                cur[c] = P[c]
+                lp_cur[c] = lq
+                accepted += 1
+        ctx.get_state(st)
+        np.testing.assert_array_equal(st.double().cpu().numpy(), cur)
+    assert accepted > 0 and band <= 1
+    ctx.set_nuts(2)
+    ctx.run(mt.KERNEL_NUTS, eps, 1, 1)
+    ctx.run(mt.KERNEL_MALA, 0.005, 1, 1)
+    ll = torch.zeros(C, dtype=torch.float64, device=DEV)
+    ctx.get_state(st, ll)
+    S = st.double().cpu().numpy()
+    for c in range(C):
+        assert abs(ll[c].item() - lpx.loglik(S[c])) <= 2e-2
     ctx.close()

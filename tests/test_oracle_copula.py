@@ -9,6 +9,7 @@ uniform marginals of u and the latent log-prior.
 import math
 
 import numpy as np
+import pytest
 from scipy.special import ndtr
 from scipy.stats import kstest
 
@@ -91,3 +92,40 @@ def test_latent_logprior():
     assert K.logprior(lat) == -0.5 * (4.0 + 5.0)
     lat[2].reshape(-1)[1] = 1.0
     assert K.logprior(lat) == -math.inf
+
+
+def test_heights_vjp_matches_central_differences():
+    """The chain rule of heights_vjp against central differences of
+    sum(gH * heights) in a few z entries and in every r."""
+    rng = np.random.default_rng(8)
+    L, R, Q = 4, 6, 5
+    lat = 0.7 * rng.standard_normal((L, R, Q))
+    lat[L - 1] = 0.0
+    lat[L - 1].reshape(-1)[:L - 1] = [0.35, 0.8, 0.97]
+    T = 150.0 + rng.standard_normal((R, Q))
+    gH = rng.standard_normal((L, R, Q))
+    f = lambda x: float(np.sum(gH[:L - 1] * K.heights(x, T)[:L - 1]))
+    g = K.heights_vjp(lat, T, gH)
+    h = 1e-6
+    idx = [(0, 1, 2), (1, 3, 0), (2, 5, 4), (2, 0, 0)] + [(L - 1, 0, j) for j in range(L - 1)]
+    for ix in idx:
+        e = np.zeros_like(lat)
+        e[ix] = h
+        fd = (f(lat + e) - f(lat - e)) / (2 * h)
+        assert g[ix] == pytest.approx(fd, rel=1e-6, abs=1e-6 * np.abs(g).max()), (ix, g[ix], fd)
+    assert np.all(g[L - 1].reshape(-1)[L - 1:] == 0.0)
+
+
+def test_heights_vjp_closed_form_at_r_zero():
+    """r -> 0: Q = 4 I, x = z / 2, Sigma_11 = 1/4, so u = Phi(z) and with two
+    surfaces H_0 = Phi(z) T: the z gradient is gH_0 T phi(z)."""
+    rng = np.random.default_rng(9)
+    R, Q = 4, 7
+    lat = np.zeros((2, R, Q))
+    lat[0] = rng.standard_normal((R, Q))
+    lat[1].reshape(-1)[0] = 1e-12
+    T = 140.0 + rng.standard_normal((R, Q))
+    gH = rng.standard_normal((2, R, Q))
+    g = K.heights_vjp(lat, T, gH)
+    phi = np.exp(-0.5 * lat[0] ** 2) / math.sqrt(2.0 * math.pi)
+    np.testing.assert_allclose(g[0], gH[0] * T * phi, rtol=1e-9, atol=1e-12)
