@@ -370,8 +370,11 @@ MT_API mt_status mt_copula_heights(mt_ctx *ctx, int n, const void *latent, void 
  * the height dtype); lambda_hat_p = lambda_p(R0) (1 - sum_v L_pv (R_v - R0_v)
  * / Lambda) with R0 the densities of h_ref ([L][R][Q] host FP64; NULL = the
  * prior mean).  The Poisson log-likelihood is -inf when some lambda_hat_p <=
- * 0.  mt_logpost and random-walk steps then use it; mt_ray_terms, gradients,
- * MALA, HMC and mt_logpost_noalloc need the march.  Live chains are
+ * 0.  mt_logpost, random-walk steps, gradients (mt_grad: the chain rule
+ * d ll / d O_p = (C_p / lambda_hat_p - 1) (-lambda_p(R0) / Lambda), the path
+ * lengths by voxel, the cell-centre sigmoids' derivatives, 1/4 to each
+ * corner node; gamma > 0) and so MALA, HMC and capped NUTS then use it;
+ * mt_ray_terms and mt_logpost_noalloc need the march.  Live chains are
  * re-evaluated.  mt_set_grid / mt_set_sensors / mt_set_pixels reset the
  * model to the march.
  * Errors: MT_EINVAL (kind, n_z outside 1..4096), MT_ESTATE (grid, sensors or

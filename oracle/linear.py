@@ -104,3 +104,41 @@ def loglik(H, prob, counts, rays, nz, H_ref):
     if np.any(lam <= 0.0):
         return -math.inf
     return float(np.sum(C * np.log(lam) - lam - gammaln(C + 1.0)))
+
+
+def loglik_grad(H, prob, counts, rays, nz, H_ref):
+    """Gradient with respect to the node heights of loglik (gamma > 0), by
+    the chain rule: d ll / d lambda_hat_p = C_p / lambda_hat_p - 1,
+    d lambda_hat_p / d R_v = -lambda_p(R0) L_pv / Lambda,
+    d R_v / d h_l(cell) = (rho_l - rho_{l+1}) varsigma'(h_l - z_k) with
+    varsigma' = varsigma (1 - varsigma) / gamma, and the cell-centre height
+    h_l(cell) the mean of the cell's four corner nodes (1/4 each)."""
+    H = np.asarray(H, np.float64)
+    L, R, Q = H.shape
+    I0, Lam, g = float(prob["I0"]), float(prob["Lambda"]), float(prob["gamma"])
+    rho = np.asarray(prob["rho"], np.float64)
+    O0 = opacity(rays, density(H_ref, prob, nz))
+    O = opacity(rays, density(H, prob, nz))
+    lam0 = I0 * np.exp(-O0 / Lam)
+    lam = lam0 * (1.0 - (O - O0) / Lam)
+    C = np.asarray(counts, np.float64).reshape(-1)
+    f = (C / lam - 1.0) * (-lam0 / Lam)              # d ll / d O_p
+    nx, ny = Q - 1, R - 1
+    gR = np.zeros(nz * ny * nx)
+    for p, ray in enumerate(rays):
+        for v, Lv in ray:
+            gR[v] += f[p] * Lv
+    gR = gR.reshape(nz, ny, nx)
+    hc = 0.25 * (H[:, :-1, :-1] + H[:, :-1, 1:] + H[:, 1:, :-1] + H[:, 1:, 1:])
+    dz = prob["box"][2] / nz
+    out = np.zeros_like(H)
+    for l in range(L):
+        gcell = np.zeros((ny, nx))
+        for k in range(nz):
+            s = 1.0 / (1.0 + np.exp(-(hc[l] - (k + 0.5) * dz) / g))
+            gcell += gR[k] * (rho[l] - rho[l + 1]) * s * (1.0 - s) / g
+        out[l, :-1, :-1] += 0.25 * gcell
+        out[l, :-1, 1:] += 0.25 * gcell
+        out[l, 1:, :-1] += 0.25 * gcell
+        out[l, 1:, 1:] += 0.25 * gcell
+    return out

@@ -125,6 +125,9 @@ struct mt_ctx {
     int lin_nz = 0;
     std::vector<double> lin_href;    // reference heights of the linearisation
     int *d_lrow = nullptr, *d_lcol = nullptr;  // voxel path lengths (CSR by ray)
+    int *d_lcptr = nullptr, *d_lcrow = nullptr;  // the same by voxel (CSC), for gradients
+    void *d_lcval = nullptr, *d_fO = nullptr, *d_gcell = nullptr;
+    size_t fO_cap = 0, gcell_cap = 0;
     void *d_lval = nullptr, *d_R0 = nullptr, *d_dR = nullptr;  // d_R0: reference voxel densities
     double *d_fine = nullptr;        // linearised model: fine-block partial sums
     size_t fine_cap = 0;
@@ -586,6 +589,10 @@ static mt_status prior_and_heights(mt_ctx *ctx, HRef h, int n, double *d_lp, HRe
     return MT_OK;
 }
 
+// Storage format of the per-CTA log-likelihood partials in d_part: the ray
+// kernel's (the linearised model writes FP64 partials in every mode).
+static int part_mode(const mt_ctx *ctx) { return ctx->linear ? MODE_F32 : ctx->mode; }
+
 // Scratch of the linearised model for n chains (dR, [voxels][n padded to 32]).
 static mt_status ensure_lin(mt_ctx *ctx, int n)
 {
@@ -660,6 +667,14 @@ static mt_status ensure_grad_bufs(mt_ctx *ctx, int n)
     TRY(grow(ctx, &ctx->d_gacc, &ctx->gacc_cap, (size_t)n * np * 8));
     TRY(grow(ctx, &ctx->d_dO, &ctx->dO_cap, (size_t)n * ctx->pb.n_rays * 4));
     if (ctx->d_gacc != old_g || ctx->d_dO != old_d) drop_graph(ctx);
+    if (ctx->linear) {  // d ll / d O per ray and the per-cell gradients, chains padded to 32
+        const size_t Cp = ((size_t)n + 31) / 32 * 32, es = elem_size(ctx);
+        const size_t ncell = (size_t)(ctx->R - 1) * (ctx->Q - 1);
+        void *of = ctx->d_fO, *oc = ctx->d_gcell;
+        TRY(grow(ctx, &ctx->d_fO, &ctx->fO_cap, (size_t)ctx->pb.n_rays * Cp * es));
+        TRY(grow(ctx, &ctx->d_gcell, &ctx->gcell_cap, (size_t)ctx->L * ncell * Cp * es));
+        if (ctx->d_fO != of || ctx->d_gcell != oc) drop_graph(ctx);
+    }
     return MT_OK;
 }
 
@@ -667,6 +682,16 @@ static mt_status ensure_grad_bufs(mt_ctx *ctx, int n)
 // adjoint's scatter into the zeroed accumulators, for n chains given by h.
 static mt_status enqueue_forward_adjoint(mt_ctx *ctx, HRef h, int n)
 {
+    if (ctx->linear) {  // the linearised model and its gradient
+        TRY(ensure_lin(ctx, n));
+        CK(ctx, launch_lin(ctx->pb, ctx->mode, h, n, ctx->lin_nz, ctx->d_lrow, ctx->d_lcol, ctx->d_lval,
+                           ctx->d_R0, ctx->d_dR, ctx->d_lam0, ctx->d_amc, ctx->d_fine, (double *)ctx->d_part,
+                           ctx->stream, ctx->d_fO));
+        CK(ctx, launch_lin_grad(ctx->pb, ctx->mode, h, n, ctx->lin_nz, ctx->d_lcptr, ctx->d_lcrow, ctx->d_lcval,
+                                ctx->d_fO, ctx->d_dR, ctx->d_gcell, (unsigned long long *)ctx->d_gacc,
+                                ctx->stream));
+        return MT_OK;
+    }
     Prob pg = ctx->pb;
     pg.dO = (float *)ctx->d_dO;
     pg.work = nullptr;
@@ -686,13 +711,13 @@ static mt_status eval_grad(mt_ctx *ctx, HRef h, int n, double *d_grad, double *d
         HRef hh;
         TRY(prior_and_heights(ctx, h, n, d_lp, &hh));
         TRY(enqueue_forward_adjoint(ctx, hh, n));
-        if (d_ll) CK(ctx, launch_reduce_ll(ctx->pb, ctx->mode, n, ctx->d_part, d_ll, ctx->stream));
+        if (d_ll) CK(ctx, launch_reduce_ll(ctx->pb, part_mode(ctx), n, ctx->d_part, d_ll, ctx->stream));
         CK(ctx, launch_copula_vjp(ctx->pb, h, hh, ctx->d_terr, (const unsigned long long *)ctx->d_gacc, d_grad,
                                   nullptr, n, ctx->stream));
         return MT_OK;
     }
     TRY(enqueue_forward_adjoint(ctx, h, n));
-    if (d_ll) CK(ctx, launch_reduce_ll(ctx->pb, ctx->mode, n, ctx->d_part, d_ll, ctx->stream));
+    if (d_ll) CK(ctx, launch_reduce_ll(ctx->pb, part_mode(ctx), n, ctx->d_part, d_ll, ctx->stream));
     if (d_lp) CK(ctx, launch_prior(ctx->pb, ctx->mode, h, ctx->d_mu, n, d_lp, ctx->stream));
     CK(ctx, launch_grad_finish(ctx->pb, ctx->mode, h, ctx->d_mu, n,
                                (const unsigned long long *)ctx->d_gacc, d_grad, ctx->stream));
@@ -701,7 +726,6 @@ static mt_status eval_grad(mt_ctx *ctx, HRef h, int n, double *d_grad, double *d
 
 static mt_status grad_ok(mt_ctx *ctx)
 {
-    if (ctx->linear) return fail(ctx, MT_EINVAL, "gradients need the marched forward model");
     if (ctx->copula && copula_vjp_smem_bytes(ctx->pb) + MT_SMEM_STATIC > MT_MAX_SMEM)
         return fail(ctx, MT_EINVAL, "grid too large for the copula transform's reverse pass");
     if (ctx->mode == MODE_F64)
@@ -804,6 +828,8 @@ mt_status mt_destroy(mt_ctx *ctx)
     if (ctx->d_diag) cudaFree(ctx->d_diag);
     if (ctx->d_terr) cudaFree(ctx->d_terr);
     if (ctx->d_lrow) cudaFree(ctx->d_lrow);
+    for (void *p : {(void *)ctx->d_lcptr, (void *)ctx->d_lcrow, ctx->d_lcval, ctx->d_fO, ctx->d_gcell})
+        if (p) cudaFree(p);
     if (ctx->d_lcol) cudaFree(ctx->d_lcol);
     if (ctx->d_lval) cudaFree(ctx->d_lval);
     if (ctx->d_R0) cudaFree(ctx->d_R0);
@@ -1132,7 +1158,7 @@ static mt_status enqueue_mala(mt_ctx *ctx, double eps, int off)
     if (ctx->timing) ev_end(ctx, 0, &ep);
     CK(ctx, launch_mala_hastings(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec,
                                  ctx->d_extra, ctx->stream));
-    CK(ctx, launch_accept_fused(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
+    CK(ctx, launch_accept_fused(ctx->pb, part_mode(ctx), ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
                                 ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
                                 ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
                                 ctx->stream, ec ? ctx->d_alpha : nullptr));
@@ -1208,7 +1234,7 @@ static mt_status enqueue_hmc(mt_ctx *ctx, double eps, int off)
     }
     CK(ctx, launch_hmc_finish(ctx->pb, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec, mi, ctx->d_P, ctx->d_k0,
                               ctx->d_extra, ctx->stream));
-    CK(ctx, launch_accept_fused(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
+    CK(ctx, launch_accept_fused(ctx->pb, part_mode(ctx), ctx->C, ctx->d_part, ctx->d_lpp, ctx->d_extra,
                                 ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
                                 ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
                                 ctx->stream, ec ? ctx->d_alpha : nullptr));
@@ -1263,7 +1289,7 @@ static mt_status enqueue_nuts(mt_ctx *ctx, double eps, int off)
             CK(ctx, launch_nuts_drift(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_cur, ctx->C, eps, ec, mi, nb,
                                       ctx->seed, ctx->d_step, off, j, ctx->stream));
             TRY(enqueue_proposal_eval(ctx, hp));
-            CK(ctx, launch_reduce_ll(ctx->pb, ctx->mode, ctx->C, ctx->d_part, ctx->d_llp, ctx->stream));
+            CK(ctx, launch_reduce_ll(ctx->pb, part_mode(ctx), ctx->C, ctx->d_part, ctx->d_llp, ctx->stream));
             CK(ctx, launch_nuts_leaf(ctx->pb, ctx->mode, ctx->d_H, bs, ctx->d_G, ctx->d_cur, ctx->C, eps, ec, mi,
                                      ctx->d_llp, ctx->d_lpp, nb, ctx->seed, ctx->d_step, off, j, leaf,
                                      ctx->stream));
@@ -1305,7 +1331,7 @@ static mt_status enqueue_step(mt_ctx *ctx, int kernel, double step, int off)
     }
     TRY(ray_kernel(ctx, hp, ctx->C));
     if (ctx->timing) ev_end(ctx, 0, &ep);
-    CK(ctx, launch_accept_fused(ctx->pb, ctx->linear ? MODE_F32 : ctx->mode, ctx->C, ctx->d_part, ctx->d_lpp, nullptr,
+    CK(ctx, launch_accept_fused(ctx->pb, part_mode(ctx), ctx->C, ctx->d_part, ctx->d_lpp, nullptr,
                                 ctx->d_ll, ctx->d_lp, ctx->d_llp, ctx->d_cur, ctx->d_psel,
                                 ctx->d_acc, ctx->d_accl, ctx->d_logu, ctx->seed, ctx->d_step, off,
                                 ctx->stream));
@@ -1325,7 +1351,6 @@ mt_status mt_run(mt_ctx *ctx, int kernel, double step, int n_super, int n_within
     if (ctx->copula) TRY(ensure_derived(ctx, ctx->C));
     TRY(ensure_lin(ctx, ctx->C));
     if (kernel == MT_KERNEL_MALA || kernel == MT_KERNEL_HMC || kernel == MT_KERNEL_NUTS) {
-        if (ctx->linear) return fail(ctx, MT_EINVAL, "MALA / HMC / NUTS need the marched forward model");
         TRY(grad_ok(ctx));
         if (!(step > 0.0)) return fail(ctx, MT_EINVAL, "MALA / HMC / NUTS need a step size eps > 0");
         if (ctx->metric_on && ctx->adapt_n > 0 && kernel == MT_KERNEL_MALA)
@@ -1803,7 +1828,8 @@ mt_status mt_set_forward(mt_ctx *ctx, int kind, int n_z, const double *h_ref)
     if (es == 4) valf.assign(val.begin(), val.end());
     const size_t nvox = R0.size();
     for (void **p : {(void **)&ctx->d_lrow, (void **)&ctx->d_lcol, &ctx->d_lval, &ctx->d_R0,
-                     (void **)&ctx->d_lam0, (void **)&ctx->d_amc}) {
+                     (void **)&ctx->d_lam0, (void **)&ctx->d_amc, (void **)&ctx->d_lcptr, (void **)&ctx->d_lcrow,
+                     &ctx->d_lcval}) {
         if (*p) cudaFree(*p);
         *p = nullptr;
     }
@@ -1816,6 +1842,19 @@ mt_status mt_set_forward(mt_ctx *ctx, int kind, int n_z, const double *h_ref)
     CK(ctx, cudaMemcpyAsync(ctx->d_lrow, row.data(), row.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->d_lcol, col.data(), nnz * 4, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->d_lval, es == 4 ? (const void *)valf.data() : (const void *)val.data(),
+                            nnz * es, cudaMemcpyHostToDevice, ctx->stream));
+    // the same path lengths by voxel, for gradients
+    std::vector<int> cptr, crow;
+    std::vector<double> cval;
+    lin_transpose((int)nr, (int)nvox, row, col, val, cptr, crow, cval);
+    std::vector<float> cvalf;
+    if (es == 4) cvalf.assign(cval.begin(), cval.end());
+    CK(ctx, cudaMalloc((void **)&ctx->d_lcptr, cptr.size() * 4));
+    CK(ctx, cudaMalloc((void **)&ctx->d_lcrow, nnz * 4 + 16));
+    CK(ctx, cudaMalloc(&ctx->d_lcval, nnz * es + 16));
+    CK(ctx, cudaMemcpyAsync(ctx->d_lcptr, cptr.data(), cptr.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->d_lcrow, crow.data(), nnz * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->d_lcval, es == 4 ? (const void *)cvalf.data() : (const void *)cval.data(),
                             nnz * es, cudaMemcpyHostToDevice, ctx->stream));
     // reference densities with the device's own arithmetic (so that the
     // densities of the reference itself differ from them by exactly 0)

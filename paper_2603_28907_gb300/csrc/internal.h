@@ -202,7 +202,18 @@ size_t interface_smem(int n_z);
 size_t copula_smem_bytes(const Prob &pb, int mode);
 cudaError_t launch_lin(const Prob &pb, int mode, HRef h, int n_chains, int nz, const int *row,
                        const int *col, const void *val, const void *R0, void *dR, const double *lam0,
-                       const double *amc, double *fine, double *partial, cudaStream_t st);
+                       const double *amc, double *fine, double *partial, cudaStream_t st,
+                       void *fO = nullptr);
+// Gradient of the linearised log-likelihood into the fixed-point accumulators
+// gacc [n][L][N] (fO: d ll / d O_p from launch_lin, [ray][Cp]; gR [voxel][Cp]
+// and gcell [L][cell][Cp] scratch; cptr / crow / cval the path lengths by
+// voxel, from lin_transpose).
+cudaError_t launch_lin_grad(const Prob &pb, int mode, HRef h, int n_chains, int nz, const int *cptr,
+                            const int *crow, const void *cval, const void *fO, void *gR, void *gcell,
+                            unsigned long long *gacc, cudaStream_t st);
+void lin_transpose(int n_rays, int nvox, const std::vector<int> &row, const std::vector<int> &col,
+                   const std::vector<double> &val, std::vector<int> &cptr, std::vector<int> &crow,
+                   std::vector<double> &cval);
 cudaError_t launch_lin_reference(const Prob &pb, int mode, HRef h, int nz, void *R0, cudaStream_t st);
 size_t lin_fine_partials(const Prob &pb, int n_chains);
 cudaError_t launch_lin_amc(int n, const double *lam0, const int32_t *cnt, double *amc, cudaStream_t st);

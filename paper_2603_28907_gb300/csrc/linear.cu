@@ -198,7 +198,7 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_lin_ll(Prob pb, int n_chains, int Cp, int rays_per_block, int nvox,
                                                  const int *row, const int *col, const T *val,
                                                  const T *dR, const double *lam0, const double *amc,
-                                                 double *partial)
+                                                 double *partial, T *fO)
 {
     __shared__ double red[32][33];
     __shared__ int bad[32];
@@ -237,6 +237,8 @@ __global__ void __launch_bounds__(1024) k_lin_ll(Prob pb, int n_chains, int Cp, 
         const T l0 = (T)lam0[p];
         const T lh = l0 * ((T)1 - dO * invL);
         neg |= !(lh > (T)0);
+        // d ll / d O_p = (C / lambda_hat - 1) (-lambda0 / Lambda), for gradients
+        if (fO) fO[(size_t)p * Cp + c] = lh > (T)0 ? ((T)Cn / lh - (T)1) * (-l0 * invL) : (T)0;
         T term;
         if (Cn > 0) {
             const T x = ((T)amc[p] - l0 * dO * invL) / (T)Cn;  // (lambda_hat - C) / C
@@ -300,7 +302,7 @@ cudaError_t launch_lin_reference(const Prob &pb, int mode, HRef h, int nz, void 
 
 cudaError_t launch_lin(const Prob &pb, int mode, HRef h, int n_chains, int nz, const int *row,
                        const int *col, const void *val, const void *R0, void *dR, const double *lam0,
-                       const double *amc, double *fine, double *partial, cudaStream_t st)
+                       const double *amc, double *fine, double *partial, cudaStream_t st, void *fO)
 {
     const int Cp = (n_chains + 31) / 32 * 32;
     const int ncol = (pb.Q - 1) * (pb.R - 1);
@@ -310,17 +312,133 @@ cudaError_t launch_lin(const Prob &pb, int mode, HRef h, int n_chains, int nz, c
     if (mode == MODE_F64) {
         k_lin_density<double><<<gd, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const double *)R0, (double *)dR);
         k_lin_ll<double><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, kLinRays, nz * ncol, row, col, (const double *)val,
-                                              (const double *)dR, lam0, amc, fine);
+                                              (const double *)dR, lam0, amc, fine, (double *)fO);
     } else {
         k_lin_density<float><<<gd, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const float *)R0, (float *)dR);
         k_lin_ll<float><<<gl, 1024, 0, st>>>(pb, n_chains, Cp, kLinRays, nz * ncol, row, col, (const float *)val,
-                                             (const float *)dR, lam0, amc, fine);
+                                             (const float *)dR, lam0, amc, fine, (float *)fO);
     }
     const int rpb = march_rays_per_block(pb);
     const int n_blk = (pb.n_rays + rpb - 1) / rpb;
     const int f = (rpb + kLinRays - 1) / kLinRays;
     k_lin_fold<<<(n_chains * n_blk + 255) / 256, 256, 0, st>>>(n_chains, n_fine, n_blk, f, fine, partial);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- gradient
+// Gradient of the linearised log-likelihood with respect to the node heights
+// (gamma > 0), written as the adjoint's 64-bit fixed-point accumulators
+// (units 2^-24) so that the prior's gradient and the copula's reverse pass
+// follow unchanged:
+//   d ll / d R_v = sum_p L_pv d ll / d O_p          (k_lin_rgrad, the path
+//                                                     lengths by voxel, CSC)
+//   d ll / d h_l(cell) = sum_k (d ll / d R_v) (rho_l - rho_{l+1})
+//                        varsigma(u) (1 - varsigma(u)) / gamma,
+//                        u = h_l(cell) - z_k          (k_lin_cellgrad)
+//   d ll / d H_l(node) = sum over the node's cells of d ll / d h_l(cell) / 4
+//                                                     (k_lin_nodegrad)
+// Lanes are chains (tiles of 32, padded to Cp); every output has one writer.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lin_rgrad(int nvox, int Cp, const int *cptr, const int *crow,
+                                                   const T *cval, const T *fO, T *gR)
+{
+    const int lane = threadIdx.x & 31, v = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int c = blockIdx.y * 32 + lane;
+    if (v >= nvox) return;
+    T s = (T)0;
+    for (int e = cptr[v]; e < cptr[v + 1]; ++e) s += cval[e] * fO[(size_t)crow[e] * Cp + c];
+    gR[(size_t)v * Cp + c] = s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lin_cellgrad(Prob pb, HRef h, int n_chains, int Cp, int nz, const T *gR,
+                                                      T *gcell)
+{
+    const int lane = threadIdx.x & 31;
+    const int nx = pb.Q - 1, ny = pb.R - 1;
+    const int colv = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int c = blockIdx.y * 32 + lane;
+    if (colv >= nx * ny || c >= n_chains) return;
+    const int i = colv / nx, j = colv - i * nx;
+    const size_t ncell = (size_t)nx * ny;
+    const T *Hc = chain_ptr<T>(h, c);
+    const T dz = (T)(pb.box[2] / nz), inv_g = (T)(1.0 / pb.gamma);
+    for (int l = 0; l < pb.L; ++l) {
+        const T *hl = Hc + (size_t)l * pb.N;
+        const T hc = (T)0.25 * (((hl[i * pb.Q + j] + hl[i * pb.Q + j + 1]) + hl[(i + 1) * pb.Q + j]) +
+                                hl[(i + 1) * pb.Q + j + 1]);
+        const T dr = (T)pb.drho[l];
+        T s = (T)0;
+        for (int k = 0; k < nz; ++k) {
+            const T u = sub_rn(hc, mul_rn((T)k + (T)0.5, dz));
+            T sg;
+            if constexpr (sizeof(T) == 4) sg = __frcp_rn(1.0f + expf(-u * inv_g));
+            else sg = 1.0 / (1.0 + exp(-u * inv_g));
+            s += gR[((size_t)k * ncell + colv) * Cp + c] * (sg * ((T)1 - sg));
+        }
+        gcell[((size_t)l * ncell + colv) * Cp + c] = s * dr * inv_g;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lin_nodegrad(Prob pb, int n_chains, int Cp, const T *gcell,
+                                                      unsigned long long *gacc)
+{
+    const int lane = threadIdx.x & 31;
+    const int node = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int c = blockIdx.y * 32 + lane, l = blockIdx.z;
+    if (node >= pb.N || c >= n_chains) return;
+    const int nx = pb.Q - 1, ny = pb.R - 1;
+    const int r = node / pb.Q, q = node - r * pb.Q;
+    const size_t ncell = (size_t)nx * ny;
+    double s = 0.0;
+    for (int di = -1; di <= 0; ++di)
+        for (int dj = -1; dj <= 0; ++dj) {
+            const int i = r + di, j = q + dj;
+            if (i >= 0 && i < ny && j >= 0 && j < nx)
+                s += (double)gcell[((size_t)l * ncell + (size_t)i * nx + j) * Cp + c];
+        }
+    gacc[((size_t)c * pb.L + l) * pb.N + node] = (unsigned long long)llrint(0.25 * s * 16777216.0);
+}
+
+cudaError_t launch_lin_grad(const Prob &pb, int mode, HRef h, int n_chains, int nz, const int *cptr,
+                            const int *crow, const void *cval, const void *fO, void *gR, void *gcell,
+                            unsigned long long *gacc, cudaStream_t st)
+{
+    const int Cp = (n_chains + 31) / 32 * 32;
+    const int ncol = (pb.Q - 1) * (pb.R - 1), nvox = nz * ncol;
+    dim3 gv((nvox + 7) / 8, Cp / 32), gc((ncol + 7) / 8, Cp / 32), gn((pb.N + 7) / 8, Cp / 32, pb.L);
+    if (mode == MODE_F64) {
+        k_lin_rgrad<double><<<gv, 256, 0, st>>>(nvox, Cp, cptr, crow, (const double *)cval, (const double *)fO,
+                                                (double *)gR);
+        k_lin_cellgrad<double><<<gc, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const double *)gR, (double *)gcell);
+        k_lin_nodegrad<double><<<gn, 256, 0, st>>>(pb, n_chains, Cp, (const double *)gcell, gacc);
+    } else {
+        k_lin_rgrad<float><<<gv, 256, 0, st>>>(nvox, Cp, cptr, crow, (const float *)cval, (const float *)fO,
+                                               (float *)gR);
+        k_lin_cellgrad<float><<<gc, 256, 0, st>>>(pb, h, n_chains, Cp, nz, (const float *)gR, (float *)gcell);
+        k_lin_nodegrad<float><<<gn, 256, 0, st>>>(pb, n_chains, Cp, (const float *)gcell, gacc);
+    }
+    return cudaGetLastError();
+}
+
+// The path lengths by voxel (CSC) from the CSR by ray.
+void lin_transpose(int n_rays, int nvox, const std::vector<int> &row, const std::vector<int> &col,
+                   const std::vector<double> &val, std::vector<int> &cptr, std::vector<int> &crow,
+                   std::vector<double> &cval)
+{
+    cptr.assign((size_t)nvox + 1, 0);
+    for (int v : col) cptr[(size_t)v + 1] += 1;
+    for (int v = 0; v < nvox; ++v) cptr[(size_t)v + 1] += cptr[v];
+    crow.assign(col.size(), 0);
+    cval.assign(col.size(), 0.0);
+    std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+    for (int p = 0; p < n_rays; ++p)
+        for (int e = row[p]; e < row[(size_t)p + 1]; ++e) {
+            const int k = fill[col[e]]++;
+            crow[k] = p;
+            cval[k] = val[e];
+        }
 }
 
 }  // namespace mt

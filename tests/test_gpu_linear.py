@@ -86,9 +86,6 @@ def test_linear_random_walk_and_refusals():
     for c in range(w.n_chains):
         ref = LN.loglik(Hn[c], pr, counts.cpu().numpy(), rays, nz, pr["mu"])
         assert abs(ll[c].item() - ref) <= 1e-6 * abs(ref)
-    g = torch.zeros((1, w.L, w.R, w.Q), dtype=torch.float64, device=DEV)
-    with pytest.raises(mt.MtError):
-        ctx.grad(H0[:1].contiguous(), g)
     O = torch.zeros((1, w.S * w.P), dtype=torch.float64, device=DEV)
     with pytest.raises(mt.MtError):
         ctx.ray_terms(H0[:1].contiguous(), O)
@@ -144,4 +141,77 @@ def test_linear_odd_grid_and_hard_indicator(gamma):
             assert ll[c].item() == -math.inf
         else:
             assert abs(ll[c].item() - ref) <= 1e-10 * abs(ref) + 1e-9, (c, ll[c].item(), ref)
+    ctx.close()
+
+
+def test_linear_gradient_matches_oracle():
+    """mt_grad under the linearised model: the chain rule through the path
+    lengths and the cell-centre sigmoids (oracle loglik_grad, pinned by
+    central differences) plus the CAR prior's gradient, within 1e-3 of the
+    largest component (FP32)."""
+    w = W.small(R=6, Q=5, bases=(40.0, 70.0, 110.0), rho=(2.65, 1.9, 0.0012, 2.65), G=48,
+                n_zenith=9, n_azimuth=13, n_sensors=3)
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    nz = 20
+    ctx.set_forward(mt.FORWARD_LINEAR, nz)
+    Hs = np.stack([W.perturbed(pr["H_true"], 1.0, [4]), W.init_chains(w, 1)[0]])
+    H = torch.tensor(Hs, dtype=torch.float32, device=DEV).contiguous()
+    g = torch.zeros(H.shape, dtype=torch.float64, device=DEV)
+    lp = torch.zeros(2, dtype=torch.float64, device=DEV)
+    ctx.grad(H, g, lp)
+    torch.cuda.synchronize()
+    g = g.cpu().numpy()
+    Hn = H.double().cpu().numpy()
+    rays = LN.lengths(pr, nz)
+    C = counts.cpu().numpy()
+    for c in range(2):
+        ref = LN.loglik_grad(Hn[c], pr, C, rays, nz, pr["mu"]) + op.grad_logprior(Hn[c])
+        scale = np.abs(ref).max()
+        assert np.max(np.abs(g[c] - ref)) <= 1e-3 * scale, (c, np.max(np.abs(g[c] - ref)), scale)
+        ref_lp = LN.loglik(Hn[c], pr, C, rays, nz, pr["mu"]) + op.logprior(Hn[c])
+        assert abs(lp[c].item() - ref_lp) <= 1e-6 * abs(ref_lp) + 1e-3
+    ctx.close()
+
+
+def test_paper_pipeline_copula_linear_nuts():
+    """The paper's combination: copula-prior latents, the linearised model and
+    capped NUTS.  The latent gradient against the oracle's (heights_vjp of
+    the linearised model's gradient, plus -z), then NUTS iterations whose
+    states' log-likelihoods match the oracle's."""
+    from oracle import copula as K
+    w = W.small(R=5, Q=7, bases=(40.0, 75.0), G=24, n_zenith=6, n_azimuth=7, n_chains=3)
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    nz = 16
+    ctx.set_forward(mt.FORWARD_LINEAR, nz)
+    ctx.set_prior(mt.PRIOR_COPULA)
+    rng = np.random.default_rng(12)
+    lat = 0.4 * rng.standard_normal((3, w.L, w.R, w.Q))
+    lat[:, w.L - 1] = 0.0
+    lat[:, w.L - 1, 0, :w.L - 1] = 0.55
+    Lt = torch.tensor(lat, dtype=torch.float32, device=DEV).contiguous()
+    g = torch.zeros(Lt.shape, dtype=torch.float64, device=DEV)
+    ctx.grad(Lt, g)
+    torch.cuda.synchronize()
+    g = g.cpu().numpy()
+    T = pr["mu"][w.L - 1]
+    rays = LN.lengths(pr, nz)
+    C = counts.cpu().numpy()
+    Ln = Lt.double().cpu().numpy()
+    for c in range(3):
+        Hh = K.heights(Ln[c], T)
+        ref = K.heights_vjp(Ln[c], T, LN.loglik_grad(Hh, pr, C, rays, nz, pr["mu"])) + K.logprior_grad(Ln[c])
+        scale = np.abs(ref).max()
+        assert np.max(np.abs(g[c] - ref)) <= 1e-3 * scale, (c, np.max(np.abs(g[c] - ref)), scale)
+    ctx.set_nuts(2)
+    ctx.init_chains(Lt, 5)
+    ctx.run(mt.KERNEL_NUTS, 0.02, 3, 1)
+    st = torch.zeros_like(Lt)
+    ll = torch.zeros(3, dtype=torch.float64, device=DEV)
+    acc = torch.zeros(3, dtype=torch.int64, device=DEV)
+    ctx.get_state(st, ll, None, acc)
+    S = st.double().cpu().numpy()
+    for c in range(3):
+        ref = LN.loglik(K.heights(S[c], T), pr, C, rays, nz, pr["mu"])
+        assert abs(ll[c].item() - ref) <= 1e-6 * abs(ref) + 1e-3, (c, ll[c].item(), ref)
+    assert acc.sum().item() > 0
     ctx.close()

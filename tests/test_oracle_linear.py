@@ -73,3 +73,23 @@ def test_linearisation_is_exact_at_the_reference_and_second_order():
         lam_hat = lam0 * (1.0 - (O - O0) / pr["Lambda"])
         errs.append(np.max(np.abs(lam_hat - lam_exact)))
     assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
+def test_loglik_grad_matches_central_differences():
+    """The chain rule of loglik_grad against central differences of loglik
+    at a few nodes (interior, edge and corner nodes of every surface)."""
+    w = W.small(R=5, Q=6, bases=(40.0, 75.0), G=16, n_zenith=5, n_azimuth=6, n_sensors=2)
+    pr = W.problem(w)
+    op = oracle.OracleProblem(pr)
+    C, _, _ = op.generate_counts(pr["H_true"], w.seed_data)
+    nz = 12
+    rays = LN.lengths(pr, nz)
+    rng = np.random.default_rng(4)
+    H = pr["mu"] + 2.0 * rng.standard_normal(pr["mu"].shape)
+    g = LN.loglik_grad(H, pr, C, rays, nz, pr["mu"])
+    h = 1e-5
+    for ix in [(0, 2, 3), (1, 0, 0), (1, 4, 5), (0, 1, 0), (1, 3, 2)]:
+        e = np.zeros_like(H)
+        e[ix] = h
+        fd = (LN.loglik(H + e, pr, C, rays, nz, pr["mu"]) - LN.loglik(H - e, pr, C, rays, nz, pr["mu"])) / (2 * h)
+        assert abs(g[ix] - fd) <= 1e-5 * max(1.0, abs(fd)) + 1e-6 * np.abs(g).max(), (ix, g[ix], fd)
