@@ -9,7 +9,8 @@ Hoffman & Gelman 2014 run to its trajectory cap):
 * the transition leaves a Gaussian invariant: the sample mean and variance
   of a long run match the target's;
 * every state of the 2^D - 1 steps is visited: the trajectory's two ends sit
-  at the right leapfrog distances.
+  at the right leapfrog distances;
+* a diagonal inverse metric is the unit metric in rescaled coordinates.
 """
 import math
 
@@ -107,3 +108,24 @@ def test_trajectory_extent():
         xi = oracle.normals(2, NU.STREAM_NUTS_P, 0, k, 1)[0]
         n = (q[0] - q0[0]) / (1e-7 * xi)
         assert abs(n - round(n)) < 1e-3 and abs(round(n)) <= 2 ** D - 1
+
+
+def test_metric_is_the_unit_metric_in_scaled_coordinates():
+    """N(0, diag s^2) with inverse metric s^2 is, in x = q / s with momentum
+    s p, N(0, I) with the unit metric: the same momenta and uniforms give the
+    same trajectory, so the chosen state maps across (x = q / s), and the
+    acceptance statistic and the decision margins are equal."""
+    rng = np.random.default_rng(8)
+    s = np.exp(rng.uniform(-3.0, 2.0, 12))
+    logpi_q, grad_q = gaussian(s)
+    logpi_x, grad_x = gaussian(np.ones(12))
+    for k in range(40):
+        q0 = s * rng.standard_normal(12)
+        a = NU.iteration(logpi_q, grad_q, q0, logpi_q(q0)[0], 0.0, grad_q(q0), 0.3, 4, 9, 2, k,
+                         state=np.float64, inv_metric=s ** 2)
+        x0 = q0 / s
+        b = NU.iteration(logpi_x, grad_x, x0, logpi_x(x0)[0], 0.0, grad_x(x0), 0.3, 4, 9, 2, k,
+                         state=np.float64)
+        np.testing.assert_allclose(a[0] / s, b[0], rtol=1e-10, atol=1e-12)
+        assert a[4] == pytest.approx(b[4], rel=1e-10, abs=1e-14)
+        assert a[5] == pytest.approx(b[5], rel=1e-8, abs=1e-10)
