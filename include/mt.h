@@ -472,7 +472,8 @@ MT_API mt_status mt_server_create(mt_server **out, int device, size_t hbm_budget
                                   int max_active);
 
 /* Queue a request (host arrays, copied).  MT_ENOMEM if it alone needs more than
- * the budget; MT_EINVAL for an incomplete request.  *id_out names it. */
+ * the budget; MT_EINVAL for an incomplete request or a kernel other than
+ * MT_KERNEL_RW / MT_KERNEL_MALA.  *id_out names it. */
 MT_API mt_status mt_server_submit(mt_server *s, const mt_request *req, int64_t *id_out);
 
 /* Wait for request `id` (timeout_s <= 0: no limit; MT_ETIMEDOUT otherwise) and
@@ -493,7 +494,8 @@ MT_API mt_status mt_server_cancel(mt_server *s, int64_t id);
 /* Aggregate latency and throughput of the requests finished so far. */
 MT_API mt_status mt_server_stats(mt_server *s, mt_server_stats_t *out);
 
-/* Stop the scheduler (requests still running end with MT_ESTATE) and free all. */
+/* Stop the scheduler (requests still queued or running end with MT_ESTATE,
+ * waking their waiters) and free all. */
 MT_API mt_status mt_server_destroy(mt_server *s);
 
 MT_API const char *mt_server_last_error(const mt_server *s);

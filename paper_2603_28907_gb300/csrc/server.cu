@@ -73,7 +73,8 @@ size_t footprint_of(const mt_request &r)
     b += C * ((rays + 4095) / 4096) * 8;            // partial sums
     b += L * N * 8 * 2;                             // prior mean, staging
     if (N * L * 8 + MT_SMEM_STATIC > MT_MAX_SMEM) b += C * N * L * 8;  // HBM (h, dx) planes
-    if (r.kernel == MT_KERNEL_MALA) b += 3 * C * L * N * 8 + C * 8;
+    if (r.kernel == MT_KERNEL_MALA)                 // gradients: two slots, accumulator,
+        b += 4 * C * L * N * 8 + C * 8 + C * rays * 4;  // staging; Hastings terms; dll/dO
     b += rays * 16 + C * L * N * es;                // output staging
     return b + (8u << 20);                          // allocator slack
 }
@@ -107,6 +108,7 @@ struct mt_server {
     std::map<int64_t, std::shared_ptr<Request>> all;
     int64_t next_id = 1;
     std::atomic<bool> stop{false};
+    std::atomic<int64_t> n_active{0};  // active.size(), which only the scheduler touches
     std::thread worker;
     std::string err;
     // aggregate statistics
@@ -227,6 +229,7 @@ static void worker_loop(mt_server *s)
             progress = true;
             if (setup_request(s, r.get())) {
                 s->active.push_back(r);
+                s->n_active.store((int64_t)s->active.size());
             } else {
                 finish_request(s, r.get());
             }
@@ -260,6 +263,7 @@ static void worker_loop(mt_server *s)
             if (r->status != MT_OK || r->supers_done >= r->spec.n_super) {
                 finish_request(s, r);
                 s->active.erase(s->active.begin() + (long)i);
+                s->n_active.store((int64_t)s->active.size());
                 continue;
             }
             cudaEventRecord(r->ev_a, r->stream);
@@ -284,6 +288,18 @@ static void worker_loop(mt_server *s)
         finish_request(s, r.get());
     }
     s->active.clear();
+    s->n_active.store(0);
+    // requests never admitted end the same way
+    std::lock_guard<std::mutex> g(s->mu);
+    for (auto &r : s->pending) {
+        r->status = MT_ESTATE;
+        r->error = "server shut down before the request was admitted";
+        r->t_done = now_s(s->t0);
+        s->n_done += 1;
+        r->done = true;
+    }
+    s->pending.clear();
+    s->cv_done.notify_all();
 }
 
 extern "C" {
@@ -315,6 +331,7 @@ MT_API mt_status mt_server_submit(mt_server *s, const mt_request *q, int64_t *id
     if (!s || !q) return srv_fail(s, MT_EINVAL, "null argument");
     if (q->n_layers < 1 || q->n_layers > MT_MAX_L || q->n_rows < 2 || q->n_cols < 2 ||
         q->n_sensors < 1 || q->n_pixels < 1 || q->n_chains < 1 || q->n_super < 0 ||
+        (q->kernel != MT_KERNEL_RW && q->kernel != MT_KERNEL_MALA) ||
         q->n_within < 1 || !q->box || !q->unit_density || !q->sensors || !q->dirs ||
         !q->heights0 || (!q->counts && !q->h_true))
         return srv_fail(s, MT_EINVAL, "mt_server_submit: incomplete or out-of-range request");
@@ -406,7 +423,7 @@ MT_API mt_status mt_server_stats(mt_server *s, mt_server_stats_t *out)
     std::lock_guard<std::mutex> g(s->mu);
     out->n_done = s->n_done;
     out->n_pending = (int64_t)s->pending.size();
-    out->n_active = (int64_t)s->active.size();
+    out->n_active = s->n_active.load();
     out->superstep_ms_p50 = pct(s->superstep_ms, 0.5);
     out->superstep_ms_p99 = pct(s->superstep_ms, 0.99);
     out->ttp_s_p50 = pct(s->ttp_s, 0.5);

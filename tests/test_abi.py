@@ -85,3 +85,28 @@ def test_bounds_checked_variant_builds_with_the_same_abi(lib):
     chk = ctypes.CDLL(path)
     for n in declared_symbols():
         assert hasattr(chk, n), n
+
+
+def test_server_calls_fail_cleanly_without_gpu(lib):
+    """The serving calls return error codes with a message (no abort) when
+    there is no device or no server."""
+    import torch
+    lib.mt_server_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_size_t,
+                                     ctypes.c_int]
+    lib.mt_server_last_error.restype = ctypes.c_char_p
+    lib.mt_server_last_error.argtypes = [ctypes.c_void_p]
+    h = ctypes.c_void_p()
+    assert lib.mt_server_create(ctypes.byref(h), 0, 0, 1) == -1        # no budget
+    assert lib.mt_server_create(ctypes.byref(h), 0, 1 << 30, 0) == -1  # no slot
+    if not torch.cuda.is_available():
+        assert lib.mt_server_create(ctypes.byref(h), 0, 1 << 30, 1) == -4  # MT_ECUDA
+        assert h.value is None
+        assert b"device" in lib.mt_server_last_error(None)
+    lib.mt_server_submit.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.mt_server_cancel.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    lib.mt_server_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.mt_server_submit(None, None, None) == -1
+    assert lib.mt_server_cancel(None, 1) == -1
+    assert lib.mt_server_stats(None, None) == -1
+    lib.mt_server_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.mt_server_destroy(None) == 0
