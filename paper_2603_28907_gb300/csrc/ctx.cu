@@ -1,7 +1,8 @@
 // ctx.cu -- host side of libmt.so: the context, argument checks, device
 // buffers, the Metropolis super-step as a CUDA graph, and the C ABI of
-// include/mt.h.  No kernel runs on the host; every step of the path is one
-// of the kernels in data.cu, march_*.cu and mcmc.cu.
+// include/mt.h.  No step of the path runs on the host; each is one of the
+// kernels in data.cu, march_*.cu, mcmc.cu, adjoint.cu, copula.cu, linear.cu
+// and diag.cu.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
