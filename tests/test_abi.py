@@ -110,3 +110,11 @@ def test_server_calls_fail_cleanly_without_gpu(lib):
     assert lib.mt_server_stats(None, None) == -1
     lib.mt_server_destroy.argtypes = [ctypes.c_void_p]
     assert lib.mt_server_destroy(None) == 0
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch):
+    """No fallback: with the library missing, the binding raises."""
+    monkeypatch.setattr(mt, "_lib", None)
+    monkeypatch.setattr(mt, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libmt.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        mt.load()
