@@ -328,8 +328,8 @@ def _scenario_contexts(precisions, local):
 def run_precision_study(args, local):
     """Accept-decision agreement, log-likelihood and MH-ratio error of the
     reduced-precision modes on the same (current, proposal) pairs, against the
-    FP64 mode (which matches the oracle to ~1e-12 relative; two chains are
-    re-checked against the oracle).  The trajectory itself is an FP32 random
+    FP64 mode (whose agreement with the oracle at this size, ~1e-12 relative,
+    is a parity test).  The trajectory itself is an FP32 random
     walk, so every state is exactly representable in all modes."""
     import torch
     from paper_2603_28907_gb300 import mt
@@ -391,14 +391,6 @@ def run_precision_study(args, local):
                              dll_abs_max=st["dll_max"], dll_abs_mean=st["dll_sum"] / nf,
                              mh_ratio_err_max=st["dd_max"], mh_ratio_err_mean=st["dd_sum"] / nf)
         out[f"chains_{C}"] = dict(steps=steps, wall_s=wall, modes=res)
-    import oracle
-    op = oracle.OracleProblem(pr, counts=counts.cpu().numpy())
-    Hf = cur[:2].double()
-    llg = f64(2)
-    ref.logpost(Hf.contiguous(), llg, None)
-    Hn = Hf.cpu().numpy()
-    out["fp64_mode_vs_oracle_rel"] = max(abs(llg[i].item() - op.loglik(Hn[i])) / abs(op.loglik(Hn[i]))
-                                         for i in range(2))
     print(json.dumps({"study": "precision", "workload": w.name, "reference": "FP64 mode", **out}), flush=True)
 
 
@@ -424,14 +416,14 @@ def _ess(x):
 
 def run_gradient_study(args, local):
     import torch
-    import oracle
     from paper_2603_28907_gb300 import mt
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w, pr, ctxs, counts = _scenario_contexts([mt.PREC_F32, mt.PREC_F64], local)
     c32, c64 = ctxs[mt.PREC_F32], ctxs[mt.PREC_F64]
     out = {}
-    # 1. gradient against the oracle on a 16x16 sub-grid of every surface
+    # 1. one gradient evaluation (its agreement with the oracle at this size
+    # is a parity test)
     H = W.geometry(w, [w.seed_init, 0]).astype(np.float32)   # an ordered geometry
     g = torch.zeros((1,) + H.shape, dtype=torch.float64, device=dev)
     t = time.perf_counter()
@@ -439,10 +431,6 @@ def run_gradient_study(args, local):
     torch.cuda.synchronize()
     out["grad_ms_one_chain"] = (time.perf_counter() - t) * 1e3
     g = g[0].cpu().numpy()
-    op = oracle.OracleProblem(pr, counts=counts.cpu().numpy())
-    ref = op.grad_loglik(H.astype(np.float64)) + op.grad_logprior(H.astype(np.float64))
-    sub = (slice(None), slice(24, 40), slice(24, 40))
-    out["grad_vs_oracle_subgrid_max_abs_err_rel_to_max"] = float(np.abs(g[sub] - ref[sub]).max() / np.abs(ref[sub]).max())
     # 2. central differences (h = 1e-3 m) of the FP64-mode log-posterior at 16 sub-grid nodes
     rng = np.random.default_rng(0)
     idx = [(int(rng.integers(0, w.L)), int(rng.integers(24, 40)), int(rng.integers(24, 40))) for _ in range(16)]
@@ -658,14 +646,18 @@ def run_diag(args, local):
     ms = timed(lambda: ctx.interface_std(H, n_z, out))
     res["interface_std"] = {"ms": ms, "samples": C, "levels": n_z,
                             "voxels": w.L * n_z * w.R * w.Q}
+    # CPU baseline: the FP64 oracle's diagnostics (numpy, one process)
     from oracle import diagnostics as D
     hn = H.cpu().double().numpy()
     t0 = time.perf_counter()
     D.nested_rhat(hn.reshape(1, C, P), K)
-    res["oracle_nested_rhat_draws_1_ms"] = (time.perf_counter() - t0) * 1e3
+    t_rhat = (time.perf_counter() - t0) * 1e3
     t0 = time.perf_counter()
     D.interface_std(hn[:128], w.box[2], n_z)
-    res["oracle_interface_std_128_samples_ms"] = (time.perf_counter() - t0) * 1e3
+    t_std = (time.perf_counter() - t0) * 1e3
+    res["cpu_baseline"] = {"kind": "oracle", "nested_rhat_draws_1_ms": t_rhat,
+                           "interface_std_128_samples_ms": t_std,
+                           "sample": "the same draws; interface std on 128 of the samples"}
     print(json.dumps({"diag": "chain diagnostics", "workload": w.name, "chains": C,
                       "super_chains": K, **res}), flush=True)
     ctx.close()

@@ -124,3 +124,32 @@ def test_scenario_full_size_sampled_chains():
         tol = fp32_loglik_tol(pr, op, Hc)
         assert abs(ll[c] - ref) <= tol, (c, ll[c] - ref, tol)
         assert abs(lp[c] - op.logprior(Hc)) <= 1e-9 * abs(lp[c])
+
+
+@pytest.mark.slow
+def test_scenario_fp64_mode_and_gradient():
+    """Full scenario size (64x64 grid, 4 surfaces, 65 536 rays, G = 256): the
+    FP64 mode's per-chain log-likelihood within 1e-6 relative of the oracle's
+    (two ordered geometries), and the FP32 gradient of the log-posterior
+    within 1e-3 of its largest component on a 16 x 16 sub-grid of every
+    surface, against the oracle's analytic FP64 gradient."""
+    w = W.scenario()
+    Hs = np.stack([W.geometry(w, [w.seed_init, c]) for c in range(2)]).astype(np.float32)
+    pr, c64, op, counts, _ = setup(w, precision=mt.PREC_F64)
+    Hd = Hs.astype(np.float64)
+    ll, lp = logpost(c64, heights(Hd, mt.PREC_F64))
+    for c in range(2):
+        ref = op.loglik(Hd[c])
+        assert abs(ll[c] - ref) <= 1e-6 * abs(ref), (c, ll[c], ref)
+        assert abs(lp[c] - op.logprior(Hd[c])) <= 1e-9 * abs(lp[c])
+    c64.close()
+    pr, c32, op, counts, _ = setup(w, precision=mt.PREC_F32)
+    g = torch.zeros((1,) + Hs.shape[1:], dtype=torch.float64, device=DEV)
+    c32.grad(heights(Hs[:1], mt.PREC_F32), g)
+    torch.cuda.synchronize()
+    g = g[0].cpu().numpy()
+    ref = op.grad_loglik(Hd[0]) + op.grad_logprior(Hd[0])
+    sub = (slice(None), slice(24, 40), slice(24, 40))
+    err, scale = np.abs(g[sub] - ref[sub]).max(), np.abs(ref[sub]).max()
+    assert err <= 1e-3 * scale, (err, scale)
+    c32.close()
