@@ -609,6 +609,22 @@ def run_copula(args, local):
     ctx.close()
 
 
+def cpu_baseline_diag(hn, K, Lz, n_z):
+    """The FP64 oracle's chain diagnostics (numpy, one process) on the same
+    draws: nested R-hat of one draw per chain, interface std of 128 samples."""
+    from oracle import diagnostics as D
+    C = hn.shape[0]
+    t0 = time.perf_counter()
+    D.nested_rhat(hn.reshape(1, C, -1), K)
+    t_rhat = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    D.interface_std(hn[:128], Lz, n_z)
+    t_std = (time.perf_counter() - t0) * 1e3
+    return {"kind": "oracle", "cores": 1, "nested_rhat_draws_1_ms": t_rhat,
+            "interface_std_128_samples_ms": t_std,
+            "sample": "the same draws; interface std on 128 of the samples"}
+
+
 def run_diag(args, local):
     """Nested R-hat over 1024 scenario chains (32 super-chains of 32; one and
     ten stored draws) and the interface standard deviation over 1024 samples
@@ -646,18 +662,7 @@ def run_diag(args, local):
     ms = timed(lambda: ctx.interface_std(H, n_z, out))
     res["interface_std"] = {"ms": ms, "samples": C, "levels": n_z,
                             "voxels": w.L * n_z * w.R * w.Q}
-    # CPU baseline: the FP64 oracle's diagnostics (numpy, one process)
-    from oracle import diagnostics as D
-    hn = H.cpu().double().numpy()
-    t0 = time.perf_counter()
-    D.nested_rhat(hn.reshape(1, C, P), K)
-    t_rhat = (time.perf_counter() - t0) * 1e3
-    t0 = time.perf_counter()
-    D.interface_std(hn[:128], w.box[2], n_z)
-    t_std = (time.perf_counter() - t0) * 1e3
-    res["cpu_baseline"] = {"kind": "oracle", "nested_rhat_draws_1_ms": t_rhat,
-                           "interface_std_128_samples_ms": t_std,
-                           "sample": "the same draws; interface std on 128 of the samples"}
+    res["cpu_baseline"] = cpu_baseline_diag(H.cpu().double().numpy(), K, w.box[2], n_z)
     print(json.dumps({"diag": "chain diagnostics", "workload": w.name, "chains": C,
                       "super_chains": K, **res}), flush=True)
     ctx.close()
