@@ -28,6 +28,13 @@ sample variance (Welford); at its end the inverse metric becomes
 (n/(n+5)) var + s 5/(n+5) (n the window length, s the shrinkage target) and
 the dual averaging starts over with mu = log(10 eps), Hbar = 0,
 log epsbar = 0.
+
+Parity pins (tests/test_oracle_adapt.py): the closed form of a constant
+acceptance, the fixed point at the target, convergence to the root of a
+noiseless acceptance curve, the window schedule, Welford against the sample
+variance, the metric leapfrog as the unit one in rescaled coordinates, and
+warm-ups that reach the target and recover a Gaussian's scales.  Every
+function is pinned.
 """
 from __future__ import annotations
 

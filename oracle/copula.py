@@ -20,6 +20,12 @@ Latent layout per chain, [L][R][Q] like the heights: planes 0 .. L-2 hold
 z_0 .. z_{L-2}; the first L-1 entries of plane L-1 hold r_0 .. r_{L-2}; the
 rest of plane L-1 is ignored.  The log-prior in latent coordinates is
 -1/2 sum z^2 (constants dropped) when every r lies in (0, 1), else -inf.
+
+Parity pins (tests/test_oracle_copula.py): the spectral root squaring to
+the dense covariance, the constant diagonal, independent columns at r = 0,
+ordering below the terrain, uniform marginals, the latent log-prior, and
+the reverse pass against central differences and a closed form at r = 0.
+Every function is pinned.
 """
 from __future__ import annotations
 

@@ -20,6 +20,11 @@ the definitions rather than to be fast.
   Fig. tomography_std_poisson): voxel columns at the surface nodes, voxel
   levels z_k = k * (Lz / n_z), k = 0 .. n_z - 1; the population standard
   deviation over the samples, sqrt(mean(B^2) - mean(B)^2).
+
+Parity pins (tests/test_oracle_diagnostics.py): a hand-computed example,
+identical super-chains, affine invariance, the Gelman-Rubin special case,
+i.i.d. draws, and closed forms of the interface deviation.  Every function
+is pinned.
 """
 from __future__ import annotations
 

@@ -13,6 +13,10 @@ States are stored in a fixed precision (FP32 heights in the FP32 modes), so
 the log-density and its gradient are evaluated at the stored, rounded
 position; the trajectory itself is carried in FP64.  ``state`` gives that
 rounding (np.float32 or np.float64).
+
+Parity pins (tests/test_oracle_hmc.py): reversibility, second-order energy
+error, the one-step trajectory as a Langevin proposal, and a full period of
+the harmonic oscillator.  Every function is pinned.
 """
 from __future__ import annotations
 

@@ -20,6 +20,11 @@ grid of Sec. 2.1.4 (Eq. def_LM_density_grid_smooth):
 Readings (the paper gives neither): voxel columns are the surface grid's
 cells with the surface at the cell centre; the voxel's density is taken at
 its centre height.
+
+Parity pins (tests/test_oracle_linear.py): voxel lengths summing to the
+in-box segment, vertical and diagonal rays, flat-layer densities, exactness
+at the reference with a second-order remainder, and central differences of
+the gradient.  Every function is pinned.
 """
 from __future__ import annotations
 

@@ -27,6 +27,11 @@ of chain c at step k from heights q0 (log-density ll0 + lp0, gradient g0):
                (the acceptance statistic the step-size adaptation uses).
 
 The chain moves to the trajectory's sample; there is no separate accept.
+
+Parity pins (tests/test_oracle_nuts.py): depth 1 as one-step HMC, uniform
+choice among equal energies, a Gaussian left invariant, the trajectory's
+extent, and a diagonal metric as the unit one in rescaled coordinates.
+Every function is pinned.
 """
 from __future__ import annotations
 
