@@ -185,6 +185,10 @@ class Clocks:
                 "power_w_max": max(pw) if pw else None}
 
 
+# chains of the oracle's timed sample: about 2 s on 16 host cores (~30 core-s)
+CPU_SAMPLE_CHAINS = 24
+
+
 def cpu_baseline(pr, counts, Hs, n_chains_sample):
     """The oracle (FP64 C, threads over (chain, sensor)) on a bounded sample of the workload."""
     import oracle
@@ -778,7 +782,7 @@ def main():
             e2e = measure_e2e(ctx, H0np, stream, args, w, rays)
         cpu = None
         if not args.no_cpu:
-            cpu = cpu_baseline(pr, counts.cpu().numpy(), H0np.astype(np.float64), 8)
+            cpu = cpu_baseline(pr, counts.cpu().numpy(), H0np.astype(np.float64), CPU_SAMPLE_CHAINS)
         out = {
             "metric": "chain-ray loglik evals/s", "value": value, "unit": "chain-ray/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
