@@ -1,0 +1,65 @@
+"""Compile-time resources of the hot kernels (ptxas -v, sm_103a, no GPU):
+every instantiation of the ray kernel and of the adjoint compiles without
+register spills, and the ray kernel of the FP32 modes fits its 1024-thread
+CTA in 64 registers per thread (65 536 registers per SM)."""
+import concurrent.futures as cf
+import os
+import re
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2603_28907_gb300 import build as B
+
+CSRC = os.path.join(os.path.dirname(B.OUT), "csrc")
+UNITS = ["march_f32.cu", "march_f32c.cu", "march_bf16.cu", "march_f64.cu", "adjoint.cu"]
+
+
+def _ptxas_report(unit, tmp):
+    cmd = [B.nvcc(), "-c", os.path.join(CSRC, unit), "-o", os.path.join(tmp, unit + ".o")] + B._flags(True)
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = {}
+    for block in r.stderr.split("Compiling entry function '")[1:]:
+        name = block.split("'", 1)[0]
+        regs = [int(x) for x in re.findall(r"Used (\d+) registers", block)]
+        spills = [int(x) for x in re.findall(r"(\d+) bytes spill (?:stores|loads)", block)]
+        out[name] = (max(regs) if regs else 0, max(spills) if spills else 0)
+    return out
+
+
+@pytest.fixture(scope="module")
+def reports():
+    try:
+        B.nvcc()
+    except Exception:
+        pytest.skip("nvcc not available")
+    tmp = tempfile.mkdtemp(prefix="mt_ptxas_")
+    try:
+        with cf.ThreadPoolExecutor(len(UNITS)) as ex:
+            res = dict(zip(UNITS, ex.map(lambda u: _ptxas_report(u, tmp), UNITS)))
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+    return res
+
+
+def test_hot_kernels_do_not_spill(reports):
+    n = 0
+    for unit, rep in reports.items():
+        for name, (regs, spill) in rep.items():
+            if "k_march" in name or "k_adjoint" in name:
+                assert spill == 0, (unit, name, regs, spill)
+                n += 1
+    assert n >= 10
+
+
+def test_fp32_ray_kernel_fits_1024_threads(reports):
+    n = 0
+    for unit in ("march_f32.cu", "march_f32c.cu"):
+        for name, (regs, _) in reports[unit].items():
+            if "k_march" in name:
+                assert 0 < regs <= 64, (unit, name, regs)
+                n += 1
+    assert n >= 2
