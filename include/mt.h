@@ -35,6 +35,7 @@
 #ifndef MT_H
 #define MT_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)

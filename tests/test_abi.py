@@ -118,3 +118,49 @@ def test_binding_fails_loudly_without_the_library(monkeypatch):
     monkeypatch.setattr(mt, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libmt.so"))
     with pytest.raises(RuntimeError, match="missing"):
         mt.load()
+
+
+def test_header_is_self_contained_c_and_cpp():
+    """include/mt.h compiles on its own as C99 and as C++11, warnings as errors."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc") or not shutil.which("g++"):
+        pytest.skip("no host compiler")
+    hdr = os.path.join(ROOT, "include", "mt.h")
+    for cc, lang, std in (("gcc", "c", "-std=c99"), ("g++", "c++", "-std=c++11")):
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                            "-x", lang, hdr], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
+def test_plain_c_client_links_and_calls(lib, tmp_path):
+    """A C99 program that includes only mt.h links against libmt.so, can take
+    the address of every declared call, and gets a status code back from
+    mt_create (MT_ECUDA without a device)."""
+    import shutil
+    import subprocess
+    import torch
+    if not shutil.which("gcc"):
+        pytest.skip("no host compiler")
+    names = declared_symbols()
+    src = ["#include <stdio.h>", '#include "mt.h"', "int main(void) {",
+           "    void *fns[] = {" + ", ".join(f"(void *)&{n}" for n in names) + "};",
+           "    mt_config cfg = {MT_PREC_F32, 64, 1.0, 1e4, 150.0, 0.01, 0.99, 0.1};",
+           "    mt_ctx *ctx = NULL;",
+           "    mt_status st = mt_create(&ctx, 0, &cfg, NULL);",
+           '    printf("%d %d\\n", (int)st, (int)(sizeof fns / sizeof fns[0]));',
+           "    if (ctx) mt_destroy(ctx);",
+           "    return 0;", "}"]
+    c = tmp_path / "client.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(B.OUT)
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", str(c), "-I", os.path.join(ROOT, "include"),
+                        "-L", libdir, "-l:" + os.path.basename(B.OUT), f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    st, n = map(int, out.stdout.split())
+    assert n == len(names)
+    assert st == (0 if torch.cuda.is_available() else -4)
