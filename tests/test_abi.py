@@ -164,3 +164,77 @@ def test_plain_c_client_links_and_calls(lib, tmp_path):
     st, n = map(int, out.stdout.split())
     assert n == len(names)
     assert st == (0 if torch.cuda.is_available() else -4)
+
+
+def _header_prototypes():
+    txt = open(os.path.join(ROOT, "include", "mt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"MT_API\s+[\w\s\*]*?\b(mt_[a-z_0-9]+)\s*\(([^)]*)\)", txt):
+        params = [p.strip() for p in m.group(2).split(",") if p.strip() and p.strip() != "void"]
+        protos[m.group(1)] = params
+    return protos
+
+
+def _ctype_class(param):
+    """Broad class of a C parameter: 'ptr:<pointee>' or the scalar type."""
+    p = re.sub(r"\bconst\b", "", param)
+    if "[" in p:                                  # an array parameter is a pointer
+        p = p.split()[0] + " *"
+    if "*" in p:
+        pointee = p.split("*")[0].split()
+        return "ptr:" + (pointee[-1] if pointee else "")
+    return p.split()[0]
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes signature has the header's arity, and each argument the
+    header's scalar type (int, double, int64_t, uint64_t, size_t) or a
+    pointer (with the pointee type where the binding names one)."""
+    import ctypes as C
+    scalar = {"int": C.c_int, "double": C.c_double, "int64_t": C.c_int64, "uint64_t": C.c_uint64,
+              "size_t": C.c_size_t}
+    pointee = {"double": C.c_double, "int": C.c_int, "int64_t": C.c_int64}
+    protos = _header_prototypes()
+    for name, args in mt.SIGNATURES.items():
+        params = protos[name]
+        assert len(params) == len(args), (name, params, args)
+        for p, a in zip(params, args):
+            k = _ctype_class(p)
+            if k.startswith("ptr:"):
+                assert a is C.c_void_p or hasattr(a, "_type_") and issubclass(a, C._Pointer), (name, p, a)
+                t = k[4:]
+                if a is not C.c_void_p and t in pointee:
+                    assert a._type_ is pointee[t], (name, p, a)
+            else:
+                assert a is scalar[k], (name, p, a)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof and every field offset of the ABI structs, as a C compiler lays
+    them out, equal the binding's ctypes structures."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no host compiler")
+    structs = {"mt_config": mt.Config, "mt_request": mt.Request, "mt_request_info": mt.RequestInfo,
+               "mt_server_stats_t": mt.ServerStats}
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "mt.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        src.append(f'    printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            src.append(f'    printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    src += ["    return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", str(c), "-I", os.path.join(ROOT, "include"),
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {(a, b): int(v) for a, b, v in (l.split() for l in out if l)}
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == C.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
