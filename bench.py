@@ -198,10 +198,16 @@ def cpu_baseline(pr, counts, Hs, n_chains_sample):
     op.loglik_batch(Hs[:n_chains_sample], n_threads=cores)
     dt = time.perf_counter() - t
     rays = n_chains_sample * pr["S"] * pr["P"]
+    # the same oracle on one thread, one chain
+    t = time.perf_counter()
+    op.loglik_batch(Hs[:1], n_threads=1)
+    dt1 = time.perf_counter() - t
     return {"value": rays / dt, "unit": "chain-ray/s", "cores": cores, "kind": "oracle",
             "sample": f"{n_chains_sample} chains x {pr['S'] * pr['P']} rays (all sensors and "
                       f"pixels) of the same workload, one log-likelihood each, FP64, "
-                      f"{dt:.2f} s wall"}
+                      f"{dt:.2f} s wall",
+            "single_thread": {"value": pr["S"] * pr["P"] / dt1, "unit": "chain-ray/s", "cores": 1,
+                              "sample": f"1 chain x {pr['S'] * pr['P']} rays, {dt1:.2f} s wall"}}
 
 
 def bench_config(w, C, world):
