@@ -248,6 +248,17 @@ class Context:
                                                        C.byref(stp)))
         return stp.value
 
+    def run_traced(self, kernel, step, n_super, n_within, loglik_trace, logprior_trace,
+                   accepts_trace=None):
+        """mt_run one super-step at a time, reading each chain's log-likelihood
+        and log-prior (and accept count) after every super-step into row k of
+        the [n_super][C] traces (device or host; one mt_get_state, which
+        synchronises, per super-step)."""
+        for k in range(n_super):
+            self.run(kernel, step, 1, n_within)
+            self.get_state(None, loglik_trace[k], logprior_trace[k],
+                           None if accepts_trace is None else accepts_trace[k])
+
     def get_last_step(self, proposal_out=None, loglik_out=None, logprior_out=None,
                       accepted_out=None, logu_out=None):
         self._ck("mt_get_last_step", self.lib.mt_get_last_step(

@@ -238,3 +238,18 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == C.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_run_traced_reads_the_state_after_every_super_step():
+    """Context.run_traced (host loop over the ABI calls): one super-step per
+    mt_run, then mt_get_state into that super-step's row of each trace."""
+    import numpy as np
+    calls = []
+    ctx = object.__new__(mt.Context)
+    ctx.run = lambda kernel, step, n_super, n_within: calls.append(("run", kernel, step, n_super, n_within))
+    ctx.get_state = lambda h, ll, lp, acc: calls.append(("state", h, ll.base is not None, lp.shape, acc))
+    ll, lp = np.zeros((3, 5)), np.zeros((3, 5))
+    ctx.run_traced(mt.KERNEL_RW, 0.01, 3, 10, ll, lp)
+    assert calls[0::2] == [("run", mt.KERNEL_RW, 0.01, 1, 10)] * 3
+    assert all(c[0] == "state" and c[1] is None and c[2] and c[3] == (5,) and c[4] is None
+               for c in calls[1::2])
