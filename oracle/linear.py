@@ -22,7 +22,8 @@ cells with the surface at the cell centre; the voxel's density is taken at
 its centre height.
 
 Parity pins (tests/test_oracle_linear.py): voxel lengths summing to the
-in-box segment, vertical and diagonal rays, flat-layer densities, exactness
+in-box segment, vertical and diagonal rays, a vertical ray through a
+non-flat column against the cell-centre reading, flat-layer densities, exactness
 at the reference with a second-order remainder, and central differences of
 the gradient.  Every function is pinned.
 """

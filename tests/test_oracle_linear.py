@@ -1,6 +1,7 @@
 """Pins of the linearised-forward-model oracle (oracle/linear.py; Sec.
 2.1.2): voxel path lengths sum to the in-box length, axis-parallel and
-diagonal rays against hand counts, the voxel density of flat layers, the
+diagonal rays against hand counts, a vertical ray's opacity through a
+non-flat column, the voxel density of flat layers, the
 linearisation exact at the reference and second order away from it."""
 import math
 
@@ -36,6 +37,36 @@ def test_vertical_and_diagonal_rays():
     seg = dict(LN.ray_voxel_lengths([1e-9, 1e-9, 1e-9], d, box, 2, 2, 2))
     assert set(seg) == {0, 7}
     assert abs(seg[0] - 50.0 * math.sqrt(3.0)) < 1e-6 and abs(seg[7] - 50.0 * math.sqrt(3.0)) < 1e-6
+
+
+def test_vertical_ray_through_a_non_flat_column():
+    """A ray straight up through column (i, j) of a non-square grid with
+    random heights (hard indicator): its opacity is the sum over levels of dz
+    times the density of the unit that contains the level's centre, the unit
+    being set by the heights at the centre of that cell (mean of its four
+    corner nodes).  Ties voxel indexing, density layout and the cell-centre
+    reading together."""
+    rng = np.random.default_rng(4)
+    R, Q, nz = 5, 7, 20                                   # 4 x 6 cells, dz = 7.5 m
+    w = W.small(R=R, Q=Q, bases=(40.0, 75.0, 110.0), rho=(2.65, 1.9, 0.0012, 2.3), gamma=0.0)
+    pr = W.problem(w)
+    H = np.stack([b + rng.uniform(-12.0, 12.0, (R, Q)) for b in (40.0, 75.0, 110.0)])
+    dx, dy, dz = pr["box"][0] / (Q - 1), pr["box"][1] / (R - 1), pr["box"][2] / nz
+    Rd = LN.density(H, pr, nz).reshape(-1)
+    for (i, j, z0) in ((1, 4, 3.0), (3, 0, 11.0), (2, 5, 0.5)):
+        o = [(j + 0.3) * dx, (i + 0.6) * dy, z0]
+        seg = LN.ray_voxel_lengths(o, [0.0, 0.0, 1.0], pr["box"], Q - 1, R - 1, nz)
+        O = sum(L * Rd[v] for v, L in seg)
+        hc = [0.25 * (H[l, i, j] + H[l, i, j + 1] + H[l, i + 1, j] + H[l, i + 1, j + 1]) for l in range(3)]
+        ref = 0.0
+        for k in range(nz):
+            lo, hi = max(k * dz, z0), (k + 1) * dz
+            if hi <= lo:
+                continue
+            zc = (k + 0.5) * dz
+            unit = sum(1 for h in hc if h < zc)           # surfaces below the level centre
+            ref += (hi - lo) * pr["rho"][unit]
+        assert abs(O - ref) < 1e-9, (i, j, O, ref)
 
 
 def test_flat_layers_density():
