@@ -22,7 +22,8 @@ rest of plane L-1 is ignored.  The log-prior in latent coordinates is
 -1/2 sum z^2 (constants dropped) when every r lies in (0, 1), else -inf.
 
 Parity pins (tests/test_oracle_copula.py): the spectral root squaring to
-the dense covariance, the constant diagonal, independent columns at r = 0,
+the dense covariance, the whole transform with one r per surface against a
+dense matrix square root, the constant diagonal, independent columns at r = 0,
 ordering below the terrain, uniform marginals, the latent log-prior, and
 the reverse pass against central differences and a closed form at r = 0.
 Every function is pinned.

@@ -62,6 +62,32 @@ def test_r_zero_gives_independent_columns():
     np.testing.assert_allclose(H[1], H[0] + u1 * (150.0 - H[0]), rtol=1e-12)
 
 
+def test_heights_against_dense_linear_algebra():
+    """The whole transform with a different r per surface, against a route
+    that shares nothing with the oracle's FFT: the symmetric square root of
+    the dense covariance Q(r_l)^-1 (scipy.linalg.sqrtm), each node's variance
+    from the dense diagonal, Phi, and the stick-breaking of Eq.
+    indep_columns (H_l = (1 - u_l) H_(l-1) + u_l T, H_(-1) = 0), top = T."""
+    from scipy.linalg import sqrtm
+    rng = np.random.default_rng(6)
+    L, R, Q = 4, 4, 5
+    lat = rng.standard_normal((L, R, Q))
+    rs = [0.3, 0.95, 0.7]
+    lat[L - 1] = 0.0
+    lat[L - 1].reshape(-1)[:L - 1] = rs
+    T = 130.0 + 10.0 * rng.random((R, Q))
+    H = K.heights(lat, T)
+    below = np.zeros((R, Q))
+    for l in range(L - 1):
+        cov = np.linalg.inv(dense_Q(R, Q, rs[l]))
+        x = np.real(sqrtm(cov)) @ lat[l].reshape(-1)
+        u = ndtr(x / np.sqrt(np.diag(cov))).reshape(R, Q)
+        ref = (1.0 - u) * below + u * T
+        np.testing.assert_allclose(H[l], ref, rtol=1e-9, atol=1e-9)
+        below = ref
+    np.testing.assert_array_equal(H[L - 1], T)
+
+
 def test_heights_are_ordered_below_the_terrain():
     rng = np.random.default_rng(2)
     L, R, Q = 4, 6, 8
