@@ -242,12 +242,13 @@ MT_API mt_status mt_set_nuts(mt_ctx *ctx, int max_depth);
  * the step size is tuned toward a target acceptance probability, 0.8 in the
  * paper) by per-chain dual averaging of log eps (Hoffman & Gelman 2014,
  * Sec. 3.2.1; gamma = 0.05, t0 = 10, kappa = 0.75, mu = log(10 eps0)).
- * n_adapt > 0 turns per-chain step sizes on: the next MALA or HMC mt_run
- * starts every chain at eps0 = its `step`, and its first n_adapt MALA / HMC
- * steps (counted across runs) each update chain c's eps from that step's
- * acceptance probability alpha = min(1, e^Delta) (0 outside the prior's
- * support); after the n_adapt-th every chain keeps its averaged step size
- * eps_bar, and later MALA / HMC runs use it and ignore `step`.  New chains
+ * n_adapt > 0 turns per-chain step sizes on: the next MALA, HMC or NUTS
+ * mt_run starts every chain at eps0 = its `step`, and its first n_adapt
+ * gradient-sampler steps (counted across runs) each update chain c's eps
+ * from that step's acceptance probability alpha = min(1, e^Delta) (0 outside
+ * the prior's support; for NUTS the trajectory's acceptance statistic, see
+ * mt_set_nuts); after the n_adapt-th every chain keeps its averaged step
+ * size eps_bar, and later MALA / HMC / NUTS runs use it and ignore `step`.  New chains
  * (mt_init_chains) restart the adaptation.  n_adapt = 0 turns it off (the
  * scalar `step` again).  target_accept in (0, 1), n_adapt >= 0, else
  * MT_EINVAL.  Random-walk steps neither use nor change the step sizes. */
@@ -277,10 +278,10 @@ MT_API mt_status mt_set_metric_adapt(mt_ctx *ctx, int on, double shrink);
  * an armed warm-up with the metric adapted. */
 MT_API mt_status mt_get_metric(mt_ctx *ctx, double *inv_metric_out);
 
-/* The per-chain step sizes the next MALA / HMC step uses and the
+/* The per-chain step sizes the next MALA / HMC / NUTS step uses and the
  * acceptance probability of each chain's last adapted step, host or device
  * double [n_chains] each (nullable).  Synchronous.  MT_ESTATE before the
- * first MALA / HMC run after mt_set_adapt (or with adaptation off). */
+ * first MALA / HMC / NUTS run after mt_set_adapt (or with adaptation off). */
 MT_API mt_status mt_get_adapt(mt_ctx *ctx, double *eps_out, double *accept_prob_out);
 
 /* Copy the chains' current state out (each pointer host or device, nullable):
