@@ -98,6 +98,10 @@ struct mt_ctx {
     float2 *d_muff = nullptr;        // float-float prior mean (FP32-mode prior)
     float4 *d_o4 = nullptr, *d_s4 = nullptr;
     float *d_kz0 = nullptr;
+    float4 *d_xa4 = nullptr, *d_xb4 = nullptr;  // ray table of the FP32 march
+    int2 *d_xc2 = nullptr;
+    float *d_kz1 = nullptr;
+    float psi_kc = 0.f;              // calibrated logistic correction (kappa * 2^-28)
     double *d_od = nullptr, *d_sd = nullptr, *d_dt = nullptr, *d_a = nullptr, *d_sumK = nullptr;
     float2 *d_dtff = nullptr, *d_aff = nullptr;
     int32_t *d_cnt = nullptr;
@@ -309,7 +313,9 @@ static void refresh_prob(mt_ctx *ctx)
     pb.tau = ctx->cfg.tau;
     pb.car_r = ctx->cfg.car_r;
     pb.delta = ctx->cfg.min_thick;
-    pb.kg = ctx->cfg.gamma > 0.0 ? (float)(1.4426950408889634074 / ctx->cfg.gamma) : 1.0f;
+    pb.kg64 = ctx->cfg.gamma > 0.0 ? 1.4426950408889634074 / ctx->cfg.gamma : 1.0;
+    pb.kg = (float)pb.kg64;
+    pb.kgl = (float)(pb.kg64 - (double)pb.kg);
     // largest float below n - 3/2 by 8 ulps: keeps the cell index <= n - 2
     auto hi = [](int n) {
         float v = (float)n - 1.5f;
@@ -339,6 +345,21 @@ static void refresh_prob(mt_ctx *ctx)
         pb.ref[l] = (float)m;
     }
     pb.kz0 = ctx->d_kz0;
+    // Grid of the march's z high parts (log2 units): 2^(e - 24) with 2^e above
+    // twice the largest kg64 * |z - ref_l| a sample can have, so that
+    // hi + k * step_hi (each off the exact value by at most half a grid step
+    // per term, k < G) stays below 2^e and is exact in FP32.
+    {
+        double rmax = 0.0;
+        for (int l = 0; l < ctx->L && l < MT_MAX_L; ++l) rmax = fmax(rmax, fabs((double)pb.ref[l]));
+        const double bound = 2.0 * (pb.kg64 * (ctx->box[2] + rmax) + 1.0);
+        pb.zgrid = ldexp(1.0, ilogb(bound) + 1 - 24);
+    }
+    pb.xa4 = ctx->d_xa4;
+    pb.xb4 = ctx->d_xb4;
+    pb.xc2 = ctx->d_xc2;
+    pb.kz1 = ctx->d_kz1;
+    pb.psi_kc = ctx->psi_kc;
     pb.mu_ff = ctx->d_muff;
     pb.lz_f = (float)ctx->box[2];
     if ((double)pb.lz_f > ctx->box[2]) pb.lz_f = nextafterf(pb.lz_f, -INFINITY);
@@ -384,6 +405,10 @@ static mt_status build_raytab(mt_ctx *ctx)
     TRY(dalloc(ctx, &ctx->d_o4, n));
     TRY(dalloc(ctx, &ctx->d_s4, n));
     TRY(dalloc(ctx, &ctx->d_kz0, 2 * (size_t)ctx->L * n));
+    TRY(dalloc(ctx, &ctx->d_xa4, n));
+    TRY(dalloc(ctx, &ctx->d_xb4, n));
+    TRY(dalloc(ctx, &ctx->d_xc2, n));
+    TRY(dalloc(ctx, &ctx->d_kz1, 2 * (size_t)ctx->L * n));
     TRY(dalloc(ctx, &ctx->d_od, 3 * n));
     TRY(dalloc(ctx, &ctx->d_sd, 3 * n));
     TRY(dalloc(ctx, &ctx->d_dt, n));
@@ -392,6 +417,20 @@ static mt_status build_raytab(mt_ctx *ctx)
     refresh_prob(ctx);
     CK(ctx, launch_raytab(ctx->pb, ctx->d_sensors, ctx->d_dirs, ctx->d_o4, ctx->d_s4, ctx->d_kz0,
                           ctx->d_od, ctx->d_sd, ctx->d_dt, ctx->d_dtff, ctx->d_flag, ctx->stream));
+    CK(ctx, launch_raytab_march(ctx->pb, ctx->d_sensors, ctx->d_dirs, ctx->d_xa4, ctx->d_xb4, ctx->d_xc2,
+                                ctx->d_kz1, ctx->d_flag, ctx->stream));
+    {
+        // the march's logistic, calibrated once per context on its device
+        double *d_k = nullptr, kappa = 0.0;
+        TRY(dalloc(ctx, &d_k, 1));
+        CK(ctx, launch_psi_calib(d_k, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(&kappa, d_k, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(d_k);
+        if (!(fabs(kappa) < 1e-5)) return fail(ctx, MT_ECUDA, "logistic calibration out of range: %g", kappa);
+        ctx->psi_kc = (float)(kappa * 0x1p-28);
+        ctx->pb.psi_kc = ctx->psi_kc;
+    }
     // March order: rays sorted by their vertical step per sample, then by the
     // height of their first sample (ties by ray index).  A surface's sample
     // window depends on those two numbers only, so a warp's 32 rays then run
@@ -808,6 +847,10 @@ mt_status mt_destroy(mt_ctx *ctx)
     dfree(ctx->d_o4);
     dfree(ctx->d_s4);
     dfree(ctx->d_kz0);
+    dfree(ctx->d_xa4);
+    dfree(ctx->d_xb4);
+    dfree(ctx->d_xc2);
+    dfree(ctx->d_kz1);
     dfree(ctx->d_od);
     dfree(ctx->d_sd);
     dfree(ctx->d_dt);

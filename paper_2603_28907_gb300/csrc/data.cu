@@ -97,6 +97,131 @@ cudaError_t launch_raytab(const Prob &pb, const double *d_sensors, const double 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- FP32 march ray table
+// The FP32 march forms sample k's cell coordinate as
+//   g = fmaf(k, sh, fmaf(k, sl, o))   (relative to the ray's start cell c0)
+// with o = gx0 - 1/2 - c0 in [-1/2, 1/2] and the step split sh + sl, so the
+// position carries no per-ray FP32 offset (the sample-0 point and the step
+// are exact to ~2^-48) and only the final rounding, which differs from
+// sample to sample.  Its cell is c0 + round(g).  g is monotone in k, so the
+// cells of the first and last sample decide whether all lie in [0, n - 2];
+// where rounding at a face of the box would leave that range, o and sh move
+// inward by a few ulps (this does not happen for rays that start inside the
+// box away from a face).
+__device__ __forceinline__ int rel_cell(float o, float sl, float sh, float kf)
+{
+    const float g = fmaf(kf, sh, fmaf(kf, sl, o));
+    return __float_as_int(g + 12582912.0f) - 0x4B400000;
+}
+
+__device__ bool fit_axis_rel(float &o, float &sh, float sl, int c0, int n, int G)
+{
+    const float kl = (float)(G - 1);
+    for (int it = 0; it < 64; ++it) {
+        const int a = c0 + rel_cell(o, sl, sh, 0.0f), b = c0 + rel_cell(o, sl, sh, kl);
+        const bool oka = a >= 0 && a <= n - 2, okb = b >= 0 && b <= n - 2;
+        if (oka && okb) return true;
+        if (!oka) o = nextafterf(o, a < 0 ? INFINITY : -INFINITY);
+        if (!okb) sh = nextafterf(sh, b < 0 ? INFINITY : -INFINITY);
+    }
+    return false;
+}
+
+// z per surface in log2 units, kg64 (z - ref_l), split into a high part on
+// the grid pb.zgrid and an FP32 remainder; likewise the per-sample step.
+// Every sample's |kg64 (z - ref_l)| lies below half the bound the grid was
+// chosen for, so hi + k * step_hi is exact in FP32 for all k < G.
+__global__ void k_raytab_march(Prob pb, const double *sensors, const double *dirs, float4 *xa4, float4 *xb4,
+                               int2 *xc2, float *kz1, int *flag)
+{
+    const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= pb.n_rays) return;
+    const int s = ray / pb.P, p = ray - s * pb.P;
+    const double o[3] = {sensors[3 * s], sensors[3 * s + 1], sensors[3 * s + 2]};
+    const double d[3] = {dirs[3 * p], dirs[3 * p + 1], dirs[3 * p + 2]};
+    double te = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        double ta = INFINITY;
+        if (d[a] > 0.0) ta = (pb.box[a] - o[a]) / d[a];
+        else if (d[a] < 0.0) ta = (0.0 - o[a]) / d[a];
+        te = fmin(te, ta);
+    }
+    const double dt = te / (double)pb.G;
+    const double sx = (double)(pb.Q - 1) / pb.box[0], sy = (double)(pb.R - 1) / pb.box[1];
+    const double gx0 = (o[0] + 0.5 * dt * d[0]) * sx - 0.5, gsx = dt * d[0] * sx;
+    const double gy0 = (o[1] + 0.5 * dt * d[1]) * sy - 0.5, gsy = dt * d[1] * sy;
+    const double z0 = o[2] + 0.5 * dt * d[2], sz = dt * d[2];
+    const int c0x = min(max((int)rint(gx0), 0), pb.Q - 2), c0y = min(max((int)rint(gy0), 0), pb.R - 2);
+    float ox = (float)(gx0 - (double)c0x), oy = (float)(gy0 - (double)c0y);
+    float sxh = (float)gsx, syh = (float)gsy;
+    const float sxl = (float)(gsx - (double)sxh), syl = (float)(gsy - (double)syh);
+    const bool ok = fit_axis_rel(ox, sxh, sxl, c0x, pb.Q, pb.G) & fit_axis_rel(oy, syh, syl, c0y, pb.R, pb.G);
+    if (!ok) atomicOr(flag, 2);
+    const double g = pb.zgrid;
+    const double ksz = pb.kg64 * sz;
+    const double szh = rint(ksz / g) * g;
+    xa4[ray] = make_float4(ox, oy, sxh, syh);
+    xb4[ray] = make_float4(ok ? sxl : 0.f, ok ? syl : 0.f, (float)szh, (float)(ksz - szh));
+    if (!ok) xa4[ray] = make_float4(0.f, 0.f, 0.f, 0.f);  // keeps every sample in the start cell
+    xc2[ray] = make_int2(c0x, c0y);
+    for (int l = 0; l < pb.L; ++l) {
+        const double kz = pb.kg64 * (z0 - (double)pb.ref[l]);
+        const double hi = rint(kz / g) * g;
+        kz1[(size_t)l * pb.n_rays + ray] = (float)hi;
+        kz1[(size_t)(pb.L + l) * pb.n_rays + ray] = (float)(kz - hi);
+    }
+}
+
+cudaError_t launch_raytab_march(const Prob &pb, const double *d_sensors, const double *d_dirs, float4 *xa4,
+                                float4 *xb4, int2 *xc2, float *kz1, int *flag, cudaStream_t st)
+{
+    k_raytab_march<<<(pb.n_rays + 255) / 256, 256, 0, st>>>(pb, d_sensors, d_dirs, xa4, xb4, xc2, kz1, flag);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- logistic calibration
+// The FP32 march forms psi = 1 / (1 + 2^a), a = |argument| >= 0, as
+// rcp.approx((ex2.approx(a) + 1) c) with c = 2^-28.  Each approximation is
+// within a few ulps, but their errors have a nonzero mean (on GB300:
+// ex2.approx ~ +3.6e-8 relative, rcp.approx ~ +4e-9), and a transition that
+// the box cuts on one side (a surface within a few gamma of the box top, a
+// ray leaving through a wall) adds one side's psi values only, so that mean
+// survives: with ~1e5 such rays a far-off chain's log-likelihood would move
+// by ~1e-3.  This kernel measures the mean on the device the march runs on:
+// over a in [0, 16) (2^16 points; beyond, psi < 2^-16 carries no weight) the
+// relative error r(a) of the march's own instruction sequence against FP64,
+// weighted by psi (a one-sided transition's sum of psi errors), and returns
+// kappa = -sum psi r / sum psi (1 - psi): the march then uses
+// (2^a (1 - kappa) + 1) c, whose psi moves by +kappa (1 - psi) relative
+// (d psi / psi = -(1 - psi) d(2^a) / 2^a), which to first order cancels the
+// psi-weighted mean error.  One block, fixed summation order: the same kappa
+// on every call.
+__global__ void __launch_bounds__(1024) k_psi_calib(double *out)
+{
+    const int n = 1 << 16;
+    const float c = __uint_as_float(0x31800000u);  // 2^-28
+    double num = 0.0, den = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float a = (float)(16.0 * ((double)i + 0.5) / (double)n);
+        const float q = rcp_approx(fmaf(ex2_approx(a), c, c));  // psi 2^28, as in the march
+        const double E = exp2((double)a);
+        const double psi = 1.0 / (1.0 + E);
+        const double r = (double)q * 0x1p-28 / psi - 1.0;
+        num += psi * r;
+        den += psi * (1.0 - psi);
+    }
+    num = block_sum(num);
+    __syncthreads();
+    den = block_sum(den);
+    if (threadIdx.x == 0) out[0] = -num / den;
+}
+
+cudaError_t launch_psi_calib(double *out, cudaStream_t st)
+{
+    k_psi_calib<<<1, 1024, 0, st>>>(out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- counts
 // a = ln(I0 / C) per ray (the centred Poisson term's offset), and the data
 // constant sum_p (C ln C - C - ln C!) reduced in a fixed order by one block.

@@ -40,6 +40,19 @@ struct Prob {
     const float4 *o4;          // FP32 sample-0 cell coordinates {gx - 1/2, gy - 1/2, 0, 0}
     const float4 *s4;          // FP32 per-sample step {dgx, dgy, kg*dz hi, kg*dz lo}
     const float *kz0;          // [2][L][n_rays] kg * (z_0 - ref_l) as FP32 hi, lo
+    // Ray table of the FP32 modes' march (k_march), kept apart so that its
+    // sample positions carry no per-ray rounding offset:
+    const float4 *xa4;         // {ox, oy, sxh, syh}: sample-0 cell coordinate minus 1/2,
+                               // relative to the start cell; per-sample step, high part
+    const float4 *xb4;         // {sxl, syl, szh, szl}: low parts of the x, y steps; z step
+                               // (log2 units, FP64 kg) on the grid zgrid and its remainder
+    const int2 *xc2;           // start cell {c0x, c0y}
+    const float *kz1;          // [2][L][n_rays] kg64 * (z_0 - ref_l) on the grid zgrid, remainder
+    float kgl;                 // kg64 - kg (FP32 remainder of log2(e) / gamma)
+    float psi_kc;              // kappa * 2^-28: calibration of the march's logistic
+                               // (launch_psi_calib); 0 = none
+    double kg64;               // log2(e) / gamma in FP64 (1 for the hard indicator)
+    double zgrid;              // grid of the z high parts: 2^(e - 24) with |z| < 2^e
     float ref[MT_MAX_L];       // per-surface reference height of the FP32 paths
     float2 drho_ff[MT_MAX_L];  // float-float of drho
     const double *o_d;         // [3] FP64 sample-0 position {gx, gy, z}
@@ -101,6 +114,13 @@ mt_status ctx_fail(mt_ctx *ctx, mt_status st, const char *msg);
 cudaError_t launch_raytab(const Prob &pb, const double *d_sensors, const double *d_dirs,
                           float4 *o4, float4 *s4, float *kz0, double *o_d, double *s_d, double *dt,
                           float2 *dt_ff, int *flag, cudaStream_t st);
+// The FP32 march's ray table (Prob::xa4, xb4, xc2, kz1); pb.zgrid, pb.kg64
+// and pb.ref must be set.
+cudaError_t launch_raytab_march(const Prob &pb, const double *d_sensors, const double *d_dirs,
+                                float4 *xa4, float4 *xb4, int2 *xc2, float *kz1, int *flag,
+                                cudaStream_t st);
+// kappa of the march's logistic on this device (one double at out).
+cudaError_t launch_psi_calib(double *out, cudaStream_t st);
 cudaError_t launch_counts_prep(const Prob &pb, double *a, float2 *a_ff, double *sumK,
                                cudaStream_t st);
 cudaError_t launch_gen_counts(const Prob &pb, const double *h_nodes, uint64_t seed, int mode,

@@ -202,24 +202,6 @@ __device__ __forceinline__ float rcp_approx(float x)
 }
 
 
-// e^y - 1 - y in FP32 without cancellation (Taylor series for |y| < 1/2).
-__device__ __forceinline__ float g_f32(float y)
-{
-    if (fabsf(y) < 0.5f) {
-        float p = 1.0f / 3628800.0f;
-        p = fmaf(p, y, 1.0f / 362880.0f);
-        p = fmaf(p, y, 1.0f / 40320.0f);
-        p = fmaf(p, y, 1.0f / 5040.0f);
-        p = fmaf(p, y, 1.0f / 720.0f);
-        p = fmaf(p, y, 1.0f / 120.0f);
-        p = fmaf(p, y, 1.0f / 24.0f);
-        p = fmaf(p, y, 1.0f / 6.0f);
-        p = fmaf(p, y, 0.5f);
-        return p * y * y;
-    }
-    return expm1f(y) - y;
-}
-
 // float-float (unevaluated sum hi + lo) arithmetic from error-free transforms.
 struct FF {
     float hi, lo;
@@ -244,6 +226,44 @@ __device__ __forceinline__ FF ff_mul(FF a, FF b)
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
     return ff_two_sum(p, e);
+}
+
+// g(y) = e^y - 1 - y of a float-float y, to ~2^-44 relative: the centred
+// Poisson term of a ray is -C g(y), and a far-off chain sums ~1e5 of those
+// per log-likelihood, so a per-ray relative error of 1e-8 would already add
+// ~1e-3.  For |y| <= 1, g = y^2 P(y) with P(y) = sum_{n>=2} y^(n-2) / n!
+// (Taylor series of the exponential): the terms n = 2..5 in float-float
+// Horner steps, the rest (relative size < |y|^4 / 360 of P) in FP32.  Larger
+// |y| (a ray's expected count off its observed count by a factor e) are
+// rare and take FP64.
+__device__ __forceinline__ FF ff_const(double v) { return FF{(float)v, (float)(v - (double)(float)v)}; }
+
+__device__ __forceinline__ FF g_ff(FF y)
+{
+    const float yh = y.hi + y.lo;
+    if (!(fabsf(yh) <= 1.0f)) {
+        const double yd = (double)y.hi + (double)y.lo;
+        const double g = expm1(yd) - yd;
+        return ff_const(g);
+    }
+    // tail sum_{n>=6} y^(n-6) / n! to n = 17 (1/18! < 2^-52)
+    float q = (float)(1.0 / 355687428096000.0);  // 1/17!
+    q = fmaf(q, yh, (float)(1.0 / 20922789888000.0));
+    q = fmaf(q, yh, (float)(1.0 / 1307674368000.0));
+    q = fmaf(q, yh, (float)(1.0 / 87178291200.0));
+    q = fmaf(q, yh, (float)(1.0 / 6227020800.0));
+    q = fmaf(q, yh, (float)(1.0 / 479001600.0));
+    q = fmaf(q, yh, (float)(1.0 / 39916800.0));
+    q = fmaf(q, yh, (float)(1.0 / 3628800.0));
+    q = fmaf(q, yh, (float)(1.0 / 362880.0));
+    q = fmaf(q, yh, (float)(1.0 / 40320.0));
+    q = fmaf(q, yh, (float)(1.0 / 5040.0));
+    q = fmaf(q, yh, (float)(1.0 / 720.0));
+    FF p = ff_add(ff_mul(FF{q, 0.f}, y), ff_const(1.0 / 120.0));
+    p = ff_add(ff_mul(p, y), ff_const(1.0 / 24.0));
+    p = ff_add(ff_mul(p, y), ff_const(1.0 / 6.0));
+    p = ff_add(ff_mul(p, y), FF{0.5f, 0.f});
+    return ff_mul(ff_mul(y, y), p);
 }
 
 // ---------------------------------------------------------------- FP32 march
@@ -389,32 +409,64 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
 
 // ---------------------------------------------------------------- FP32 march, (h, dx) planes
 // One surface along one ray, two consecutive samples per step: lane .x of
-// every paired FP32 instruction carries sample k, lane .y sample k + 1.  Each
-// lane's arithmetic is that of one sample: position g = o + k gs, cell split,
-// bilinear height from the two left corners' (h, dx) records, float-float
-// z, sigmoid argument, 2^arg, reciprocal, sigma + 1.  The x-lerps read the
-// records as loaded (scalar FMAs), which leaves no register shuffling when a
-// sample enters a new cell; the corner records of both samples are cached
-// and reloaded when either sample enters a new cell.
+// every paired FP32 instruction carries sample k, lane .y sample k + 1.
+//
+// Arithmetic of one sample (the FP32 modes' accuracy rests on its order):
+//   position  g = fmaf(k, sh, fmaf(k, sl, o)) per axis, relative to the ray's
+//             start cell (the step split hi + lo), so no per-ray FP32 offset
+//             enters and each sample's rounding is its own; the cell split
+//             rounds g by adding 1.5 * 2^23 and the fraction g - round(g) is
+//             exact.
+//   height    the x-lerps read the (h_mid, dx) records as loaded (scalar
+//             FMAs), then the y-lerp; the result sl = s_l - ref_l.
+//   argument  a = kg64 (z - s_l) in log2 units with z - ref_l = zhi + zlo,
+//             zhi = zh + k szh exact (zh, szh on a grid), evaluated as
+//             (fmaf(-kgh, sl, fmaf(-kgl, sl, zlo))) + zhi: the small terms
+//             (the z remainder and the low part of kg) enter through the
+//             addend of a fused multiply-add whose product has full-width
+//             bits, and the final addition of the grid-aligned zhi is exact
+//             where |a| is small.  (Adding a small smooth term to an FP32 value
+//             already on its own grid would round coherently along the ray.)
+//   indicator varsigma = 1 / (1 + 2^a) through psi = 1 / (1 + 2^|a|) <= 1/2:
+//             varsigma = psi above the surface (a > 0), 1 - psi below it.  psi
+//             is formed as rcp((2^|a| (1 - kappa) + 1) c) with c = +-2^-28
+//             carrying a's sign (kappa: the approximations' mean error,
+//             calibrated per device, see k_psi_calib), rounded to the nearest
+//             integer q (units 2^-28), and the
+//             sample adds q + 2^28 [a < 0], i.e. round(varsigma 2^28), exactly:
+//             no 1 - psi is ever rounded in FP32, and tails of psi down to
+//             2^-29 are kept.
+// The integer adds c_bits >> 3 = 2^28 [a < 0] + kJunk per sample (the
+// exponent bits of 2^-28 shifted down); kJunk is subtracted once per window.
+// The corner records of both samples are cached and reloaded when either
+// sample enters a new cell.
+constexpr uint32_t kQuantBits = 0x31800000u;      // FP32 bits of 2^-28
+constexpr uint32_t kJunk = kQuantBits >> 3;       // added per sample by the sign trick
+constexpr unsigned long long kUnit = 1ull << 28;  // one indicator = 2^28 units
+
 template <bool HARD, bool GLOBAL>
-__device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, int R, int *flag, float2 kf2, float2 ox2,
-                                          float2 oy2, float2 sx2, float2 sy2, float2 szh2, float2 szl2,
-                                          float2 zh2, float2 zl2, float2 nkg2, int &curA, int &curB,
-                                          float2 &rA0, float2 &rA1, float2 &rB0, float2 &rB1)  // (h, dx): A/B x row r0/r0+1
+__device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int *flag, float2 kf2, float2 ox2,
+                                            float2 oy2, float2 sxh2, float2 sxl2, float2 syh2, float2 syl2,
+                                            float2 szh2, float2 szl2, float2 zh2, float2 zl2, float2 nkgh2,
+                                            float2 nkgl2, uint32_t nkc, uint32_t k0, int cell0, int2 c0,
+                                            int &curA, int &curB,
+                                            float2 &rA0, float2 &rA1, float2 &rB0, float2 &rB1)
 {
     const float2 M2 = f2(12582912.0f);  // 1.5 * 2^23: adding it rounds to an integer
-    const float2 gx = fma2(kf2, sx2, ox2), gy = fma2(kf2, sy2, oy2);
+    const float2 gx = fma2(kf2, sxh2, fma2(kf2, sxl2, ox2));
+    const float2 gy = fma2(kf2, syh2, fma2(kf2, syl2, oy2));
     const float2 tx = add2(gx, M2), ty = add2(gy, M2);
     const float2 fx = fma2(add2(tx, f2(-12582912.0f)), f2(-1.0f), gx);  // in [-1/2, 1/2] about the midpoint
     const float2 fy = add2(fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy), f2(0.5f));
 #ifdef MT_BOUNDS_CHECK
-    const bool in_grid = cell_ok(__float_as_int(tx.x) - 0x4B400000, __float_as_int(ty.x) - 0x4B400000, Q - 1, R - 1) &&
-                         cell_ok(__float_as_int(tx.y) - 0x4B400000, __float_as_int(ty.y) - 0x4B400000, Q - 1, R - 1);
+    const bool in_grid =
+        cell_ok(c0.x + __float_as_int(tx.x) - 0x4B400000, c0.y + __float_as_int(ty.x) - 0x4B400000, Q - 1, R - 1) &&
+        cell_ok(c0.x + __float_as_int(tx.y) - 0x4B400000, c0.y + __float_as_int(ty.y) - 0x4B400000, Q - 1, R - 1);
     if (!in_grid) atomicOr(flag, 4);
 #endif
     if constexpr (GLOBAL) {
-        int nA = (__float_as_int(ty.x) - 0x4B400000) * Q + (__float_as_int(tx.x) - 0x4B400000);
-        int nB = (__float_as_int(ty.y) - 0x4B400000) * Q + (__float_as_int(tx.y) - 0x4B400000);
+        int nA = cell0 + (__float_as_int(ty.x) - 0x4B400000) * Q + (__float_as_int(tx.x) - 0x4B400000);
+        int nB = cell0 + (__float_as_int(ty.y) - 0x4B400000) * Q + (__float_as_int(tx.y) - 0x4B400000);
 #ifdef MT_BOUNDS_CHECK
         if (!in_grid) nA = nB = 0;
 #endif
@@ -430,15 +482,14 @@ __device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, int R, int *f
         // reload both samples' corner records when either entered a new cell:
         // predicated shared loads instead of a divergent branch.  The record's
         // byte address 8 (Q iy + ix) + base comes straight from the float bits
-        // (ix = bits(tx) - 0x4B400000, likewise iy), modulo 2^32; the current
-        // cells are tracked by address (-1 is never one).
-        const uint32_t base = (uint32_t)__cvta_generic_to_shared(pl);
-        const uint32_t k0 = base - 8u * 0x4B400000u * (uint32_t)(Q + 1);
+        // (ix = bits(tx) - 0x4B400000 + c0x, likewise iy; k0 folds the base,
+        // the start cell and the bit offsets), modulo 2^32; the current cells
+        // are tracked by address (-1 is never one).
         const uint32_t rowb = 8u * (uint32_t)Q;
         uint32_t aA0 = (uint32_t)__float_as_int(ty.x) * rowb + ((uint32_t)__float_as_int(tx.x) * 8u + k0);
         uint32_t aB0 = (uint32_t)__float_as_int(ty.y) * rowb + ((uint32_t)__float_as_int(tx.y) * 8u + k0);
 #ifdef MT_BOUNDS_CHECK
-        if (!in_grid) aA0 = aB0 = base;
+        if (!in_grid) aA0 = aB0 = (uint32_t)__cvta_generic_to_shared(pl);
 #endif
         const uint32_t aA1 = aA0 + rowb, aB1 = aB0 + rowb;
         const uint32_t need = (uint32_t)(((int)aA0 != curA) | ((int)aB0 != curB));
@@ -456,61 +507,84 @@ __device__ __forceinline__ float2 dx_pair(const float2 *pl, int Q, int R, int *f
     const float2 a = make_float2(fmaf(fx.x, rA0.y, rA0.x), fmaf(fx.y, rB0.y, rB0.x));  // row r0
     const float2 b = make_float2(fmaf(fx.x, rA1.y, rA1.x), fmaf(fx.y, rB1.y, rB1.x));  // row r0 + 1
     const float2 sl = fma2(fy, fma2(a, f2(-1.0f), b), a);               // s_l - ref_l
-    const float2 zl = fma2(kf2, szl2, add2(fma2(kf2, szh2, zh2), zl2));
-    const float2 arg = fma2(nkg2, sl, zl);                              // -kg (s_l - z)
-    float2 sg;
+    const float2 zhi = fma2(kf2, szh2, zh2);                            // exact
+    const float2 zlo = fma2(kf2, szl2, zl2);
+    const float2 arg = add2(fma2(nkgh2, sl, fma2(nkgl2, sl, zlo)), zhi);  // kg64 (z - s_l)
     if constexpr (HARD) {
-        sg.x = arg.x < 0.f ? 1.f : (arg.x > 0.f ? 0.f : 0.5f);
-        sg.y = arg.y < 0.f ? 1.f : (arg.y > 0.f ? 0.f : 0.5f);
+        const uint32_t vx = arg.x < 0.f ? (uint32_t)kUnit : (arg.x > 0.f ? 0u : (uint32_t)(kUnit >> 1));
+        const uint32_t vy = arg.y < 0.f ? (uint32_t)kUnit : (arg.y > 0.f ? 0u : (uint32_t)(kUnit >> 1));
+        return vx + vy + 2u * kJunk;
     } else {
-        const float2 e = add2(make_float2(ex2_approx(arg.x), ex2_approx(arg.y)), f2(1.0f));
-        sg = make_float2(rcp_approx(e.x), rcp_approx(e.y));
+        const uint32_t cbx = (__float_as_uint(arg.x) & 0x80000000u) | kQuantBits;
+        const uint32_t cby = (__float_as_uint(arg.y) & 0x80000000u) | kQuantBits;
+        const float2 c = make_float2(__uint_as_float(cbx), __uint_as_float(cby));
+        // -kappa c with c's sign: (2^|a| (1 - kappa) + 1) c, the calibrated logistic
+        const float2 nk = make_float2(__uint_as_float((__float_as_uint(arg.x) & 0x80000000u) ^ nkc),
+                                      __uint_as_float((__float_as_uint(arg.y) & 0x80000000u) ^ nkc));
+        const float2 E = make_float2(ex2_approx(fabsf(arg.x)), ex2_approx(fabsf(arg.y)));
+        const float2 e = fma2(E, c, fma2(E, nk, c));
+        const int qx = __float2int_rn(rcp_approx(e.x)), qy = __float2int_rn(rcp_approx(e.y));
+        return ((uint32_t)qx + (cbx >> 3)) + ((uint32_t)qy + (cby >> 3));
     }
-    return add2(sg, f2(1.0f));
 }
 
-// Samples [lo, he) of one surface; adds the integer indicator sum (units
-// 2^-23) to t.  An odd count ends with one sample evaluated in both lanes and
+// Samples [lo, he) of one surface; adds the indicator sum in units of 2^-28
+// to t.  Per four steps (eight samples, < 2^32 with kJunk) the 32-bit sum
+// moves to t.  An odd count ends with one sample evaluated in both lanes and
 // counted once.
 template <bool HARD, bool GLOBAL>
-__device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, int R, int *flag, float4 o, float4 st,
-                                                 float nkg, float zh, float zl, int lo, int he,
-                                                 unsigned long long &t)
+__device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, int R, int *flag, float4 xa, float4 xb,
+                                                 float nkgh, float nkgl, uint32_t nkc, float zh, float zl, uint32_t k0,
+                                                 int cell0, int2 c0, int lo, int he, unsigned long long &t)
 {
-    const float2 ox2 = f2(o.x), oy2 = f2(o.y), sx2 = f2(st.x), sy2 = f2(st.y);
-    const float2 szh2 = f2(st.z), szl2 = f2(st.w), zh2 = f2(zh), zl2 = f2(zl), nkg2 = f2(nkg);
+    const float2 ox2 = f2(xa.x), oy2 = f2(xa.y), sxh2 = f2(xa.z), syh2 = f2(xa.w);
+    const float2 sxl2 = f2(xb.x), syl2 = f2(xb.y), szh2 = f2(xb.z), szl2 = f2(xb.w);
+    const float2 zh2 = f2(zh), zl2 = f2(zl), nkgh2 = f2(nkgh), nkgl2 = f2(nkgl);
     float2 rA0 = f2(0.f), rA1 = f2(0.f), rB0 = f2(0.f), rB1 = f2(0.f);
     int curA = -1, curB = -1;
     float2 kf2 = make_float2((float)lo, (float)lo + 1.0f);
     const int np = (he - lo) >> 1;
-    for (int j0 = 0; j0 < np; j0 += 128) {
-        const int jn = min(128, np - j0);
-        uint32_t acc = 0u;
-#pragma unroll 4
-        for (int j = 0; j < jn; ++j) {
-            const float2 v = dx_pair<HARD, GLOBAL>(pl, Q, R, flag, kf2, ox2, oy2, sx2, sy2, szh2, szl2, zh2, zl2,
-                                                   nkg2, curA, curB, rA0, rA1, rB0, rB1);
-            acc += __float_as_uint(v.x) + __float_as_uint(v.y);
-            kf2 = add2(kf2, f2(2.0f));
-        }
-        t += (unsigned long long)(acc - (uint32_t)(2 * jn) * 0x3F800000u);
+#define MT_PAIR()                                                                                             \
+    dx_pair<HARD, GLOBAL>(pl, Q, R, flag, kf2, ox2, oy2, sxh2, sxl2, syh2, syl2, szh2, szl2, zh2, zl2, nkgh2, \
+                          nkgl2, nkc, k0, cell0, c0, curA, curB, rA0, rA1, rB0, rB1)
+    int j = 0;
+    for (; j + 4 <= np; j += 4) {
+        uint32_t acc = MT_PAIR();
+        kf2 = add2(kf2, f2(2.0f));
+        acc += MT_PAIR();
+        kf2 = add2(kf2, f2(2.0f));
+        acc += MT_PAIR();
+        kf2 = add2(kf2, f2(2.0f));
+        acc += MT_PAIR();
+        kf2 = add2(kf2, f2(2.0f));
+        t += acc;
     }
+    uint32_t acc = 0u;
+    for (; j < np; ++j) {
+        acc += MT_PAIR();
+        kf2 = add2(kf2, f2(2.0f));
+    }
+    t += acc;
+    unsigned long long ns = 2ull * (unsigned long long)np;
     if ((he - lo) & 1) {
         kf2 = f2((float)(he - 1));
-        const float2 v = dx_pair<HARD, GLOBAL>(pl, Q, R, flag, kf2, ox2, oy2, sx2, sy2, szh2, szl2, zh2, zl2,
-                                               nkg2, curA, curB, rA0, rA1, rB0, rB1);
-        t += (unsigned long long)(__float_as_uint(v.x) - 0x3F800000u);
+        t += (unsigned long long)(MT_PAIR() >> 1);  // both lanes evaluated the same sample
+        ns += 1ull;
     }
+#undef MT_PAIR
+    t -= ns * (unsigned long long)kJunk;
 }
 
-// Samples whose sigmoid argument is at least kSat (log2 units) from zero have
-// integer contributions known without evaluating them.  Above the surface
-// (arg >= kSat > 24) 2^arg > 2^24 even with ex2.approx's relative error
-// (~2^-22), so sigma = rcp(1 + 2^arg) < 2^-24 and sigma + 1 rounds to exactly
-// 1.0f; below it (arg <= -kSat) 2^arg < 2^-24, 1 + 2^arg rounds to exactly
-// 1.0f, and the sample adds rcp(1) + 1.  The margin 0.25 over 24 is four
-// orders of magnitude above the FP32 rounding of the argument and of the
-// window bounds (~2e-5 log2 units).
+// Samples whose sigmoid argument is at least kSatX (log2 units) from zero
+// have integer contributions known without evaluating them: there
+// psi = 1 / (1 + 2^|a|) <= 2^-29.25 (1 + 2^-21) even with ex2.approx's and
+// rcp.approx's relative errors, so psi 2^28 < 1/2 rounds to 0 and the sample
+// adds exactly 0 above the surface and 2^28 below it.  The margin 0.25 over
+// 29 is four orders of magnitude above the FP32 rounding of the argument and
+// of the window bounds (~2e-5 log2 units).
+constexpr float kSatX = 29.25f;
+// The same bound for the adjoint's and the BF16 march's sigma + 1 form
+// (exact integer round(sigma 2^23) outside 24.25 log2 units).
 constexpr float kSat = 24.25f;
 
 // Sample window [lo, hi] in which surface l can be transitional along a ray:
@@ -544,29 +618,34 @@ __device__ __forceinline__ void transition_window(float z0, float dz, float rdz,
 }
 
 // The FP32 modes' march of one ray: per surface l, the exact integer sum
-// N_l = sum_k varsigma(s_l - z_k) * 2^23 (see march_ray_f32 for the
+// N_l = sum_k round(varsigma(s_l - z_k) 2^28) (see dx_pair for the
 // arithmetic), computed over the samples where surface l can be
 // transitional (transition_window with ext = per-surface min / max offsets);
-// the other samples' contributions are exact and added analytically (one
-// sample below the surface adds rcp(1) + 1 - 1 in units of 2^-23, one above
-// adds 0).  A window of odd length is widened by one saturated sample where
-// the ray has one, so that samples go in pairs.  emit(l, N_l * 2^23) is
-// called for l = 0 .. L-1 in order.
+// the other samples' contributions are exact and added analytically (2^28
+// below the surface, 0 above).  A window of odd length is widened by one
+// saturated sample where the ray has one, so that samples go in pairs.
+// emit(l, N_l) is called for l = 0 .. L-1 in order.
 template <int L, bool HARD, bool GLOBAL, typename Emit>
 __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *planes, int ray,
                                              const float *ext, unsigned long long *evaluated,
                                              Emit &&emit)
 {
-    const float4 o = pb.o4[ray], st = pb.s4[ray];
-    const uint32_t q_one = HARD ? 0x00800000u : __float_as_uint(rcp_approx(1.0f) + 1.0f) - 0x3F800000u;
+    const float4 xa = pb.xa4[ray], xb = pb.xb4[ray];
+    const int2 c0 = pb.xc2[ray];
+    const int cell0 = c0.y * pb.Q + c0.x;
     const int G = pb.G;
-    const float rdz = rcp_approx(st.z);
-#pragma unroll (L <= 5 ? L : 1)  // unrolled where registers allow (no spills)
+    const float dz = xb.z + xb.w;
+    const float rdz = rcp_approx(dz);
+    uint32_t k0 = 0u;
+    if constexpr (!GLOBAL)
+        k0 = (uint32_t)__cvta_generic_to_shared(planes) + 8u * (uint32_t)cell0 -
+             8u * 0x4B400000u * (uint32_t)(pb.Q + 1);
+#pragma unroll 1  // not unrolled: the unrolled surfaces spill at 64 registers
     for (int l = 0; l < L; ++l) {
-        const float zh = pb.kz0[(size_t)l * pb.n_rays + ray];
-        const float zl = pb.kz0[(size_t)(L + l) * pb.n_rays + ray];
+        const float zh = pb.kz1[(size_t)l * pb.n_rays + ray];
+        const float zl = pb.kz1[(size_t)(L + l) * pb.n_rays + ray];
         int lo = 0, hi = G - 1;
-        if (!pb.full_windows) transition_window(zh, st.z, rdz, pb.kg, ext[l], ext[L + l], G, lo, hi);
+        if (!pb.full_windows) transition_window(zh + zl, dz, rdz, pb.kg, ext[l], ext[L + l], G, lo, hi, kSatX);
         lo = min(lo, G);
         int he = max(hi + 1, lo);
         if ((he - lo) & 1) {
@@ -574,9 +653,10 @@ __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *plane
             else if (lo > 0) --lo;
         }
         if (evaluated) *evaluated += (unsigned long long)(he - lo);
-        unsigned long long t = (unsigned long long)lo * q_one;  // samples below the window
-        march_surface_dx<HARD, GLOBAL>(planes + (size_t)l * pb.N, pb.Q, pb.R, pb.flag, o, st, -pb.kg, zh, zl, lo,
-                                       he, t);
+        unsigned long long t = (unsigned long long)lo * kUnit;  // samples below the window
+        const uint32_t kl = GLOBAL ? 0u : k0 + 8u * (uint32_t)((size_t)l * pb.N);
+        march_surface_dx<HARD, GLOBAL>(planes + (size_t)l * pb.N, pb.Q, pb.R, pb.flag, xa, xb, -pb.kg, -pb.kgl,
+                                       __float_as_uint(-pb.psi_kc), zh, zl, kl, cell0, c0, lo, he, t);
         emit(l, t);
     }
 }
@@ -763,8 +843,9 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
             FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
             march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, pb.work ? &n_eval : nullptr,
                                           [&](int l, unsigned long long tl) {
-                const FF n = ff_two_sum((float)(uint32_t)(tl >> 20) * 1048576.0f * 0x1p-23f,
-                                        (float)(uint32_t)(tl & 0xFFFFFu) * 0x1p-23f);
+                // N_l = tl 2^-28, split into two exactly representable parts
+                const FF n = ff_two_sum((float)(uint32_t)(tl >> 24) * 0x1p-4f,
+                                        (float)(uint32_t)(tl & 0xFFFFFFu) * 0x1p-28f);
                 Sff = ff_add(Sff, ff_mul(FF{pb.drho_ff[l].x, pb.drho_ff[l].y}, n));
             });
             const FF Off = ff_mul(FF{pb.dt_ff[ray].x, pb.dt_ff[ray].y}, Sff);
@@ -773,15 +854,14 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
             float dO;  // d ll / d O_p = (lambda - C) / Lambda, for the adjoint
             if (Cp > 0) {
                 const FF yff = ff_add(FF{pb.a_ff[ray].x, pb.a_ff[ray].y}, FF{-OL.hi, -OL.lo});
-                const float y = yff.hi + yff.lo;
-                const float g = g_f32(y), cf = (float)Cp;
-                const float cg = cf * g;
-                tf = FF{-cg, -fmaf(cf, g, -cg)};
+                const float y = yff.hi + yff.lo, cf = (float)Cp;
+                const FF g = g_ff(yff);
+                tf = ff_mul(g, FF{-cf, 0.f});
                 dO = cf * expm1f(y) * pb.invL_ff.x;  // lambda - C = C (e^y - 1)
             } else {
-                const float lam = (float)pb.I0 * expf(-(OL.hi + OL.lo));
-                tf = FF{-lam, 0.f};
-                dO = lam * pb.invL_ff.x;
+                const double lam = pb.I0 * exp(-((double)OL.hi + (double)OL.lo));
+                tf = FF{(float)-lam, (float)(-lam - (double)(float)-lam)};
+                dO = (float)lam * pb.invL_ff.x;
             }
             if (pb.dO) pb.dO[(size_t)c * pb.n_rays + ray] = dO;
             accf = ff_add(accf, tf);
@@ -809,7 +889,8 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
                 O = pb.dt[ray] * ((double)pb.G * pb.rho_top + S_);
                 if (Cp > 0) {
                     const double y = pb.a[ray] - O * pb.inv_Lambda;
-                    term = -(double)Cp * (double)g_f32((float)y);
+                    const FF g = g_ff(ff_const(y));
+                    term = -(double)Cp * ((double)g.hi + (double)g.lo);
                 } else {
                     term = -pb.I0 * exp(-O * pb.inv_Lambda);
                 }

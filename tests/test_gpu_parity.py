@@ -82,20 +82,25 @@ def test_ray_opacity_f32(precision):
 
 
 def fp32_loglik_tol(pr, op=None, H=None):
-    """Per-chain |ll_FP32 - ll_oracle| bound.  1e-3, times dt/gamma when the
-    sample spacing exceeds the sigmoid width (each sample's indicator is then
-    more sensitive to FP32 position error), plus the first-order propagation
-    of the FP32 per-ray opacity error, |d ll / d O_p| = |lambda_p - C_p| / Lambda
-    times 5e-7 mwe (measured bias <= 3e-7 mwe per ray): negligible near the
-    data-generating geometry, dominant for chains far from it."""
+    """Per-chain |ll_FP32 - ll_oracle| bound of the FP32 modes: 1e-3 absolute,
+    at every size (the per-chain log-likelihood bound the FP32 march is built
+    to; Eq. def_likelihood summed over all rays)."""
+    return 1e-3
+
+
+def bf16_loglik_tol(pr, op, H):
+    """Per-chain bound of the BF16-heights mode against the oracle evaluated on
+    the BF16-rounded heights: 1e-3 times max(1, dt/gamma) plus 5e-7 mwe of
+    opacity error per ray propagated through |d ll / d O_p| = |lambda_p -
+    C_p| / Lambda.  That mode marches on FP32 absolute cell coordinates with a
+    2^-23 indicator quantum, so its error is stated, not held to the FP32
+    modes' bar."""
     T = [oracle.t_exit(s_, d_, pr["box"]) for s_ in pr["sensors"] for d_ in pr["dirs"]]
     dt_max = max(T) / pr["G"]
     tol = 1e-3 * max(1.0, dt_max / pr["gamma"]) if pr["gamma"] > 0 else 1e-3
-    if op is not None:
-        O = op.opacities(H).ravel()
-        sens = np.abs(pr["I0"] * np.exp(-O / pr["Lambda"]) - op.counts.ravel()) / pr["Lambda"]
-        tol += 5e-7 * sens.sum()
-    return tol
+    O = op.opacities(H).ravel()
+    sens = np.abs(pr["I0"] * np.exp(-O / pr["Lambda"]) - op.counts.ravel()) / pr["Lambda"]
+    return tol + 5e-7 * sens.sum()
 
 
 # ---------------------------------------------------------------- per chain
@@ -127,7 +132,7 @@ def test_logpost_reduced_precision(w, precision):
         Hq = Hn
     for c in range(Hs.shape[0]):
         ref_ll = op.loglik(Hq[c])
-        tol = fp32_loglik_tol(pr, op, Hq[c])
+        tol = bf16_loglik_tol(pr, op, Hq[c]) if precision == mt.PREC_BF16 else fp32_loglik_tol(pr)
         assert abs(ll[c] - ref_ll) <= tol, (c, ll[c], ref_ll, ll[c] - ref_ll, tol)
         ref_lp = op.logprior(Hn[c])
         assert abs(lp[c] - ref_lp) <= 1e-9 * max(1.0, abs(ref_lp))
@@ -212,7 +217,7 @@ def _lockstep(precision, n_steps, sigma, w):
                 stats["max_dll"] = max(stats["max_dll"], abs(llp_gpu[c] - lln))
             delta = (lln + lpn) - (ll_cur[c] + lp_cur[c])
             a_ref = oracle.mh_decide(lpn, lln, lp_cur[c], ll_cur[c], lu[c])
-            band = 1e-6 if precision == mt.PREC_F64 else 1e-6 + 3e-3
+            band = 1e-6  # the same tie band in every precision
             if bool(a_gpu[c]) == a_ref:
                 stats["match"] += 1
             elif abs(lu[c] - delta) < band:
@@ -236,9 +241,13 @@ def test_mh_lockstep_f64():
     assert 0 < s["accepted"] < 60 * w.n_chains, s
 
 
-def test_mh_lockstep_f32():
+@pytest.mark.parametrize("precision", [mt.PREC_F32, mt.PREC_F32C])
+def test_mh_lockstep_f32(precision):
+    """FP32 march: identical accept decisions to the oracle's except where
+    |ln u - Delta_oracle| < 1e-6 (ties are counted, mismatches outside the
+    band fail), proposals' log-likelihoods within 1e-3."""
     w = W.tiny()
-    s = _lockstep(mt.PREC_F32, 40, w.rw_sigma, w)
+    s = _lockstep(precision, 40, w.rw_sigma, w)
     assert s["mismatch"] == 0, s
     assert s["max_dll"] <= 1e-3, s
 
