@@ -33,9 +33,9 @@ size_t nodes_bytes_f64(int L, int N);
 
 int march_rays_per_block(const Prob &pb)
 {
-    // up to 8192 rays per CTA (8 per thread of the FP32 modes' 1024-thread
-    // CTAs); small problems use fewer.
-    const int per = 8192;
+    // up to MT_RAYS_PER_CTA rays per CTA (8 per thread of the FP32 modes'
+    // 768-thread CTAs); small problems use fewer.
+    const int per = MT_RAYS_PER_CTA;
     const int need = ((pb.n_rays + 255) / 256) * 256;
     return need < per ? need : per;
 }

@@ -19,6 +19,11 @@
 #define MT_MAX_SMEM 232448  // opt-in shared memory per block on sm_100/sm_103
 // static shared memory a kernel may use on top of its dynamic allocation
 #define MT_SMEM_STATIC 4096
+// ray slots per CTA of the ray kernels (the FP32 march's CTAs hold one chain
+// and this many rays; the chain's CTA partials follow from it)
+#ifndef MT_RAYS_PER_CTA
+#define MT_RAYS_PER_CTA 6144
+#endif
 
 namespace mt {
 

@@ -282,7 +282,7 @@ cudaError_t launch_lin_amc(int n, const double *lam0, const int32_t *cnt, double
     return cudaGetLastError();
 }
 
-// rays per k_lin_ll block (divides the march's 8192): two per warp, so that
+// rays per k_lin_ll block (divides the march's ray slots per CTA): two per warp, so that
 // one 32-chain tile fills the GPU and the CTAs in flight share its dR in L2
 constexpr int kLinRays = 64;
 

@@ -24,7 +24,18 @@
 
 #include "internal.h"
 
+// Threads per CTA of the FP32 modes' march (one CTA per SM: the planes take
+// the shared memory) and the unroll of its surface loop: 768 threads leave 80
+// registers per thread, enough to unroll four surfaces without spilling.
+#ifndef MT_DX_THREADS
+#define MT_DX_THREADS 768
+#endif
+#ifndef MT_SURF_UNROLL
+#define MT_SURF_UNROLL 4
+#endif
+
 namespace mt {
+constexpr int kSurfUnroll = MT_SURF_UNROLL;
 
 // ---------------------------------------------------------------- types
 template <int MODE> struct Types;
@@ -445,16 +456,16 @@ constexpr uint32_t kJunk = kQuantBits >> 3;       // added per sample by the sig
 constexpr unsigned long long kUnit = 1ull << 28;  // one indicator = 2^28 units
 
 template <bool HARD, bool GLOBAL>
-__device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int *flag, float2 kf2, float2 ox2,
-                                            float2 oy2, float2 sxh2, float2 sxl2, float2 syh2, float2 syl2,
+__device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int *flag, float2 kf2, float2 ix2,
+                                            float2 iy2, float2 sxh2, float2 syh2,
                                             float2 szh2, float2 szl2, float2 zh2, float2 zl2, float2 nkgh2,
                                             float2 nkgl2, uint32_t nkc, uint32_t k0, int cell0, int2 c0,
                                             int &curA, int &curB,
                                             float2 &rA0, float2 &rA1, float2 &rB0, float2 &rB1)
 {
     const float2 M2 = f2(12582912.0f);  // 1.5 * 2^23: adding it rounds to an integer
-    const float2 gx = fma2(kf2, sxh2, fma2(kf2, sxl2, ox2));
-    const float2 gy = fma2(kf2, syh2, fma2(kf2, syl2, oy2));
+    const float2 gx = fma2(kf2, sxh2, ix2);  // ix2 = o + k sl (see march_surface_dx)
+    const float2 gy = fma2(kf2, syh2, iy2);
     const float2 tx = add2(gx, M2), ty = add2(gy, M2);
     const float2 fx = fma2(add2(tx, f2(-12582912.0f)), f2(-1.0f), gx);  // in [-1/2, 1/2] about the midpoint
     const float2 fy = add2(fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy), f2(0.5f));
@@ -528,10 +539,10 @@ __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int 
     }
 }
 
-// Samples [lo, he) of one surface; adds the indicator sum in units of 2^-28
-// to t.  Per four steps (eight samples, < 2^32 with kJunk) the 32-bit sum
-// moves to t.  An odd count ends with one sample evaluated in both lanes and
-// counted once.
+// Samples [lo, he) of one surface (lo even); adds the indicator sum in units
+// of 2^-28 to t.  Per block of up to eight samples (< 2^32 with kJunk) the
+// 32-bit sum moves to t.  An odd count (he = G) ends with one sample
+// evaluated in both lanes and counted once.
 template <bool HARD, bool GLOBAL>
 __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, int R, int *flag, float4 xa, float4 xb,
                                                  float nkgh, float nkgl, uint32_t nkc, float zh, float zl, uint32_t k0,
@@ -543,32 +554,57 @@ __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, int R,
     float2 rA0 = f2(0.f), rA1 = f2(0.f), rB0 = f2(0.f), rB1 = f2(0.f);
     int curA = -1, curB = -1;
     float2 kf2 = make_float2((float)lo, (float)lo + 1.0f);
-    const int np = (he - lo) >> 1;
-#define MT_PAIR()                                                                                             \
-    dx_pair<HARD, GLOBAL>(pl, Q, R, flag, kf2, ox2, oy2, sxh2, sxl2, syh2, syl2, szh2, szl2, zh2, zl2, nkgh2, \
-                          nkgl2, nkc, k0, cell0, c0, curA, curB, rA0, rA1, rB0, rB1)
-    int j = 0;
-    for (; j + 4 <= np; j += 4) {
-        uint32_t acc = MT_PAIR();
-        kf2 = add2(kf2, f2(2.0f));
-        acc += MT_PAIR();
-        kf2 = add2(kf2, f2(2.0f));
-        acc += MT_PAIR();
-        kf2 = add2(kf2, f2(2.0f));
-        acc += MT_PAIR();
-        kf2 = add2(kf2, f2(2.0f));
-        t += acc;
-    }
+#define MT_PAIR(IX, IY)                                                                                     \
+    dx_pair<HARD, GLOBAL>(pl, Q, R, flag, kf2, IX, IY, sxh2, syh2, szh2, szl2, zh2, zl2, nkgh2, nkgl2, nkc, k0, \
+                          cell0, c0, curA, curB, rA0, rA1, rB0, rB1)
+    // The low part of the step, o + k sl, changes by far less than an ulp of
+    // o per sample: it is taken once per block of eight samples [8m, 8m + 8),
+    // at the block's centre for each lane (k = 8m + 3 for the even samples of
+    // lane .x, 8m + 4 for the odd ones of lane .y), which leaves an error
+    // within +-4 |sl| (< 4e-8 cells) that averages to zero over the block.
+    // The centre depends on k only, not on where the window starts (lo is
+    // even), so a sample's arithmetic is the same in every window that holds
+    // it and the exact-saturation windows stay bit-identical to full ones.
+    auto centre = [&](int k) {
+        const float b = (float)(k & ~7);
+        return make_float2(b + 3.0f, b + 4.0f);
+    };
+    int k = lo;
     uint32_t acc = 0u;
-    for (; j < np; ++j) {
-        acc += MT_PAIR();
+    float2 kc2 = centre(k), ix2 = fma2(kc2, sxl2, ox2), iy2 = fma2(kc2, syl2, oy2);
+    for (; (k & 7) != 0 && k + 2 <= he; k += 2) {  // up to three steps to a block boundary
+        acc += MT_PAIR(ix2, iy2);
         kf2 = add2(kf2, f2(2.0f));
     }
     t += acc;
-    unsigned long long ns = 2ull * (unsigned long long)np;
-    if ((he - lo) & 1) {
-        kf2 = f2((float)(he - 1));
-        t += (unsigned long long)(MT_PAIR() >> 1);  // both lanes evaluated the same sample
+    for (; k + 8 <= he; k += 8) {  // whole blocks
+        kc2 = add2(kf2, make_float2(3.0f, 3.0f));
+        ix2 = fma2(kc2, sxl2, ox2);
+        iy2 = fma2(kc2, syl2, oy2);
+        acc = MT_PAIR(ix2, iy2);
+        kf2 = add2(kf2, f2(2.0f));
+        acc += MT_PAIR(ix2, iy2);
+        kf2 = add2(kf2, f2(2.0f));
+        acc += MT_PAIR(ix2, iy2);
+        kf2 = add2(kf2, f2(2.0f));
+        acc += MT_PAIR(ix2, iy2);
+        kf2 = add2(kf2, f2(2.0f));
+        t += acc;
+    }
+    acc = 0u;
+    kc2 = centre(k);
+    ix2 = fma2(kc2, sxl2, ox2);
+    iy2 = fma2(kc2, syl2, oy2);
+    for (; k + 2 <= he; k += 2) {  // up to three steps in the last block
+        acc += MT_PAIR(ix2, iy2);
+        kf2 = add2(kf2, f2(2.0f));
+    }
+    t += acc;
+    unsigned long long ns = (unsigned long long)(k - lo);
+    if (k < he) {  // one sample left (he == G): both lanes evaluate it, it counts once
+        kf2 = f2((float)k);
+        const float c = (float)(k & ~7) + ((k & 1) ? 4.0f : 3.0f);
+        t += (unsigned long long)(MT_PAIR(fma2(f2(c), sxl2, ox2), fma2(f2(c), syl2, oy2)) >> 1);
         ns += 1ull;
     }
 #undef MT_PAIR
@@ -623,8 +659,10 @@ __device__ __forceinline__ void transition_window(float z0, float dz, float rdz,
 // transitional (transition_window with ext = per-surface min / max offsets);
 // the other samples' contributions are exact and added analytically (2^28
 // below the surface, 0 above).  A window of odd length is widened by one
-// saturated sample where the ray has one, so that samples go in pairs.
-// emit(l, N_l) is called for l = 0 .. L-1 in order.
+// saturated sample where the ray has one and starts at an even sample (one
+// more saturated sample below), so that samples go in pairs aligned with the
+// blocks of march_surface_dx.  emit(l, N_l) is called for l = 0 .. L-1 in
+// order.
 template <int L, bool HARD, bool GLOBAL, typename Emit>
 __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *planes, int ray,
                                              const float *ext, unsigned long long *evaluated,
@@ -640,18 +678,15 @@ __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *plane
     if constexpr (!GLOBAL)
         k0 = (uint32_t)__cvta_generic_to_shared(planes) + 8u * (uint32_t)cell0 -
              8u * 0x4B400000u * (uint32_t)(pb.Q + 1);
-#pragma unroll 1  // not unrolled: the unrolled surfaces spill at 64 registers
+#pragma unroll kSurfUnroll
     for (int l = 0; l < L; ++l) {
         const float zh = pb.kz1[(size_t)l * pb.n_rays + ray];
         const float zl = pb.kz1[(size_t)(L + l) * pb.n_rays + ray];
         int lo = 0, hi = G - 1;
         if (!pb.full_windows) transition_window(zh + zl, dz, rdz, pb.kg, ext[l], ext[L + l], G, lo, hi, kSatX);
-        lo = min(lo, G);
+        lo = min(lo, G) & ~1;  // even start (one more, saturated, sample below)
         int he = max(hi + 1, lo);
-        if ((he - lo) & 1) {
-            if (he < G) ++he;
-            else if (lo > 0) --lo;
-        }
+        if (((he - lo) & 1) && he < G) ++he;  // even length where the ray allows
         if (evaluated) *evaluated += (unsigned long long)(he - lo);
         unsigned long long t = (unsigned long long)lo * kUnit;  // samples below the window
         const uint32_t kl = GLOBAL ? 0u : k0 + 8u * (uint32_t)((size_t)l * pb.N);
@@ -776,7 +811,7 @@ __device__ __forceinline__ FF block_sum(FF v)
 // 4-corner node records to halve shared memory; FP64 has its own march.
 template <int MODE, int L> struct MarchCfg {
     static constexpr bool DX = MODE == MODE_F32 || MODE == MODE_F32C;
-    static constexpr int THREADS = DX ? 1024 : 256;
+    static constexpr int THREADS = DX ? MT_DX_THREADS : 256;
 };
 
 // (h, dx) planes of every chain into HBM for grids too large for shared

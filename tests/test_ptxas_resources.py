@@ -55,11 +55,23 @@ def test_hot_kernels_do_not_spill(reports):
     assert n >= 10
 
 
-def test_fp32_ray_kernel_fits_1024_threads(reports):
+def _march_threads():
+    """The FP32 march's CTA size, as march.cuh defines it."""
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_2603_28907_gb300", "csrc", "march.cuh")).read()
+    return int(re.search(r"#define MT_DX_THREADS (\d+)", src).group(1))
+
+
+def test_fp32_ray_kernel_fits_its_cta(reports):
+    """Registers per thread times the CTA's threads fit the SM's 65 536
+    registers (allocated in units of 8 per thread), so the launch succeeds."""
+    threads = _march_threads()
+    limit = (65536 // threads) // 8 * 8
     n = 0
     for unit in ("march_f32.cu", "march_f32c.cu"):
         for name, (regs, _) in reports[unit].items():
             if "k_march" in name:
-                assert 0 < regs <= 64, (unit, name, regs)
+                assert 0 < regs <= limit, (unit, name, regs, threads)
                 n += 1
     assert n >= 2
