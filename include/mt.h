@@ -158,14 +158,17 @@ MT_API mt_status mt_logpost(mt_ctx *ctx, int n_chains, const void *heights, doub
  *    staging them would need an allocation.
  *  - The per-(chain, CTA) partial sums live in one 1 MiB array inside the
  *    library (held by every GPU that loads it until the process exits), so
- *    n_chains * ceil(S*P / 8192) * 8 bytes must fit in 1 MiB (16384 chains
+ *    n_chains * ceil(S*P / 6144) * 8 bytes must fit in 1 MiB (11915 chains
  *    of a 16 x 4096-ray problem); larger calls fail with MT_EINVAL.
- *  - The first call on each device looks up the array's device address;
- *    make that first call before any stream capture.
+ *  - The first call on each device looks up the array's device address and
+ *    keeps it for the process (so the device's primary context must live as
+ *    long as the process: no device reset in between); make that first call
+ *    before any stream capture.
  *  - All calls share the array: two calls whose kernels overlap on the GPU
  *    (on different streams or contexts) race and both may return garbage.
  *    Calls on one stream are ordered and safe.
- * Results equal mt_logpost's.  Asynchronous on the context's stream. */
+ * Results equal mt_logpost's bit for bit (the same kernels in the same
+ * order).  Asynchronous on the context's stream. */
 MT_API mt_status mt_logpost_noalloc(mt_ctx *ctx, int n_chains, const void *heights,
                                     double *loglik_out, double *logprior_out);
 

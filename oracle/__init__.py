@@ -83,6 +83,7 @@ def _load():
                 "or_loglik_terms": (None, [P, _dp, _dp, _dp]),
                 "or_logprior": (C.c_double, [P, _dp]),
                 "or_poisson_draw": (C.c_int32, [C.c_double, C.c_uint64, C.c_uint32, C.POINTER(C.c_int)]),
+                "or_poisson_mean_attempts": (C.c_double, [C.c_double, C.c_uint64, C.c_int]),
                 "or_generate_counts": (C.c_int, [P, _dp, C.c_uint64, C.c_int, _ip, _dp]),
                 "or_rw_propose": (None, [P, _dp, C.c_double, C.c_uint64, C.c_uint32, C.c_uint32, _dp]),
                 "or_accept_logu": (C.c_double, [C.c_uint64, C.c_uint32, C.c_uint32]),
@@ -298,6 +299,11 @@ def poisson_draw(lam, seed, ray):
     st = C.c_int(0)
     k = _load().or_poisson_draw(float(lam), seed, ray, C.byref(st))
     return int(k), int(st.value)
+
+
+def poisson_mean_attempts(lam, seed, n):
+    """Mean number of attempts of the count sampler over rays 0 .. n-1 (test instrumentation)."""
+    return _load().or_poisson_mean_attempts(float(lam), seed, int(n))
 
 
 def accept_logu(seed, chain, step):

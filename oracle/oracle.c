@@ -303,7 +303,7 @@ double or_logprior(const or_problem *pb, const double *H)
  * method for generating Poisson random variables", Insurance: Mathematics
  * and Economics 12, 1993) for lambda >= 10.  Attempts are bounded; running
  * out sets *status = 1. */
-int32_t or_poisson_draw(double lam, uint64_t seed, uint32_t ray, int *status)
+static int32_t poisson_draw_n(double lam, uint64_t seed, uint32_t ray, int *status, int *attempts)
 {
     const int max_attempts = 256;
     if (lam < 10.0) {
@@ -316,11 +316,15 @@ int32_t or_poisson_draw(double lam, uint64_t seed, uint32_t ray, int *status)
             double uu[2] = {or_u01(w[0], w[1]), or_u01(w[2], w[3])};
             for (int h = 0; h < 2; ++h) {
                 prod = prod * uu[h];
-                if (prod <= limit) return k;
+                if (prod <= limit) {
+                    if (attempts) *attempts = j + 1;
+                    return k;
+                }
                 k = k + 1;
             }
         }
         if (status) *status = 1;
+        if (attempts) *attempts = max_attempts;
         return k;
     }
     double slam = sqrt(lam);
@@ -336,6 +340,7 @@ int32_t or_poisson_draw(double lam, uint64_t seed, uint32_t ray, int *status)
         double V = or_u01(w[2], w[3]);
         double us = 0.5 - fabs(U);
         double kf = floor((2.0 * a / us + b) * U + lam + 0.43);
+        if (attempts) *attempts = j + 1;
         if (us >= 0.07 && V <= v_r) return (int32_t)kf;
         if (kf < 0.0 || (us < 0.013 && V > us)) continue;
         double lhs = log(V) + log(inv_alpha) - log(a / (us * us) + b);
@@ -343,7 +348,29 @@ int32_t or_poisson_draw(double lam, uint64_t seed, uint32_t ray, int *status)
         if (lhs <= rhs) return (int32_t)kf;
     }
     if (status) *status = 1;
+    if (attempts) *attempts = max_attempts;
     return 0;
+}
+
+int32_t or_poisson_draw(double lam, uint64_t seed, uint32_t ray, int *status)
+{
+    return poisson_draw_n(lam, seed, ray, status, NULL);
+}
+
+/* Test instrumentation (no arithmetic of its own): the mean number of
+ * attempts or_poisson_draw takes for lambda over rays 0 .. n-1.  For
+ * lambda >= 10 one attempt of the transformed rejection accepts value k with
+ * probability p(k) / inv_alpha (the hat dominates p), so the attempts are
+ * geometric with mean inv_alpha = 1.1239 + 1.1328 / (b - 3.4). */
+double or_poisson_mean_attempts(double lam, uint64_t seed, int n)
+{
+    double tot = 0.0;
+    for (int i = 0; i < n; ++i) {
+        int att = 0, st = 0;
+        poisson_draw_n(lam, seed, (uint32_t)i, &st, &att);
+        tot += att;
+    }
+    return n > 0 ? tot / n : 0.0;
 }
 
 /* Counts for every (sensor, pixel) of the true geometry; lambda_out and

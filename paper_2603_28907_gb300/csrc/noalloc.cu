@@ -22,7 +22,9 @@ __device__ __align__(256) unsigned char g_partials[kScratchBytes];
 std::mutex g_lock;
 void *g_partials_addr[kMaxDevices] = {};
 
-// Device address of g_partials on the current device (set up on first use).
+// Device address of g_partials on the current device (set up on first use
+// and kept for the process: the cache assumes the device's primary context
+// lives as long as the process, i.e. nobody resets the device in between).
 // In host code the name g_partials is only a stand-in for the symbol; a
 // kernel must be given the address cudaGetSymbolAddress returns.
 cudaError_t partials_address(int device, void **out)
@@ -38,14 +40,17 @@ cudaError_t partials_address(int device, void **out)
     return cudaSuccess;
 }
 
-bool on_device(const void *p)
+// Device memory of `device` (or managed memory, which every device can
+// reach); host memory and another GPU's memory are rejected, since the kernels
+// would read them without a copy.
+bool on_device(const void *p, int device)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == device);
 }
 
 }  // namespace
@@ -62,10 +67,11 @@ extern "C" MT_API mt_status mt_logpost_noalloc(mt_ctx *ctx, int n_chains, const 
         return ctx_fail(ctx, MT_EINVAL, "mt_logpost_noalloc: need 1 <= n_chains <= 65535");
     if (!heights || !loglik_out)
         return ctx_fail(ctx, MT_EINVAL, "mt_logpost_noalloc: heights and loglik_out are required");
-    if (!on_device(heights) || !on_device(loglik_out) || (logprior_out && !on_device(logprior_out)))
+    if (!on_device(heights, v.device) || !on_device(loglik_out, v.device) ||
+        (logprior_out && !on_device(logprior_out, v.device)))
         return ctx_fail(ctx, MT_EINVAL,
-                        "mt_logpost_noalloc: every array must be device memory (staging host "
-                        "memory would need an allocation)");
+                        "mt_logpost_noalloc: every array must be device memory of the context's "
+                        "device (staging host memory would need an allocation)");
     if (!march_fits_smem(v.pb, v.mode))
         return ctx_fail(ctx, MT_EINVAL,
                         "mt_logpost_noalloc: the grid's surfaces do not fit in shared memory "

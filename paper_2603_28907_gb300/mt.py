@@ -156,6 +156,7 @@ class Context:
         if st != 0:
             raise MtError("mt_create", st, self.lib.mt_last_error(None).decode())
         self.h = h
+        self.device = device
         self.precision = precision
         self._keep = []
 
@@ -212,13 +213,51 @@ class Context:
         return dict(zip(["L", "R", "Q", "S", "P", "C"], [x.value for x in v]))
 
     # -- evaluation
+    def _check_batch(self, name, heights, outs, device_only=False):
+        """Reject arrays the library would read or write out of bounds: heights
+        [n][L][R][Q] of the precision's dtype (FP64 / FP32), outputs of at least
+        n doubles, torch tensors on the context's device."""
+        want = np.dtype(self.height_dtype)
+        sz = self.sizes()
+        lrq = (sz["L"], sz["R"], sz["Q"])
+        arrs = [("heights", heights)] + [(k, v) for k, v in outs if v is not None]
+        for label, a in arrs:
+            if hasattr(a, "data_ptr"):
+                dt = np.dtype(str(a.dtype).replace("torch.", ""))
+                dev = a.device.index if a.device.type == "cuda" else None
+                if device_only and a.device.type != "cuda":
+                    raise ValueError(f"{name}: {label} must be a CUDA tensor")
+                if a.device.type == "cuda" and dev != self.device:
+                    raise ValueError(f"{name}: {label} is on cuda:{dev}, the context on cuda:{self.device}")
+            elif isinstance(a, np.ndarray):
+                if device_only:
+                    raise ValueError(f"{name}: {label} must be device memory")
+                dt = a.dtype
+            else:
+                raise TypeError(f"{name}: {label}: unsupported array type {type(a)}")
+            if label == "heights":
+                if dt != want:
+                    raise ValueError(f"{name}: heights must be {want} for this precision, got {dt}")
+                if tuple(a.shape[1:]) != lrq:
+                    raise ValueError(f"{name}: heights must be [n][{lrq[0]}][{lrq[1]}][{lrq[2]}], "
+                                     f"got {tuple(a.shape)}")
+            else:
+                if dt != np.dtype(np.float64):
+                    raise ValueError(f"{name}: {label} must be float64, got {dt}")
+                size = a.numel() if hasattr(a, "numel") else a.size
+                if size < heights.shape[0]:
+                    raise ValueError(f"{name}: {label} holds {size} values, need {heights.shape[0]}")
+
     def logpost(self, heights, loglik_out=None, logprior_out=None):
+        self._check_batch("mt_logpost", heights, [("loglik_out", loglik_out), ("logprior_out", logprior_out)])
         n = heights.shape[0]
         self._ck("mt_logpost", self.lib.mt_logpost(self.h, n, _ptr(heights), _ptr(loglik_out),
                                                    _ptr(logprior_out)))
 
     def logpost_noalloc(self, heights, loglik_out, logprior_out=None):
         """mt_logpost_noalloc: device arrays only; allocates nothing."""
+        self._check_batch("mt_logpost_noalloc", heights,
+                          [("loglik_out", loglik_out), ("logprior_out", logprior_out)], device_only=True)
         n = heights.shape[0]
         self._ck("mt_logpost_noalloc", self.lib.mt_logpost_noalloc(
             self.h, n, _ptr(heights), _ptr(loglik_out), _ptr(logprior_out)))

@@ -44,6 +44,21 @@ def test_counts_bit_exact(w, gamma):
     np.testing.assert_array_equal(counts.cpu().numpy(), c_ref)
 
 
+def test_counts_knuth_and_ptrs_bit_exact():
+    """A data set whose expected counts straddle 10 (I0 = 40: lambda from 3.7
+    to 15.5, 1351 pixels below 10 and 697 above): the Knuth
+    multiplication branch (lambda < 10) and Hoermann's PTRS branch both draw,
+    bit-identical to the oracle's draws from the same Philox streams."""
+    w = W.tiny()
+    pr, ctx, op, counts, lam = setup(w, I0=40.0)
+    lamv = lam.cpu().numpy()
+    assert (lamv < 10.0).sum() > 500 and (lamv >= 10.0).sum() > 500, (lamv.min(), lamv.max())
+    c_ref, lam_ref, bad = op.generate_counts(pr["H_true"], w.seed_data)
+    assert bad == 0
+    np.testing.assert_allclose(lamv, lam_ref, rtol=1e-12)
+    np.testing.assert_array_equal(counts.cpu().numpy(), c_ref)
+
+
 def test_counts_round_mode():
     w = W.tiny()
     pr, ctx, op, counts, lam = setup(w, count_mode=mt.COUNTS_ROUND)
@@ -344,3 +359,22 @@ def test_large_grid_uses_hbm_records():
     H2 = Hs2.double().cpu().numpy()
     for c in range(3):
         assert abs(ll2[c].item() - op.loglik(H2[c])) <= fp32_loglik_tol(pr, op, H2[c])
+
+
+def test_binding_rejects_mismatched_arrays():
+    """The binding refuses arrays the library would read or write out of
+    bounds: FP32 heights for an FP64 context, a wrong grid shape, too short an
+    output; nothing is launched for them."""
+    w = W.tiny()
+    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F64)
+    H64 = heights(W.init_chains(w, 2), mt.PREC_F64)
+    ll = torch.zeros(2, dtype=torch.float64, device=DEV)
+    with pytest.raises(ValueError):
+        ctx.logpost(H64.float(), ll)                         # dtype of another precision
+    with pytest.raises(ValueError):
+        ctx.logpost(H64[:, :, :, :-1].contiguous(), ll)      # not [n][L][R][Q]
+    with pytest.raises(ValueError):
+        ctx.logpost(H64, torch.zeros(1, dtype=torch.float64, device=DEV))  # output too short
+    with pytest.raises(ValueError):
+        ctx.logpost(H64, torch.zeros(2, dtype=torch.float32, device=DEV))  # output not FP64
+    ctx.logpost(H64, ll)                                      # the right arrays pass

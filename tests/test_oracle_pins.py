@@ -457,3 +457,21 @@ def test_mala_proposal_and_logq():
     # with zero gradient the kernel is symmetric
     z = np.zeros_like(H)
     assert op.mala_logq(Hp, H, z, eps) == pytest.approx(op.mala_logq(H, Hp, z, eps), rel=1e-14)
+
+
+@pytest.mark.parametrize("lam", [10.0, 30.0, 400.0, 5000.0])
+def test_poisson_ptrs_acceptance_rate_closed_form(lam):
+    """Hoermann's transformed rejection (1993) accepts value k with probability
+    p(k) / alpha per attempt, alpha = 1.1239 + 1.1328 / (b - 3.4),
+    b = 0.931 + 2.53 sqrt(lambda): the hat dominates the Poisson pmf, so one
+    attempt succeeds with probability exactly 1 / alpha and the number of
+    attempts is geometric with mean alpha.  A misread constant (in b, a,
+    alpha or v_r) that keeps the drawn distribution close still moves this
+    mean, which the moment and chi-square tests would not see."""
+    b = 0.931 + 2.53 * np.sqrt(lam)
+    alpha = 1.1239 + 1.1328 / (b - 3.4)
+    n = 400000
+    p = 1.0 / alpha
+    sd = np.sqrt((1.0 - p) / p ** 2 / n)
+    mean = oracle.poisson_mean_attempts(lam, 123, n)
+    assert abs(mean - alpha) < 5.0 * sd, (lam, mean, alpha, sd)
