@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--chains", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the precision / gradient / serving legs of the default line")
     ap.add_argument("--serve", action="store_true",
                     help="serving mix instead of the Metropolis step benchmark")
     ap.add_argument("--requests", type=int, default=24)
@@ -314,7 +316,10 @@ def run_serve(args, rank, local):
                     "ttp_s_p50": st["ttp_s_p50"], "ttp_s_p99": st["ttp_s_p99"],
                     "chain_ray_evals_per_s": st["chain_ray_evals_per_s"],
                     "wall_s": wall, "chain_ray_evals": evals, "n_done": st["n_done"],
-                    "queue_wait_s_max": max(r["info"]["admit_s"] - r["info"]["submit_s"] for r in res)},
+                    "queue_wait_s_max": max(r["info"]["admit_s"] - r["info"]["submit_s"] for r in res),
+                    "pool_bytes_at_start": st["pool_bytes_at_start"], "pool_bytes_now": st["pool_bytes_now"],
+                    "gpu_busy_over_span": sum(r["info"]["gpu_busy_ms"] for r in res) / max(
+                        1e-9, max(r["info"]["gpu_end_ms"] for r in res) - min(r["info"]["gpu_start_ms"] for r in res))},
         "requests": sizes,
         "clocks": clk,
     }), flush=True)
@@ -808,7 +813,7 @@ def main():
                          "launches": march_n,
                          "evaluated": evaluated_roofline(achieved, work_eval, work_total),
                          "note": "units are the method's surface-samples (12+9L FP32 ops and "
-                                 "2L MUFU per sample); samples at least 24.25 log2 units from "
+                                 "2L MUFU per sample); samples at least 29.25 log2 units from "
                                  "their surface are exactly 0/1 and added without evaluation "
                                  "(bit-identical), so frac can exceed 1; 'evaluated' rates the "
                                  "samples the kernel did compute against the pipes' limit for "
@@ -817,11 +822,132 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
+        if not args.no_extras and world == 1:
+            out["extras"] = bench_extras(ctx, stream, w, pr, counts, local)
         print(json.dumps(out), flush=True)
     ctx.close()
     if pg:
         pg.barrier()
         pg.destroy_process_group()
+
+
+def bench_extras(ctx, stream, w, pr, counts, local):
+    """Short legs of the other configurations on the bench's own states, after
+    the timed region, each with its clock record: the FP32 mode's per-chain
+    error and accept decisions against the FP64 mode (whose agreement with the
+    oracle at this size is a parity test), gradient and MALA step times, and a
+    short serving mix."""
+    import torch
+    from paper_2603_28907_gb300 import mt
+    dev = torch.device("cuda", local)
+    C = w.n_chains
+    f64 = lambda n: torch.zeros(n, dtype=torch.float64, device=dev)
+    res = {}
+
+    # precision: the chains' current states and two random-walk steps' proposals
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    ref = mt.from_workload(pr, precision=mt.PREC_F64, device=local)
+    ref.set_counts(counts)
+    H = torch.zeros((C, w.L, w.R, w.Q), dtype=torch.float32, device=dev)
+    ll32, lp = f64(C), f64(C)
+    ctx.get_state(H, ll32, lp)
+    ll64 = f64(C)
+    ref.logpost(H.double(), ll64, None)
+    dll = (ll32 - ll64).abs()
+    agree = tot = tie = 0
+    prop, llp, lpp, logu = torch.zeros_like(H), f64(C), f64(C), f64(C)
+    acc = torch.zeros(C, dtype=torch.int32, device=dev)
+    dd_max = 0.0
+    for _ in range(2):
+        ctx.run(mt.KERNEL_RW, w.rw_sigma, 1, 1)
+        ctx.get_last_step(prop, llp, lpp, acc, logu)
+        l64p = f64(C)
+        ref.logpost(prop.double(), l64p, None)
+        fin = torch.isfinite(lpp)
+        d_ref = (l64p + lpp) - (ll64 + lp)
+        d32 = (llp + lpp) - (ll32 + lp)
+        a_ref = fin & (logu < d_ref)
+        same = acc.bool() == a_ref
+        near = (logu - d_ref).abs() < 1e-6
+        agree += int(same.sum().item())
+        tie += int((~same & near).sum().item())
+        tot += C
+        if fin.any():
+            dd_max = max(dd_max, float((d32 - d_ref).abs()[fin].max().item()))
+        took = acc.bool()
+        ll64 = torch.where(took, l64p, ll64)
+        ll32 = torch.where(took, llp, ll32)
+        lp = torch.where(took, lpp, lp)
+    ref.close()
+    res["precision"] = {
+        "states": f"{C} scenario chains after the timed steps, then 2 random-walk steps ({tot} proposals)",
+        "dll_abs_mean": float(dll.mean().item()), "dll_abs_max": float(dll.max().item()),
+        "accept_agreement": agree / tot, "disagree_outside_1e-6_band": tot - agree - tie,
+        "mh_ratio_err_max": dd_max, "reference": "FP64 mode", "wall_s": time.perf_counter() - t0,
+        "clocks": clocks.stop()}
+
+    # gradient (mt_grad) and MALA step on a context of their own
+    clocks = Clocks(local)
+    clocks.start()
+    g = mt.from_workload(pr, precision=mt.PREC_F32, device=local, stream=stream.cuda_stream)
+    g.set_counts(counts)
+    G = torch.zeros((C, w.L, w.R, w.Q), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        g.grad(H, G)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            g.grad(H, G)
+        e1.record(stream)
+    stream.synchronize()
+    grad_ms = e0.elapsed_time(e1) / 3
+    g.init_chains(H, w.seed_mcmc + 1)
+    with torch.cuda.stream(stream):
+        g.run(mt.KERNEL_MALA, 0.005, 1, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.run(mt.KERNEL_MALA, 0.005, 1, 3)
+        e1.record(stream)
+    stream.synchronize()
+    mala_ms = e0.elapsed_time(e1) / 3
+    g.close()
+    rays = w.S * w.P
+    res["gradient"] = {"chains": C, "mt_grad_ms": grad_ms,
+                       "surface_samples_per_s": C * rays * w.G * w.L / (grad_ms / 1e3),
+                       "mala_step_ms": mala_ms, "mala_eps_m": 0.005, "clocks": clocks.stop()}
+
+    # serving: eight requests of the serving mix, step budgets scaled by 1/200
+    clocks = Clocks(local)
+    clocks.start()
+    reqs = W.serving_mix(8, seed=5)
+    for q in reqs:
+        steps = max(1, int(round(q.n_super * q.n_within / 200)))
+        q.n_within = min(10, steps)
+        q.n_super = max(1, steps // q.n_within)
+    free, _ = torch.cuda.mem_get_info()
+    srv = mt.Server(device=local, hbm_budget_bytes=int(free * 0.5), max_active=8)
+    t0 = time.perf_counter()
+    ids = []
+    for q in reqs:
+        wait = q.extra["arrival_s"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        ids.append(srv.submit(W.problem(q), W.init_chains(q).astype(np.float32), precision=mt.PREC_F32,
+                              data_seed=q.seed_data, seed=q.seed_mcmc, step=0.002, n_super=q.n_super,
+                              n_within=q.n_within))
+    infos = [srv.wait(i)["info"] for i in ids]
+    st = srv.stats()
+    srv.close()
+    span = max(f["gpu_end_ms"] for f in infos) - min(f["gpu_start_ms"] for f in infos)
+    res["serving"] = {"requests": len(reqs), "superstep_ms_p50": st["superstep_ms_p50"],
+                      "superstep_ms_p99": st["superstep_ms_p99"], "ttp_s_p50": st["ttp_s_p50"],
+                      "ttp_s_p99": st["ttp_s_p99"], "chain_ray_evals_per_s": st["chain_ray_evals_per_s"],
+                      "gpu_busy_over_span": sum(f["gpu_busy_ms"] for f in infos) / max(span, 1e-9),
+                      "pool_grew_bytes": st["pool_bytes_now"] - st["pool_bytes_at_start"],
+                      "wall_s": time.perf_counter() - t0, "clocks": clocks.stop()}
+    return res
 
 
 def evaluated_roofline(achieved_t, work_eval, work_total):
@@ -834,7 +960,7 @@ def evaluated_roofline(achieved_t, work_eval, work_total):
     peak = march_peak_evaluated() / 1e12
     return {"fraction": frac_eval, "achieved": ach, "peak": peak, "frac": ach / peak,
             "unit": "T evaluated surface-samples/s",
-            "ops_per_sample": f"{EVAL_FP32_OPS:g} FP32 lane-ops + ex2 + rcp"}
+            "ops_per_sample": f"{EVAL_FP32_OPS:g} FP32 lane-ops + ex2 + rcp + cvt"}
 
 
 def measure_e2e(ctx, H0np, stream, args, w, rays):

@@ -461,6 +461,12 @@ typedef struct {
     int n_supersteps;
     double submit_s, admit_s, done_s;          /* server clock, seconds */
     double superstep_ms_p50, superstep_ms_p99; /* CUDA-event time per super-step */
+    /* device clock (CUDA events, ms from an event the server records at
+     * creation): start of the request's first super-step, end of its last,
+     * and the sum of its super-steps' durations.  Two requests whose
+     * [gpu_start_ms, gpu_end_ms] spans intersect had work on the device at
+     * the same time. */
+    double gpu_start_ms, gpu_end_ms, gpu_busy_ms;
 } mt_request_info;
 
 typedef struct {
@@ -469,10 +475,20 @@ typedef struct {
     double ttp_s_p50, ttp_s_p99;               /* time to posterior: submit -> done */
     double chain_ray_evals_per_s;              /* finished work / (last done - first admit) */
     size_t bytes_in_use;                       /* estimated device memory of active requests */
+    /* the server's device-memory pool: bytes it held once creation had
+     * filled it, and now; equal while no request needed more than the pool
+     * held, i.e. no request's memory came from the driver */
+    size_t pool_bytes_at_start, pool_bytes_now;
 } mt_server_stats_t;
 
 /* Start a server on `device` with a device-memory budget (bytes) and at most
- * max_active requests in flight.  A host thread runs the scheduler. */
+ * max_active requests in flight.  A host thread runs the scheduler.
+ * Creation reserves the device memory requests draw from: a stream-ordered
+ * pool that keeps up to the budget and is filled here with min(budget,
+ * 32 GiB); each request's contexts allocate from it and give it back on their
+ * own stream, so admitting and finishing a request neither calls cudaMalloc /
+ * cudaFree nor synchronises the device.  The max_active streams and events
+ * the requests run on are created here too and reused. */
 MT_API mt_status mt_server_create(mt_server **out, int device, size_t hbm_budget_bytes,
                                   int max_active);
 

@@ -83,6 +83,7 @@ struct EvPair {
 struct mt_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;    // a server's stream-ordered pool (nullptr: cudaMalloc)
     bool own_stream = false;
     mt_config cfg{};
     int mode = MODE_F32;
@@ -225,28 +226,45 @@ static bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-template <typename T> static void dfree(T *&p)
+// Device memory of a context: from the server's stream-ordered pool when the
+// context belongs to a server (allocation and release are ordered on the
+// context's stream, and neither goes to the driver nor synchronises the
+// device), otherwise cudaMalloc / cudaFree.
+static cudaError_t dev_alloc(mt_ctx *ctx, void **p, size_t bytes)
 {
-    if (p) cudaFree((void *)p);
+    if (ctx->pool) return cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
+    return cudaMalloc(p, bytes);
+}
+
+static void dev_free(mt_ctx *ctx, void *p)
+{
+    if (!p) return;
+    if (ctx->pool) cudaFreeAsync(p, ctx->stream);
+    else cudaFree(p);
+}
+
+template <typename T> static void dfree(mt_ctx *ctx, T *&p)
+{
+    dev_free(ctx, (void *)p);
     p = nullptr;
 }
 
 static mt_status grow(mt_ctx *ctx, void **p, size_t *cap, size_t bytes)
 {
     if (bytes <= *cap && *p) return MT_OK;
-    if (*p) cudaFree(*p);
+    if (*p) dev_free(ctx, *p);
     *p = nullptr;
     *cap = 0;
     size_t want = bytes < 256 ? 256 : bytes;
-    CK(ctx, cudaMalloc(p, want));
+    CK(ctx, dev_alloc(ctx, (void **)p, want));
     *cap = want;
     return MT_OK;
 }
 
 template <typename T> static mt_status dalloc(mt_ctx *ctx, T **p, size_t n)
 {
-    dfree(*p);
-    CK(ctx, cudaMalloc((void **)p, n * sizeof(T) + 16));
+    dfree(ctx, *p);
+    CK(ctx, dev_alloc(ctx, (void **)p, n * sizeof(T) + 16));
     return MT_OK;
 }
 
@@ -263,32 +281,32 @@ static void drop_graph(mt_ctx *ctx)
 static void drop_chains(mt_ctx *ctx)
 {
     drop_graph(ctx);
-    dfree(ctx->d_H);
-    dfree(ctx->d_cur);
-    dfree(ctx->d_psel);
-    dfree(ctx->d_ll);
-    dfree(ctx->d_lp);
-    dfree(ctx->d_llp);
-    dfree(ctx->d_lpp);
-    dfree(ctx->d_logu);
-    dfree(ctx->d_acc);
-    dfree(ctx->d_accl);
-    dfree(ctx->d_G);
-    dfree(ctx->d_extra);
-    dfree(ctx->d_P);
-    dfree(ctx->d_Q64);
-    dfree(ctx->d_k0);
-    dfree(ctx->d_eps);
-    dfree(ctx->d_da);
-    dfree(ctx->d_alpha);
-    dfree(ctx->d_minv);
-    dfree(ctx->d_wmean);
-    dfree(ctx->d_wm2);
+    dfree(ctx, ctx->d_H);
+    dfree(ctx, ctx->d_cur);
+    dfree(ctx, ctx->d_psel);
+    dfree(ctx, ctx->d_ll);
+    dfree(ctx, ctx->d_lp);
+    dfree(ctx, ctx->d_llp);
+    dfree(ctx, ctx->d_lpp);
+    dfree(ctx, ctx->d_logu);
+    dfree(ctx, ctx->d_acc);
+    dfree(ctx, ctx->d_accl);
+    dfree(ctx, ctx->d_G);
+    dfree(ctx, ctx->d_extra);
+    dfree(ctx, ctx->d_P);
+    dfree(ctx, ctx->d_Q64);
+    dfree(ctx, ctx->d_k0);
+    dfree(ctx, ctx->d_eps);
+    dfree(ctx, ctx->d_da);
+    dfree(ctx, ctx->d_alpha);
+    dfree(ctx, ctx->d_minv);
+    dfree(ctx, ctx->d_wmean);
+    dfree(ctx, ctx->d_wm2);
     for (double **p : {&ctx->nuts.qL, &ctx->nuts.pL, &ctx->nuts.gL, &ctx->nuts.qR, &ctx->nuts.pR,
                        &ctx->nuts.gR, &ctx->nuts.ph, &ctx->nuts.gsel, &ctx->nuts.gsub, &ctx->nuts.sc})
-        dfree(*p);
-    dfree(ctx->nuts.hsel);
-    dfree(ctx->nuts.hsub);
+        dfree(ctx, *p);
+    dfree(ctx, ctx->nuts.hsel);
+    dfree(ctx, ctx->nuts.hsub);
     ctx->adapt_pending = ctx->adapt_n > 0;  // new chains adapt from the start
     ctx->g_valid = false;
     ctx->C = 0;
@@ -426,7 +444,7 @@ static mt_status build_raytab(mt_ctx *ctx)
         CK(ctx, launch_psi_calib(d_k, ctx->stream));
         CK(ctx, cudaMemcpyAsync(&kappa, d_k, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         CK(ctx, cudaStreamSynchronize(ctx->stream));
-        dfree(d_k);
+        dfree(ctx, d_k);
         if (!(fabs(kappa) < 1e-5)) return fail(ctx, MT_ECUDA, "logistic calibration out of range: %g", kappa);
         ctx->psi_kc = (float)(kappa * 0x1p-28);
         ctx->pb.psi_kc = ctx->psi_kc;
@@ -786,6 +804,16 @@ extern "C" {
 
 mt_status mt_create(mt_ctx **out, int device, const mt_config *cfg, void *cuda_stream)
 {
+    return mt::ctx_create_pooled(out, device, cfg, cuda_stream, nullptr);
+}
+
+}  // extern "C"
+
+// A context whose device memory comes from `pool` (stream-ordered on its
+// stream; the server's contexts) or from cudaMalloc (pool == nullptr).
+mt_status mt::ctx_create_pooled(mt_ctx **out, int device, const mt_config *cfg, void *cuda_stream,
+                                cudaMemPool_t pool)
+{
     if (!out || !cfg) return fail(nullptr, MT_EINVAL, "mt_create: null argument");
     *out = nullptr;
     if (cfg->precision < MT_PREC_F64 || cfg->precision > MT_PREC_BF16)
@@ -807,6 +835,7 @@ mt_status mt_create(mt_ctx **out, int device, const mt_config *cfg, void *cuda_s
     mt_ctx *ctx = new (std::nothrow) mt_ctx();
     if (!ctx) return fail(nullptr, MT_ENOMEM, "mt_create: out of host memory");
     ctx->device = device;
+    ctx->pool = pool;
     ctx->cfg = *cfg;
     ctx->mode = cfg->precision;
     const char *fw = getenv("MT_FULL_WINDOWS");
@@ -820,9 +849,9 @@ mt_status mt_create(mt_ctx **out, int device, const mt_config *cfg, void *cuda_s
             ctx->own_stream = e == cudaSuccess;
         }
     }
-    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_flag, sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc(ctx, (void **)&ctx->d_flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_step, sizeof(int64_t));
+    if (e == cudaSuccess) e = dev_alloc(ctx, (void **)&ctx->d_step, sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_step, 0, sizeof(int64_t), ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -834,56 +863,58 @@ mt_status mt_create(mt_ctx **out, int device, const mt_config *cfg, void *cuda_s
     return MT_OK;
 }
 
+extern "C" {
+
 mt_status mt_destroy(mt_ctx *ctx)
 {
     if (!ctx) return MT_OK;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     drop_chains(ctx);
-    dfree(ctx->d_mu);
-    dfree(ctx->d_muff);
-    dfree(ctx->d_sensors);
-    dfree(ctx->d_dirs);
-    dfree(ctx->d_o4);
-    dfree(ctx->d_s4);
-    dfree(ctx->d_kz0);
-    dfree(ctx->d_xa4);
-    dfree(ctx->d_xb4);
-    dfree(ctx->d_xc2);
-    dfree(ctx->d_kz1);
-    dfree(ctx->d_od);
-    dfree(ctx->d_sd);
-    dfree(ctx->d_dt);
-    dfree(ctx->d_dtff);
-    dfree(ctx->d_a);
-    dfree(ctx->d_aff);
-    dfree(ctx->d_sumK);
-    dfree(ctx->d_cnt);
-    dfree(ctx->d_flag);
-    dfree(ctx->d_perm);
-    dfree(ctx->d_step);
-    dfree(ctx->d_work);
-    if (ctx->d_part) cudaFree(ctx->d_part);
-    if (ctx->d_in) cudaFree(ctx->d_in);
-    if (ctx->d_out) cudaFree(ctx->d_out);
-    if (ctx->d_out2) cudaFree(ctx->d_out2);
-    if (ctx->d_gacc) cudaFree(ctx->d_gacc);
-    if (ctx->d_dO) cudaFree(ctx->d_dO);
-    if (ctx->d_diag) cudaFree(ctx->d_diag);
-    if (ctx->d_terr) cudaFree(ctx->d_terr);
-    if (ctx->d_lrow) cudaFree(ctx->d_lrow);
+    dfree(ctx, ctx->d_mu);
+    dfree(ctx, ctx->d_muff);
+    dfree(ctx, ctx->d_sensors);
+    dfree(ctx, ctx->d_dirs);
+    dfree(ctx, ctx->d_o4);
+    dfree(ctx, ctx->d_s4);
+    dfree(ctx, ctx->d_kz0);
+    dfree(ctx, ctx->d_xa4);
+    dfree(ctx, ctx->d_xb4);
+    dfree(ctx, ctx->d_xc2);
+    dfree(ctx, ctx->d_kz1);
+    dfree(ctx, ctx->d_od);
+    dfree(ctx, ctx->d_sd);
+    dfree(ctx, ctx->d_dt);
+    dfree(ctx, ctx->d_dtff);
+    dfree(ctx, ctx->d_a);
+    dfree(ctx, ctx->d_aff);
+    dfree(ctx, ctx->d_sumK);
+    dfree(ctx, ctx->d_cnt);
+    dfree(ctx, ctx->d_flag);
+    dfree(ctx, ctx->d_perm);
+    dfree(ctx, ctx->d_step);
+    dfree(ctx, ctx->d_work);
+    if (ctx->d_part) dev_free(ctx, ctx->d_part);
+    if (ctx->d_in) dev_free(ctx, ctx->d_in);
+    if (ctx->d_out) dev_free(ctx, ctx->d_out);
+    if (ctx->d_out2) dev_free(ctx, ctx->d_out2);
+    if (ctx->d_gacc) dev_free(ctx, ctx->d_gacc);
+    if (ctx->d_dO) dev_free(ctx, ctx->d_dO);
+    if (ctx->d_diag) dev_free(ctx, ctx->d_diag);
+    if (ctx->d_terr) dev_free(ctx, ctx->d_terr);
+    if (ctx->d_lrow) dev_free(ctx, ctx->d_lrow);
     for (void *p : {(void *)ctx->d_lcptr, (void *)ctx->d_lcrow, ctx->d_lcval, ctx->d_fO, ctx->d_gcell})
-        if (p) cudaFree(p);
-    if (ctx->d_lcol) cudaFree(ctx->d_lcol);
-    if (ctx->d_lval) cudaFree(ctx->d_lval);
-    if (ctx->d_R0) cudaFree(ctx->d_R0);
-    if (ctx->d_dR) cudaFree(ctx->d_dR);
-    if (ctx->d_lam0) cudaFree(ctx->d_lam0);
-    if (ctx->d_amc) cudaFree(ctx->d_amc);
-    if (ctx->d_fine) cudaFree(ctx->d_fine);
-    if (ctx->d_Hd) cudaFree(ctx->d_Hd);
-    if (ctx->d_nodes) cudaFree(ctx->d_nodes);
-    if (ctx->d_tmp) cudaFree(ctx->d_tmp);
+        if (p) dev_free(ctx, p);
+    if (ctx->d_lcol) dev_free(ctx, ctx->d_lcol);
+    if (ctx->d_lval) dev_free(ctx, ctx->d_lval);
+    if (ctx->d_R0) dev_free(ctx, ctx->d_R0);
+    if (ctx->d_dR) dev_free(ctx, ctx->d_dR);
+    if (ctx->d_lam0) dev_free(ctx, ctx->d_lam0);
+    if (ctx->d_amc) dev_free(ctx, ctx->d_amc);
+    if (ctx->d_fine) dev_free(ctx, ctx->d_fine);
+    if (ctx->d_Hd) dev_free(ctx, ctx->d_Hd);
+    if (ctx->d_nodes) dev_free(ctx, ctx->d_nodes);
+    if (ctx->d_tmp) dev_free(ctx, ctx->d_tmp);
     for (int i = 0; i < 2; ++i)
         for (auto &p : ctx->ev_open[i]) {
             cudaEventDestroy(p.a);
@@ -1116,7 +1147,7 @@ mt_status mt_init_chains(mt_ctx *ctx, int n_chains, const void *heights0, uint64
     if (n_chains != ctx->C) {
         drop_chains(ctx);
         void *h = nullptr;
-        CK(ctx, cudaMalloc(&h, 2 * (size_t)n_chains * np * es));
+        CK(ctx, dev_alloc(ctx, (void **)&h, 2 * (size_t)n_chains * np * es));
         ctx->d_H = h;
         TRY(dalloc(ctx, &ctx->d_cur, n_chains));
         TRY(dalloc(ctx, &ctx->d_psel, n_chains));
@@ -1303,8 +1334,8 @@ static mt_status ensure_nuts(mt_ctx *ctx)
     TRY(dalloc(ctx, &b.sc, (size_t)kNS * ctx->C));
     const size_t es = elem_size(ctx);
     for (void **p : {&b.hsel, &b.hsub}) {
-        dfree(*p);
-        CK(ctx, cudaMalloc(p, n * es + 16));
+        dfree(ctx, *p);
+        CK(ctx, dev_alloc(ctx, (void **)p, n * es + 16));
     }
     return MT_OK;
 }
@@ -1553,9 +1584,10 @@ mt_status mt_sync(mt_ctx *ctx, double timeout_s)
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
     int flag = 0;
-    CK(ctx, cudaMemcpy(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
     if (flag) {
-        CK(ctx, cudaMemset(ctx->d_flag, 0, sizeof(int)));
+        CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
         return fail(ctx, MT_EDEVFLAG,
                     "a kernel latched device status %d (1: a Poisson draw ran out of attempts; 2: a "
                     "ray's samples left the grid; 4: a cell index out of range, MT_BOUNDS_CHECK builds)",
@@ -1710,9 +1742,9 @@ mt_status mt_set_prior(mt_ctx *ctx, int kind)
         std::vector<double> t(ctx->mu.begin() + (ctx->L - 1) * N, ctx->mu.begin() + ctx->L * N);
         std::vector<float> tf(N);
         for (size_t i = 0; i < N; ++i) tf[i] = (float)t[i];
-        if (ctx->d_terr) cudaFree(ctx->d_terr);
+        if (ctx->d_terr) dev_free(ctx, ctx->d_terr);
         ctx->d_terr = nullptr;
-        CK(ctx, cudaMalloc(&ctx->d_terr, N * es));
+        CK(ctx, dev_alloc(ctx, (void **)&ctx->d_terr, N * es));
         CK(ctx, cudaMemcpyAsync(ctx->d_terr, es == 8 ? (const void *)t.data() : (const void *)tf.data(),
                                 N * es, cudaMemcpyHostToDevice, ctx->stream));
         CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1762,12 +1794,12 @@ mt_status mt_set_adapt(mt_ctx *ctx, double target_accept, int n_adapt)
     ctx->adapt_pending = n_adapt > 0;
     if (n_adapt == 0) {
         CK(ctx, cudaStreamSynchronize(ctx->stream));
-        dfree(ctx->d_eps);
-        dfree(ctx->d_da);
-        dfree(ctx->d_alpha);
-        dfree(ctx->d_minv);
-        dfree(ctx->d_wmean);
-        dfree(ctx->d_wm2);
+        dfree(ctx, ctx->d_eps);
+        dfree(ctx, ctx->d_da);
+        dfree(ctx, ctx->d_alpha);
+        dfree(ctx, ctx->d_minv);
+        dfree(ctx, ctx->d_wmean);
+        dfree(ctx, ctx->d_wm2);
     }
     return MT_OK;
 }
@@ -1793,9 +1825,9 @@ mt_status mt_set_metric_adapt(mt_ctx *ctx, int on, double shrink)
     ctx->adapt_pending = ctx->adapt_n > 0;  // the warm-up starts over
     if (!on) {
         CK(ctx, cudaStreamSynchronize(ctx->stream));
-        dfree(ctx->d_minv);
-        dfree(ctx->d_wmean);
-        dfree(ctx->d_wm2);
+        dfree(ctx, ctx->d_minv);
+        dfree(ctx, ctx->d_wmean);
+        dfree(ctx, ctx->d_wm2);
     }
     return MT_OK;
 }
@@ -1874,15 +1906,15 @@ mt_status mt_set_forward(mt_ctx *ctx, int kind, int n_z, const double *h_ref)
     for (void **p : {(void **)&ctx->d_lrow, (void **)&ctx->d_lcol, &ctx->d_lval, &ctx->d_R0,
                      (void **)&ctx->d_lam0, (void **)&ctx->d_amc, (void **)&ctx->d_lcptr, (void **)&ctx->d_lcrow,
                      &ctx->d_lcval}) {
-        if (*p) cudaFree(*p);
+        if (*p) dev_free(ctx, *p);
         *p = nullptr;
     }
-    CK(ctx, cudaMalloc((void **)&ctx->d_lrow, row.size() * 4));
-    CK(ctx, cudaMalloc((void **)&ctx->d_lcol, nnz * 4 + 16));
-    CK(ctx, cudaMalloc(&ctx->d_lval, nnz * es + 16));
-    CK(ctx, cudaMalloc(&ctx->d_R0, nvox * es));
-    CK(ctx, cudaMalloc((void **)&ctx->d_lam0, nr * 8));
-    CK(ctx, cudaMalloc((void **)&ctx->d_amc, nr * 8));
+    CK(ctx, dev_alloc(ctx, (void **)&ctx->d_lrow, row.size() * 4));
+    CK(ctx, dev_alloc(ctx, (void **)&ctx->d_lcol, nnz * 4 + 16));
+    CK(ctx, dev_alloc(ctx, (void **)&ctx->d_lval, nnz * es + 16));
+    CK(ctx, dev_alloc(ctx, (void **)&ctx->d_R0, nvox * es));
+    CK(ctx, dev_alloc(ctx, (void **)&ctx->d_lam0, nr * 8));
+    CK(ctx, dev_alloc(ctx, (void **)&ctx->d_amc, nr * 8));
     CK(ctx, cudaMemcpyAsync(ctx->d_lrow, row.data(), row.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->d_lcol, col.data(), nnz * 4, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->d_lval, es == 4 ? (const void *)valf.data() : (const void *)val.data(),
@@ -1893,9 +1925,9 @@ mt_status mt_set_forward(mt_ctx *ctx, int kind, int n_z, const double *h_ref)
     lin_transpose((int)nr, (int)nvox, row, col, val, cptr, crow, cval);
     std::vector<float> cvalf;
     if (es == 4) cvalf.assign(cval.begin(), cval.end());
-    CK(ctx, cudaMalloc((void **)&ctx->d_lcptr, cptr.size() * 4));
-    CK(ctx, cudaMalloc((void **)&ctx->d_lcrow, nnz * 4 + 16));
-    CK(ctx, cudaMalloc(&ctx->d_lcval, nnz * es + 16));
+    CK(ctx, dev_alloc(ctx, (void **)&ctx->d_lcptr, cptr.size() * 4));
+    CK(ctx, dev_alloc(ctx, (void **)&ctx->d_lcrow, nnz * 4 + 16));
+    CK(ctx, dev_alloc(ctx, (void **)&ctx->d_lcval, nnz * es + 16));
     CK(ctx, cudaMemcpyAsync(ctx->d_lcptr, cptr.data(), cptr.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->d_lcrow, crow.data(), nnz * 4, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->d_lcval, es == 4 ? (const void *)cvalf.data() : (const void *)cval.data(),

@@ -113,6 +113,11 @@ struct CtxView {
     cudaStream_t stream;
 };
 mt_status ctx_view(mt_ctx *ctx, CtxView *v);
+// mt_create with the context's device memory taken from a stream-ordered
+// pool (allocated and released on the context's stream; the server's
+// request contexts), or from cudaMalloc when pool is nullptr.
+mt_status ctx_create_pooled(mt_ctx **out, int device, const mt_config *cfg, void *cuda_stream,
+                            cudaMemPool_t pool);
 mt_status ctx_fail(mt_ctx *ctx, mt_status st, const char *msg);
 
 // Launchers (stream-ordered, return cudaGetLastError()).

@@ -3,7 +3,10 @@
 // Requests (a problem, its data, its chains and a step budget) arrive at any
 // time.  A scheduler thread admits them in arrival order while the device
 // memory they would hold fits the budget and a slot is free, builds each one
-// its own context and CUDA stream (chain state stays resident), and keeps
+// its own context on the slot's CUDA stream (chain state stays resident; its
+// device memory comes from the server's stream-ordered pool, filled at
+// creation, so admission and completion neither allocate from the driver nor
+// synchronise the device), and keeps
 // every admitted request busy: whenever a request's previous super-step has
 // finished on the GPU it launches the next one (one CUDA-graph replay of
 // n_within Metropolis steps), so super-steps of different requests overlap on
@@ -46,7 +49,9 @@ struct Request {
     mt_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    int slot = -1;
     bool inflight = false;
+    double gpu_start = NAN, gpu_end = NAN, gpu_busy = 0.0;  // device clock, ms
     std::atomic<bool> cancel{false};
     int supers_done = 0;
     std::vector<float> superstep_ms;
@@ -100,6 +105,15 @@ struct mt_server {
     int device = 0;
     size_t budget = 0, used = 0;
     int max_active = 0;
+    cudaMemPool_t pool = nullptr;     // device memory of the requests' contexts
+    size_t pool_start = 0;            // bytes the pool held once filled
+    struct Slot {
+        cudaStream_t stream = nullptr;
+        cudaEvent_t a = nullptr, b = nullptr;
+        bool used = false;
+    };
+    std::vector<Slot> slots;          // max_active streams and events, reused
+    cudaEvent_t ev_ref = nullptr;     // device-clock origin
     clock_t_::time_point t0;
     std::mutex mu;
     std::condition_variable cv_done;
@@ -131,14 +145,21 @@ static bool setup_request(mt_server *s, Request *r)
 {
     const mt_request &q = r->spec;
     mt_status st;
-    if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&r->ev_a) != cudaSuccess || cudaEventCreate(&r->ev_b) != cudaSuccess) {
-        cudaGetLastError();
-        r->error = "stream/event creation failed";
-        r->status = MT_ECUDA;
+    for (size_t i = 0; i < s->slots.size(); ++i)  // a free slot exists: active < max_active
+        if (!s->slots[i].used) {
+            s->slots[i].used = true;
+            r->slot = (int)i;
+            r->stream = s->slots[i].stream;
+            r->ev_a = s->slots[i].a;
+            r->ev_b = s->slots[i].b;
+            break;
+        }
+    if (r->slot < 0) {
+        r->error = "no free stream slot";
+        r->status = MT_ESTATE;
         return false;
     }
-    st = mt_create(&r->ctx, s->device, &q.cfg, r->stream);
+    st = mt::ctx_create_pooled(&r->ctx, s->device, &q.cfg, r->stream, s->pool);
     if (st != MT_OK) {
         r->error = mt_last_error(nullptr);
         r->status = st;
@@ -184,11 +205,10 @@ static void finish_request(mt_server *s, Request *r)
             r->error = mt_last_error(r->ctx);
         }
     }
-    if (r->ctx) mt_destroy(r->ctx);
+    if (r->ctx) mt_destroy(r->ctx);  // its memory goes back to the pool on its stream
     r->ctx = nullptr;
-    if (r->ev_a) cudaEventDestroy(r->ev_a);
-    if (r->ev_b) cudaEventDestroy(r->ev_b);
-    if (r->stream) cudaStreamDestroy(r->stream);
+    if (r->slot >= 0) s->slots[r->slot].used = false;  // stream and events are reused
+    r->slot = -1;
     r->ev_a = r->ev_b = nullptr;
     r->stream = nullptr;
     std::lock_guard<std::mutex> g(s->mu);
@@ -204,6 +224,72 @@ static void finish_request(mt_server *s, Request *r)
     s->n_done += 1;
     r->done = true;
     s->cv_done.notify_all();
+}
+
+// The device memory, streams and events of a server, made once at creation:
+// a stream-ordered pool that keeps up to the budget (release threshold) and is
+// filled with min(budget, 32 GiB) in 2 GiB blocks, max_active stream slots,
+// and the device-clock origin event.  False (with s->err) on failure.
+static bool server_reserve(mt_server *s)
+{
+    auto bad = [&](cudaError_t e, const char *what) {
+        cudaGetLastError();
+        s->err = std::string("mt_server_create: ") + what + ": " + cudaGetErrorString(e);
+        return false;
+    };
+    cudaError_t e = cudaSetDevice(s->device);
+    if (e != cudaSuccess) return bad(e, "cudaSetDevice");
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = s->device;
+    if ((e = cudaMemPoolCreate(&s->pool, &props)) != cudaSuccess) return bad(e, "cudaMemPoolCreate");
+    uint64_t thr = s->budget;
+    if ((e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &thr)) != cudaSuccess)
+        return bad(e, "pool release threshold");
+    s->slots.resize(s->max_active);
+    for (auto &sl : s->slots) {
+        if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreate(&sl.a)) != cudaSuccess || (e = cudaEventCreate(&sl.b)) != cudaSuccess)
+            return bad(e, "stream / event");
+    }
+    cudaStream_t st = s->slots[0].stream;
+    const size_t block = (size_t)2 << 30, fill = std::min(s->budget, (size_t)32 << 30);
+    std::vector<void *> blocks;
+    for (size_t got = 0; got < fill;) {
+        const size_t want = std::min(block, fill - got);
+        void *p = nullptr;
+        if (cudaMallocFromPoolAsync(&p, want, s->pool, st) != cudaSuccess) {
+            cudaGetLastError();  // the device is fuller than the budget: keep what was reserved
+            break;
+        }
+        blocks.push_back(p);
+        got += want;
+    }
+    for (void *p : blocks) cudaFreeAsync(p, st);
+    if ((e = cudaEventCreate(&s->ev_ref)) != cudaSuccess) return bad(e, "cudaEventCreate");
+    if ((e = cudaEventRecord(s->ev_ref, st)) != cudaSuccess) return bad(e, "cudaEventRecord");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bad(e, "pool fill");
+    uint64_t held = 0;
+    cudaMemPoolGetAttribute(s->pool, cudaMemPoolAttrReservedMemCurrent, &held);
+    s->pool_start = (size_t)held;
+    return true;
+}
+
+static void server_release(mt_server *s)
+{
+    cudaSetDevice(s->device);
+    for (auto &sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.a) cudaEventDestroy(sl.a);
+        if (sl.b) cudaEventDestroy(sl.b);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    s->slots.clear();
+    if (s->ev_ref) cudaEventDestroy(s->ev_ref);
+    s->ev_ref = nullptr;
+    if (s->pool) cudaMemPoolDestroy(s->pool);
+    s->pool = nullptr;
 }
 
 static void worker_loop(mt_server *s)
@@ -250,8 +336,13 @@ static void worker_loop(mt_server *s)
                     r->status = MT_ECUDA;
                     r->error = cudaGetErrorString(e);
                 } else {
-                    float ms = 0.f;
+                    float ms = 0.f, ta = 0.f, tb = 0.f;
                     cudaEventElapsedTime(&ms, r->ev_a, r->ev_b);
+                    cudaEventElapsedTime(&ta, s->ev_ref, r->ev_a);
+                    cudaEventElapsedTime(&tb, s->ev_ref, r->ev_b);
+                    if (!(r->gpu_start <= ta)) r->gpu_start = ta;
+                    r->gpu_end = tb;
+                    r->gpu_busy += ms;
                     r->superstep_ms.push_back(ms);
                     r->supers_done += 1;
                 }
@@ -321,6 +412,12 @@ MT_API mt_status mt_server_create(mt_server **out, int device, size_t hbm_budget
     s->budget = hbm_budget_bytes;
     s->max_active = max_active;
     s->t0 = clock_t_::now();
+    if (!server_reserve(s)) {
+        std::string m = s->err;
+        server_release(s);
+        delete s;
+        return srv_fail(nullptr, MT_ECUDA, m);
+    }
     s->worker = std::thread(worker_loop, s);
     *out = s;
     return MT_OK;
@@ -384,6 +481,9 @@ MT_API mt_status mt_server_wait(mt_server *s, int64_t id, double timeout_s, void
         info->superstep_ms_p50 = pct(v, 0.5);
         info->superstep_ms_p99 = pct(v, 0.99);
         info->n_supersteps = (int)v.size();
+        info->gpu_start_ms = r->gpu_start;
+        info->gpu_end_ms = r->gpu_end;
+        info->gpu_busy_ms = r->gpu_busy;
     }
     if (r->status != MT_OK) return srv_fail(s, (mt_status)r->status, r->error);
     if (heights_out) memcpy(heights_out, r->heights.data(), r->heights.size());
@@ -431,6 +531,10 @@ MT_API mt_status mt_server_stats(mt_server *s, mt_server_stats_t *out)
     const double span = s->last_done - s->first_admit;
     out->chain_ray_evals_per_s = span > 0 ? s->chain_ray_evals / span : NAN;
     out->bytes_in_use = s->used;
+    uint64_t held = 0;
+    cudaMemPoolGetAttribute(s->pool, cudaMemPoolAttrReservedMemCurrent, &held);
+    out->pool_bytes_at_start = s->pool_start;
+    out->pool_bytes_now = (size_t)held;
     return MT_OK;
 }
 
@@ -439,6 +543,7 @@ MT_API mt_status mt_server_destroy(mt_server *s)
     if (!s) return MT_OK;
     s->stop.store(true);
     if (s->worker.joinable()) s->worker.join();
+    server_release(s);
     delete s;
     return MT_OK;
 }

@@ -52,14 +52,16 @@ class Request(C.Structure):
 class RequestInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("n_supersteps", C.c_int), ("submit_s", C.c_double),
                 ("admit_s", C.c_double), ("done_s", C.c_double),
-                ("superstep_ms_p50", C.c_double), ("superstep_ms_p99", C.c_double)]
+                ("superstep_ms_p50", C.c_double), ("superstep_ms_p99", C.c_double),
+                ("gpu_start_ms", C.c_double), ("gpu_end_ms", C.c_double), ("gpu_busy_ms", C.c_double)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [("n_done", C.c_int64), ("n_pending", C.c_int64), ("n_active", C.c_int64),
                 ("superstep_ms_p50", C.c_double), ("superstep_ms_p99", C.c_double),
                 ("ttp_s_p50", C.c_double), ("ttp_s_p99", C.c_double),
-                ("chain_ray_evals_per_s", C.c_double), ("bytes_in_use", C.c_size_t)]
+                ("chain_ray_evals_per_s", C.c_double), ("bytes_in_use", C.c_size_t),
+                ("pool_bytes_at_start", C.c_size_t), ("pool_bytes_now", C.c_size_t)]
 
 
 _lib = None

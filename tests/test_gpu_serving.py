@@ -119,3 +119,37 @@ def test_cancel_queued_and_running_requests():
     alone.close()
     np.testing.assert_array_equal(got["heights"], ref["heights"])
     np.testing.assert_array_equal(got["loglik"], ref["loglik"])
+
+
+def test_requests_overlap_on_device_without_allocating():
+    """Six scenario-size requests submitted at once to a three-slot server:
+    their super-steps run on the device at the same time (device-clock spans
+    of different requests intersect, and the requests' summed super-step time
+    exceeds the span of the whole mix), and serving them took no device memory
+    beyond what the server reserved at creation (its pool held the same bytes
+    before and after: no request's memory came from the driver, and no
+    cudaFree synchronised the device)."""
+    reqs = []
+    for k in range(6):  # the scenario workload with 64 chains: ~1.5 ms per step
+        w = W.scenario()
+        w.n_chains, w.n_super, w.n_within = 64, 12, 2
+        w.seed_init, w.seed_mcmc = 50 + k, 60 + k
+        reqs.append(w)
+    srv = mt.Server(hbm_budget_bytes=1 << 30, max_active=3)
+    ids = _submit_all(srv, reqs, pace=False)
+    infos = [srv.wait(i, 120.0)["info"] for i in ids]
+    st = srv.stats()
+    srv.close()
+    spans = [(f["gpu_start_ms"], f["gpu_end_ms"]) for f in infos]
+    assert all(np.isfinite(a) and b > a for a, b in spans), spans
+    pairs = [(i, j) for i in range(len(spans)) for j in range(i + 1, len(spans))
+             if spans[i][0] < spans[j][1] and spans[j][0] < spans[i][1]]
+    assert pairs, spans
+    # one request's super-steps run in order on its own stream, so its busy time
+    # fits in its span; a sum over requests above the span of the whole mix
+    # means super-steps of different requests ran at the same time
+    span_all = max(b for _, b in spans) - min(a for a, _ in spans)
+    busy = sum(f["gpu_busy_ms"] for f in infos)
+    assert busy > span_all, (busy, span_all)
+    assert st["pool_bytes_at_start"] >= 1 << 30, st
+    assert st["pool_bytes_now"] == st["pool_bytes_at_start"], st
