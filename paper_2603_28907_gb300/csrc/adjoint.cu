@@ -188,6 +188,265 @@ __device__ __forceinline__ void scatter_surface(const Prob &pb, const float *sh,
     if (cur >= 0) flush_cell(al, cur, Q, c00, c01, c10, c11);
 }
 
+// ---------------------------------------------------------------- adjoint on the (h, dx) planes
+// The scatter on the forward march's scaled (h, dx) planes (shared memory),
+// one surface at a time: a CTA holds every surface's plane plus one plane of
+// fixed-point accumulators, which it adds to the chain's accumulators in HBM
+// after each surface.  The fixed-point unit is a power of two per chain,
+// 2^E with 2^(E + 28) >= max_p |coef_p| (coef_p = dO_p dt_p max_l |drho_l| /
+// gamma), so a sample's weight is at most 2^28 units and a cell's sums
+// nearly always convert with one 32-bit rounding; the totals are rescaled
+// exactly to the shared 2^-24 unit when they leave the CTA (a right shift,
+// rounding to nearest, for chains whose unit is finer).
+#ifndef MT_ADJ_THREADS
+#define MT_ADJ_THREADS 1024
+#endif
+constexpr int kAdjDxThreads = MT_ADJ_THREADS;
+
+// Add round(v) (units) to the shared-memory accumulator at shared-window
+// address a.  |v| < 2^31 converts with one 32-bit rounding; larger v split
+// into a multiple of 2^22 (rounded by adding 1.5 * 2^45; |v| is clamped to
+// 2^43, far beyond any weight a finite state produces) and a remainder.
+__device__ __forceinline__ void red_fixed(uint32_t a, float v)
+{
+    long long q;
+    if (fabsf(v) < 2147483520.0f) {  // the largest FP32 value below 2^31
+        q = (long long)__float2int_rn(v);
+    } else {
+        const float M45 = 52776558133248.0f;  // 1.5 * 2^45: ulp 2^22
+        const float vc = fminf(fmaxf(v, -8796093022208.0f), 8796093022208.0f);
+        const float t = vc + M45;
+        const float lo = vc - (t - M45);  // exact, |lo| <= 2^21
+        q = ((long long)(__float_as_int(t) - __float_as_int(M45)) << 22) +
+            (long long)(__float_as_int(lo + 12582912.0f) - 0x4B400000);
+    }
+    if (q != 0) asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a), "l"(q) : "memory");
+}
+
+// A cell's sums U0, U1 (row r), V0, V1 (row r + 1) onto its four nodes; a:
+// accumulator address of node (r, c), rowb: bytes per row.
+__device__ __forceinline__ void flush_dx(uint32_t a, uint32_t rowb, float U0, float U1, float V0, float V1)
+{
+    red_fixed(a, fmaf(0.5f, U0, -U1));
+    red_fixed(a + 8u, fmaf(0.5f, U0, U1));
+    red_fixed(a + rowb, fmaf(0.5f, V0, -V1));
+    red_fixed(a + rowb + 8u, fmaf(0.5f, V0, V1));
+}
+
+// Surface l along one ray: samples within the window where a weight can
+// reach one unit, two per step in paired FP32 lanes (lane .x sample k,
+// lane .y sample k + 1; positions, records and the argument a = kg64 (z - s_l)
+// formed as in the forward march).  Per sample the weight
+// v = coef psi (1 - psi) with psi (1 - psi) = 2^-|a| / (1 + 2^-|a|)^2
+// (d varsigma / d s_l = psi (1 - psi) / gamma) goes to the cell's nodes with
+// the bilinear weights: with the records' x-fraction f in [-1/2, 1/2] the
+// two nodes of a row get 1/2 - f and 1/2 + f, and the rows 1 - fy and fy.
+// A lane keeps per cell the sums U0 = sum v (1 - fy), U1 = sum v (1 - fy) f,
+// V0 = sum v fy, V1 = sum v fy f and moves them to a pending slot when a
+// sample enters the next cell (samples in order along the ray visit each
+// cell once); the warp's pending slots are added to the accumulators
+// together, when some lane needs its slot again.  pbase: shared-window
+// address of plane l; to_acc: accumulator address minus record address.
+template <int L>
+__device__ __forceinline__ void scatter_ray_dx(const Prob &pb, int ray, int l, float coef, const float *ext,
+                                               uint32_t pbase, uint32_t to_acc)
+{
+    const float4 xa = pb.xa4[ray], xb = pb.xb4[ray];
+    const int2 c0 = pb.xc2[ray];
+    const int Q = pb.Q, G = pb.G;
+    const float dz = xb.z + xb.w, rdz = rcp_approx(dz);
+    const float zh = pb.kz1[(size_t)l * pb.n_rays + ray], zl = pb.kz1[(size_t)(L + l) * pb.n_rays + ray];
+    // psi (1 - psi) <= 2^-|a|: beyond |a| = log2|coef| a sample adds less
+    // than one unit (2^-28 of the chain's largest ray weight) to any node,
+    // and all of them together, falling off geometrically along the ray, less
+    // than 1 / (1 - 2^-s) units per node and side (s: the vertical step per
+    // sample in log2 units); the warp takes its largest width so that its
+    // lanes run loops of near-equal length
+    float ka = fmaxf(log2f(fabsf(coef) + 1e-30f), 1.0f);
+    ka = __int_as_float(__reduce_max_sync(__activemask(), __float_as_int(ka)));
+    int lo, hi;
+    transition_window(zh + zl, dz, rdz, 1.0f, -ext[L + l], -ext[l], G, lo, hi, ka);
+    lo = min(lo, G);
+    const int he = max(hi + 1, lo);
+
+    const float2 M2 = f2(12582912.0f);
+    const float2 ox2 = f2(xa.x), oy2 = f2(xa.y), sxh2 = f2(xa.z), syh2 = f2(xa.w);
+    const float2 sxl2 = f2(xb.x), syl2 = f2(xb.y), szh2 = f2(xb.z), szl2 = f2(xb.w);
+    const float2 zh2 = f2(zh), zl2 = f2(zl);
+    const uint32_t rowb = 8u * (uint32_t)Q;
+    // record address 8 (Q iy + ix) + pbase from the float bits of the cell
+    // coordinates (as in the forward march)
+    const uint32_t k0 = pbase + 8u * (uint32_t)(c0.y * Q + c0.x) - 8u * 0x4B400000u * (uint32_t)(Q + 1);
+    float2 rA0 = f2(0.f), rA1 = f2(0.f), rB0 = f2(0.f), rB1 = f2(0.f);
+    int curA = -1, curB = -1, cur = -1, pend = -1;
+    float2 uu = f2(0.f), ww = f2(0.f), pu = f2(0.f), pw = f2(0.f);  // {U0, U1}, {V0, V1}; pending
+
+    auto step = [&](float2 kf, float cB) {
+        const float2 gx = fma2(kf, sxh2, fma2(kf, sxl2, ox2)), gy = fma2(kf, syh2, fma2(kf, syl2, oy2));
+        const float2 tx = add2(gx, M2), ty = add2(gy, M2);
+        const float2 fx = fma2(add2(tx, f2(-12582912.0f)), f2(-1.0f), gx);
+        const float2 fy = add2(fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy), f2(0.5f));
+        uint32_t aA0 = (uint32_t)__float_as_int(ty.x) * rowb + ((uint32_t)__float_as_int(tx.x) * 8u + k0);
+        uint32_t aB0 = (uint32_t)__float_as_int(ty.y) * rowb + ((uint32_t)__float_as_int(tx.y) * 8u + k0);
+#ifdef MT_BOUNDS_CHECK
+        if (!(cell_ok(c0.x + __float_as_int(tx.x) - 0x4B400000, c0.y + __float_as_int(ty.x) - 0x4B400000, Q - 1,
+                      pb.R - 1) &&
+              cell_ok(c0.x + __float_as_int(tx.y) - 0x4B400000, c0.y + __float_as_int(ty.y) - 0x4B400000, Q - 1,
+                      pb.R - 1))) {
+            atomicOr(pb.flag, 4);
+            aA0 = aB0 = pbase;
+        }
+#endif
+        reload_pair(aA0, aB0, rowb, curA, curB, rA0, rA1, rB0, rB1);
+        const float2 a = make_float2(fmaf(fx.x, rA0.y, rA0.x), fmaf(fx.y, rB0.y, rB0.x));  // row r
+        const float2 b = make_float2(fmaf(fx.x, rA1.y, rA1.x), fmaf(fx.y, rB1.y, rB1.x));  // row r + 1
+        const float2 sl = fma2(fy, fma2(a, f2(-1.0f), b), a);  // -kg64 (s_l - ref_l)
+        const float2 arg = add2(add2(sl, fma2(kf, szh2, zh2)), fma2(kf, szl2, zl2));
+        const float2 e = make_float2(ex2_approx(-fabsf(arg.x)), ex2_approx(-fabsf(arg.y)));
+        const float2 d = add2(e, f2(1.0f));
+        const float2 r = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+        const float2 v = mul2(mul2(make_float2(coef, cB), e), mul2(r, r));
+        const float2 vy = mul2(v, fy);
+        const float2 vny = fma2(vy, f2(-1.0f), v);  // v (1 - fy)
+        // sample A, then B, in order along the ray
+        const int ia = (int)aA0, ib = (int)aB0;
+        const bool chA = ia != cur, chB = ib != ia;
+        if (__any_sync(__activemask(), (chA || chB) && pend >= 0)) {
+            if (pend >= 0) {
+                flush_dx((uint32_t)pend + to_acc, rowb, pu.x, pu.y, pw.x, pw.y);
+                pend = -1;
+            }
+        }
+        if (chA) {
+            if (cur >= 0) {
+                pend = cur;
+                pu = uu;
+                pw = ww;
+            }
+            uu = ww = f2(0.f);
+            cur = ia;
+        }
+        uu = fma2(f2(vny.x), make_float2(1.0f, fx.x), uu);
+        ww = fma2(f2(vy.x), make_float2(1.0f, fx.x), ww);
+        if (chB) {  // B entered the next cell: a second move in this step if A moved too (rare)
+            if (pend >= 0) flush_dx((uint32_t)pend + to_acc, rowb, pu.x, pu.y, pw.x, pw.y);
+            pend = cur;
+            pu = uu;
+            pw = ww;
+            uu = ww = f2(0.f);
+            cur = ib;
+        }
+        uu = fma2(f2(vny.y), make_float2(1.0f, fx.y), uu);
+        ww = fma2(f2(vy.y), make_float2(1.0f, fx.y), ww);
+    };
+
+    int k = lo;
+    float2 kf2 = make_float2((float)lo, (float)lo + 1.0f);
+    for (; k + 2 <= he; k += 2) {
+        step(kf2, coef);
+        kf2 = add2(kf2, f2(2.0f));
+    }
+    if (k < he) step(f2(kf2.x), 0.0f);  // last sample of an odd window: lane .y repeats it with weight 0
+    if (pend >= 0) flush_dx((uint32_t)pend + to_acc, rowb, pu.x, pu.y, pw.x, pw.y);
+    if (cur >= 0) flush_dx((uint32_t)cur + to_acc, rowb, uu.x, uu.y, ww.x, ww.y);
+}
+
+// A CTA total in units 2^E as a multiple of 2^-24 (shift = E + 24): exact
+// for shift >= 0, rounded to nearest otherwise.
+__device__ __forceinline__ unsigned long long to_fix24(long long v, int shift)
+{
+    if (shift >= 0) return (unsigned long long)v << shift;
+    if (shift <= -63) return 0ull;
+    return (unsigned long long)((v + (1ll << (-shift - 1))) >> (-shift));
+}
+
+// Per chain: unit_e[c] = E with 2^(E + 27) < max_p |dO_p dt_p| max_l |drho_l|
+// / gamma <= 2^(E + 28) (E = -24, the absolute unit, when that is 0 or not
+// finite); E is kept in [-100, 100].
+__global__ void __launch_bounds__(1024) k_adj_unit(Prob pb, int *unit_e)
+{
+    const int c = blockIdx.x;
+    const float *dO = pb.dO + (size_t)c * pb.n_rays;
+    float m = 0.f;
+    for (int p = threadIdx.x; p < pb.n_rays; p += blockDim.x) m = fmaxf(m, fabsf(dO[p] * pb.dt_ff[p].x));
+    __shared__ int red[32];
+    int mi = __reduce_max_sync(0xffffffffu, __float_as_int(m));  // m >= 0: ordered as integers
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mi;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = 1; j < (int)(blockDim.x >> 5); ++j) mi = max(mi, red[j]);
+        float dr = 0.f;
+        for (int l = 0; l < pb.L; ++l) dr = fmaxf(dr, fabsf(pb.drho_f[l]));
+        const float mm = __int_as_float(mi) * dr * (float)(1.0 / pb.gamma);
+        int e = 4;
+        if (mm > 0.f && mm <= 3.0e38f) frexpf(mm, &e);
+        unit_e[c] = min(max(e - 28, -100), 100);
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kAdjDxThreads)
+k_adjoint_dx(Prob pb, HRef h, int rays_per_block, const int *unit_e, unsigned long long *gacc)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *planes = reinterpret_cast<float2 *>(smem_raw);
+    const int c = blockIdx.y, N = pb.N;
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)L * N * sizeof(float2));
+    stage_planes_dx_scaled<float, L>(planes, chain_ptr<float>(h, c), N, pb.Q, pb.ref, pb.kg, pb.kgl);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) acc[i] = 0ull;
+    __shared__ float ext[2 * MT_MAX_L];
+    __syncthreads();
+    surface_extent<L>(planes, N, ext);
+    __syncthreads();
+    const int E = unit_e[c];
+    const float cg = ldexpf((float)(1.0 / pb.gamma), -E);  // 1 / (gamma 2^E)
+    const uint32_t sp = (uint32_t)__cvta_generic_to_shared(planes);
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(acc);
+    unsigned long long *gc = gacc + (size_t)c * L * N;
+    const int r_begin = blockIdx.x * rays_per_block;
+    const int r_end = min(r_begin + rays_per_block, pb.n_rays);
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+        const uint32_t pbase = sp + 8u * (uint32_t)(l * N);
+        const float cl = pb.drho_f[l] * cg;
+        for (int slot = r_begin + threadIdx.x; slot < r_end; slot += blockDim.x) {
+            const int ray = pb.perm ? pb.perm[slot] : slot;
+            const float coef = cl * (pb.dO[(size_t)c * pb.n_rays + ray] * pb.dt_ff[ray].x);
+            scatter_ray_dx<L>(pb, ray, l, coef, ext, pbase, sa - pbase);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const long long v = (long long)acc[i];
+            acc[i] = 0ull;
+            if (v) atomicAdd(gc + (size_t)l * N + i, to_fix24(v, E + 24));
+        }
+        __syncthreads();
+    }
+}
+
+bool adjoint_dx_fits(const Prob &pb)
+{
+    return (size_t)(pb.L + 1) * pb.N * 8 + MT_SMEM_STATIC <= MT_MAX_SMEM;
+}
+
+template <int L>
+static cudaError_t adj_dx_l(const Prob &pb, HRef h, int n_chains, int rpb, unsigned long long *gacc,
+                            cudaStream_t st)
+{
+    const size_t bytes = (size_t)(L + 1) * pb.N * 8;
+    static size_t set = 0;
+    if (bytes > 48 * 1024 && bytes > set) {
+        cudaError_t e = cudaFuncSetAttribute(k_adjoint_dx<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        set = bytes;
+    }
+    int *unit_e = reinterpret_cast<int *>(pb.dO + (size_t)n_chains * pb.n_rays);
+    k_adj_unit<<<n_chains, 1024, 0, st>>>(pb, unit_e);
+    dim3 grid((pb.n_rays + rpb - 1) / rpb, n_chains);
+    k_adjoint_dx<L><<<grid, kAdjDxThreads, bytes, st>>>(pb, h, rpb, unit_e, gacc);
+    return cudaGetLastError();
+}
+
 // One CTA = one chain x one block of ray slots (slot i -> ray perm[i]).  SMEM:
 // accumulate in shared memory and flush once per CTA; otherwise add straight
 // into global memory.
@@ -276,11 +535,25 @@ static cudaError_t adj_l(const Prob &pb, HRef h, int n_chains, int rpb, unsigned
     return cudaGetLastError();
 }
 
-// gacc: [n_chains][L][N] zeroed by the caller; pb.dO: [n_chains][n_rays].
+// gacc: [n_chains][L][N] zeroed by the caller; pb.dO: [n_chains][n_rays] followed by
+// n_chains ints of scratch (the per-chain fixed-point units).
 cudaError_t launch_adjoint(const Prob &pb, HRef h, int n_chains, unsigned long long *gacc, cudaStream_t st)
 {
     if (!pb.dO) return cudaErrorInvalidValue;
     const int rpb = march_rays_per_block(pb);
+    if (adjoint_dx_fits(pb)) {
+        switch (pb.L) {
+            case 1: return adj_dx_l<1>(pb, h, n_chains, rpb, gacc, st);
+            case 2: return adj_dx_l<2>(pb, h, n_chains, rpb, gacc, st);
+            case 3: return adj_dx_l<3>(pb, h, n_chains, rpb, gacc, st);
+            case 4: return adj_dx_l<4>(pb, h, n_chains, rpb, gacc, st);
+            case 5: return adj_dx_l<5>(pb, h, n_chains, rpb, gacc, st);
+            case 6: return adj_dx_l<6>(pb, h, n_chains, rpb, gacc, st);
+            case 7: return adj_dx_l<7>(pb, h, n_chains, rpb, gacc, st);
+            case 8: return adj_dx_l<8>(pb, h, n_chains, rpb, gacc, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (pb.L) {
         case 1: return adj_l<1>(pb, h, n_chains, rpb, gacc, st);
         case 2: return adj_l<2>(pb, h, n_chains, rpb, gacc, st);

@@ -723,7 +723,7 @@ static mt_status ensure_grad_bufs(mt_ctx *ctx, int n)
     const size_t np = n_per_chain(ctx);
     void *old_g = ctx->d_gacc, *old_d = ctx->d_dO;
     TRY(grow(ctx, &ctx->d_gacc, &ctx->gacc_cap, (size_t)n * np * 8));
-    TRY(grow(ctx, &ctx->d_dO, &ctx->dO_cap, (size_t)n * ctx->pb.n_rays * 4));
+    TRY(grow(ctx, &ctx->d_dO, &ctx->dO_cap, (size_t)n * (ctx->pb.n_rays + 1) * 4));  // + the adjoint's units
     if (ctx->d_gacc != old_g || ctx->d_dO != old_d) drop_graph(ctx);
     if (ctx->linear) {  // d ll / d O per ray and the per-cell gradients, chains padded to 32
         const size_t Cp = ((size_t)n + 31) / 32 * 32, es = elem_size(ctx);

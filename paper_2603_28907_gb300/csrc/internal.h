@@ -150,7 +150,8 @@ cudaError_t launch_propose_rw(const Prob &pb, int mode, void *hbuf, long long bu
 cudaError_t launch_advance(int64_t *step, int n, cudaStream_t st);
 size_t adjoint_smem_bytes(const Prob &pb, bool with_acc);
 // The adjoint's scatter of pb.dO (written by an FP32-mode march of the same
-// heights) into gacc [n_chains][L][N] (zeroed by the caller).
+// heights) into gacc [n_chains][L][N] (zeroed by the caller; units 2^-24).
+// pb.dO holds n_chains * n_rays floats followed by n_chains ints of scratch.
 cudaError_t launch_adjoint(const Prob &pb, HRef h, int n_chains, unsigned long long *gacc,
                            cudaStream_t st);
 cudaError_t launch_grad_finish(const Prob &pb, int mode, HRef h, const double *mu, int n_chains,

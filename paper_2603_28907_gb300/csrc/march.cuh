@@ -126,9 +126,40 @@ __device__ __forceinline__ void stage_planes_dx(float2 *sh, const H *Hc, int N, 
     }
 }
 
-// Per-surface minimum and maximum of the node offsets h - ref_l, from the
-// staged records (planes in shared memory or HBM): ext[l] = min,
-// ext[L + l] = max.  All threads must call it, after the planes are complete
+// The same planes scaled to sigmoid-argument units (log2, kg64 = log2(e) /
+// gamma = kgh + kgl), for the adjoint: {-kg64 hm, -kg64 dx}, so that the
+// lerp of the records is -kg64 (s_l - ref_l) directly.  hm is formed exactly
+// (float-float two-sum) and each product by kg64 is rounded once.
+template <typename H>
+__device__ __forceinline__ float2 dx_record_scaled(const H *Hc, int N, int Q, float ref, float kgh, float kgl,
+                                                   int l, int i)
+{
+    const float h = (float)Hc[(size_t)l * N + i] - ref;
+    const float d = (i % Q) == Q - 1 ? 0.f : ((float)Hc[(size_t)l * N + i + 1] - ref) - h;
+    const float hd = 0.5f * d, mh = h + hd, v = mh - h;
+    const float ml = (h - (mh - v)) + (hd - v);  // h + d / 2 = mh + ml exactly
+    const float p = kgh * mh;
+    float e = fmaf(kgh, mh, -p);
+    e = fmaf(kgh, ml, e);
+    e = fmaf(kgl, mh, e);
+    const float pd = kgh * d;
+    const float ed = fmaf(kgl, d, fmaf(kgh, d, -pd));
+    return make_float2(-(p + e), -(pd + ed));
+}
+
+template <typename H, int L>
+__device__ __forceinline__ void stage_planes_dx_scaled(float2 *sh, const H *Hc, int N, int Q, const float *ref,
+                                                       float kgh, float kgl)
+{
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+#pragma unroll
+        for (int l = 0; l < L; ++l) sh[(size_t)l * N + i] = dx_record_scaled<H>(Hc, N, Q, ref[l], kgh, kgl, l, i);
+    }
+}
+
+// Per-surface minimum and maximum of the node offsets h - ref_l (or of
+// -kg64 (h - ref_l) for scaled planes), from the staged records (planes in
+// shared memory or HBM): ext[l] = min, ext[L + l] = max.  All threads must call it, after the planes are complete
 // and visible.
 template <int L>
 __device__ __forceinline__ void surface_extent(const float2 *planes, int N, float *ext)
@@ -449,11 +480,30 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
 //             2^-29 are kept.
 // The integer adds c_bits >> 3 = 2^28 [a < 0] + kJunk per sample (the
 // exponent bits of 2^-28 shifted down); kJunk is subtracted once per window.
-// The corner records of both samples are cached and reloaded when either
+// The corner records of each sample are cached and reloaded when that
 // sample enters a new cell.
 constexpr uint32_t kQuantBits = 0x31800000u;      // FP32 bits of 2^-28
 constexpr uint32_t kJunk = kQuantBits >> 3;       // added per sample by the sign trick
 constexpr unsigned long long kUnit = 1ull << 28;  // one indicator = 2^28 units
+
+// Records of rows r and r + 1 for the two samples of a step, each pair
+// loaded (predicated, no branch) only when its sample's cell address differs
+// from the one cached in cA / cB.
+__device__ __forceinline__ void reload_pair(uint32_t aA, uint32_t aB, uint32_t rowb, int &cA, int &cB,
+                                            float2 &rA0, float2 &rA1, float2 &rB0, float2 &rB1)
+{
+    const uint32_t nA = (uint32_t)((int)aA != cA), nB = (uint32_t)((int)aB != cB);
+    cA = (int)aA;
+    cB = (int)aB;
+    asm volatile("{\n\t.reg .pred pa, pb;\n\tsetp.ne.u32 pa, %8, 0;\n\tsetp.ne.u32 pb, %9, 0;\n\t"
+                 "@pa ld.shared.v2.f32 {%0, %1}, [%10];\n\t"
+                 "@pa ld.shared.v2.f32 {%2, %3}, [%11];\n\t"
+                 "@pb ld.shared.v2.f32 {%4, %5}, [%12];\n\t"
+                 "@pb ld.shared.v2.f32 {%6, %7}, [%13];\n\t}"
+                 : "+f"(rA0.x), "+f"(rA0.y), "+f"(rA1.x), "+f"(rA1.y),
+                   "+f"(rB0.x), "+f"(rB0.y), "+f"(rB1.x), "+f"(rB1.y)
+                 : "r"(nA), "r"(nB), "r"(aA), "r"(aA + rowb), "r"(aB), "r"(aB + rowb));
+}
 
 template <bool HARD, bool GLOBAL>
 __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int *flag, float2 kf2, float2 ix2,
@@ -490,7 +540,7 @@ __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int 
             rB1 = __ldg(pl + nB + Q);
         }
     } else {
-        // reload both samples' corner records when either entered a new cell:
+        // reload a sample's corner records when it entered a new cell:
         // predicated shared loads instead of a divergent branch.  The record's
         // byte address 8 (Q iy + ix) + base comes straight from the float bits
         // (ix = bits(tx) - 0x4B400000 + c0x, likewise iy; k0 folds the base,
@@ -502,18 +552,7 @@ __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int 
 #ifdef MT_BOUNDS_CHECK
         if (!in_grid) aA0 = aB0 = (uint32_t)__cvta_generic_to_shared(pl);
 #endif
-        const uint32_t aA1 = aA0 + rowb, aB1 = aB0 + rowb;
-        const uint32_t need = (uint32_t)(((int)aA0 != curA) | ((int)aB0 != curB));
-        curA = (int)aA0;
-        curB = (int)aB0;
-        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %8, 0;\n\t"
-                     "@p ld.shared.v2.f32 {%0, %1}, [%9];\n\t"
-                     "@p ld.shared.v2.f32 {%2, %3}, [%10];\n\t"
-                     "@p ld.shared.v2.f32 {%4, %5}, [%11];\n\t"
-                     "@p ld.shared.v2.f32 {%6, %7}, [%12];\n\t}"
-                     : "+f"(rA0.x), "+f"(rA0.y), "+f"(rA1.x), "+f"(rA1.y),
-                       "+f"(rB0.x), "+f"(rB0.y), "+f"(rB1.x), "+f"(rB1.y)
-                     : "r"(need), "r"(aA0), "r"(aA1), "r"(aB0), "r"(aB1));
+        reload_pair(aA0, aB0, rowb, curA, curB, rA0, rA1, rB0, rB1);
     }
     const float2 a = make_float2(fmaf(fx.x, rA0.y, rA0.x), fmaf(fx.y, rB0.y, rB0.x));  // row r0
     const float2 b = make_float2(fmaf(fx.x, rA1.y, rA1.x), fmaf(fx.y, rB1.y, rB1.x));  // row r0 + 1
