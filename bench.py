@@ -831,6 +831,9 @@ def main():
         pg.destroy_process_group()
 
 
+ESS_STEPS = 120  # per sampler in the default line's effective-sample-size leg
+
+
 def bench_extras(ctx, stream, w, pr, counts, local):
     """Short legs of the other configurations on the bench's own states, after
     the timed region, each with its clock record: the FP32 mode's per-chain
@@ -912,11 +915,45 @@ def bench_extras(ctx, stream, w, pr, counts, local):
         e1.record(stream)
     stream.synchronize()
     mala_ms = e0.elapsed_time(e1) / 3
+    # effective samples per second of each surface's mean height, random walk
+    # against MALA, from the same starts (second half of a short run)
+    ess = {}
+    for name, kern, step in (("rw_sigma_0.002", mt.KERNEL_RW, w.rw_sigma), ("mala_eps_0.005", mt.KERNEL_MALA, 0.005)):
+        g.init_chains(H, w.seed_mcmc + 2)
+        with torch.cuda.stream(stream):
+            g.run(kern, step, 1, 1)
+        stream.synchronize()
+        a0 = torch.zeros(C, dtype=torch.int64, device=dev)
+        g.get_state(accepts_out=a0)
+        n_steps, t_s = ESS_STEPS, 0.0
+        trace = np.zeros((n_steps, C, w.L))
+        cur = torch.zeros_like(H)
+        for k in range(n_steps):
+            with torch.cuda.stream(stream):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.run(kern, step, 1, 1)
+                e1.record(stream)
+            stream.synchronize()
+            t_s += e0.elapsed_time(e1) / 1e3 if k >= n_steps // 2 else 0.0
+            g.get_state(cur)
+            trace[k] = cur.mean(dim=(2, 3)).double().cpu().numpy()
+        a1 = torch.zeros(C, dtype=torch.int64, device=dev)
+        g.get_state(accepts_out=a1)
+        burn = n_steps // 2
+        e = np.array([[_ess(trace[burn:, c, l]) for l in range(w.L)] for c in range(C)])
+        ess[name] = {"acceptance": float((a1 - a0).double().mean().item()) / n_steps,
+                     "ess_per_chain_mean": float(e.mean()),
+                     "ess_per_s": float(e.sum(0).mean() / t_s), "step_ms": t_s / (n_steps - burn) * 1e3}
     g.close()
     rays = w.S * w.P
     res["gradient"] = {"chains": C, "mt_grad_ms": grad_ms,
                        "surface_samples_per_s": C * rays * w.G * w.L / (grad_ms / 1e3),
-                       "mala_step_ms": mala_ms, "mala_eps_m": 0.005, "clocks": clocks.stop()}
+                       "mala_step_ms": mala_ms, "mala_eps_m": 0.005,
+                       "ess": {"steps": ESS_STEPS, "statistic": "mean height of each surface, second half",
+                               **ess, "mala_over_rw_ess_per_s": ess["mala_eps_0.005"]["ess_per_s"] /
+                               max(ess["rw_sigma_0.002"]["ess_per_s"], 1e-300)},
+                       "clocks": clocks.stop()}
 
     # serving: eight requests of the serving mix, step budgets scaled by 1/200
     clocks = Clocks(local)

@@ -55,6 +55,17 @@ bool march_fits_smem(const Prob &pb, int mode)
     return march_smem_bytes(pb, mode) + MT_SMEM_STATIC <= MT_MAX_SMEM;
 }
 
+size_t march_phased_smem_bytes(const Prob &pb)
+{
+    // one surface's (h, dx) plane and a float-float sum per ray slot
+    return (size_t)8 * pb.N + (size_t)8 * march_rays_per_block(pb);
+}
+
+bool march_fits_phased(const Prob &pb, int mode)
+{
+    return (mode == MODE_F32 || mode == MODE_F32C) && march_phased_smem_bytes(pb) + MT_SMEM_STATIC <= MT_MAX_SMEM;
+}
+
 cudaError_t launch_march(const Prob &pb, int mode, HRef h, int n_chains, void *partial,
                          double *ray_O, double *ray_term, cudaStream_t st)
 {
@@ -558,17 +569,20 @@ static mt_status ensure_partials(mt_ctx *ctx, int n_chains)
     return ensure_nodes(ctx, n_chains);
 }
 
-// Grids whose node records exceed shared memory run the FP32 modes from
-// records in HBM (see k_stage_dx_global); the other modes need them to fit.
+// Grids whose planes exceed shared memory run the FP32 modes one surface's
+// plane at a time (k_march_phased) or, when not even one plane and the
+// rays' sums fit, from records in HBM (see k_stage_dx_global); the other
+// modes need their records to fit.
 static bool use_global_nodes(const mt_ctx *ctx)
 {
-    return !march_fits_smem(ctx->pb, ctx->mode) && (ctx->mode == MODE_F32 || ctx->mode == MODE_F32C);
+    return !march_fits_smem(ctx->pb, ctx->mode) && !march_fits_phased(ctx->pb, ctx->mode) &&
+           (ctx->mode == MODE_F32 || ctx->mode == MODE_F32C);
 }
 
 static mt_status check_smem(mt_ctx *ctx)
 {
     const size_t smem = march_smem_bytes(ctx->pb, ctx->mode);
-    if (!march_fits_smem(ctx->pb, ctx->mode) && !use_global_nodes(ctx))
+    if (!march_fits_smem(ctx->pb, ctx->mode) && !march_fits_phased(ctx->pb, ctx->mode) && !use_global_nodes(ctx))
         return fail(ctx, MT_EINVAL,
                     "surfaces need %zu bytes of shared memory per block (limit %d): use "
                     "MT_PREC_F32 (records in HBM) or a smaller grid",

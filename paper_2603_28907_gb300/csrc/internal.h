@@ -138,6 +138,9 @@ cudaError_t launch_gen_counts(const Prob &pb, const double *h_nodes, uint64_t se
 int march_rays_per_block(const Prob &pb);
 size_t march_smem_bytes(const Prob &pb, int mode);
 bool march_fits_smem(const Prob &pb, int mode);  // records + static part within a block's limit
+// One surface's plane plus a float-float sum per ray slot (FP32 modes' phased march)
+size_t march_phased_smem_bytes(const Prob &pb);
+bool march_fits_phased(const Prob &pb, int mode);
 cudaError_t launch_march(const Prob &pb, int mode, HRef h, int n_chains, void *partial,
                          double *ray_O, double *ray_term, cudaStream_t st);
 cudaError_t launch_reduce_ll(const Prob &pb, int mode, int n_chains, const void *partial,

@@ -492,17 +492,16 @@ constexpr unsigned long long kUnit = 1ull << 28;  // one indicator = 2^28 units
 __device__ __forceinline__ void reload_pair(uint32_t aA, uint32_t aB, uint32_t rowb, int &cA, int &cB,
                                             float2 &rA0, float2 &rA1, float2 &rB0, float2 &rB1)
 {
-    const uint32_t nA = (uint32_t)((int)aA != cA), nB = (uint32_t)((int)aB != cB);
-    cA = (int)aA;
-    cB = (int)aB;
-    asm volatile("{\n\t.reg .pred pa, pb;\n\tsetp.ne.u32 pa, %8, 0;\n\tsetp.ne.u32 pb, %9, 0;\n\t"
-                 "@pa ld.shared.v2.f32 {%0, %1}, [%10];\n\t"
-                 "@pa ld.shared.v2.f32 {%2, %3}, [%11];\n\t"
-                 "@pb ld.shared.v2.f32 {%4, %5}, [%12];\n\t"
+    asm volatile("{\n\t.reg .pred pa, pb;\n\tsetp.ne.u32 pa, %8, %9;\n\tsetp.ne.u32 pb, %10, %11;\n\t"
+                 "@pa ld.shared.v2.f32 {%0, %1}, [%8];\n\t"
+                 "@pa ld.shared.v2.f32 {%2, %3}, [%12];\n\t"
+                 "@pb ld.shared.v2.f32 {%4, %5}, [%10];\n\t"
                  "@pb ld.shared.v2.f32 {%6, %7}, [%13];\n\t}"
                  : "+f"(rA0.x), "+f"(rA0.y), "+f"(rA1.x), "+f"(rA1.y),
                    "+f"(rB0.x), "+f"(rB0.y), "+f"(rB1.x), "+f"(rB1.y)
-                 : "r"(nA), "r"(nB), "r"(aA), "r"(aA + rowb), "r"(aB), "r"(aB + rowb));
+                 : "r"(aA), "r"((uint32_t)cA), "r"(aB), "r"((uint32_t)cB), "r"(aA + rowb), "r"(aB + rowb));
+    cA = (int)aA;
+    cB = (int)aB;
 }
 
 template <bool HARD, bool GLOBAL>
@@ -692,16 +691,41 @@ __device__ __forceinline__ void transition_window(float z0, float dz, float rdz,
     hi = min((int)kb, G - 1);
 }
 
-// The FP32 modes' march of one ray: per surface l, the exact integer sum
+// Surface l of one ray in the FP32 modes: the exact integer sum
 // N_l = sum_k round(varsigma(s_l - z_k) 2^28) (see dx_pair for the
 // arithmetic), computed over the samples where surface l can be
-// transitional (transition_window with ext = per-surface min / max offsets);
+// transitional (transition_window over the surface's offsets [smin, smax]);
 // the other samples' contributions are exact and added analytically (2^28
 // below the surface, 0 above).  A window of odd length is widened by one
 // saturated sample where the ray has one and starts at an even sample (one
 // more saturated sample below), so that samples go in pairs aligned with the
-// blocks of march_surface_dx.  emit(l, N_l) is called for l = 0 .. L-1 in
-// order.
+// blocks of march_surface_dx.  plane: surface l's records; kl: their
+// shared-window base folded as in march_ray_dx (0 for HBM records).
+// Returns N_l 2^28.
+template <bool HARD, bool GLOBAL>
+__device__ __forceinline__ unsigned long long march_ray_surface_dx(const Prob &pb, const float2 *plane, uint32_t kl,
+                                                                   int ray, int l, float4 xa, float4 xb, int2 c0,
+                                                                   int cell0, float dz, float rdz, float smin,
+                                                                   float smax, unsigned long long *evaluated)
+{
+    const int G = pb.G;
+    const float zh = pb.kz1[(size_t)l * pb.n_rays + ray];
+    const float zl = pb.kz1[(size_t)(pb.L + l) * pb.n_rays + ray];
+    int lo = 0, hi = G - 1;
+    if (!pb.full_windows) transition_window(zh + zl, dz, rdz, pb.kg, smin, smax, G, lo, hi, kSatX);
+    lo = min(lo, G) & ~1;  // even start (one more, saturated, sample below)
+    int he = max(hi + 1, lo);
+    if (((he - lo) & 1) && he < G) ++he;  // even length where the ray allows
+    if (evaluated) *evaluated += (unsigned long long)(he - lo);
+    unsigned long long t = (unsigned long long)lo * kUnit;  // samples below the window
+    march_surface_dx<HARD, GLOBAL>(plane, pb.Q, pb.R, pb.flag, xa, xb, -pb.kg, -pb.kgl, __float_as_uint(-pb.psi_kc),
+                                   zh, zl, kl, cell0, c0, lo, he, t);
+    return t;
+}
+
+// The FP32 modes' march of one ray over all L surfaces (planes [l][node],
+// ext = per-surface min / max offsets): emit(l, N_l 2^28) is called for
+// l = 0 .. L-1 in order.
 template <int L, bool HARD, bool GLOBAL, typename Emit>
 __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *planes, int ray,
                                              const float *ext, unsigned long long *evaluated,
@@ -710,7 +734,6 @@ __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *plane
     const float4 xa = pb.xa4[ray], xb = pb.xb4[ray];
     const int2 c0 = pb.xc2[ray];
     const int cell0 = c0.y * pb.Q + c0.x;
-    const int G = pb.G;
     const float dz = xb.z + xb.w;
     const float rdz = rcp_approx(dz);
     uint32_t k0 = 0u;
@@ -719,19 +742,9 @@ __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *plane
              8u * 0x4B400000u * (uint32_t)(pb.Q + 1);
 #pragma unroll kSurfUnroll
     for (int l = 0; l < L; ++l) {
-        const float zh = pb.kz1[(size_t)l * pb.n_rays + ray];
-        const float zl = pb.kz1[(size_t)(L + l) * pb.n_rays + ray];
-        int lo = 0, hi = G - 1;
-        if (!pb.full_windows) transition_window(zh + zl, dz, rdz, pb.kg, ext[l], ext[L + l], G, lo, hi, kSatX);
-        lo = min(lo, G) & ~1;  // even start (one more, saturated, sample below)
-        int he = max(hi + 1, lo);
-        if (((he - lo) & 1) && he < G) ++he;  // even length where the ray allows
-        if (evaluated) *evaluated += (unsigned long long)(he - lo);
-        unsigned long long t = (unsigned long long)lo * kUnit;  // samples below the window
         const uint32_t kl = GLOBAL ? 0u : k0 + 8u * (uint32_t)((size_t)l * pb.N);
-        march_surface_dx<HARD, GLOBAL>(planes + (size_t)l * pb.N, pb.Q, pb.R, pb.flag, xa, xb, -pb.kg, -pb.kgl,
-                                       __float_as_uint(-pb.psi_kc), zh, zl, kl, cell0, c0, lo, he, t);
-        emit(l, t);
+        emit(l, march_ray_surface_dx<HARD, GLOBAL>(pb, planes + (size_t)l * pb.N, kl, ray, l, xa, xb, c0, cell0, dz,
+                                                   rdz, ext[l], ext[L + l], evaluated));
     }
 }
 
@@ -844,6 +857,60 @@ __device__ __forceinline__ FF block_sum(FF v)
     return v;
 }
 
+// ---------------------------------------------------------------- FP32 epilogue
+// S + drho_l N_l with N_l = tl 2^-28 split into two exactly representable
+// parts (float-float).
+__device__ __forceinline__ FF add_surface(const Prob &pb, FF S, int l, unsigned long long tl)
+{
+    const FF n = ff_two_sum((float)(uint32_t)(tl >> 24) * 0x1p-4f, (float)(uint32_t)(tl & 0xFFFFFFu) * 0x1p-28f);
+    return ff_add(S, ff_mul(FF{pb.drho_ff[l].x, pb.drho_ff[l].y}, n));
+}
+
+// One ray's term of the FP32 modes from S = G rho_top + sum_l drho_l N_l:
+// O = dt S and y = a - O / Lambda in float-float; the term -C (e^y - 1 - y)
+// (or -I0 e^{-O/Lambda} for C = 0) in FP32, its product by C kept exact as
+// a float-float.  Writes d ll / d O_p (for the adjoint) and the ray's
+// opacity and full term where asked.
+__device__ __forceinline__ FF ray_term_dx(const Prob &pb, int c, int ray, int Cp, FF Sff, double *ray_O,
+                                          double *ray_term)
+{
+    const FF Off = ff_mul(FF{pb.dt_ff[ray].x, pb.dt_ff[ray].y}, Sff);
+    const FF OL = ff_mul(Off, FF{pb.invL_ff.x, pb.invL_ff.y});
+    FF tf;
+    float dO;  // d ll / d O_p = (lambda - C) / Lambda
+    if (Cp > 0) {
+        const FF yff = ff_add(FF{pb.a_ff[ray].x, pb.a_ff[ray].y}, FF{-OL.hi, -OL.lo});
+        const float y = yff.hi + yff.lo, cf = (float)Cp;
+        const FF g = g_ff(yff);
+        tf = ff_mul(g, FF{-cf, 0.f});
+        dO = cf * expm1f(y) * pb.invL_ff.x;  // lambda - C = C (e^y - 1)
+    } else {
+        const double lam = pb.I0 * exp(-((double)OL.hi + (double)OL.lo));
+        tf = FF{(float)-lam, (float)(-lam - (double)(float)-lam)};
+        dO = (float)lam * pb.invL_ff.x;
+    }
+    if (pb.dO) pb.dO[(size_t)c * pb.n_rays + ray] = dO;
+    if (ray_O) ray_O[(size_t)c * pb.n_rays + ray] = (double)Off.hi + (double)Off.lo;
+    if (ray_term) ray_term[(size_t)c * pb.n_rays + ray] = ((double)tf.hi + (double)tf.lo) + poisson_K(Cp);
+    return tf;
+}
+
+// The CTA's float-float sum of ray terms into its chain partial: float2 in
+// the compensated mode, FP64 otherwise (the chain's partials are then summed
+// in FP64).
+template <int MODE>
+__device__ __forceinline__ void store_partial_ff(void *partial, FF accf)
+{
+    accf = block_sum(accf);
+    if (threadIdx.x == 0) {
+        const size_t at = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        if constexpr (MODE == MODE_F32C)
+            reinterpret_cast<float2 *>(partial)[at] = make_float2(accf.hi, accf.lo);
+        else
+            reinterpret_cast<double *>(partial)[at] = (double)accf.hi + (double)accf.lo;
+    }
+}
+
 // ---------------------------------------------------------------- kernel
 // FP32 and float-float modes use per-surface (h, dx) planes and 1024-thread
 // CTAs (one per SM with the scenario's 128 KB of records); BF16 keeps
@@ -911,37 +978,10 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
         const int ray = pb.perm ? pb.perm[slot] : slot;
         const int Cp = pb.cnt[ray];
         if constexpr (DX) {
-            // O = dt (G rho_top + sum_l drho_l N_l) and y = a - O / Lambda in
-            // float-float; the term -C (e^y - 1 - y) (or -I0 e^{-O/Lambda} for
-            // C = 0) in FP32, its product by C kept exact as a float-float.
             FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
             march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, pb.work ? &n_eval : nullptr,
-                                          [&](int l, unsigned long long tl) {
-                // N_l = tl 2^-28, split into two exactly representable parts
-                const FF n = ff_two_sum((float)(uint32_t)(tl >> 24) * 0x1p-4f,
-                                        (float)(uint32_t)(tl & 0xFFFFFFu) * 0x1p-28f);
-                Sff = ff_add(Sff, ff_mul(FF{pb.drho_ff[l].x, pb.drho_ff[l].y}, n));
-            });
-            const FF Off = ff_mul(FF{pb.dt_ff[ray].x, pb.dt_ff[ray].y}, Sff);
-            const FF OL = ff_mul(Off, FF{pb.invL_ff.x, pb.invL_ff.y});
-            FF tf;
-            float dO;  // d ll / d O_p = (lambda - C) / Lambda, for the adjoint
-            if (Cp > 0) {
-                const FF yff = ff_add(FF{pb.a_ff[ray].x, pb.a_ff[ray].y}, FF{-OL.hi, -OL.lo});
-                const float y = yff.hi + yff.lo, cf = (float)Cp;
-                const FF g = g_ff(yff);
-                tf = ff_mul(g, FF{-cf, 0.f});
-                dO = cf * expm1f(y) * pb.invL_ff.x;  // lambda - C = C (e^y - 1)
-            } else {
-                const double lam = pb.I0 * exp(-((double)OL.hi + (double)OL.lo));
-                tf = FF{(float)-lam, (float)(-lam - (double)(float)-lam)};
-                dO = (float)lam * pb.invL_ff.x;
-            }
-            if (pb.dO) pb.dO[(size_t)c * pb.n_rays + ray] = dO;
-            accf = ff_add(accf, tf);
-            if (ray_O) ray_O[(size_t)c * pb.n_rays + ray] = (double)Off.hi + (double)Off.lo;
-            if (ray_term)
-                ray_term[(size_t)c * pb.n_rays + ray] = ((double)tf.hi + (double)tf.lo) + poisson_K(Cp);
+                                          [&](int l, unsigned long long tl) { Sff = add_surface(pb, Sff, l, tl); });
+            accf = ff_add(accf, ray_term_dx(pb, c, ray, Cp, Sff, ray_O, ray_term));
         } else {
             double O, term;
             if constexpr (MODE == MODE_F64) {
@@ -975,22 +1015,71 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
         }
     }
     if (pb.work && n_eval) atomicAdd(pb.work, n_eval);
-    if constexpr (MODE == MODE_F32C) {
-        accf = block_sum(accf);
-        if (threadIdx.x == 0)
-            reinterpret_cast<float2 *>(partial)[(size_t)c * gridDim.x + blockIdx.x] =
-                make_float2(accf.hi, accf.lo);
-    } else if constexpr (MODE == MODE_F32) {
+    if constexpr (DX) {
         // the CTA's ray terms are summed in float-float (relative error ~2^-44,
-        // and it leaves the FP32 pipes to the march); the chain's CTA partials
-        // are summed in FP64
-        accf = block_sum(accf);
-        if (threadIdx.x == 0)
-            reinterpret_cast<double *>(partial)[(size_t)c * gridDim.x + blockIdx.x] = (double)accf.hi + (double)accf.lo;
+        // and it leaves the FP32 pipes to the march)
+        store_partial_ff<MODE>(partial, accf);
     } else {
         acc = block_sum(acc);
         if (threadIdx.x == 0) reinterpret_cast<double *>(partial)[(size_t)c * gridDim.x + blockIdx.x] = acc;
     }
+}
+
+
+// The FP32 modes' march for grids whose planes do not all fit in shared
+// memory but one plane does: the CTA stages one surface's plane at a time
+// and marches every ray of its block over that surface, keeping each ray's
+// float-float sum G rho_top + sum_l drho_l N_l in shared memory between
+// surfaces (same order of operations as k_march, so the results are
+// identical), then forms the ray terms.  Shared memory: N (h, dx) records and
+// rays_per_block float-float sums.
+template <int MODE, int L, bool HARD>
+__global__ void __launch_bounds__(MT_DX_THREADS)
+k_march_phased(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, double *ray_term)
+{
+    using Hh = typename Types<MODE>::H;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *plane = reinterpret_cast<float2 *>(smem_raw);
+    float2 *sums = reinterpret_cast<float2 *>(smem_raw + (size_t)pb.N * sizeof(float2));
+    const int c = blockIdx.y;
+    const Hh *Hc = chain_ptr<Hh>(h, c);
+    __shared__ float ext[2];
+    const int r_begin = blockIdx.x * rays_per_block;
+    const int r_end = min(r_begin + rays_per_block, pb.n_rays);
+    const uint32_t sp = (uint32_t)__cvta_generic_to_shared(plane);
+    unsigned long long n_eval = 0ull;
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+        if (l) __syncthreads();  // every ray is done with the previous plane
+        for (int i = threadIdx.x; i < pb.N; i += blockDim.x)
+            plane[i] = dx_record<Hh>(Hc, pb.N, pb.Q, pb.ref[l], l, i);
+        __syncthreads();
+        surface_extent<1>(plane, pb.N, ext);
+        __syncthreads();
+        const float smin = ext[0], smax = ext[1];
+        for (int slot = r_begin + (int)threadIdx.x, j = threadIdx.x; slot < r_end; slot += blockDim.x, j += blockDim.x) {
+            const int ray = pb.perm ? pb.perm[slot] : slot;
+            const float4 xa = pb.xa4[ray], xb = pb.xb4[ray];
+            const int2 c0 = pb.xc2[ray];
+            const int cell0 = c0.y * pb.Q + c0.x;
+            const float dz = xb.z + xb.w;
+            const uint32_t kl = sp + 8u * (uint32_t)cell0 - 8u * 0x4B400000u * (uint32_t)(pb.Q + 1);
+            const unsigned long long t =
+                march_ray_surface_dx<HARD, false>(pb, plane, kl, ray, l, xa, xb, c0, cell0, dz, rcp_approx(dz),
+                                                  smin, smax, pb.work ? &n_eval : nullptr);
+            const float2 s0 = l ? sums[j] : pb.grho_ff;
+            const FF S = add_surface(pb, FF{s0.x, s0.y}, l, t);
+            sums[j] = make_float2(S.hi, S.lo);
+        }
+    }
+    FF accf = {0.f, 0.f};
+    for (int slot = r_begin + (int)threadIdx.x, j = threadIdx.x; slot < r_end; slot += blockDim.x, j += blockDim.x) {
+        const int ray = pb.perm ? pb.perm[slot] : slot;
+        const float2 S = sums[j];  // written by this thread
+        accf = ff_add(accf, ray_term_dx(pb, c, ray, pb.cnt[ray], FF{S.x, S.y}, ray_O, ray_term));
+    }
+    if (pb.work && n_eval) atomicAdd(pb.work, n_eval);
+    store_partial_ff<MODE>(partial, accf);
 }
 
 }  // namespace mt

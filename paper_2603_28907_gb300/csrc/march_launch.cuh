@@ -24,10 +24,35 @@ static cudaError_t launch_global(const Prob &pb, HRef h, int n_chains, int rpb, 
 }
 
 template <int MODE, int L>
+static cudaError_t launch_phased(const Prob &pb, HRef h, int n_chains, int rpb, void *partial, double *ray_O,
+                                 double *ray_term, cudaStream_t st)
+{
+    if constexpr (MODE == MODE_F32 || MODE == MODE_F32C) {
+        const bool hard = pb.gamma == 0.0;
+        void (*fn)(Prob, HRef, int, void *, double *, double *) =
+            hard ? k_march_phased<MODE, L, true> : k_march_phased<MODE, L, false>;
+        const size_t smem = march_phased_smem_bytes(pb);
+        static size_t smem_set[2] = {0, 0};
+        if (smem > 48 * 1024 && smem > smem_set[hard]) {
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            smem_set[hard] = smem;
+        }
+        dim3 grid((pb.n_rays + rpb - 1) / rpb, n_chains);
+        fn<<<grid, MarchCfg<MODE, L>::THREADS, smem, st>>>(pb, h, rpb, partial, ray_O, ray_term);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <int MODE, int L>
 static cudaError_t launch_l(const Prob &pb, HRef h, int n_chains, int rpb, size_t smem,
                             void *partial, double *ray_O, double *ray_term, cudaStream_t st)
 {
     if (pb.gnodes) return launch_global<MODE, L>(pb, h, n_chains, rpb, partial, ray_O, ray_term, st);
+    if (smem + MT_SMEM_STATIC > MT_MAX_SMEM)  // one surface's plane at a time
+        return launch_phased<MODE, L>(pb, h, n_chains, rpb, partial, ray_O, ray_term, st);
     const bool hard = pb.gamma == 0.0;
     void (*fn)(Prob, HRef, int, void *, double *, double *) =
         hard ? k_march<MODE, L, true> : k_march<MODE, L, false>;

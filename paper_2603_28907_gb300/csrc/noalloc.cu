@@ -72,9 +72,9 @@ extern "C" MT_API mt_status mt_logpost_noalloc(mt_ctx *ctx, int n_chains, const 
         return ctx_fail(ctx, MT_EINVAL,
                         "mt_logpost_noalloc: every array must be device memory of the context's "
                         "device (staging host memory would need an allocation)");
-    if (!march_fits_smem(v.pb, v.mode))
+    if (!march_fits_smem(v.pb, v.mode) && !march_fits_phased(v.pb, v.mode))
         return ctx_fail(ctx, MT_EINVAL,
-                        "mt_logpost_noalloc: the grid's surfaces do not fit in shared memory "
+                        "mt_logpost_noalloc: not even one surface of the grid fits in shared memory "
                         "(that path needs an HBM buffer); use mt_logpost");
     v.pb.gnodes = nullptr;
     const int rpb = march_rays_per_block(v.pb);

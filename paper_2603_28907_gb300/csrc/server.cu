@@ -77,7 +77,9 @@ size_t footprint_of(const mt_request &r)
     b += rays * (16 + 16 + 8 * L + 24 + 24 + 8 + 8 + 8 + 8 + 4 + 8);  // ray table, counts
     b += C * ((rays + 4095) / 4096) * 8;            // partial sums
     b += L * N * 8 * 2;                             // prior mean, staging
-    if (N * L * 8 + MT_SMEM_STATIC > MT_MAX_SMEM) b += C * N * L * 8;  // HBM (h, dx) planes
+    const size_t rpb = std::min<size_t>(MT_RAYS_PER_CTA, (rays + 255) / 256 * 256);
+    if (N * L * 8 + MT_SMEM_STATIC > MT_MAX_SMEM && N * 8 + rpb * 8 + MT_SMEM_STATIC > MT_MAX_SMEM)
+        b += C * N * L * 8;                         // HBM (h, dx) planes (not even one plane fits)
     if (r.kernel == MT_KERNEL_MALA)                 // gradients: two slots, accumulator,
         b += 4 * C * L * N * 8 + C * 8 + C * rays * 4;  // staging; Hastings terms; dll/dO
     b += rays * 16 + C * L * N * es;                // output staging

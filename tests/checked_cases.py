@@ -26,9 +26,11 @@ def run():
         "tiny_bf16": (W.tiny(), mt.PREC_BF16),
         "odd_down_f32c": (W.small(R=5, Q=7, n_sensors=3, n_zenith=6, n_azimuth=7, G=20,
                                   zenith_max_deg=120.0), mt.PREC_F32C),
-        "large_hbm_f32": (W.small(R=100, Q=100, bases=(40.0, 70.0, 110.0, 140.0),
-                                  rho=(2.65, 1.9, 0.0012, 2.65, 0.0012), G=64, n_zenith=6, n_azimuth=9,
-                                  n_sensors=2), mt.PREC_F32),
+        "large_phased_f32": (W.small(R=100, Q=100, bases=(40.0, 70.0, 110.0, 140.0),
+                                     rho=(2.65, 1.9, 0.0012, 2.65, 0.0012), G=64, n_zenith=6, n_azimuth=9,
+                                     n_sensors=2), mt.PREC_F32),
+        "huge_hbm_f32": (W.small(R=170, Q=170, bases=(40.0, 70.0), G=48, n_zenith=5, n_azimuth=7,
+                                 n_sensors=2), mt.PREC_F32),
     }
     for name, (w, prec) in cases.items():
         pr, ctx, op, counts, _ = setup(w, precision=prec)
@@ -36,7 +38,7 @@ def run():
         H = torch.tensor(np.concatenate([pr["H_true"][None], W.init_chains(w, 2)]), dtype=dt, device=DEV)
         ll = _ll(ctx, H)
         rec = {"ll": ll.cpu().tolist()}
-        if prec in (mt.PREC_F32, mt.PREC_F32C) and name != "large_hbm_f32":
+        if prec in (mt.PREC_F32, mt.PREC_F32C) and name not in ("large_phased_f32", "huge_hbm_f32"):
             g = torch.zeros(H.shape, dtype=torch.float64, device=DEV)
             ctx.grad(H, g)
             rec["grad_sum"] = float(g.abs().sum().item())

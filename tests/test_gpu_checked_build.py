@@ -1,7 +1,8 @@
 """The bounds-checked build (MT_BOUNDS_CHECK, libmt_checked.so): every cell
 and voxel index the kernels form from the ray table is verified and one out
 of range would latch bit 4 of the device status word.  On the edge cases
-(odd grids, downward-looking pixels, a grid whose records live in HBM, every
+(odd grids, downward-looking pixels, a grid marched one surface at a time and
+one whose records live in HBM, every
 precision, the gradient, the linearised model, capped NUTS) the checked
 library must report a clean status word and give exactly the normal
 library's results."""

@@ -145,10 +145,11 @@ def test_mala_lockstep():
 
 
 def test_grad_large_grid_global_paths():
-    """A 100 x 100 grid with 4 surfaces: the march reads its (h, dx) records from
-    HBM and the adjoint adds straight into global fixed-point accumulators (its
-    records fit in shared memory, the accumulators do not); the gradient must
-    still match the oracle's, and a MALA step runs on those paths."""
+    """A 100 x 100 grid with 4 surfaces: the march stages one surface's (h, dx)
+    plane at a time and the adjoint adds straight into global fixed-point
+    accumulators (its node records fit in shared memory, the accumulators do
+    not); the gradient must still match the oracle's, and a MALA step runs on
+    those paths."""
     w = W.small(R=100, Q=100, bases=(40.0, 70.0, 110.0, 140.0),
                 rho=(2.65, 1.9, 0.0012, 2.65, 0.0012), G=64, n_zenith=6, n_azimuth=9,
                 n_sensors=2)

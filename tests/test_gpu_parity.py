@@ -337,12 +337,16 @@ def test_bad_arguments():
         ctx.set_grid(9, 4, 4, [1, 1, 1], np.ones(10))
 
 
-def test_large_grid_uses_hbm_records():
-    """A 100x100 grid with 4 surfaces exceeds shared memory in the FP32 layout; the
-    kernel then reads node records from HBM and must agree with the oracle."""
-    w = W.small(R=100, Q=100, bases=(40.0, 70.0, 110.0, 140.0),
-                rho=(2.65, 1.9, 0.0012, 2.65, 0.0012), G=64, n_zenith=6, n_azimuth=9,
-                n_sensors=2)
+@pytest.mark.parametrize("grid,bases", [(100, (40.0, 70.0, 110.0, 140.0)), (170, (40.0, 70.0, 110.0))],
+                         ids=["phased-100x100x4", "hbm-170x170x3"])
+def test_large_grid_paths(grid, bases):
+    """Grids whose FP32 planes exceed shared memory: at 100 x 100 with 4
+    surfaces (313 KB of planes) the march stages one surface's plane at a
+    time; at 170 x 170 not even one plane and the rays' sums fit and the
+    kernel reads its records from HBM.  Both must agree with the oracle, and
+    the Metropolis loop runs on them."""
+    rho = (2.65, 1.9, 0.0012, 2.65, 0.0012)[:len(bases) + 1]
+    w = W.small(R=grid, Q=grid, bases=bases, rho=rho, G=64, n_zenith=6, n_azimuth=9, n_sensors=2)
     pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
     Hs = np.concatenate([pr["H_true"][None], W.init_chains(w, 2)])
     H = heights(Hs, mt.PREC_F32)
