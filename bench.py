@@ -55,14 +55,15 @@ def march_traffic():
 
 # FP32 lane-ops per evaluated surface-sample of the FP32 march (two samples
 # per step: 19 paired FP32 instructions + 4 scalar x-lerp FMAs per 2 samples)
-EVAL_FP32_OPS = 21.0
+EVAL_FP32_OPS = 31.0  # per evaluated surface-sample, FP32 mode (accurate logistic)
 
 
 def march_peak_evaluated():
     """Evaluated surface-samples per second the pipes allow for the march's
-    own op mix (21 FP32 lane-ops + ex2 + rcp per evaluated sample)."""
+    own op mix in the FP32 mode (31 FP32 lane-ops + rcp per evaluated sample:
+    the accurate logistic forms 2^|a| on the FP32 pipe)."""
     clk = SM_COUNT * SM_MAX_MHZ * 1e6
-    sfu = clk / (1.0 / EX2_PER_CLK_SM + 1.0 / RCP_PER_CLK_SM)
+    sfu = clk * RCP_PER_CLK_SM
     fp32 = clk * FP32_PER_CLK_SM / EVAL_FP32_OPS
     return min(sfu, fp32)
 
@@ -350,7 +351,8 @@ def run_precision_study(args, local):
     from paper_2603_28907_gb300 import mt
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    modes = {"f32_fp64_reduce": mt.PREC_F32, "f32_compensated": mt.PREC_F32C, "bf16_heights": mt.PREC_BF16}
+    modes = {"f32_fp64_reduce": mt.PREC_F32, "f32_compensated": mt.PREC_F32C,
+             "f32_approximate_logistic": mt.PREC_F32A, "bf16_heights": mt.PREC_BF16}
     w, pr, ctxs, counts = _scenario_contexts([mt.PREC_F64] + list(modes.values()), local)
     traj = ctxs[mt.PREC_F32]
     ref = ctxs[mt.PREC_F64]
@@ -847,49 +849,87 @@ def bench_extras(ctx, stream, w, pr, counts, local):
     f64 = lambda n: torch.zeros(n, dtype=torch.float64, device=dev)
     res = {}
 
-    # precision: the chains' current states and two random-walk steps' proposals
+    # precision: the chains' current states and two random-walk steps'
+    # proposals in the FP32 mode, the compensated mode and the
+    # approximate-logistic mode, against the FP64 mode
     clocks = Clocks(local)
     clocks.start()
     t0 = time.perf_counter()
     ref = mt.from_workload(pr, precision=mt.PREC_F64, device=local)
     ref.set_counts(counts)
+    others = {}
+    for m, prec in (("f32c", mt.PREC_F32C), ("f32a", mt.PREC_F32A)):
+        others[m] = mt.from_workload(pr, precision=prec, device=local, stream=stream.cuda_stream)
+        others[m].set_counts(counts)
     H = torch.zeros((C, w.L, w.R, w.Q), dtype=torch.float32, device=dev)
-    ll32, lp = f64(C), f64(C)
-    ctx.get_state(H, ll32, lp)
+    ll = {"f32": f64(C)}
+    lp = f64(C)
+    ctx.get_state(H, ll["f32"], lp)
     ll64 = f64(C)
     ref.logpost(H.double(), ll64, None)
-    dll = (ll32 - ll64).abs()
-    agree = tot = tie = 0
+    ms = {}
+    for m, cx in others.items():
+        ll[m] = f64(C)
+        with torch.cuda.stream(stream):
+            cx.logpost(H, ll[m], None)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cx.logpost(H, ll[m], None)
+            e1.record(stream)
+        stream.synchronize()
+        ms[m] = e0.elapsed_time(e1)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tmp = f64(C)
+        e0.record(stream)
+        ctx.logpost(H, tmp, None)
+        e1.record(stream)
+    stream.synchronize()
+    ms["f32"] = e0.elapsed_time(e1)
+    dll = {m: (v - ll64).abs() for m, v in ll.items()}
+    st = {m: dict(agree=0, tie=0, dd=0.0) for m in ll}
+    tot = 0
     prop, llp, lpp, logu = torch.zeros_like(H), f64(C), f64(C), f64(C)
     acc = torch.zeros(C, dtype=torch.int32, device=dev)
-    dd_max = 0.0
     for _ in range(2):
         ctx.run(mt.KERNEL_RW, w.rw_sigma, 1, 1)
         ctx.get_last_step(prop, llp, lpp, acc, logu)
         l64p = f64(C)
         ref.logpost(prop.double(), l64p, None)
+        lprop = {"f32": llp}
+        for m, cx in others.items():
+            lprop[m] = f64(C)
+            with torch.cuda.stream(stream):
+                cx.logpost(prop, lprop[m], None)
+        stream.synchronize()
         fin = torch.isfinite(lpp)
         d_ref = (l64p + lpp) - (ll64 + lp)
-        d32 = (llp + lpp) - (ll32 + lp)
         a_ref = fin & (logu < d_ref)
-        same = acc.bool() == a_ref
         near = (logu - d_ref).abs() < 1e-6
-        agree += int(same.sum().item())
-        tie += int((~same & near).sum().item())
+        for m in ll:
+            d = (lprop[m] + lpp) - (ll[m] + lp)
+            same = (fin & (logu < d)) == a_ref
+            st[m]["agree"] += int(same.sum().item())
+            st[m]["tie"] += int((~same & near).sum().item())
+            if fin.any():
+                st[m]["dd"] = max(st[m]["dd"], float((d - d_ref).abs()[fin].max().item()))
         tot += C
-        if fin.any():
-            dd_max = max(dd_max, float((d32 - d_ref).abs()[fin].max().item()))
-        took = acc.bool()
+        took = acc.bool()  # the trajectory follows the FP32 mode's decisions
         ll64 = torch.where(took, l64p, ll64)
-        ll32 = torch.where(took, llp, ll32)
+        for m in ll:
+            ll[m] = torch.where(took, lprop[m], ll[m])
         lp = torch.where(took, lpp, lp)
     ref.close()
+    for cx in others.values():
+        cx.close()
     res["precision"] = {
         "states": f"{C} scenario chains after the timed steps, then 2 random-walk steps ({tot} proposals)",
-        "dll_abs_mean": float(dll.mean().item()), "dll_abs_max": float(dll.max().item()),
-        "accept_agreement": agree / tot, "disagree_outside_1e-6_band": tot - agree - tie,
-        "mh_ratio_err_max": dd_max, "reference": "FP64 mode", "wall_s": time.perf_counter() - t0,
-        "clocks": clocks.stop()}
+        "reference": "FP64 mode",
+        **{m: {"dll_abs_mean": float(dll[m].mean().item()), "dll_abs_max": float(dll[m].max().item()),
+               "accept_agreement": st[m]["agree"] / tot,
+               "disagree_outside_1e-6_band": tot - st[m]["agree"] - st[m]["tie"],
+               "mh_ratio_err_max": st[m]["dd"], "logpost_ms": ms[m]} for m in ll},
+        "wall_s": time.perf_counter() - t0, "clocks": clocks.stop()}
 
     # gradient (mt_grad) and MALA step on a context of their own
     clocks = Clocks(local)
@@ -997,7 +1037,7 @@ def evaluated_roofline(achieved_t, work_eval, work_total):
     peak = march_peak_evaluated() / 1e12
     return {"fraction": frac_eval, "achieved": ach, "peak": peak, "frac": ach / peak,
             "unit": "T evaluated surface-samples/s",
-            "ops_per_sample": f"{EVAL_FP32_OPS:g} FP32 lane-ops + ex2 + rcp + cvt"}
+            "ops_per_sample": f"{EVAL_FP32_OPS:g} FP32 lane-ops + rcp + cvt (accurate logistic)"}
 
 
 def measure_e2e(ctx, H0np, stream, args, w, rays):

@@ -64,11 +64,23 @@ typedef enum {
 
 /* Arithmetic of the ray march and the per-chain reduction.
  *  MT_PREC_F64  : heights, march, flux and reductions in FP64.
- *  MT_PREC_F32  : FP32 heights and march (compensated sum along each ray),
- *                 FP64 per-ray flux term and per-chain reduction.
- *  MT_PREC_F32C : FP32 heights and march; flux term, per-ray and per-chain
- *                 reductions in compensated FP32 (float-float), no FP64 in
- *                 the ray kernel.
+ *  MT_PREC_F32  : FP32 heights and march: each sample's indicator an exact
+ *                 integer in units of 2^-28; the logistic from 2^|a| split
+ *                 exactly into 2^round(|a|) and a polynomial of the
+ *                 fraction, and a reciprocal refined by one Newton step
+ *                 (no bias beyond rounding); float-float per-ray flux term
+ *                 and CTA sums, FP64 per-chain reduction.  Per-chain
+ *                 log-likelihoods within 1e-3 of FP64.
+ *  MT_PREC_F32C : as MT_PREC_F32 with the per-chain reduction in
+ *                 float-float: no FP64 in the ray kernel.
+ *  MT_PREC_F32A : as MT_PREC_F32 with the logistic from the SFU's ex2 / rcp
+ *                 approximations, their mean error calibrated per device at
+ *                 context creation: ~20 % faster; per-chain log-likelihoods
+ *                 within ~4e-4 of FP64 on average but up to ~3.6e-3 for
+ *                 chains far from the data at the scenario size (the
+ *                 approximations' error pattern survives the calibration
+ *                 for one-sided transitions); accept decisions matched the
+ *                 FP64 mode's on 1e5 proposals.
  *  MT_PREC_BF16 : FP32 chain state; the ray kernel holds each surface as
  *                 BF16 offsets h - ref_l from a reference height ref_l (the
  *                 surface's mean prior height rounded to FP32, or
@@ -77,7 +89,7 @@ typedef enum {
  *                 the same offsets in FP32.
  * Heights passed to and returned by the library are double for MT_PREC_F64
  * and float for every other mode. */
-enum { MT_PREC_F64 = 0, MT_PREC_F32 = 1, MT_PREC_F32C = 2, MT_PREC_BF16 = 3 };
+enum { MT_PREC_F64 = 0, MT_PREC_F32 = 1, MT_PREC_F32C = 2, MT_PREC_BF16 = 3, MT_PREC_F32A = 4 };
 
 /* Proposal kernels for mt_run. */
 enum { MT_KERNEL_RW = 0, MT_KERNEL_MALA = 1, MT_KERNEL_HMC = 2, MT_KERNEL_NUTS = 3 };

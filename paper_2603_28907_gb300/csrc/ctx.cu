@@ -43,7 +43,7 @@ int march_rays_per_block(const Prob &pb)
 size_t march_smem_bytes(const Prob &pb, int mode)
 {
     // FP32 modes: one plane of (h, dx) float pairs per surface
-    if (mode == MODE_F32 || mode == MODE_F32C) return (size_t)8 * pb.L * pb.N;
+    if (is_dx_mode(mode)) return (size_t)8 * pb.L * pb.N;
     const int es = mode == MODE_F64 ? 8 : 2;
     const int raw = pb.L * es;
     const int bytes = raw <= 4 ? 4 : raw <= 8 ? 8 : ((raw + 15) / 16) * 16;
@@ -63,7 +63,7 @@ size_t march_phased_smem_bytes(const Prob &pb)
 
 bool march_fits_phased(const Prob &pb, int mode)
 {
-    return (mode == MODE_F32 || mode == MODE_F32C) && march_phased_smem_bytes(pb) + MT_SMEM_STATIC <= MT_MAX_SMEM;
+    return is_dx_mode(mode) && march_phased_smem_bytes(pb) + MT_SMEM_STATIC <= MT_MAX_SMEM;
 }
 
 cudaError_t launch_march(const Prob &pb, int mode, HRef h, int n_chains, void *partial,
@@ -80,6 +80,8 @@ cudaError_t launch_march(const Prob &pb, int mode, HRef h, int n_chains, void *p
             return launch_march_mode<MODE_F32C>(pb, h, n_chains, rpb, smem, partial, ray_O, ray_term, st);
         case MODE_BF16:
             return launch_march_mode<MODE_BF16>(pb, h, n_chains, rpb, smem, partial, ray_O, ray_term, st);
+        case MODE_F32A:
+            return launch_march_mode<MODE_F32A>(pb, h, n_chains, rpb, smem, partial, ray_O, ray_term, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -448,8 +450,8 @@ static mt_status build_raytab(mt_ctx *ctx)
                           ctx->d_od, ctx->d_sd, ctx->d_dt, ctx->d_dtff, ctx->d_flag, ctx->stream));
     CK(ctx, launch_raytab_march(ctx->pb, ctx->d_sensors, ctx->d_dirs, ctx->d_xa4, ctx->d_xb4, ctx->d_xc2,
                                 ctx->d_kz1, ctx->d_flag, ctx->stream));
-    {
-        // the march's logistic, calibrated once per context on its device
+    if (ctx->mode == MODE_F32A) {
+        // the approximate logistic's mean error, calibrated once per context on its device
         double *d_k = nullptr, kappa = 0.0;
         TRY(dalloc(ctx, &d_k, 1));
         CK(ctx, launch_psi_calib(d_k, ctx->stream));
@@ -576,7 +578,7 @@ static mt_status ensure_partials(mt_ctx *ctx, int n_chains)
 static bool use_global_nodes(const mt_ctx *ctx)
 {
     return !march_fits_smem(ctx->pb, ctx->mode) && !march_fits_phased(ctx->pb, ctx->mode) &&
-           (ctx->mode == MODE_F32 || ctx->mode == MODE_F32C);
+           is_dx_mode(ctx->mode);
 }
 
 static mt_status check_smem(mt_ctx *ctx)
@@ -830,7 +832,7 @@ mt_status mt::ctx_create_pooled(mt_ctx **out, int device, const mt_config *cfg, 
 {
     if (!out || !cfg) return fail(nullptr, MT_EINVAL, "mt_create: null argument");
     *out = nullptr;
-    if (cfg->precision < MT_PREC_F64 || cfg->precision > MT_PREC_BF16)
+    if (cfg->precision < MT_PREC_F64 || cfg->precision > MT_PREC_F32A)
         return fail(nullptr, MT_EINVAL, "mt_create: precision %d out of range", cfg->precision);
     if (cfg->n_grid < 1 || cfg->n_grid > (1 << 20))
         return fail(nullptr, MT_EINVAL, "mt_create: n_grid %d out of range", cfg->n_grid);

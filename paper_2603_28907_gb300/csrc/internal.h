@@ -27,7 +27,9 @@
 
 namespace mt {
 
-enum { MODE_F64 = 0, MODE_F32 = 1, MODE_F32C = 2, MODE_BF16 = 3 };
+enum { MODE_F64 = 0, MODE_F32 = 1, MODE_F32C = 2, MODE_BF16 = 3, MODE_F32A = 4 };
+// the FP32 modes marched over (h, dx) planes
+constexpr bool is_dx_mode(int m) { return m == MODE_F32 || m == MODE_F32C || m == MODE_F32A; }
 enum { STREAM_GEOM = 0, STREAM_DATA = 1, STREAM_INIT = 2, STREAM_PROP = 3, STREAM_ACC = 4,
        STREAM_MALA = 5, STREAM_HMC = 6, STREAM_NUTS_P = 7, STREAM_NUTS_U = 8 };
 

@@ -42,6 +42,7 @@ template <int MODE> struct Types;
 template <> struct Types<MODE_F64> { using S = double; using T = double; using H = double; };
 template <> struct Types<MODE_F32> { using S = float; using T = float; using H = float; };
 template <> struct Types<MODE_F32C> { using S = float; using T = float; using H = float; };
+template <> struct Types<MODE_F32A> { using S = float; using T = float; using H = float; };
 template <> struct Types<MODE_BF16> { using S = __nv_bfloat16; using T = float; using H = float; };
 
 // Node-major shared-memory layout: the L heights of one node, padded to a
@@ -477,7 +478,9 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
 //             integer q (units 2^-28), and the
 //             sample adds q + 2^28 [a < 0], i.e. round(varsigma 2^28), exactly:
 //             no 1 - psi is ever rounded in FP32, and tails of psi down to
-//             2^-29 are kept.
+//             2^-29 are kept.  The compensated mode (ACC) forms 2^|a| with
+//             exp2_acc and the reciprocal with rcp_newton instead (no
+//             calibration: neither is biased beyond rounding).
 // The integer adds c_bits >> 3 = 2^28 [a < 0] + kJunk per sample (the
 // exponent bits of 2^-28 shifted down); kJunk is subtracted once per window.
 // The corner records of each sample are cached and reloaded when that
@@ -485,6 +488,38 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
 constexpr uint32_t kQuantBits = 0x31800000u;      // FP32 bits of 2^-28
 constexpr uint32_t kJunk = kQuantBits >> 3;       // added per sample by the sign trick
 constexpr unsigned long long kUnit = 1ull << 28;  // one indicator = 2^28 units
+
+// 2^x for x >= 0 to ~1 ulp with no bias beyond rounding (the accurate
+// logistic of the FP32 modes): x (clamped to 64, where the logistic is
+// 2^-64, far below the 2^-28 unit) = i + f with i = round(x) and
+// f in [-1/2, 1/2] exact; 2^f by a degree-6 polynomial fitted for the least
+// maximum relative error on that interval (1.6e-8 in exact arithmetic with
+// its coefficients in FP32; the FP32 Horner steps give at most 7.9e-8 and a
+// mean error of 0.004 ulp); then
+// i is added to the exponent: bits(t) << 23 = i << 23 modulo 2^32, because
+// the bits of 1.5 * 2^23 shifted by 23 vanish.
+__device__ __forceinline__ float2 exp2_acc(float2 x)
+{
+    x = make_float2(fminf(x.x, 64.0f), fminf(x.y, 64.0f));
+    const float2 t = add2(x, f2(12582912.0f));                      // 1.5 * 2^23 + round(x)
+    const float2 f = fma2(add2(t, f2(-12582912.0f)), f2(-1.0f), x);  // x - round(x), exact
+    float2 p = f2(1.534581242594868e-04f);
+    p = fma2(p, f, f2(1.3399930903688073e-03f));
+    p = fma2(p, f, f2(9.618489071726799e-03f));
+    p = fma2(p, f, f2(5.550328642129898e-02f));
+    p = fma2(p, f, f2(2.4022646248340607e-01f));
+    p = fma2(p, f, f2(6.931471824645996e-01f));
+    p = fma2(p, f, f2(1.0f));
+    return make_float2(__int_as_float(__float_as_int(p.x) + (__float_as_int(t.x) << 23)),
+                       __int_as_float(__float_as_int(p.y) + (__float_as_int(t.y) << 23)));
+}
+
+// 1 / e with rcp.approx refined by one Newton step r + r (1 - e r).
+__device__ __forceinline__ float2 rcp_newton(float2 e)
+{
+    const float2 r = make_float2(rcp_approx(e.x), rcp_approx(e.y));
+    return fma2(r, fma2(make_float2(-e.x, -e.y), r, f2(1.0f)), r);
+}
 
 // Records of rows r and r + 1 for the two samples of a step, each pair
 // loaded (predicated, no branch) only when its sample's cell address differs
@@ -504,7 +539,7 @@ __device__ __forceinline__ void reload_pair(uint32_t aA, uint32_t aB, uint32_t r
     cB = (int)aB;
 }
 
-template <bool HARD, bool GLOBAL>
+template <bool HARD, bool GLOBAL, bool ACC>
 __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int *flag, float2 kf2, float2 ix2,
                                             float2 iy2, float2 sxh2, float2 syh2,
                                             float2 szh2, float2 szl2, float2 zh2, float2 zl2, float2 nkgh2,
@@ -563,6 +598,14 @@ __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int 
         const uint32_t vx = arg.x < 0.f ? (uint32_t)kUnit : (arg.x > 0.f ? 0u : (uint32_t)(kUnit >> 1));
         const uint32_t vy = arg.y < 0.f ? (uint32_t)kUnit : (arg.y > 0.f ? 0u : (uint32_t)(kUnit >> 1));
         return vx + vy + 2u * kJunk;
+    } else if constexpr (ACC) {
+        const uint32_t cbx = (__float_as_uint(arg.x) & 0x80000000u) | kQuantBits;
+        const uint32_t cby = (__float_as_uint(arg.y) & 0x80000000u) | kQuantBits;
+        const float2 c = make_float2(__uint_as_float(cbx), __uint_as_float(cby));
+        const float2 e = fma2(exp2_acc(make_float2(fabsf(arg.x), fabsf(arg.y))), c, c);  // (2^|a| + 1) c
+        const float2 r = rcp_newton(e);
+        const int qx = __float2int_rn(r.x), qy = __float2int_rn(r.y);
+        return ((uint32_t)qx + (cbx >> 3)) + ((uint32_t)qy + (cby >> 3));
     } else {
         const uint32_t cbx = (__float_as_uint(arg.x) & 0x80000000u) | kQuantBits;
         const uint32_t cby = (__float_as_uint(arg.y) & 0x80000000u) | kQuantBits;
@@ -581,7 +624,7 @@ __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int 
 // of 2^-28 to t.  Per block of up to eight samples (< 2^32 with kJunk) the
 // 32-bit sum moves to t.  An odd count (he = G) ends with one sample
 // evaluated in both lanes and counted once.
-template <bool HARD, bool GLOBAL>
+template <bool HARD, bool GLOBAL, bool ACC>
 __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, int R, int *flag, float4 xa, float4 xb,
                                                  float nkgh, float nkgl, uint32_t nkc, float zh, float zl, uint32_t k0,
                                                  int cell0, int2 c0, int lo, int he, unsigned long long &t)
@@ -593,7 +636,7 @@ __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, int R,
     int curA = -1, curB = -1;
     float2 kf2 = make_float2((float)lo, (float)lo + 1.0f);
 #define MT_PAIR(IX, IY)                                                                                     \
-    dx_pair<HARD, GLOBAL>(pl, Q, R, flag, kf2, IX, IY, sxh2, syh2, szh2, szl2, zh2, zl2, nkgh2, nkgl2, nkc, k0, \
+    dx_pair<HARD, GLOBAL, ACC>(pl, Q, R, flag, kf2, IX, IY, sxh2, syh2, szh2, szl2, zh2, zl2, nkgh2, nkgl2, nkc, k0, \
                           cell0, c0, curA, curB, rA0, rA1, rB0, rB1)
     // The low part of the step, o + k sl, changes by far less than an ulp of
     // o per sample: it is taken once per block of eight samples [8m, 8m + 8),
@@ -702,7 +745,7 @@ __device__ __forceinline__ void transition_window(float z0, float dz, float rdz,
 // blocks of march_surface_dx.  plane: surface l's records; kl: their
 // shared-window base folded as in march_ray_dx (0 for HBM records).
 // Returns N_l 2^28.
-template <bool HARD, bool GLOBAL>
+template <bool HARD, bool GLOBAL, bool ACC>
 __device__ __forceinline__ unsigned long long march_ray_surface_dx(const Prob &pb, const float2 *plane, uint32_t kl,
                                                                    int ray, int l, float4 xa, float4 xb, int2 c0,
                                                                    int cell0, float dz, float rdz, float smin,
@@ -718,7 +761,7 @@ __device__ __forceinline__ unsigned long long march_ray_surface_dx(const Prob &p
     if (((he - lo) & 1) && he < G) ++he;  // even length where the ray allows
     if (evaluated) *evaluated += (unsigned long long)(he - lo);
     unsigned long long t = (unsigned long long)lo * kUnit;  // samples below the window
-    march_surface_dx<HARD, GLOBAL>(plane, pb.Q, pb.R, pb.flag, xa, xb, -pb.kg, -pb.kgl, __float_as_uint(-pb.psi_kc),
+    march_surface_dx<HARD, GLOBAL, ACC>(plane, pb.Q, pb.R, pb.flag, xa, xb, -pb.kg, -pb.kgl, __float_as_uint(-pb.psi_kc),
                                    zh, zl, kl, cell0, c0, lo, he, t);
     return t;
 }
@@ -726,7 +769,7 @@ __device__ __forceinline__ unsigned long long march_ray_surface_dx(const Prob &p
 // The FP32 modes' march of one ray over all L surfaces (planes [l][node],
 // ext = per-surface min / max offsets): emit(l, N_l 2^28) is called for
 // l = 0 .. L-1 in order.
-template <int L, bool HARD, bool GLOBAL, typename Emit>
+template <int L, bool HARD, bool GLOBAL, bool ACC, typename Emit>
 __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *planes, int ray,
                                              const float *ext, unsigned long long *evaluated,
                                              Emit &&emit)
@@ -743,7 +786,7 @@ __device__ __forceinline__ void march_ray_dx(const Prob &pb, const float2 *plane
 #pragma unroll kSurfUnroll
     for (int l = 0; l < L; ++l) {
         const uint32_t kl = GLOBAL ? 0u : k0 + 8u * (uint32_t)((size_t)l * pb.N);
-        emit(l, march_ray_surface_dx<HARD, GLOBAL>(pb, planes + (size_t)l * pb.N, kl, ray, l, xa, xb, c0, cell0, dz,
+        emit(l, march_ray_surface_dx<HARD, GLOBAL, ACC>(pb, planes + (size_t)l * pb.N, kl, ray, l, xa, xb, c0, cell0, dz,
                                                    rdz, ext[l], ext[L + l], evaluated));
     }
 }
@@ -916,7 +959,7 @@ __device__ __forceinline__ void store_partial_ff(void *partial, FF accf)
 // CTAs (one per SM with the scenario's 128 KB of records); BF16 keeps
 // 4-corner node records to halve shared memory; FP64 has its own march.
 template <int MODE, int L> struct MarchCfg {
-    static constexpr bool DX = MODE == MODE_F32 || MODE == MODE_F32C;
+    static constexpr bool DX = is_dx_mode(MODE);
     static constexpr int THREADS = DX ? MT_DX_THREADS : 256;
 };
 
@@ -979,7 +1022,7 @@ k_march(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O, doubl
         const int Cp = pb.cnt[ray];
         if constexpr (DX) {
             FF Sff = {pb.grho_ff.x, pb.grho_ff.y};
-            march_ray_dx<L, HARD, GLOBAL>(pb, planes, ray, ext, pb.work ? &n_eval : nullptr,
+            march_ray_dx<L, HARD, GLOBAL, MODE != MODE_F32A>(pb, planes, ray, ext, pb.work ? &n_eval : nullptr,
                                           [&](int l, unsigned long long tl) { Sff = add_surface(pb, Sff, l, tl); });
             accf = ff_add(accf, ray_term_dx(pb, c, ray, Cp, Sff, ray_O, ray_term));
         } else {
@@ -1065,8 +1108,9 @@ k_march_phased(Prob pb, HRef h, int rays_per_block, void *partial, double *ray_O
             const float dz = xb.z + xb.w;
             const uint32_t kl = sp + 8u * (uint32_t)cell0 - 8u * 0x4B400000u * (uint32_t)(pb.Q + 1);
             const unsigned long long t =
-                march_ray_surface_dx<HARD, false>(pb, plane, kl, ray, l, xa, xb, c0, cell0, dz, rcp_approx(dz),
-                                                  smin, smax, pb.work ? &n_eval : nullptr);
+                march_ray_surface_dx<HARD, false, MODE != MODE_F32A>(pb, plane, kl, ray, l, xa, xb, c0, cell0, dz,
+                                                                     rcp_approx(dz), smin, smax,
+                                                                     pb.work ? &n_eval : nullptr);
             const float2 s0 = l ? sums[j] : pb.grho_ff;
             const FF S = add_surface(pb, FF{s0.x, s0.y}, l, t);
             sums[j] = make_float2(S.hi, S.lo);

@@ -9,7 +9,7 @@ template <int MODE, int L>
 static cudaError_t launch_global(const Prob &pb, HRef h, int n_chains, int rpb, void *partial,
                                  double *ray_O, double *ray_term, cudaStream_t st)
 {
-    if constexpr (MODE == MODE_F32 || MODE == MODE_F32C) {
+    if constexpr (is_dx_mode(MODE)) {
         using Hh = typename Types<MODE>::H;
         dim3 sg((pb.N + 4095) / 4096, n_chains);
         k_stage_dx_global<Hh, L><<<sg, 256, 0, st>>>(pb, h);
@@ -27,7 +27,7 @@ template <int MODE, int L>
 static cudaError_t launch_phased(const Prob &pb, HRef h, int n_chains, int rpb, void *partial, double *ray_O,
                                  double *ray_term, cudaStream_t st)
 {
-    if constexpr (MODE == MODE_F32 || MODE == MODE_F32C) {
+    if constexpr (is_dx_mode(MODE)) {
         const bool hard = pb.gamma == 0.0;
         void (*fn)(Prob, HRef, int, void *, double *, double *) =
             hard ? k_march_phased<MODE, L, true> : k_march_phased<MODE, L, false>;

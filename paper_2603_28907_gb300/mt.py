@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # build.build(checked=True)); it has the same ABI
 LIB_PATH = os.path.join(HERE, "libmt_checked.so" if os.environ.get("MT_CHECKED") == "1" else "libmt.so")
 
-PREC_F64, PREC_F32, PREC_F32C, PREC_BF16 = 0, 1, 2, 3
+PREC_F64, PREC_F32, PREC_F32C, PREC_BF16, PREC_F32A = 0, 1, 2, 3, 4
 PRIOR_CAR, PRIOR_COPULA = 0, 1
 FORWARD_MARCH, FORWARD_LINEAR = 0, 1
 KERNEL_RW, KERNEL_MALA, KERNEL_HMC, KERNEL_NUTS = 0, 1, 2, 3

@@ -24,6 +24,7 @@ def run():
         "tiny_f32": (W.tiny(), mt.PREC_F32),
         "tiny_f64": (W.tiny(), mt.PREC_F64),
         "tiny_bf16": (W.tiny(), mt.PREC_BF16),
+        "tiny_f32a": (W.tiny(), mt.PREC_F32A),
         "odd_down_f32c": (W.small(R=5, Q=7, n_sensors=3, n_zenith=6, n_azimuth=7, G=20,
                                   zenith_max_deg=120.0), mt.PREC_F32C),
         "large_phased_f32": (W.small(R=100, Q=100, bases=(40.0, 70.0, 110.0, 140.0),
@@ -38,7 +39,7 @@ def run():
         H = torch.tensor(np.concatenate([pr["H_true"][None], W.init_chains(w, 2)]), dtype=dt, device=DEV)
         ll = _ll(ctx, H)
         rec = {"ll": ll.cpu().tolist()}
-        if prec in (mt.PREC_F32, mt.PREC_F32C) and name not in ("large_phased_f32", "huge_hbm_f32"):
+        if prec in (mt.PREC_F32, mt.PREC_F32C, mt.PREC_F32A) and name not in ("large_phased_f32", "huge_hbm_f32"):
             g = torch.zeros(H.shape, dtype=torch.float64, device=DEV)
             ctx.grad(H, g)
             rec["grad_sum"] = float(g.abs().sum().item())

@@ -107,34 +107,47 @@ def test_long_run_counters():
         assert abs(lp[c].item() - op.logprior(Hn[c])) <= 1e-9 * abs(lp[c].item())
 
 
-def _scenario_sampled():
-    """1024 scenario chains through mt_logpost (the bench's kernel and launch
-    configuration); 16 of them against the oracle: independent starts far
-    from the data (where sum_p |d ll / d O_p| ~ 1e5 turns any systematic
-    opacity error into a per-chain one) and states near the data-generating
-    geometry."""
+_SCENARIO_REF = {}
+
+
+def _scenario_states():
+    """1024 scenario states and the oracle's log-likelihood of 16 of them:
+    independent starts far from the data (where sum_p |d ll / d O_p| ~ 1e5
+    turns any systematic opacity error into a per-chain one) and states near
+    the data-generating geometry (computed once per session)."""
+    if not _SCENARIO_REF:
+        w = W.scenario()
+        pr = W.problem(w)
+        Hs = np.stack([W.geometry(w, [w.seed_init, c]) for c in range(1024)])
+        for c in range(1000, 1024):  # states near the truth
+            Hs[c] = W.perturbed(pr["H_true"], 0.05, [9, c])
+        Hs = Hs.astype(np.float32)
+        pick = [0, 1, 2, 3, 64, 200, 333, 511, 640, 777, 900, 999, 1000, 1007, 1015, 1023]
+        _SCENARIO_REF.update(w=w, Hs=Hs, pick=pick)
+    return _SCENARIO_REF
+
+
+def _scenario_sampled(precision=mt.PREC_F32):
+    """The 1024 states through mt_logpost (the bench's kernel and launch
+    configuration) in one precision mode; |dll| of the 16 picked chains
+    against the oracle."""
     import os
-    w = W.scenario()
-    pr, ctx, op, counts, _ = setup(w, precision=mt.PREC_F32)
-    Hs = np.stack([W.geometry(w, [w.seed_init, c]) for c in range(1024)])
-    for c in range(1000, 1024):  # states near the truth
-        Hs[c] = W.perturbed(pr["H_true"], 0.05, [9, c])
-    Hs = Hs.astype(np.float32)
-    H = heights(Hs, mt.PREC_F32)
+    ref = _scenario_states()
+    w, Hs, pick = ref["w"], ref["Hs"], ref["pick"]
+    pr, ctx, op, counts, _ = setup(w, precision=precision)
+    if "ll" not in ref:
+        ref["ll"] = op.loglik_batch(Hs[pick].astype(np.float64), n_threads=os.cpu_count() or 1)
+    H = heights(Hs, precision)
     ll, lp = logpost(ctx, H)
-    pick = [0, 1, 2, 3, 64, 200, 333, 511, 640, 777, 900, 999, 1000, 1007, 1015, 1023]
-    ref = op.loglik_batch(Hs[pick].astype(np.float64), n_threads=os.cpu_count() or 1)
-    return w, pr, ctx, op, Hs, H, ll, lp, pick, np.abs(ll[pick] - ref)
+    return w, pr, ctx, op, Hs, H, ll, lp, pick, np.abs(ll[pick] - ref["ll"])
 
 
 @pytest.mark.slow
 def test_scenario_full_size_sampled_chains():
-    """Full-size FP32 mode against the oracle, at the bound it achieves: per
-    chain |dll| <= 3e-3 and <= 5e-4 on average over the sampled chains
-    (the precision study over 1e5 proposals measured mean 4.0e-4, max
-    3.5e-3); per-ray opacity within 1e-5 mwe on two chains."""
+    """Full-size FP32 mode against the oracle: per-ray opacity within 1e-5 mwe
+    on two chains and the log-prior within 1e-9 relative (the per-chain bar is
+    test_scenario_fp32_bar_every_chain)."""
     w, pr, ctx, op, Hs, H, ll, lp, pick, err = _scenario_sampled()
-    assert err.max() <= 3e-3 and err.mean() <= 5e-4, dict(zip(pick, err))
     for c in (0, 777):
         Hc = Hs[c].astype(np.float64)
         Or = op.opacities(Hc).ravel()
@@ -145,12 +158,29 @@ def test_scenario_full_size_sampled_chains():
 
 
 @pytest.mark.slow
-@pytest.mark.xfail(strict=False, reason="FP32 logistic: ex2.approx's mean error (~0.6 ulp) survives the "
-                   "calibration at some arguments, and rays leaving through the box top see one-sided "
-                   "transitions at identical sampling phases; a few far-off chains reach ~1e-3 to 3.5e-3")
-def test_scenario_fp32_bar_every_chain():
-    """The stated FP32 bar, |dll| <= 1e-3 for every sampled scenario chain."""
-    *_, pick, err = _scenario_sampled()
+def test_scenario_f32a_sampled_chains():
+    """The approximate-logistic mode at full size, at the bound it achieves:
+    per chain |dll| <= 4e-3 and <= 5e-4 on average over the sampled chains
+    (the precision study over 1e5 proposals measured mean 4.0e-4, max
+    3.6e-3, and no accept decision differing from the FP64 mode's)."""
+    *_, pick, err = _scenario_sampled(mt.PREC_F32A)
+    assert err.max() <= 4e-3 and err.mean() <= 5e-4, dict(zip(pick, err))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [
+    mt.PREC_F32, mt.PREC_F32C,
+    pytest.param(mt.PREC_F32A, marks=pytest.mark.xfail(
+        strict=False, reason="approximate logistic (ex2.approx / rcp.approx with a calibrated mean "
+        "error): the approximations' error pattern survives the calibration at some arguments, and "
+        "rays leaving through the box top see one-sided transitions at identical sampling phases; a "
+        "few far-off chains reach ~1e-3 to 3.6e-3"))], ids=["f32", "f32c", "f32a"])
+def test_scenario_fp32_bar_every_chain(precision):
+    """The stated FP32 bar, |dll| <= 1e-3 for every sampled scenario chain
+    (far-off starts and states near the truth): met by the FP32 and
+    compensated modes (accurate logistic), missed by a few far-off chains in
+    the approximate-logistic mode."""
+    *_, pick, err = _scenario_sampled(precision)
     assert err.max() <= 1e-3, dict(zip(pick, err))
 
 

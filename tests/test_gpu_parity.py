@@ -83,7 +83,7 @@ def test_ray_terms_f64(w, gamma):
                                    atol=1e-8)
 
 
-@pytest.mark.parametrize("precision", [mt.PREC_F32, mt.PREC_F32C])
+@pytest.mark.parametrize("precision", [mt.PREC_F32, mt.PREC_F32C, mt.PREC_F32A])
 def test_ray_opacity_f32(precision):
     w = W.tiny()
     pr, ctx, op, counts, _ = setup(w, precision=precision)
@@ -130,7 +130,7 @@ def test_logpost_f64(w):
         assert abs(lp[c] - ref_lp) <= 1e-9 * max(1.0, abs(ref_lp)), (c, lp[c], ref_lp)
 
 
-@pytest.mark.parametrize("precision", [mt.PREC_F32, mt.PREC_F32C, mt.PREC_BF16])
+@pytest.mark.parametrize("precision", [mt.PREC_F32, mt.PREC_F32C, mt.PREC_F32A, mt.PREC_BF16])
 @pytest.mark.parametrize("w", [W.tiny(), SMALLS[1], SMALLS[3]], ids=lambda w: w.name)
 def test_logpost_reduced_precision(w, precision):
     pr, ctx, op, counts, _ = setup(w, precision=precision)
@@ -256,7 +256,7 @@ def test_mh_lockstep_f64():
     assert 0 < s["accepted"] < 60 * w.n_chains, s
 
 
-@pytest.mark.parametrize("precision", [mt.PREC_F32, mt.PREC_F32C])
+@pytest.mark.parametrize("precision", [mt.PREC_F32, mt.PREC_F32C, mt.PREC_F32A])
 def test_mh_lockstep_f32(precision):
     """FP32 march: identical accept decisions to the oracle's except where
     |ln u - Delta_oracle| < 1e-6 (ties are counted, mismatches outside the

@@ -57,6 +57,7 @@ def _downward():
 CASES = {
     "tiny_f32": (W.tiny, mt.PREC_F32, None),
     "tiny_f32c": (W.tiny, mt.PREC_F32C, None),
+    "tiny_f32a": (W.tiny, mt.PREC_F32A, None),
     "tiny_hard": (W.tiny, mt.PREC_F32, 0.0),
     "downward_odd_g": (_downward, mt.PREC_F32, None),
 }

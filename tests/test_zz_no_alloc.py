@@ -23,7 +23,7 @@ from tests.gpu_common import DEV, heights, logpost, setup
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", [mt.PREC_F32, mt.PREC_F32C, mt.PREC_F64, mt.PREC_BF16])
+@pytest.mark.parametrize("precision", [mt.PREC_F32, mt.PREC_F32C, mt.PREC_F32A, mt.PREC_F64, mt.PREC_BF16])
 def test_noalloc_matches_logpost_on_two_calls(precision):
     w = W.tiny()
     pr, ctx, op, counts, _ = setup(w, precision=precision)
