@@ -283,9 +283,9 @@ __device__ __forceinline__ void scatter_ray_dx(const Prob &pb, int ray, int l, f
 
     auto step = [&](float2 kf, float cB) {
         const float2 gx = fma2(kf, sxh2, fma2(kf, sxl2, ox2)), gy = fma2(kf, syh2, fma2(kf, syl2, oy2));
-        const float2 tx = add2(gx, M2), ty = add2(gy, M2);
+        const float2 tx = add2(gx, M2), ty = __fadd2_rd(gy, M2);  // x rounded to nearest, y down
         const float2 fx = fma2(add2(tx, f2(-12582912.0f)), f2(-1.0f), gx);
-        const float2 fy = add2(fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy), f2(0.5f));
+        const float2 fy = fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy);
         uint32_t aA0 = (uint32_t)__float_as_int(ty.x) * rowb + ((uint32_t)__float_as_int(tx.x) * 8u + k0);
         uint32_t aB0 = (uint32_t)__float_as_int(ty.y) * rowb + ((uint32_t)__float_as_int(tx.y) * 8u + k0);
 #ifdef MT_BOUNDS_CHECK

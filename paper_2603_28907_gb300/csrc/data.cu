@@ -108,17 +108,22 @@ cudaError_t launch_raytab(const Prob &pb, const double *d_sensors, const double 
 // where rounding at a face of the box would leave that range, o and sh move
 // inward by a few ulps (this does not happen for rays that start inside the
 // box away from a face).
-__device__ __forceinline__ int rel_cell(float o, float sl, float sh, float kf)
+// Cell of sample kf as the march computes it: the coordinate rounded to the
+// nearest integer (x: coordinates relative to the cell's centre) or down
+// (FLOOR, y: relative to the cell's lower edge), from the bits of
+// g + 1.5 * 2^23.
+__device__ __forceinline__ int rel_cell(float o, float sl, float sh, float kf, bool floor_axis)
 {
     const float g = fmaf(kf, sh, fmaf(kf, sl, o));
-    return __float_as_int(g + 12582912.0f) - 0x4B400000;
+    const float t = floor_axis ? __fadd_rd(g, 12582912.0f) : g + 12582912.0f;
+    return __float_as_int(t) - 0x4B400000;
 }
 
-__device__ bool fit_axis_rel(float &o, float &sh, float sl, int c0, int n, int G)
+__device__ bool fit_axis_rel(float &o, float &sh, float sl, int c0, int n, int G, bool floor_axis)
 {
     const float kl = (float)(G - 1);
     for (int it = 0; it < 64; ++it) {
-        const int a = c0 + rel_cell(o, sl, sh, 0.0f), b = c0 + rel_cell(o, sl, sh, kl);
+        const int a = c0 + rel_cell(o, sl, sh, 0.0f, floor_axis), b = c0 + rel_cell(o, sl, sh, kl, floor_axis);
         const bool oka = a >= 0 && a <= n - 2, okb = b >= 0 && b <= n - 2;
         if (oka && okb) return true;
         if (!oka) o = nextafterf(o, a < 0 ? INFINITY : -INFINITY);
@@ -149,13 +154,14 @@ __global__ void k_raytab_march(Prob pb, const double *sensors, const double *dir
     const double dt = te / (double)pb.G;
     const double sx = (double)(pb.Q - 1) / pb.box[0], sy = (double)(pb.R - 1) / pb.box[1];
     const double gx0 = (o[0] + 0.5 * dt * d[0]) * sx - 0.5, gsx = dt * d[0] * sx;
-    const double gy0 = (o[1] + 0.5 * dt * d[1]) * sy - 0.5, gsy = dt * d[1] * sy;
+    const double gy0 = (o[1] + 0.5 * dt * d[1]) * sy, gsy = dt * d[1] * sy;  // y from the cell's lower edge
     const double z0 = o[2] + 0.5 * dt * d[2], sz = dt * d[2];
-    const int c0x = min(max((int)rint(gx0), 0), pb.Q - 2), c0y = min(max((int)rint(gy0), 0), pb.R - 2);
+    const int c0x = min(max((int)rint(gx0), 0), pb.Q - 2), c0y = min(max((int)floor(gy0), 0), pb.R - 2);
     float ox = (float)(gx0 - (double)c0x), oy = (float)(gy0 - (double)c0y);
     float sxh = (float)gsx, syh = (float)gsy;
     const float sxl = (float)(gsx - (double)sxh), syl = (float)(gsy - (double)syh);
-    const bool ok = fit_axis_rel(ox, sxh, sxl, c0x, pb.Q, pb.G) & fit_axis_rel(oy, syh, syl, c0y, pb.R, pb.G);
+    const bool ok = fit_axis_rel(ox, sxh, sxl, c0x, pb.Q, pb.G, false) &
+                    fit_axis_rel(oy, syh, syl, c0y, pb.R, pb.G, true);
     if (!ok) atomicOr(flag, 2);
     const double g = pb.zgrid;
     const double ksz = pb.kg64 * sz;

@@ -458,8 +458,10 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
 //   position  g = fmaf(k, sh, fmaf(k, sl, o)) per axis, relative to the ray's
 //             start cell (the step split hi + lo), so no per-ray FP32 offset
 //             enters and each sample's rounding is its own; the cell split
-//             rounds g by adding 1.5 * 2^23 and the fraction g - round(g) is
-//             exact.
+//             adds 1.5 * 2^23, rounding x to the nearest integer (x is taken
+//             from the cell's centre) and y down (y from the cell's lower
+//             edge; __fadd2_rd), and the fractions g - round(g) and
+//             g - floor(g) are exact.
 //   height    the x-lerps read the (h_mid, dx) records as loaded (scalar
 //             FMAs), then the y-lerp; the result sl = s_l - ref_l.
 //   argument  a = kg64 (z - s_l) in log2 units with z - ref_l = zhi + zlo,
@@ -550,9 +552,9 @@ __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int 
     const float2 M2 = f2(12582912.0f);  // 1.5 * 2^23: adding it rounds to an integer
     const float2 gx = fma2(kf2, sxh2, ix2);  // ix2 = o + k sl (see march_surface_dx)
     const float2 gy = fma2(kf2, syh2, iy2);
-    const float2 tx = add2(gx, M2), ty = add2(gy, M2);
+    const float2 tx = add2(gx, M2), ty = __fadd2_rd(gy, M2);  // x rounded to nearest, y down
     const float2 fx = fma2(add2(tx, f2(-12582912.0f)), f2(-1.0f), gx);  // in [-1/2, 1/2] about the midpoint
-    const float2 fy = add2(fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy), f2(0.5f));
+    const float2 fy = fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy);  // in [0, 1) from the lower row
 #ifdef MT_BOUNDS_CHECK
     const bool in_grid =
         cell_ok(c0.x + __float_as_int(tx.x) - 0x4B400000, c0.y + __float_as_int(ty.x) - 0x4B400000, Q - 1, R - 1) &&
