@@ -1,12 +1,12 @@
 """The FP32 ray kernel's exact-saturation windows change no bit of the result.
 
-Samples whose sigmoid argument lies at least 24.25 log2 units from zero have
-an FP32 indicator of exactly 0 or 1 (Sec. 2.1.1 opacity sum; Eq.
+Samples whose sigmoid argument lies at least 29.25 log2 units from zero add
+exactly 0 or 2^28 units of 2^-28 (Sec. 2.1.1 opacity sum; Eq.
 smooth_layer_indicators evaluated in FP32), so the kernel adds their integer
-contributions without evaluating them.  These tests run the same data through
-a context with the windows (the default) and one created with
-MT_FULL_WINDOWS=1 (every sample evaluated) and require bit-identical per-ray
-opacities, terms and log-likelihoods, and that the windows did skip work.
+contributions without evaluating them.  These tests run the same data through a context with the windows (the
+default) and one created with MT_FULL_WINDOWS=1 (every sample evaluated) and
+require bit-identical per-ray opacities, terms and log-likelihoods, and that
+the windows did skip work.
 """
 import os
 
@@ -54,12 +54,19 @@ def _downward():
                    n_chains=6)
 
 
+def _large():
+    # 100 x 100 nodes and 4 surfaces: one surface's plane at a time
+    return W.small(R=100, Q=100, bases=(40.0, 70.0, 110.0, 140.0), rho=(2.65, 1.9, 0.0012, 2.65, 0.0012),
+                   G=64, n_zenith=6, n_azimuth=9, n_sensors=2, n_chains=6)
+
+
 CASES = {
     "tiny_f32": (W.tiny, mt.PREC_F32, None),
     "tiny_f32c": (W.tiny, mt.PREC_F32C, None),
     "tiny_f32a": (W.tiny, mt.PREC_F32A, None),
     "tiny_hard": (W.tiny, mt.PREC_F32, 0.0),
     "downward_odd_g": (_downward, mt.PREC_F32, None),
+    "large_phased": (_large, mt.PREC_F32, None),
 }
 
 
