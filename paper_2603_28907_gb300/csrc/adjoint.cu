@@ -233,6 +233,46 @@ __device__ __forceinline__ void flush_dx(uint32_t a, uint32_t rowb, float U0, fl
     red_fixed(a + rowb + 8u, fmaf(0.5f, V0, V1));
 }
 
+// A pending cell's sums (record address x; pu = {U0, U1}, pw = {V0, V1})
+// leave the lane while the next cell along the ray (record address y, sums
+// uu, ww) is still accumulating.  After a step in x or y the two cells share
+// two nodes: those two corner sums are added to the next cell's sums (the
+// U/V form takes them as they are: a node on the shared column adds +-q/2 to
+// U1 or V1 and q to U0 or V0, a shared row moves whole), and only the other
+// two nodes are added to the accumulators; after a diagonal step all four.
+// This halves the accumulator atomics along a ray; every node's share still
+// reaches the accumulators exactly once.
+__device__ __forceinline__ void flush_carry(uint32_t to_acc, uint32_t rowb, int x, float2 pu, float2 pw, int y,
+                                            float2 &uu, float2 &ww)
+{
+    const float q00 = fmaf(0.5f, pu.x, -pu.y), q01 = fmaf(0.5f, pu.x, pu.y);
+    const float q10 = fmaf(0.5f, pw.x, -pw.y), q11 = fmaf(0.5f, pw.x, pw.y);
+    const int d = y - x;
+    const bool xp = d == 8, xm = d == -8, yp = d == (int)rowb, ym = d == -(int)rowb;
+    const uint32_t a = (uint32_t)x + to_acc;
+    // the two nodes the next cell does not share (the lower two after a step
+    // up, the upper two after a step down, the left column after a step
+    // right, the right one after a step left; the lower two otherwise)
+    const uint32_t a0 = xm ? a + 8u : (ym ? a + rowb : a);
+    const uint32_t a1 = (xp | xm) ? a0 + rowb : a0 + 8u;
+    const float v0 = xm ? q01 : (ym ? q10 : q00);
+    const float v1 = xp ? q10 : (xm ? q11 : (ym ? q11 : q01));
+    red_fixed(a0, v0);
+    red_fixed(a1, v1);
+    if (xp | xm) {  // the shared column: q carried to the next cell's other column
+        const float cu = xp ? q01 : q00, cw = xp ? q11 : q10, h = xp ? -0.5f : 0.5f;
+        uu = add2(uu, make_float2(cu, h * cu));
+        ww = add2(ww, make_float2(cw, h * cw));
+    } else if (yp) {  // the upper row becomes the next cell's lower row
+        uu = add2(uu, pw);
+    } else if (ym) {  // the lower row becomes the next cell's upper row
+        ww = add2(ww, pu);
+    } else {  // a diagonal step: the upper two nodes as well
+        red_fixed(a + rowb, q10);
+        red_fixed(a + rowb + 8u, q11);
+    }
+}
+
 // Surface l along one ray: samples within the window where a weight can
 // reach one unit, two per step in paired FP32 lanes (lane .x sample k,
 // lane .y sample k + 1; positions, records and the argument a = kg64 (z - s_l)
@@ -313,7 +353,7 @@ __device__ __forceinline__ void scatter_ray_dx(const Prob &pb, int ray, int l, f
         const bool chA = ia != cur, chB = ib != ia;
         if (__any_sync(__activemask(), (chA || chB) && pend >= 0)) {
             if (pend >= 0) {
-                flush_dx((uint32_t)pend + to_acc, rowb, pu.x, pu.y, pw.x, pw.y);
+                flush_carry(to_acc, rowb, pend, pu, pw, cur, uu, ww);
                 pend = -1;
             }
         }
@@ -329,7 +369,7 @@ __device__ __forceinline__ void scatter_ray_dx(const Prob &pb, int ray, int l, f
         uu = fma2(f2(vny.x), make_float2(1.0f, fx.x), uu);
         ww = fma2(f2(vy.x), make_float2(1.0f, fx.x), ww);
         if (chB) {  // B entered the next cell: a second move in this step if A moved too (rare)
-            if (pend >= 0) flush_dx((uint32_t)pend + to_acc, rowb, pu.x, pu.y, pw.x, pw.y);
+            if (pend >= 0) flush_carry(to_acc, rowb, pend, pu, pw, cur, uu, ww);
             pend = cur;
             pu = uu;
             pw = ww;
@@ -347,7 +387,7 @@ __device__ __forceinline__ void scatter_ray_dx(const Prob &pb, int ray, int l, f
         kf2 = add2(kf2, f2(2.0f));
     }
     if (k < he) step(f2(kf2.x), 0.0f);  // last sample of an odd window: lane .y repeats it with weight 0
-    if (pend >= 0) flush_dx((uint32_t)pend + to_acc, rowb, pu.x, pu.y, pw.x, pw.y);
+    if (pend >= 0) flush_carry(to_acc, rowb, pend, pu, pw, cur, uu, ww);
     if (cur >= 0) flush_dx((uint32_t)cur + to_acc, rowb, uu.x, uu.y, ww.x, ww.y);
 }
 
