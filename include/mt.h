@@ -85,7 +85,9 @@ typedef enum {
  *                 BF16 offsets h - ref_l from a reference height ref_l (the
  *                 surface's mean prior height rounded to FP32, or
  *                 Lz (l+1)/(L+1) when that mean is 0) and widens them to FP32
- *                 when read; otherwise as MT_PREC_F32.  The FP32 modes use
+ *                 when read; its march evaluates every sample with the
+ *                 SFU's logistic, indicators as integers in units of 2^-23,
+ *                 and FP64 per-ray and per-chain sums.  The FP32 modes use
  *                 the same offsets in FP32.
  * Heights passed to and returned by the library are double for MT_PREC_F64
  * and float for every other mode. */
