@@ -217,7 +217,7 @@ def bench_config(w, C, world):
     """The workload description both arms print."""
     return {"workload": w.name, "chains_per_gpu": C, "surfaces": w.L,
             "grid": [w.R, w.Q], "sensors": w.S, "pixels": w.P, "n_grid": w.G,
-            "precision": "f32 march, f64 reduction", "sampler": "random-walk",
+            "precision": "f32 march (accurate logistic), f64 reduction", "sampler": "random-walk",
             "rw_sigma_m": w.rw_sigma, "l2": "flushed (256 MB write) between steps",
             "parallelism": f"chains sharded, {world} independent rank(s)"}
 
