@@ -259,15 +259,16 @@ __device__ __forceinline__ void flush_carry(uint32_t to_acc, uint32_t rowb, int 
     const float v1 = xp ? q10 : (xm ? q11 : (ym ? q11 : q01));
     red_fixed(a0, v0);
     red_fixed(a1, v1);
-    if (xp | xm) {  // the shared column: q carried to the next cell's other column
-        const float cu = xp ? q01 : q00, cw = xp ? q11 : q10, h = xp ? -0.5f : 0.5f;
-        uu = add2(uu, make_float2(cu, h * cu));
-        ww = add2(ww, make_float2(cw, h * cw));
-    } else if (yp) {  // the upper row becomes the next cell's lower row
-        uu = add2(uu, pw);
-    } else if (ym) {  // the lower row becomes the next cell's upper row
-        ww = add2(ww, pu);
-    } else {  // a diagonal step: the upper two nodes as well
+    // carried into the next cell (selects, no branch): a shared column adds q
+    // to U0 / V0 and -+q/2 to U1 / V1; the upper row moves whole into the
+    // lower one after a step up, the lower into the upper after a step down
+    const bool ax = xp | xm;
+    const float cu = xp ? q01 : q00, cw = xp ? q11 : q10, h = xp ? -0.5f : 0.5f;
+    const float2 du = ax ? make_float2(cu, h * cu) : (yp ? pw : f2(0.f));
+    const float2 dw = ax ? make_float2(cw, h * cw) : (ym ? pu : f2(0.f));
+    uu = add2(uu, du);
+    ww = add2(ww, dw);
+    if (!(ax | yp | ym)) {  // a diagonal step: the upper two nodes as well
         red_fixed(a + rowb, q10);
         red_fixed(a + rowb + 8u, q11);
     }
