@@ -332,8 +332,9 @@ MT_API mt_status mt_get_timing(mt_ctx *ctx, int id, double *total_ms, int64_t *l
 /* Work of the FP32 ray kernel launched while timing was on: *total = the
  * method's surface-samples (chains x rays x n_grid x n_layers), *evaluated =
  * those whose logistic was computed; the others lay so far from their surface
- * (|s - z| >= 24.25 gamma / log2(e)) that their indicator is exactly 0 or 1 in
- * FP32 and was added without evaluation (the result is bit-identical).
+ * (|s - z| >= 29.25 gamma / log2(e)) that their integer indicator (units of
+ * 2^-28) is exactly 0 or 2^28 and was added without evaluation (the result
+ * is bit-identical).
  * reset = 1 clears both. */
 MT_API mt_status mt_get_work(mt_ctx *ctx, double *evaluated, double *total, int reset);
 

@@ -474,15 +474,15 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
 //             already on its own grid would round coherently along the ray.)
 //   indicator varsigma = 1 / (1 + 2^a) through psi = 1 / (1 + 2^|a|) <= 1/2:
 //             varsigma = psi above the surface (a > 0), 1 - psi below it.  psi
-//             is formed as rcp((2^|a| (1 - kappa) + 1) c) with c = +-2^-28
-//             carrying a's sign (kappa: the approximations' mean error,
-//             calibrated per device, see k_psi_calib), rounded to the nearest
-//             integer q (units 2^-28), and the
+//             is formed as 1 / ((2^|a| + 1) c) with c = +-2^-28 carrying a's
+//             sign, rounded to the nearest integer q (units 2^-28), and the
 //             sample adds q + 2^28 [a < 0], i.e. round(varsigma 2^28), exactly:
 //             no 1 - psi is ever rounded in FP32, and tails of psi down to
-//             2^-29 are kept.  The compensated mode (ACC) forms 2^|a| with
-//             exp2_acc and the reciprocal with rcp_newton instead (no
-//             calibration: neither is biased beyond rounding).
+//             2^-29 are kept.  The FP32 and compensated modes (ACC) form
+//             2^|a| with exp2_acc and the reciprocal with rcp_newton, neither
+//             biased beyond rounding; the approximate-logistic mode uses
+//             ex2.approx and rcp.approx with their mean error corrected by a
+//             factor (1 - kappa) calibrated per device (k_psi_calib).
 // The integer adds c_bits >> 3 = 2^28 [a < 0] + kJunk per sample (the
 // exponent bits of 2^-28 shifted down); kJunk is subtracted once per window.
 // The corner records of each sample are cached and reloaded when that
@@ -957,7 +957,7 @@ __device__ __forceinline__ void store_partial_ff(void *partial, FF accf)
 }
 
 // ---------------------------------------------------------------- kernel
-// FP32 and float-float modes use per-surface (h, dx) planes and 1024-thread
+// The FP32 modes use per-surface (h, dx) planes and MT_DX_THREADS-thread
 // CTAs (one per SM with the scenario's 128 KB of records); BF16 keeps
 // 4-corner node records to halve shared memory; FP64 has its own march.
 template <int MODE, int L> struct MarchCfg {

@@ -1,7 +1,7 @@
 """Compile-time resources of the hot kernels (ptxas -v, sm_103a, no GPU):
 every instantiation of the ray kernel and of the adjoint compiles without
-register spills, and the ray kernel of the FP32 modes fits its 1024-thread
-CTA in 64 registers per thread (65 536 registers per SM)."""
+register spills, and the ray kernel of the FP32 modes fits its CTA of
+MT_DX_THREADS threads in the registers an SM has (65 536)."""
 import concurrent.futures as cf
 import os
 import re

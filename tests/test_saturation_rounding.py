@@ -1,9 +1,9 @@
 """The rounding argument behind the ray kernel's exact saturation windows,
 checked in IEEE FP32 on the CPU (numpy float32, round to nearest).
 
-Per surface-sample the adjoint's scatter windows and the BF16 march form
-e = 2^a (a = the sigmoid argument in log2 units), sigma = 1 / (1 + e) and
-accumulate sigma + 1, whose mantissa
+Per surface-sample the BF16 march forms e = 2^a (a = the sigmoid argument
+in log2 units), sigma = 1 / (1 + e) and accumulates sigma + 1, whose
+mantissa
 carries round(sigma * 2^23).  Samples with |a| >= 24.25 are skipped and
 their contribution added exactly; that is exact when, for every such a and
 for relative errors of the exponential and the reciprocal up to 2^-21 (the
@@ -49,13 +49,15 @@ def test_inside_the_window_rounding_is_not_exact():
 
 
 # ---------------------------------------------------------------- the FP32 march's complementary logistic
-# The FP32 modes' march forms, per sample, psi = 1 / (1 + 2^|a|) scaled by
-# 2^28: q = round(rcp(fma(E, c, fma(E, -kappa c, c)))) with E = 2^|a|, c =
-# 2^-28 and kappa the per-device calibration (|kappa| < 1e-5 is enforced at
-# set-up), and adds q above the surface, 2^28 - q below it.  Samples with
-# |a| >= 29.25 are skipped and add exactly 0 / 2^28: exact when q rounds to 0
-# there, for relative errors of the exponential and the reciprocal up to
-# 2^-21.
+# The approximate-logistic mode's march forms, per sample, psi = 1 / (1 +
+# 2^|a|) scaled by 2^28: q = round(rcp(fma(E, c, fma(E, -kappa c, c)))) with
+# E = 2^|a| from ex2.approx, c = 2^-28 and kappa the per-device calibration
+# (|kappa| < 1e-5 is enforced at set-up), and adds q above the surface,
+# 2^28 - q below it.  Samples with |a| >= 29.25 are skipped and add exactly
+# 0 / 2^28: exact when q rounds to 0 there, for relative errors of the
+# exponential and the reciprocal up to 2^-21.  (The FP32 and compensated
+# modes form E with the accurate exp2 instead; tests/test_accurate_logistic.py
+# checks the same rounding for it.)
 
 
 def _q(a, ee, er, kappa):
