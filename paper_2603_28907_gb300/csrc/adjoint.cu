@@ -358,44 +358,34 @@ __device__ __forceinline__ void scatter_ray_dx(const Prob &pb, int ray, int l, f
                 pend = -1;
             }
         }
-        // the cell sums move on when a sample enters the next cell; one move
-        // per step (the common case) takes one region: A's share goes to the
-        // sums before the move if B moved (A stayed), after it otherwise
-        const float2 ua = make_float2(1.0f, fx.x);
-        if (chA && chB) {  // A and B each entered a new cell (rare)
+        // the cell sums move on when a sample enters the next cell: one
+        // region for the first (or only) move of the step, A's share added
+        // before it when only B moved (A stayed) and after it otherwise, and
+        // a rare second region when B moved on again
+        if (chB && !chA) {
+            uu = fma2(f2(vny.x), make_float2(1.0f, fx.x), uu);
+            ww = fma2(f2(vy.x), make_float2(1.0f, fx.x), ww);
+        }
+        if (chA || chB) {
             if (cur >= 0) {
                 pend = cur;
                 pu = uu;
                 pw = ww;
             }
             uu = ww = f2(0.f);
-            cur = ia;
-            uu = fma2(f2(vny.x), ua, uu);
-            ww = fma2(f2(vy.x), ua, ww);
+            cur = chA ? ia : ib;
+        }
+        if (chA || !chB) {
+            uu = fma2(f2(vny.x), make_float2(1.0f, fx.x), uu);
+            ww = fma2(f2(vy.x), make_float2(1.0f, fx.x), ww);
+        }
+        if (chA && chB) {  // B entered yet another cell (rare): the second move
             flush_carry(to_acc, rowb, pend, pu, pw, cur, uu, ww);
             pend = cur;
             pu = uu;
             pw = ww;
             uu = ww = f2(0.f);
             cur = ib;
-        } else {
-            if (chB) {
-                uu = fma2(f2(vny.x), ua, uu);
-                ww = fma2(f2(vy.x), ua, ww);
-            }
-            if (chA || chB) {
-                if (cur >= 0) {
-                    pend = cur;
-                    pu = uu;
-                    pw = ww;
-                }
-                uu = ww = f2(0.f);
-                cur = chA ? ia : ib;
-            }
-            if (!chB) {
-                uu = fma2(f2(vny.x), ua, uu);
-                ww = fma2(f2(vy.x), ua, ww);
-            }
         }
         uu = fma2(f2(vny.y), make_float2(1.0f, fx.y), uu);
         ww = fma2(f2(vy.y), make_float2(1.0f, fx.y), ww);
