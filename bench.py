@@ -54,13 +54,14 @@ def march_traffic():
 
 
 # FP32 lane-ops per evaluated surface-sample of the FP32 march (two samples
-# per step: 19 paired FP32 instructions + 4 scalar x-lerp FMAs per 2 samples)
-EVAL_FP32_OPS = 31.0  # per evaluated surface-sample, FP32 mode (accurate logistic)
+# per step: 27 paired FP32 instructions and 8 scalar ones, the x-lerps and the
+# exact differences h_mid - z, per 2 samples, plus 3 paired per block of 8)
+EVAL_FP32_OPS = 32.0  # per evaluated surface-sample, FP32 mode (accurate logistic)
 
 
 def march_peak_evaluated():
     """Evaluated surface-samples per second the pipes allow for the march's
-    own op mix in the FP32 mode (31 FP32 lane-ops + rcp per evaluated sample:
+    own op mix in the FP32 mode (32 FP32 lane-ops + rcp per evaluated sample:
     the accurate logistic forms 2^|a| on the FP32 pipe)."""
     clk = SM_COUNT * SM_MAX_MHZ * 1e6
     sfu = clk * RCP_PER_CLK_SM

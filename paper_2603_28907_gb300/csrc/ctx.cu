@@ -115,6 +115,8 @@ struct mt_ctx {
     float4 *d_xa4 = nullptr, *d_xb4 = nullptr;  // ray table of the FP32 march
     int2 *d_xc2 = nullptr;
     float *d_kz1 = nullptr;
+    float *d_kzm = nullptr;   // z in metres of the FP32 march
+    float2 *d_szm = nullptr;
     float psi_kc = 0.f;              // calibrated logistic correction (kappa * 2^-28)
     double *d_od = nullptr, *d_sd = nullptr, *d_dt = nullptr, *d_a = nullptr, *d_sumK = nullptr;
     float2 *d_dtff = nullptr, *d_aff = nullptr;
@@ -385,11 +387,15 @@ static void refresh_prob(mt_ctx *ctx)
         for (int l = 0; l < ctx->L && l < MT_MAX_L; ++l) rmax = fmax(rmax, fabs((double)pb.ref[l]));
         const double bound = 2.0 * (pb.kg64 * (ctx->box[2] + rmax) + 1.0);
         pb.zgrid = ldexp(1.0, ilogb(bound) + 1 - 24);
+        const double bound_m = 2.0 * (ctx->box[2] + rmax + 1.0);
+        pb.zgrid_m = ldexp(1.0, ilogb(bound_m) + 1 - 24);
     }
     pb.xa4 = ctx->d_xa4;
     pb.xb4 = ctx->d_xb4;
     pb.xc2 = ctx->d_xc2;
     pb.kz1 = ctx->d_kz1;
+    pb.kzm = ctx->d_kzm;
+    pb.szm = ctx->d_szm;
     pb.psi_kc = ctx->psi_kc;
     pb.mu_ff = ctx->d_muff;
     pb.lz_f = (float)ctx->box[2];
@@ -440,6 +446,8 @@ static mt_status build_raytab(mt_ctx *ctx)
     TRY(dalloc(ctx, &ctx->d_xb4, n));
     TRY(dalloc(ctx, &ctx->d_xc2, n));
     TRY(dalloc(ctx, &ctx->d_kz1, 2 * (size_t)ctx->L * n));
+    TRY(dalloc(ctx, &ctx->d_kzm, 2 * (size_t)ctx->L * n));
+    TRY(dalloc(ctx, &ctx->d_szm, n));
     TRY(dalloc(ctx, &ctx->d_od, 3 * n));
     TRY(dalloc(ctx, &ctx->d_sd, 3 * n));
     TRY(dalloc(ctx, &ctx->d_dt, n));
@@ -449,7 +457,7 @@ static mt_status build_raytab(mt_ctx *ctx)
     CK(ctx, launch_raytab(ctx->pb, ctx->d_sensors, ctx->d_dirs, ctx->d_o4, ctx->d_s4, ctx->d_kz0,
                           ctx->d_od, ctx->d_sd, ctx->d_dt, ctx->d_dtff, ctx->d_flag, ctx->stream));
     CK(ctx, launch_raytab_march(ctx->pb, ctx->d_sensors, ctx->d_dirs, ctx->d_xa4, ctx->d_xb4, ctx->d_xc2,
-                                ctx->d_kz1, ctx->d_flag, ctx->stream));
+                                ctx->d_kz1, ctx->d_kzm, ctx->d_szm, ctx->d_flag, ctx->stream));
     if (ctx->mode == MODE_F32A) {
         // the approximate logistic's mean error, calibrated once per context on its device
         double *d_k = nullptr, kappa = 0.0;
@@ -898,6 +906,8 @@ mt_status mt_destroy(mt_ctx *ctx)
     dfree(ctx, ctx->d_xb4);
     dfree(ctx, ctx->d_xc2);
     dfree(ctx, ctx->d_kz1);
+    dfree(ctx, ctx->d_kzm);
+    dfree(ctx, ctx->d_szm);
     dfree(ctx, ctx->d_od);
     dfree(ctx, ctx->d_sd);
     dfree(ctx, ctx->d_dt);

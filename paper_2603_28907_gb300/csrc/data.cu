@@ -135,9 +135,12 @@ __device__ bool fit_axis_rel(float &o, float &sh, float sl, int c0, int n, int G
 // z per surface in log2 units, kg64 (z - ref_l), split into a high part on
 // the grid pb.zgrid and an FP32 remainder; likewise the per-sample step.
 // Every sample's |kg64 (z - ref_l)| lies below half the bound the grid was
-// chosen for, so hi + k * step_hi is exact in FP32 for all k < G.
+// chosen for, so hi + k * step_hi is exact in FP32 for all k < G.  (These
+// place the exact-saturation windows and serve the adjoint.)  The march's
+// own arithmetic takes z - ref_l in metres, its high part on the grid
+// pb.zgrid_m (exact in the same way) and kg64 times the remainder (kzm, szm).
 __global__ void k_raytab_march(Prob pb, const double *sensors, const double *dirs, float4 *xa4, float4 *xb4,
-                               int2 *xc2, float *kz1, int *flag)
+                               int2 *xc2, float *kz1, float *kzm, float2 *szm, int *flag)
 {
     const int ray = blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= pb.n_rays) return;
@@ -170,18 +173,27 @@ __global__ void k_raytab_march(Prob pb, const double *sensors, const double *dir
     xb4[ray] = make_float4(ok ? sxl : 0.f, ok ? syl : 0.f, (float)szh, (float)(ksz - szh));
     if (!ok) xa4[ray] = make_float4(0.f, 0.f, 0.f, 0.f);  // keeps every sample in the start cell
     xc2[ray] = make_int2(c0x, c0y);
+    const double gm = pb.zgrid_m;
+    const double szh_m = rint(sz / gm) * gm;
+    szm[ray] = make_float2((float)szh_m, (float)(pb.kg64 * (sz - szh_m)));
     for (int l = 0; l < pb.L; ++l) {
         const double kz = pb.kg64 * (z0 - (double)pb.ref[l]);
         const double hi = rint(kz / g) * g;
         kz1[(size_t)l * pb.n_rays + ray] = (float)hi;
         kz1[(size_t)(pb.L + l) * pb.n_rays + ray] = (float)(kz - hi);
+        const double zm = z0 - (double)pb.ref[l];
+        const double hm = rint(zm / gm) * gm;
+        kzm[(size_t)l * pb.n_rays + ray] = (float)hm;
+        kzm[(size_t)(pb.L + l) * pb.n_rays + ray] = (float)(pb.kg64 * (zm - hm));
     }
 }
 
 cudaError_t launch_raytab_march(const Prob &pb, const double *d_sensors, const double *d_dirs, float4 *xa4,
-                                float4 *xb4, int2 *xc2, float *kz1, int *flag, cudaStream_t st)
+                                float4 *xb4, int2 *xc2, float *kz1, float *kzm, float2 *szm, int *flag,
+                                cudaStream_t st)
 {
-    k_raytab_march<<<(pb.n_rays + 255) / 256, 256, 0, st>>>(pb, d_sensors, d_dirs, xa4, xb4, xc2, kz1, flag);
+    k_raytab_march<<<(pb.n_rays + 255) / 256, 256, 0, st>>>(pb, d_sensors, d_dirs, xa4, xb4, xc2, kz1, kzm, szm,
+                                                            flag);
     return cudaGetLastError();
 }
 

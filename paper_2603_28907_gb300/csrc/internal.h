@@ -55,11 +55,15 @@ struct Prob {
                                // (log2 units, FP64 kg) on the grid zgrid and its remainder
     const int2 *xc2;           // start cell {c0x, c0y}
     const float *kz1;          // [2][L][n_rays] kg64 * (z_0 - ref_l) on the grid zgrid, remainder
+    const float *kzm;          // [2][L][n_rays] z_0 - ref_l in metres on the grid zgrid_m, and
+                               // kg64 times the remainder (log2 units)
+    const float2 *szm;         // [n_rays] z step in metres on the grid zgrid_m, kg64 times the remainder
     float kgl;                 // kg64 - kg (FP32 remainder of log2(e) / gamma)
     float psi_kc;              // kappa * 2^-28: calibration of the march's logistic
                                // (launch_psi_calib); 0 = none
     double kg64;               // log2(e) / gamma in FP64 (1 for the hard indicator)
     double zgrid;              // grid of the z high parts: 2^(e - 24) with |z| < 2^e
+    double zgrid_m;            // the same for z - ref_l in metres
     float ref[MT_MAX_L];       // per-surface reference height of the FP32 paths
     float2 drho_ff[MT_MAX_L];  // float-float of drho
     const double *o_d;         // [3] FP64 sample-0 position {gx, gy, z}
@@ -129,8 +133,8 @@ cudaError_t launch_raytab(const Prob &pb, const double *d_sensors, const double 
 // The FP32 march's ray table (Prob::xa4, xb4, xc2, kz1); pb.zgrid, pb.kg64
 // and pb.ref must be set.
 cudaError_t launch_raytab_march(const Prob &pb, const double *d_sensors, const double *d_dirs,
-                                float4 *xa4, float4 *xb4, int2 *xc2, float *kz1, int *flag,
-                                cudaStream_t st);
+                                float4 *xa4, float4 *xb4, int2 *xc2, float *kz1, float *kzm, float2 *szm,
+                                int *flag, cudaStream_t st);
 // kappa of the march's logistic on this device (one double at out).
 cudaError_t launch_psi_calib(double *out, cudaStream_t st);
 cudaError_t launch_counts_prep(const Prob &pb, double *a, float2 *a_ff, double *sumK,

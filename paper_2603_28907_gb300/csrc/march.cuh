@@ -458,20 +458,28 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
 //   position  g = fmaf(k, sh, fmaf(k, sl, o)) per axis, relative to the ray's
 //             start cell (the step split hi + lo), so no per-ray FP32 offset
 //             enters and each sample's rounding is its own; the cell split
-//             adds 1.5 * 2^23, rounding x to the nearest integer (x is taken
-//             from the cell's centre) and y down (y from the cell's lower
-//             edge; __fadd2_rd), and the fractions g - round(g) and
-//             g - floor(g) are exact.
-//   height    the x-lerps read the (h_mid, dx) records as loaded (scalar
-//             FMAs), then the y-lerp; the result sl = s_l - ref_l.
-//   argument  a = kg64 (z - s_l) in log2 units with z - ref_l = zhi + zlo,
-//             zhi = zh + k szh exact (zh, szh on a grid), evaluated as
-//             (fmaf(-kgh, sl, fmaf(-kgl, sl, zlo))) + zhi: the small terms
-//             (the z remainder and the low part of kg) enter through the
-//             addend of a fused multiply-add whose product has full-width
-//             bits, and the final addition of the grid-aligned zhi is exact
-//             where |a| is small.  (Adding a small smooth term to an FP32 value
-//             already on its own grid would round coherently along the ray.)
+//             adds 1.5 * 2^23, rounding x to the nearest integer i (x is
+//             taken from the cell's centre) and y down (y from the cell's
+//             lower edge; __fadd2_rd).  The fraction is then formed again as
+//             (k sh - i) + fmaf(k, sl, o), the product exact inside the
+//             fused multiply-add, so it carries the rounding of a number
+//             below one cell instead of that of g (up to 2^-18 cells after
+//             64 cells of travel).
+//   height    z - ref_l in metres is split into zhi = zh + k szh, exact
+//             (zh, szh on a grid), and a remainder carried as kg64 times it
+//             in log2 units, zlo.  Each loaded (h_mid, dx) record enters as
+//             h_mid - zhi, exact within 32 m of the surface (both on fine
+//             grids), so the x-lerps (scalar FMAs on the records as loaded)
+//             and the y-lerp round at the scale of the distance to the
+//             surface, not of the surface's offset from ref_l (tens of
+//             metres for chains far from the data); the result is
+//             d = s_l - zhi.
+//   argument  a = kg64 (z - s_l) in log2 units, evaluated as
+//             fmaf(-kgh, d, fmaf(-kgl, d, zlo)): the small terms (the z
+//             remainder and the low part of kg) enter through the addend of a
+//             fused multiply-add whose product has full-width bits.  (Adding
+//             a small smooth term to an FP32 value already on its own grid
+//             would round coherently along the ray.)
 //   indicator varsigma = 1 / (1 + 2^a) through psi = 1 / (1 + 2^|a|) <= 1/2:
 //             varsigma = psi above the surface (a > 0), 1 - psi below it.  psi
 //             is formed as 1 / ((2^|a| + 1) c) with c = +-2^-28 carrying a's
@@ -553,8 +561,12 @@ __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int 
     const float2 gx = fma2(kf2, sxh2, ix2);  // ix2 = o + k sl (see march_surface_dx)
     const float2 gy = fma2(kf2, syh2, iy2);
     const float2 tx = add2(gx, M2), ty = __fadd2_rd(gy, M2);  // x rounded to nearest, y down
-    const float2 fx = fma2(add2(tx, f2(-12582912.0f)), f2(-1.0f), gx);  // in [-1/2, 1/2] about the midpoint
-    const float2 fy = fma2(add2(ty, f2(-12582912.0f)), f2(-1.0f), gy);  // in [0, 1) from the lower row
+    // The fractions (about the row segment's midpoint in x, from the lower
+    // row in y) from the exact product k sh minus the cell offset, then the
+    // block's low part: rounded at the scale of the fraction, not of the
+    // distance from the start cell as g - round(g) would be.
+    const float2 fx = add2(fma2(kf2, sxh2, fma2(tx, f2(-1.0f), M2)), ix2);
+    const float2 fy = add2(fma2(kf2, syh2, fma2(ty, f2(-1.0f), M2)), iy2);
 #ifdef MT_BOUNDS_CHECK
     const bool in_grid =
         cell_ok(c0.x + __float_as_int(tx.x) - 0x4B400000, c0.y + __float_as_int(ty.x) - 0x4B400000, Q - 1, R - 1) &&
@@ -590,12 +602,15 @@ __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int 
 #endif
         reload_pair(aA0, aB0, rowb, curA, curB, rA0, rA1, rB0, rB1);
     }
-    const float2 a = make_float2(fmaf(fx.x, rA0.y, rA0.x), fmaf(fx.y, rB0.y, rB0.x));  // row r0
-    const float2 b = make_float2(fmaf(fx.x, rA1.y, rA1.x), fmaf(fx.y, rB1.y, rB1.x));  // row r0 + 1
-    const float2 sl = fma2(fy, fma2(a, f2(-1.0f), b), a);               // s_l - ref_l
-    const float2 zhi = fma2(kf2, szh2, zh2);                            // exact
-    const float2 zlo = fma2(kf2, szl2, zl2);
-    const float2 arg = add2(fma2(nkgh2, sl, fma2(nkgl2, sl, zlo)), zhi);  // kg64 (z - s_l)
+    const float2 zhi = fma2(kf2, szh2, zh2);  // z - ref_l in metres on its grid, exact
+    const float2 zlo = fma2(kf2, szl2, zl2);  // kg64 times the remainder (log2 units)
+    // Heights minus zhi: h_mid - zhi is exact within 32 m of the surface
+    // (both on fine grids), so the x-lerps and the y-lerp round at the scale
+    // of the distance to the surface, not of its offset from ref_l.
+    const float2 a = make_float2(fmaf(fx.x, rA0.y, rA0.x - zhi.x), fmaf(fx.y, rB0.y, rB0.x - zhi.y));  // row r0
+    const float2 b = make_float2(fmaf(fx.x, rA1.y, rA1.x - zhi.x), fmaf(fx.y, rB1.y, rB1.x - zhi.y));  // row r0 + 1
+    const float2 d = fma2(fy, fma2(a, f2(-1.0f), b), a);           // s_l - zhi
+    const float2 arg = fma2(nkgh2, d, fma2(nkgl2, d, zlo));        // kg64 (z - s_l)
     if constexpr (HARD) {
         const uint32_t vx = arg.x < 0.f ? (uint32_t)kUnit : (arg.x > 0.f ? 0u : (uint32_t)(kUnit >> 1));
         const uint32_t vy = arg.y < 0.f ? (uint32_t)kUnit : (arg.y > 0.f ? 0u : (uint32_t)(kUnit >> 1));
@@ -628,11 +643,12 @@ __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int 
 // evaluated in both lanes and counted once.
 template <bool HARD, bool GLOBAL, bool ACC>
 __device__ __forceinline__ void march_surface_dx(const float2 *pl, int Q, int R, int *flag, float4 xa, float4 xb,
-                                                 float nkgh, float nkgl, uint32_t nkc, float zh, float zl, uint32_t k0,
-                                                 int cell0, int2 c0, int lo, int he, unsigned long long &t)
+                                                 float2 szm, float nkgh, float nkgl, uint32_t nkc, float zh, float zl,
+                                                 uint32_t k0, int cell0, int2 c0, int lo, int he,
+                                                 unsigned long long &t)
 {
     const float2 ox2 = f2(xa.x), oy2 = f2(xa.y), sxh2 = f2(xa.z), syh2 = f2(xa.w);
-    const float2 sxl2 = f2(xb.x), syl2 = f2(xb.y), szh2 = f2(xb.z), szl2 = f2(xb.w);
+    const float2 sxl2 = f2(xb.x), syl2 = f2(xb.y), szh2 = f2(szm.x), szl2 = f2(szm.y);
     const float2 zh2 = f2(zh), zl2 = f2(zl), nkgh2 = f2(nkgh), nkgl2 = f2(nkgl);
     float2 rA0 = f2(0.f), rA1 = f2(0.f), rB0 = f2(0.f), rB1 = f2(0.f);
     int curA = -1, curB = -1;
@@ -754,17 +770,21 @@ __device__ __forceinline__ unsigned long long march_ray_surface_dx(const Prob &p
                                                                    float smax, unsigned long long *evaluated)
 {
     const int G = pb.G;
-    const float zh = pb.kz1[(size_t)l * pb.n_rays + ray];
-    const float zl = pb.kz1[(size_t)(pb.L + l) * pb.n_rays + ray];
     int lo = 0, hi = G - 1;
-    if (!pb.full_windows) transition_window(zh + zl, dz, rdz, pb.kg, smin, smax, G, lo, hi, kSatX);
+    if (!pb.full_windows) {
+        const float zh = pb.kz1[(size_t)l * pb.n_rays + ray];
+        const float zl = pb.kz1[(size_t)(pb.L + l) * pb.n_rays + ray];
+        transition_window(zh + zl, dz, rdz, pb.kg, smin, smax, G, lo, hi, kSatX);
+    }
+    const float zhm = pb.kzm[(size_t)l * pb.n_rays + ray];
+    const float zlm = pb.kzm[(size_t)(pb.L + l) * pb.n_rays + ray];
     lo = min(lo, G) & ~1;  // even start (one more, saturated, sample below)
     int he = max(hi + 1, lo);
     if (((he - lo) & 1) && he < G) ++he;  // even length where the ray allows
     if (evaluated) *evaluated += (unsigned long long)(he - lo);
     unsigned long long t = (unsigned long long)lo * kUnit;  // samples below the window
-    march_surface_dx<HARD, GLOBAL, ACC>(plane, pb.Q, pb.R, pb.flag, xa, xb, -pb.kg, -pb.kgl, __float_as_uint(-pb.psi_kc),
-                                   zh, zl, kl, cell0, c0, lo, he, t);
+    march_surface_dx<HARD, GLOBAL, ACC>(plane, pb.Q, pb.R, pb.flag, xa, xb, pb.szm[ray], -pb.kg, -pb.kgl,
+                                        __float_as_uint(-pb.psi_kc), zhm, zlm, kl, cell0, c0, lo, he, t);
     return t;
 }
 

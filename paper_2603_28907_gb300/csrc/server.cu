@@ -74,7 +74,7 @@ size_t footprint_of(const mt_request &r)
     const size_t rays = (size_t)r.n_sensors * r.n_pixels, es = elem_size(r.cfg.precision);
     size_t b = 2 * C * L * N * es;                 // double-buffered heights
     b += C * 64;                                    // per-chain scalars
-    b += rays * (16 + 16 + 8 * L + 24 + 24 + 8 + 8 + 8 + 8 + 4 + 8);  // ray table, counts
+    b += rays * (16 + 16 + 8 * L + 8 * L + 8 + 24 + 24 + 8 + 8 + 8 + 8 + 4 + 8);  // ray table, counts
     b += C * ((rays + 4095) / 4096) * 8;            // partial sums
     b += L * N * 8 * 2;                             // prior mean, staging
     const size_t rpb = std::min<size_t>(MT_RAYS_PER_CTA, (rays + 255) / 256 * 256);

@@ -22,11 +22,11 @@ def test_method_peak_from_unit_counts():
 
 def test_evaluated_roofline():
     clk = 152 * 2070e6
-    # FP32 binds: 31 lane-ops per evaluated sample of the accurate logistic
-    assert bench.march_peak_evaluated() == pytest.approx(clk * 128 / 31)
+    # FP32 binds: 32 lane-ops per evaluated sample of the accurate logistic
+    assert bench.march_peak_evaluated() == pytest.approx(clk * 128 / 32)
     r = bench.evaluated_roofline(3.0, 0.25, 1.0)
     assert r["fraction"] == 0.25 and r["achieved"] == pytest.approx(0.75)
-    assert r["frac"] == pytest.approx(0.75 / (clk * 128 / 31 / 1e12))
+    assert r["frac"] == pytest.approx(0.75 / (clk * 128 / 32 / 1e12))
     assert bench.evaluated_roofline(3.0, 1.0, 0.0) is None
 
 
