@@ -43,7 +43,7 @@ FP32_PER_CLK_SM = 128    # FP32 lanes per SM (probe: 114.6 FMA/clk at the nomina
 # DRAM traffic of one k_march launch (read + write bytes) from the ncu capture
 # summarised in profiles/k_march_scenario_c128_ncu.md, scaled from 128 to 1024
 # chains; valid only for the kernel source it was measured on.
-MARCH_TRAFFIC = {"source_sha1": "2f8d8f44998b", "bytes": 73.0e6}
+MARCH_TRAFFIC = {"source_sha1": "742e55f14d6e", "bytes": 76.1e6}
 
 
 def march_traffic():
