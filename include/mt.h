@@ -64,23 +64,27 @@ typedef enum {
 
 /* Arithmetic of the ray march and the per-chain reduction.
  *  MT_PREC_F64  : heights, march, flux and reductions in FP64.
- *  MT_PREC_F32  : FP32 heights and march: each sample's indicator an exact
- *                 integer in units of 2^-28; the logistic from 2^|a| split
- *                 exactly into 2^round(|a|) and a polynomial of the
- *                 fraction, and a reciprocal refined by one Newton step
- *                 (no bias beyond rounding); float-float per-ray flux term
- *                 and CTA sums, FP64 per-chain reduction.  Per-chain
- *                 log-likelihoods within 1e-3 of FP64.
+ *  MT_PREC_F32  : FP32 heights and march: each sample's cell fraction and
+ *                 sigmoid argument formed from exact products and exact
+ *                 differences (heights minus z on fine grids), so they
+ *                 round at the scale of one cell and of the distance to the
+ *                 surface; each sample's indicator an exact integer in
+ *                 units of 2^-28; the logistic from 2^|a| split exactly
+ *                 into 2^round(|a|) and a polynomial of the fraction, and a
+ *                 reciprocal refined by one Newton step (no bias beyond
+ *                 rounding); float-float per-ray flux term and CTA sums,
+ *                 FP64 per-chain reduction.  Per-chain log-likelihoods
+ *                 within 1e-3 of FP64 (9e-5 on average, 6e-4 at worst over
+ *                 2e5 proposals at the scenario size).
  *  MT_PREC_F32C : as MT_PREC_F32 with the per-chain reduction in
  *                 float-float: no FP64 in the ray kernel.
  *  MT_PREC_F32A : as MT_PREC_F32 with the logistic from the SFU's ex2 / rcp
  *                 approximations, their mean error calibrated per device at
- *                 context creation: ~20 % faster; per-chain log-likelihoods
- *                 within ~4e-4 of FP64 on average but up to ~3.6e-3 for
+ *                 context creation: ~17 % faster; per-chain log-likelihoods
+ *                 within ~4e-4 of FP64 on average but up to ~3.4e-3 for
  *                 chains far from the data at the scenario size (the
  *                 approximations' error pattern survives the calibration
- *                 for one-sided transitions); accept decisions matched the
- *                 FP64 mode's on 1e5 proposals.
+ *                 for one-sided transitions).
  *  MT_PREC_BF16 : FP32 chain state; the ray kernel holds each surface as
  *                 BF16 offsets h - ref_l from a reference height ref_l (the
  *                 surface's mean prior height rounded to FP32, or
