@@ -44,13 +44,35 @@ FP32_PER_CLK_SM = 128    # FP32 lanes per SM (probe: 114.6 FMA/clk at the nomina
 # summarised in profiles/k_march_scenario_c128_ncu.md, scaled from 128 to 1024
 # chains; valid only for the kernel source it was measured on.
 MARCH_TRAFFIC = {"source_sha1": "742e55f14d6e", "bytes": 76.1e6}
+# Warp instructions one k_march launch issues per chain (smsp__inst_executed.sum
+# of the same capture / 128 chains), for the issue-slot share of the launch.
+MARCH_INST = {"source_sha1": "742e55f14d6e", "per_chain": 3.681e9 / 128}
+SMSP_PER_SM = 4
+
+
+def march_source_sha1():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2603_28907_gb300", "csrc", "march.cuh")
+    return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
 
 
 def march_traffic():
-    import hashlib
-    src = os.path.join(ROOT, "paper_2603_28907_gb300", "csrc", "march.cuh")
-    h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-    return MARCH_TRAFFIC["bytes"] if h == MARCH_TRAFFIC["source_sha1"] else None
+    return MARCH_TRAFFIC["bytes"] if march_source_sha1() == MARCH_TRAFFIC["source_sha1"] else None
+
+
+def issue_share(n_chains, launch_s):
+    """Share of the GPU's instruction-issue slots (one per cycle per
+    sub-partition at the maximum SM clock) that one ray-kernel launch of
+    n_chains used, from the captured instruction count per chain; None once
+    the kernel source differs from the capture's."""
+    if march_source_sha1() != MARCH_INST["source_sha1"] or not launch_s:
+        return None
+    inst = MARCH_INST["per_chain"] * n_chains
+    slots = launch_s * SM_COUNT * SMSP_PER_SM * SM_MAX_MHZ * 1e6
+    return {"instructions": inst, "slots": slots, "frac": inst / slots,
+            "basis": "smsp__inst_executed.sum per chain from the ncu capture of the same source "
+                     "(profiles/k_march_scenario_c128_ncu.md) x chains, against 4 issue slots per "
+                     "SM-cycle at 2070 MHz"}
 
 
 # FP32 lane-ops per evaluated surface-sample of the FP32 march (two samples
@@ -815,12 +837,14 @@ def main():
                          "kernel": "k_march", "kernel_ms_avg": avg_launch_s * 1e3,
                          "launches": march_n,
                          "evaluated": evaluated_roofline(achieved, work_eval, work_total),
+                         "issue": issue_share(C, avg_launch_s),
                          "note": "units are the method's surface-samples (12+9L FP32 ops and "
                                  "2L MUFU per sample); samples at least 29.25 log2 units from "
                                  "their surface are exactly 0/1 and added without evaluation "
                                  "(bit-identical), so frac can exceed 1; 'evaluated' rates the "
                                  "samples the kernel did compute against the pipes' limit for "
-                                 "its own op mix"},
+                                 "its own op mix; 'issue' is the share of instruction-issue "
+                                 "slots the launch used"},
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -32,3 +32,13 @@ def test_evaluated_roofline():
 
 def test_max_over_ranks_single_process():
     assert bench.max_over_ranks(12.5) == 12.5
+
+
+def test_issue_share_arithmetic(monkeypatch):
+    monkeypatch.setattr(bench, "march_source_sha1", lambda: bench.MARCH_INST["source_sha1"])
+    r = bench.issue_share(1024, 0.0341)
+    slots = 0.0341 * 152 * 4 * 2070e6
+    assert r["slots"] == pytest.approx(slots)
+    assert r["frac"] == pytest.approx(bench.MARCH_INST["per_chain"] * 1024 / slots)
+    monkeypatch.setattr(bench, "march_source_sha1", lambda: "0" * 12)
+    assert bench.issue_share(1024, 0.0341) is None and bench.march_traffic() is None
