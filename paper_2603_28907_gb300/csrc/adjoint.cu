@@ -276,8 +276,11 @@ __device__ __forceinline__ void flush_carry(uint32_t to_acc, uint32_t rowb, int 
 
 // Surface l along one ray: samples within the window where a weight can
 // reach one unit, two per step in paired FP32 lanes (lane .x sample k,
-// lane .y sample k + 1; positions, records and the argument a = kg64 (z - s_l)
-// formed as in the forward march).  Per sample the weight
+// lane .y sample k + 1; positions from the ray's start cell, the records
+// scaled to argument units and lerped, z added in log2 units: the argument
+// a = kg64 (z - s_l) to the rounding of the surface's offset, which the
+// gradient's accuracy does not need to go below; the forward march forms it
+// from exact differences instead).  Per sample the weight
 // v = coef psi (1 - psi) with psi (1 - psi) = 2^-|a| / (1 + 2^-|a|)^2
 // (d varsigma / d s_l = psi (1 - psi) / gamma) goes to the cell's nodes with
 // the bilinear weights: with the records' x-fraction f in [-1/2, 1/2] the
