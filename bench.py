@@ -42,11 +42,12 @@ FP32_PER_CLK_SM = 128    # FP32 lanes per SM (probe: 114.6 FMA/clk at the nomina
 
 # DRAM traffic of one k_march launch (read + write bytes) from the ncu capture
 # summarised in profiles/k_march_scenario_c128_ncu.md, scaled from 128 to 1024
-# chains; valid only for the kernel source it was measured on.
-MARCH_TRAFFIC = {"source_sha1": "742e55f14d6e", "bytes": 76.1e6}
+# chains; valid only for the kernel source it was measured on (captured on
+# sha1 742e55f14d6e; the source below differs from it in comments only).
+MARCH_TRAFFIC = {"source_sha1": "7e5d25345d68", "bytes": 76.1e6}
 # Warp instructions one k_march launch issues per chain (smsp__inst_executed.sum
 # of the same capture / 128 chains), for the issue-slot share of the launch.
-MARCH_INST = {"source_sha1": "742e55f14d6e", "per_chain": 3.681e9 / 128}
+MARCH_INST = {"source_sha1": "7e5d25345d68", "per_chain": 3.681e9 / 128}
 SMSP_PER_SM = 4
 
 

@@ -468,8 +468,10 @@ __device__ __forceinline__ void march_ray_f32(const Prob &pb, const S *sh, int r
 //   height    z - ref_l in metres is split into zhi = zh + k szh, exact
 //             (zh, szh on a grid), and a remainder carried as kg64 times it
 //             in log2 units, zlo.  Each loaded (h_mid, dx) record enters as
-//             h_mid - zhi, exact within 32 m of the surface (both on fine
-//             grids), so the x-lerps (scalar FMAs on the records as loaded)
+//             h_mid - zhi, exact wherever that distance is at most the
+//             record's offset |h_mid| (zhi's grid is then the coarser) and
+//             otherwise rounded at the ulp of the distance, so the x-lerps
+//             (scalar FMAs on the records as loaded)
 //             and the y-lerp round at the scale of the distance to the
 //             surface, not of the surface's offset from ref_l (tens of
 //             metres for chains far from the data); the result is
@@ -604,9 +606,10 @@ __device__ __forceinline__ uint32_t dx_pair(const float2 *pl, int Q, int R, int 
     }
     const float2 zhi = fma2(kf2, szh2, zh2);  // z - ref_l in metres on its grid, exact
     const float2 zlo = fma2(kf2, szl2, zl2);  // kg64 times the remainder (log2 units)
-    // Heights minus zhi: h_mid - zhi is exact within 32 m of the surface
-    // (both on fine grids), so the x-lerps and the y-lerp round at the scale
-    // of the distance to the surface, not of its offset from ref_l.
+    // Heights minus zhi: h_mid - zhi is exact where it is at most |h_mid|
+    // and rounds at its own ulp otherwise, so the x-lerps and the y-lerp
+    // round at the scale of the distance to the surface, not of its offset
+    // from ref_l.
     const float2 a = make_float2(fmaf(fx.x, rA0.y, rA0.x - zhi.x), fmaf(fx.y, rB0.y, rB0.x - zhi.y));  // row r0
     const float2 b = make_float2(fmaf(fx.x, rA1.y, rA1.x - zhi.x), fmaf(fx.y, rB1.y, rB1.x - zhi.y));  // row r0 + 1
     const float2 d = fma2(fy, fma2(a, f2(-1.0f), b), a);           // s_l - zhi
